@@ -1,0 +1,163 @@
+"""Backward-Euler momentum objective, its gradient and Hessian-vector products.
+
+TEST INFRASTRUCTURE ONLY (FP64 oracle).
+
+Paper, section "Momentum Update" (Eq. disc_force, the discrete energy e(y) and
+Eq. fe). With y = x + dt v (the grid nodes moved by the new velocity) the
+backward-Euler equations m (v - v^n)/dt = f(x + dt v) + m g are the stationarity
+conditions of
+
+  Phi(v) = sum_i 1/2 m_i |v_i - v^n_i|^2 - dt sum_i m_i g.v_i + e(x + dt v)
+           + dt mu/2 sum_p V^n_p |eps(v; x_p)|^2,
+
+e(y) = sum_p [psi^h(F_p) + lambda/2 (J_p - 1)^2] V^0_p + sum_r k_r |cof(F^_r) dA_r|,
+
+with, at a point z, L(z) = sum_i v_i gradN_i(z)^T (so sum_i y_i gradN_i^T = I + dt L):
+  liquid  J_p = (1 + dt tr L(x_p)) J^n_p        (the paper's (1 - d + y.gradN) J^n)
+  solid   F_p = (I + dt L(x_p)) F^n_p
+  surface F^_r = I + dt L(s_r), the surface term |J^ F^-T dA| = |cof(F^) dA|
+  viscous eps = sym L(x_p), weight V^n_p = J^n_p V^0_p (the paper's V^n approximation).
+Reading: Eq. fe evaluates the surface term's gradN at x_p; the surface samples
+are the quadrature points of the surface integral, so it is evaluated at s_r.
+
+Hessian-vector products (the linearisation the paper defers to earlier work):
+  kinetic   m_i dv_i
+  liquid    dt^2 lambda (J^n)^2 V^0 gradN_i (sum_j gradN_j . dv_j)     (rank one, PSD)
+  viscous   dt mu V^n sym(dL) gradN_i                                  (PSD)
+  solid     dt^2 V^0 dP(F; dL F^n) F^nT gradN_i                         (exact)
+  surface   dt^2 dG gradN_i(s_r) with, for c = cof(F^) a, n = c/|c|, C = dc/dF^,
+            dc = C : dF, dn = (I - n n^T) dc / |c|,
+            dG_gd = k (dn_a C_agd + n_a dC_agd)         EXACT
+            dG_gd = k  dn_a C_agd                        PROJECTED (Gauss-Newton part,
+            PSD; the reading of the paper's deferred "definiteness fix")
+"""
+import numpy as np
+
+from .constitutive import EPS, cof, fcr_energy, fcr_P, fcr_dP
+from .spline import Stencil, scatter
+
+HESS_EXACT, HESS_PROJECTED = 0, 1
+
+
+def _L(st, v):
+    return np.einsum("pqa,pqb->pab", v[st.node], st.dN)
+
+
+class NewtonState:
+    """Everything fixed during one backward-Euler solve."""
+
+    def __init__(self, n, dx, dt, gravity, m, vn, x, V0, Jn, Fn, phase, lam_l, mu_l,
+                 mu_h, lam_h, s, dA, gamma):
+        self.n, self.dx, self.dt = tuple(n), dx, dt
+        self.G = int(np.prod(n))
+        self.g = np.asarray(gravity, float)
+        self.m = m
+        self.active = m > 0
+        self.vn = vn
+        self.st = Stencil(x, dx, n)
+        self.ss = Stencil(s, dx, n)
+        self.V0 = V0
+        self.Jn = Jn
+        self.Fn = Fn
+        self.liq = phase == 0
+        self.sol = phase == 1
+        self.lam_l, self.mu_l = lam_l, mu_l
+        self.mu_h, self.lam_h = mu_h, lam_h
+        self.dA = dA
+        self.gamma = gamma
+        detF = np.linalg.det(Fn)
+        self.Vn = np.where(self.liq, Jn, detF) * V0
+
+    # ---- per-particle kinematics at the iterate v ----
+    def kinematics(self, v):
+        dt = self.dt
+        Lp = _L(self.st, v)
+        J = (1.0 + dt * np.trace(Lp, axis1=1, axis2=2)) * self.Jn
+        F = np.einsum("pab,pbc->pac", np.eye(3) + dt * Lp, self.Fn)
+        Fh = np.eye(3) + dt * _L(self.ss, v)
+        c = np.einsum("rab,rb->ra", cof(Fh), self.dA)
+        return Lp, J, F, Fh, c
+
+    def energy(self, v):
+        dt = self.dt
+        a = self.active
+        dv = v - self.vn
+        kin = 0.5 * np.sum(self.m[a] * np.sum(dv[a] ** 2, -1)) - dt * np.sum(self.m[a] * (v[a] @ self.g))
+        Lp, J, F, Fh, c = self.kinematics(v)
+        liq = self.liq
+        e = np.sum(0.5 * self.lam_l * (J[liq] - 1.0) ** 2 * self.V0[liq])
+        eps = 0.5 * (Lp + np.swapaxes(Lp, 1, 2))
+        e_visc = dt * 0.5 * self.mu_l * np.sum(self.Vn[liq] * np.sum(eps[liq] ** 2, (1, 2)))
+        sol = self.sol
+        e_sol = 0.0
+        if np.any(sol):
+            e_sol = np.sum(fcr_energy(F[sol], self.mu_h[sol], self.lam_h[sol]) * self.V0[sol])
+        e_surf = np.sum(self.gamma * np.linalg.norm(c, axis=1))
+        return kin + e + e_visc + e_sol + e_surf
+
+    def _surface_C(self, Fh):
+        # C_agd = dc_a / dF_gd = eps_agk eps_bdl a_b F_kl
+        return np.einsum("agk,bdl,rb,rkl->ragd", EPS, EPS, self.dA, Fh)
+
+    def gradient(self, v):
+        """dPhi/dv on every node (G, 3); zero on massless nodes."""
+        dt = self.dt
+        G = self.G
+        out = np.zeros((G, 3))
+        a = self.active
+        out[a] = self.m[a, None] * (v[a] - self.vn[a]) - dt * self.m[a, None] * self.g
+        Lp, J, F, Fh, c = self.kinematics(v)
+        st = self.st
+        liq = self.liq.astype(float)
+        sol = self.sol
+        # liquid pressure and viscosity: sum a stress-like 3x3 per particle, then scatter M gradN
+        M = ((dt * self.lam_l * (J - 1.0) * self.Jn * self.V0) * liq)[:, None, None] * np.eye(3)
+        eps = 0.5 * (Lp + np.swapaxes(Lp, 1, 2))
+        M = M + (dt * self.mu_l * self.Vn * liq)[:, None, None] * eps
+        if np.any(sol):
+            Ps = np.zeros((st.count, 3, 3))
+            Ps[sol] = fcr_P(F[sol], self.mu_h[sol], self.lam_h[sol])
+            M = M + (dt * self.V0)[:, None, None] * np.einsum("pab,pcb->pac", Ps, self.Fn)
+        out += scatter(G, st.node, np.einsum("pab,pqb->pqa", M, st.dN))
+        # surface
+        if self.ss.count:
+            nrm = c / np.linalg.norm(c, axis=1, keepdims=True)
+            Gs = self.gamma[:, None, None] * np.einsum("ra,ragd->rgd", nrm, self._surface_C(Fh))
+            out += scatter(G, self.ss.node, dt * np.einsum("rgd,rqd->rqg", Gs, self.ss.dN))
+        return out
+
+    def hessvec(self, v, dv, mode=HESS_PROJECTED):
+        """(d^2 Phi / dv^2) dv on every node (G, 3)."""
+        dt = self.dt
+        G = self.G
+        out = np.zeros((G, 3))
+        a = self.active
+        out[a] = self.m[a, None] * dv[a]
+        Lp, J, F, Fh, c = self.kinematics(v)
+        st = self.st
+        dL = _L(st, dv)
+        liq = self.liq.astype(float)
+        sol = self.sol
+        M = ((dt * dt * self.lam_l * self.Jn ** 2 * self.V0 * np.trace(dL, axis1=1, axis2=2)) * liq)[:, None, None] * np.eye(3)
+        M = M + (dt * self.mu_l * self.Vn * liq)[:, None, None] * 0.5 * (dL + np.swapaxes(dL, 1, 2))
+        if np.any(sol):
+            dF = np.einsum("pab,pbc->pac", dL[sol], self.Fn[sol])
+            dP = np.zeros((st.count, 3, 3))
+            dP[sol] = fcr_dP(F[sol], dF, self.mu_h[sol], self.lam_h[sol])
+            M = M + (dt * dt * self.V0)[:, None, None] * np.einsum("pab,pcb->pac", dP, self.Fn)
+        out += scatter(G, st.node, np.einsum("pab,pqb->pqa", M, st.dN))
+        if self.ss.count:
+            ss = self.ss
+            dFh = _L(ss, dv)
+            C = self._surface_C(Fh)
+            cn = np.linalg.norm(c, axis=1)
+            nrm = c / cn[:, None]
+            dc = np.einsum("ragd,rgd->ra", C, dFh)
+            dn = (dc - nrm * np.sum(nrm * dc, 1, keepdims=True)) / cn[:, None]
+            dG = np.einsum("ra,ragd->rgd", dn, C)
+            if mode == HESS_EXACT:
+                dC = np.einsum("agk,bdl,rb,rkl->ragd", EPS, EPS, self.dA, dFh)
+                dG = dG + np.einsum("ra,ragd->rgd", nrm, dC)
+            dG = self.gamma[:, None, None] * dG
+            out += scatter(G, ss.node, dt * dt * np.einsum("rgd,rqd->rqg", dG, ss.dN))
+        return out

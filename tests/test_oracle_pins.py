@@ -1,0 +1,434 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+(B-spline moments, ellipsoid area, rigid/affine motions), textbook or library
+routines (cofactor = det * inverse^T, SVD), conservation laws the paper claims
+(split, P2G, merge), finite differences of the energy, brute-force symmetry and
+definiteness, and special cases with known answers.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle
+from oracle import constitutive as cst
+from oracle.energy import HESS_EXACT, HESS_PROJECTED
+from paper_2101_12408_gb300 import scenes
+
+RNG = np.random.default_rng(7)
+
+
+# ----------------------------------------------------------------------------
+# B-spline (section "Transfer: P2G": quadratic B-splines, nodes at cell centres)
+# ----------------------------------------------------------------------------
+
+def _bspline_1d(d):
+    """Textbook quadratic B-spline, written piecewise in the distance."""
+    d = np.abs(d)
+    return np.where(d < 0.5, 0.75 - d * d, np.where(d < 1.5, 0.5 * (1.5 - d) ** 2, 0.0))
+
+
+def test_spline_matches_piecewise_definition():
+    n = (10, 10, 10)
+    dx = 0.1
+    X = RNG.uniform(1.0, 9.0, size=(200, 3)) * dx
+    st = oracle.Stencil(X, dx, n)
+    # brute force over every node of the grid
+    xi = oracle.node_positions(n, dx)
+    for p in range(0, 200, 17):
+        d = (X[p] - xi) / dx
+        w = np.prod(_bspline_1d(d), -1)
+        dense = np.zeros(xi.shape[0])
+        dense[st.node[p]] = st.N[p]
+        np.testing.assert_allclose(dense, w, atol=1e-15)
+        # gradient by central differences of the piecewise definition
+        h = 1e-6
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            fd = (np.prod(_bspline_1d((X[p] + e - xi) / dx), -1) - np.prod(_bspline_1d((X[p] - e - xi) / dx), -1)) / (2 * h)
+            g = np.zeros(xi.shape[0])
+            g[st.node[p]] = st.dN[p, :, a]
+            np.testing.assert_allclose(g, fd, atol=1e-6 / dx)
+
+
+def test_spline_moment_identities():
+    n = (12, 12, 12)
+    dx = 1.0 / 12
+    X = RNG.uniform(1.0, 11.0, size=(500, 3)) * dx
+    st = oracle.Stencil(X, dx, n)
+    r = st.xi - X[:, None, :]
+    np.testing.assert_allclose(st.N.sum(1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(np.einsum("pq,pqa->pa", st.N, r), 0.0, atol=1e-15)
+    D = np.einsum("pq,pqa,pqb->pab", st.N, r, r)
+    # second moment dx^2/4 I (the constant APIC inertia the paper's merge relies on)
+    np.testing.assert_allclose(D, np.broadcast_to(np.eye(3) * dx * dx / 4, D.shape), atol=1e-15)
+    np.testing.assert_allclose(st.dN.sum(1), 0.0, atol=1e-12)
+    np.testing.assert_allclose(np.einsum("pqa,pqb->pab", st.xi, st.dN), np.broadcast_to(np.eye(3), D.shape), atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# cofactor, polar SVD, fixed corotated (section "Constitutive Models")
+# ----------------------------------------------------------------------------
+
+def test_cofactor_is_det_inverse_transpose():
+    F = np.eye(3) + 0.3 * RNG.standard_normal((50, 3, 3))
+    C = cst.cof(F)
+    ref = np.linalg.det(F)[:, None, None] * np.swapaxes(np.linalg.inv(F), 1, 2)
+    np.testing.assert_allclose(C, ref, rtol=1e-11, atol=1e-12)
+    dF = RNG.standard_normal((50, 3, 3))
+    h = 1e-6
+    fd = (cst.cof(F + h * dF) - cst.cof(F - h * dF)) / (2 * h)
+    np.testing.assert_allclose(cst.dcof(F, dF), fd, atol=1e-8)
+
+
+def test_polar_and_fixed_corotated():
+    F = np.eye(3) + 0.25 * RNG.standard_normal((40, 3, 3))
+    F[:5] = F[:5] * np.array([1, 1, -1])[None, :, None]  # a few inverted
+    R, S, sig = cst.polar(F)
+    np.testing.assert_allclose(np.einsum("pka,pkb->pab", R, R), np.broadcast_to(np.eye(3), R.shape), atol=1e-12)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-12)
+    np.testing.assert_allclose(S, np.swapaxes(S, 1, 2), atol=1e-12)
+    np.testing.assert_allclose(R @ S, F, atol=1e-12)
+    # singular values: |sigma| equal numpy's, sign of the product = sign det F
+    np.testing.assert_allclose(np.sort(np.abs(sig), 1), np.sort(np.linalg.svd(F, compute_uv=False), 1), atol=1e-12)
+    np.testing.assert_allclose(np.prod(sig, 1), np.linalg.det(F), rtol=1e-10)
+    mu = RNG.uniform(1, 3, 40)
+    lam = RNG.uniform(1, 3, 40)
+    h = 1e-6
+    dF = RNG.standard_normal((40, 3, 3))
+    P = cst.fcr_P(F, mu, lam)
+    fd = (cst.fcr_energy(F + h * dF, mu, lam) - cst.fcr_energy(F - h * dF, mu, lam)) / (2 * h)
+    np.testing.assert_allclose(np.einsum("pab,pab->p", P, dF), fd, rtol=1e-6, atol=1e-7)
+    ok = np.abs(np.linalg.det(F)) > 0.2  # away from degenerate polar
+    fdP = (cst.fcr_P(F + h * dF, mu, lam) - cst.fcr_P(F - h * dF, mu, lam)) / (2 * h)
+    np.testing.assert_allclose(cst.fcr_dP(F, dF, mu, lam)[ok], fdP[ok], rtol=1e-5, atol=1e-6)
+
+
+# ----------------------------------------------------------------------------
+# split (Eq. pbal, Eq. cons_mom), P2G and merge conservation
+# ----------------------------------------------------------------------------
+
+def _moving_droplet(**kw):
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=11, **kw)
+    rng = np.random.default_rng(3)
+    sc.v = rng.standard_normal(sc.v.shape)
+    sc.A = rng.standard_normal(sc.A.shape) * 3.0
+    return sc
+
+
+def _angular(x, m, v, A, dx):
+    # APIC angular momentum of a particle: x x m v + m dx^2/4 eps_abg A_gb
+    return np.sum(np.cross(x, m[:, None] * v), 0) + dx * dx / 4 * np.einsum("abg,p,pgb->a", cst.EPS, m, A)
+
+
+def test_nearest_parent_against_kdtree_distance():
+    from scipy.spatial import cKDTree
+    sc = _moving_droplet()
+    parent, best = oracle.nearest_parent(sc.x, sc.s)
+    d, _ = cKDTree(sc.x).query(sc.s)
+    np.testing.assert_allclose(np.sqrt(best), d, rtol=1e-12)
+    np.testing.assert_allclose(np.linalg.norm(sc.x[parent] - sc.s, axis=1), d, rtol=1e-12)
+
+
+def test_split_conserves_mass_momentum_com():
+    sc = _moving_droplet()
+    parent, count, mt, b = oracle.split(sc.x, sc.m, sc.s)
+    assert np.all(count[parent] >= 1)
+    # mass: every group member carries m~, 2|Pi|+1 members
+    np.testing.assert_allclose(np.sum(mt * (2 * count + 1)), np.sum(sc.m), rtol=1e-14)
+    # centre of mass of each group is x_p (Eq. cons_mom)
+    com = mt[:, None] * sc.x
+    np.add.at(com, parent, mt[parent][:, None] * (sc.s + b))
+    np.testing.assert_allclose(com / sc.m[:, None], sc.x, rtol=1e-13, atol=1e-15)
+    # linear and angular momentum of the split collection
+    allx = np.concatenate([sc.x, sc.s, b])
+    allm = np.concatenate([mt, mt[parent], mt[parent]])
+    allv = np.concatenate([sc.v, sc.v[parent], sc.v[parent]])
+    allA = np.concatenate([sc.A, sc.A[parent], sc.A[parent]])
+    np.testing.assert_allclose(np.sum(allm[:, None] * allv, 0), np.sum(sc.m[:, None] * sc.v, 0), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(_angular(allx, allm, allv, allA, sc.dx), _angular(sc.x, sc.m, sc.v, sc.A, sc.dx),
+                               rtol=1e-12, atol=1e-14)
+
+
+def test_p2g_conserves_and_preserves_affine():
+    sc = _moving_droplet()
+    parent, count, mt, b = oracle.split(sc.x, sc.m, sc.s)
+    g = oracle.p2g(sc.n, sc.dx, sc.x, sc.v, sc.A, mt, sc.s, b, parent)
+    xi = oracle.node_positions(sc.n, sc.dx)
+    np.testing.assert_allclose(g["m"].sum(), sc.m.sum(), rtol=1e-13)
+    np.testing.assert_allclose(g["mv"].sum(0), np.sum(sc.m[:, None] * sc.v, 0), rtol=1e-12, atol=1e-14)
+    Lg = np.sum(np.cross(xi, g["mv"]), 0)
+    np.testing.assert_allclose(Lg, _angular(sc.x, sc.m, sc.v, sc.A, sc.dx), rtol=1e-11, atol=1e-13)
+    # affine field v = a + B x with A = B transfers exactly (plain APIC, no split:
+    # split members carry the parent's v_p, not the field at their own position)
+    a = np.array([0.3, -0.2, 0.1])
+    B = RNG.standard_normal((3, 3))
+    v = a + sc.x @ B.T
+    A = np.broadcast_to(B, sc.A.shape).copy()
+    g = oracle.p2g(sc.n, sc.dx, sc.x, v, A, sc.m)
+    vi = oracle.grid_velocity(g["m"], g["mv"])
+    act = g["m"] > 0
+    np.testing.assert_allclose(vi[act], a + xi[act] @ B.T, atol=1e-12)
+
+
+def test_g2p_merge_conserves():
+    sc = _moving_droplet()
+    parent, count, mt, b = oracle.split(sc.x, sc.m, sc.s)
+    g = oracle.p2g(sc.n, sc.dx, sc.x, sc.v, sc.A, mt, sc.s, b, parent)
+    act = g["m"] > 0
+    vhat = np.zeros((g["m"].size, 3))
+    vhat[act] = RNG.standard_normal((act.sum(), 3))
+    out = oracle.g2p(sc.n, sc.dx, vhat, sc.x, sc.m, mt, sc.s, b, parent)
+    xi = oracle.node_positions(sc.n, sc.dx)
+    np.testing.assert_allclose(np.sum(sc.m[:, None] * out["v"], 0), np.sum(g["m"][:, None] * vhat, 0), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(_angular(sc.x, sc.m, out["v"], out["A"], sc.dx),
+                               np.sum(np.cross(xi, g["m"][:, None] * vhat), 0), rtol=1e-11, atol=1e-13)
+    # unsplit particles reproduce an affine grid field exactly (APIC)
+    a = np.array([0.1, 0.2, -0.3])
+    B = RNG.standard_normal((3, 3))
+    vhat = np.where(act[:, None], a + xi @ B.T, 0.0)
+    out = oracle.g2p(sc.n, sc.dx, vhat, sc.x, sc.m, mt, sc.s, b, parent)
+    free = count == 0
+    np.testing.assert_allclose(out["v"][free], a + sc.x[free] @ B.T, atol=1e-12)
+    np.testing.assert_allclose(out["A"][free], np.broadcast_to(B, out["A"][free].shape), atol=1e-10)
+
+
+# ----------------------------------------------------------------------------
+# energy (section "Momentum Update")
+# ----------------------------------------------------------------------------
+
+def _state(sc, v=None):
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    st = sim.newton_state()
+    return sim, st
+
+
+def _affine_grid_velocity(sc, B, a=np.zeros(3)):
+    xi = oracle.node_positions(sc.n, sc.dx)
+    return a + xi @ B.T
+
+
+def _ellipsoid_area(a, b, c):
+    a, b, c = sorted([a, b, c], reverse=True)
+    phi = math.acos(c / a)
+    m = (a * a * (b * b - c * c)) / (b * b * (a * a - c * c))
+    return 2 * math.pi * c * c + 2 * math.pi * a * b / math.sin(phi) * (
+        special.ellipeinc(phi, m) * math.sin(phi) ** 2 + special.ellipkinc(phi, m) * math.cos(phi) ** 2)
+
+
+def test_surface_energy_sphere_scaling_and_ellipsoid():
+    sc = scenes.droplet(n=32, r_cells=8.0, seed=5, surf_per_cell=6.0, gamma=0.7)
+    sc.params.lambda_l = 0.0
+    sim, st = _state(sc)
+    dt = sc.params.dt
+    r = 0.25
+    e_surf = lambda v: st.energy(v) - (0.5 * np.sum(st.m[st.active] * np.sum((v - st.vn)[st.active] ** 2, -1)))
+    # at rest: gamma 4 pi r^2
+    np.testing.assert_allclose(e_surf(np.zeros((st.G, 3))), 0.7 * 4 * math.pi * r * r, rtol=1e-12)
+    # uniform scaling F^ = s I: gamma s^2 4 pi r^2
+    s_fac = 1.3
+    v = _affine_grid_velocity(sc, (s_fac - 1.0) / dt * np.eye(3))
+    np.testing.assert_allclose(e_surf(v), 0.7 * s_fac ** 2 * 4 * math.pi * r * r, rtol=1e-11)
+    # general affine map: area of the image ellipsoid (exact elliptic-integral formula)
+    Fm = np.array([[1.2, 0.1, 0.0], [0.05, 0.9, 0.2], [0.0, -0.1, 1.1]])
+    v = _affine_grid_velocity(sc, (Fm - np.eye(3)) / dt)
+    sv = np.linalg.svd(Fm, compute_uv=False) * r
+    np.testing.assert_allclose(e_surf(v), 0.7 * _ellipsoid_area(*sv), rtol=2e-4)
+
+
+def test_liquid_energy_affine_closed_form():
+    sc = _moving_droplet()
+    sc.params.gamma_lg = 0.0
+    sc.params.lambda_l = 37.0
+    sc.J = RNG.uniform(0.9, 1.1, sc.J.shape)
+    sim, st = _state(sc)
+    B = 5.0 * RNG.standard_normal((3, 3))
+    v = _affine_grid_velocity(sc, B)
+    J = (1.0 + sc.params.dt * np.trace(B)) * sc.J
+    kin = 0.5 * np.sum(st.m[st.active] * np.sum((v - st.vn)[st.active] ** 2, -1))
+    np.testing.assert_allclose(st.energy(v) - kin, np.sum(0.5 * 37.0 * (J - 1) ** 2 * sc.V0), rtol=1e-11)
+
+
+def _mixed_scene():
+    """Tiny scene with liquid + solid particles, viscosity, gravity and surface."""
+    sc = scenes.droplet(n=10, r_cells=2.6, seed=9, gravity=(0.0, -3.0, 0.5), mu_l=0.05, lambda_l=40.0)
+    rng = np.random.default_rng(1)
+    half = sc.x[:, 0] > 0.5
+    sc.phase[half] = scenes.PHASE_SOLID
+    sc.F[half] = np.eye(3) + 0.05 * rng.standard_normal((half.sum(), 3, 3))
+    sc.J = rng.uniform(0.95, 1.05, sc.J.shape)
+    sc.params.E0 = 30.0
+    sc.params.T_melt = 10.0
+    sc.T = rng.uniform(0.0, 5.0, sc.T.shape)
+    sc.v = rng.standard_normal(sc.v.shape) * 0.3
+    sc.params.dt = 0.02
+    sc.params.gamma_lg = 0.8
+    return sc
+
+
+def test_gradient_and_exact_hessian_match_finite_differences():
+    sc = _mixed_scene()
+    sim, st = _state(sc)
+    act = st.active[:, None]
+    rng = np.random.default_rng(2)
+    v = (st.vn + 0.5 * rng.standard_normal(st.vn.shape)) * act
+    for _ in range(3):
+        d = rng.standard_normal(v.shape) * act
+        h = 1e-5
+        fd = (st.energy(v + h * d) - st.energy(v - h * d)) / (2 * h)
+        an = np.sum(st.gradient(v) * d)
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-8), (fd, an)
+        fdg = (st.gradient(v + h * d) - st.gradient(v - h * d)) / (2 * h)
+        hv = st.hessvec(v, d, HESS_EXACT)
+        assert np.max(np.abs(fdg - hv)) <= 1e-6 * np.max(np.abs(hv))
+
+
+def test_hessian_symmetric_and_projected_psd():
+    sc = scenes.droplet(n=8, r_cells=1.6, seed=4, mu_l=0.1, lambda_l=50.0)
+    sc.params.dt = 0.05
+    sc.params.gamma_lg = 2.0
+    sim, st = _state(sc)
+    rng = np.random.default_rng(5)
+    v = (st.vn + rng.standard_normal(st.vn.shape)) * st.active[:, None]
+    idx = np.flatnonzero(st.active)
+    ncol = idx.size * 3
+    for mode in (HESS_EXACT, HESS_PROJECTED):
+        H = np.zeros((ncol, ncol))
+        for c in range(ncol):
+            e = np.zeros((st.G, 3))
+            e[idx[c // 3], c % 3] = 1.0
+            H[:, c] = st.hessvec(v, e, mode)[idx].ravel()
+        np.testing.assert_allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+        if mode == HESS_PROJECTED:
+            ev = np.linalg.eigvalsh(0.5 * (H + H.T))
+            # M + (PSD terms): no eigenvalue below the smallest node mass (up to round-off)
+            assert ev.min() >= st.m[idx].min() - 1e-12 * np.abs(ev).max()
+
+
+def test_internal_forces_sum_to_zero():
+    sc = _mixed_scene()
+    sc.params.gravity = (0.0, 0.0, 0.0)
+    sim, st = _state(sc)
+    rng = np.random.default_rng(8)
+    v = (st.vn + rng.standard_normal(st.vn.shape)) * st.active[:, None]
+    r = st.gradient(v) - st.m[:, None] * (v - st.vn) * st.active[:, None]
+    # translation invariance of e: sum_i de/dy_i = 0
+    assert np.max(np.abs(r.sum(0))) <= 1e-12 * np.max(np.abs(r))
+    d = rng.standard_normal(v.shape) * st.active[:, None]
+    hv = st.hessvec(v, d) - st.m[:, None] * d
+    assert np.max(np.abs(hv.sum(0))) <= 1e-12 * np.max(np.abs(hv))
+
+
+# ----------------------------------------------------------------------------
+# Newton (special cases with known answers)
+# ----------------------------------------------------------------------------
+
+def test_newton_zero_forces_is_free_fall():
+    sc = _moving_droplet(gravity=(0.0, -9.8, 1.0))
+    sc.params.lambda_l = 0.0
+    sc.params.gamma_lg = 0.0
+    sim = oracle.OracleSim(sc)
+    sim.resample(); sim.p2g(); sim.grid_update()
+    act = sim.grid["m"] > 0
+    np.testing.assert_allclose(sim.vhat[act], sim.vn[act] + sc.params.dt * np.array([0.0, -9.8, 1.0]), atol=1e-14)
+
+
+def test_newton_pure_liquid_is_one_step():
+    sc = _moving_droplet()
+    sc.params.gamma_lg = 0.0
+    sc.params.lambda_l = 2000.0
+    sc.params.cg_rtol = 1e-13
+    sc.params.max_cg = 5000
+    sim = oracle.OracleSim(sc)
+    sim.resample(); sim.p2g(); sim.grid_update()
+    assert sim.stats["newton"] == 1
+    assert sim.stats["residual"][-1] <= 1e-10 * sim.stats["residual"][0]
+
+
+# ----------------------------------------------------------------------------
+# heat (section "Temperature Update")
+# ----------------------------------------------------------------------------
+
+def _thermal_scene():
+    sc = scenes.droplet(n=12, r_cells=3.0, seed=21, thermal=True)
+    rng = np.random.default_rng(4)
+    sc.T = rng.uniform(0.0, 2.0, sc.T.shape)
+    sc.gradT = rng.standard_normal(sc.gradT.shape)
+    sc.params.h = 3.0
+    sc.params.H = 0.7
+    sc.params.K = 0.2
+    sc.b = rng.uniform(0, 1, sc.n_surface)
+    sc.Tbar = rng.uniform(0, 1, sc.n_surface)
+    return sc
+
+
+def test_heat_operator_symmetric_spd_and_balance():
+    sc = _thermal_scene()
+    sim = oracle.OracleSim(sc)
+    sim.resample(); sim.p2g()
+    hs = sim.heat_system()
+    idx = np.flatnonzero(hs.unknown)
+    A = np.zeros((idx.size, idx.size))
+    for c in range(idx.size):
+        e = np.zeros(hs.G)
+        e[idx[c]] = 1.0
+        A[:, c] = hs.apply(e)[idx]
+    np.testing.assert_allclose(A, A.T, atol=1e-13 * np.abs(A).max())
+    assert np.linalg.eigvalsh(A).min() > 0
+    # balance: summing all rows, the Laplacian cancels
+    T, _ = oracle.heat_solve(hs, 1e-12, 5000)
+    lhs = np.sum(hs.diag * (T - hs.Tn))
+    # Robin flux of each sample: interpolate T over the stencil nodes that carry
+    # thermal mass with renormalised weights
+    w = hs.ss.N * hs.unknown[hs.ss.node]
+    w = w / w.sum(1, keepdims=True)
+    Ts = np.sum(w * T[hs.ss.node], 1)
+    rhs = (-np.sum(sc.params.h * hs.area * Ts) + np.sum((sc.params.h * sc.Tbar + sc.b) * hs.area)
+           + np.sum(sc.params.H * hs.Vn))
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-9)
+
+
+def test_heat_uniform_ambient_is_fixed_point():
+    sc = _thermal_scene()
+    sc.T[:] = 1.5
+    sc.gradT[:] = 0.0
+    sc.Tbar[:] = 1.5
+    sc.b[:] = 0.0
+    sc.params.H = 0.0
+    sim = oracle.OracleSim(sc)
+    sim.resample(); sim.p2g()
+    hs = sim.heat_system()
+    T, _ = oracle.heat_solve(hs, 1e-13, 5000)
+    np.testing.assert_allclose(T[hs.unknown], 1.5, rtol=1e-10)
+
+
+# ----------------------------------------------------------------------------
+# whole step (section "Conservation" example: explicit steps conserve exactly)
+# ----------------------------------------------------------------------------
+
+def test_explicit_step_conserves_momentum_and_angular_momentum():
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=31, spin=2.0, v0=(0.1, 0.0, -0.2), lambda_l=20.0)
+    sc.params.gamma_lg = 0.2
+    sc.params.dt = 1e-4
+    m0 = np.sum(sc.m[:, None] * sc.v, 0)
+    L0 = _angular(sc.x, sc.m, sc.v, sc.A, sc.dx)
+    sim = oracle.OracleSim(sc, explicit=True)
+    for _ in range(2):
+        sim.step()
+    s = sim.sc
+    np.testing.assert_allclose(np.sum(s.m[:, None] * s.v, 0), m0, atol=1e-13 * np.abs(m0).max())
+    np.testing.assert_allclose(_angular(s.x, s.m, s.v, s.A, s.dx), L0, atol=1e-12 * np.abs(L0).max())
+
+
+def test_implicit_step_conserves_linear_momentum():
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=32, v0=(0.3, -0.1, 0.2), spin=1.0, lambda_l=50.0)
+    m0 = np.sum(sc.m[:, None] * sc.v, 0)
+    sim = oracle.OracleSim(sc)
+    sim.step()
+    s = sim.sc
+    np.testing.assert_allclose(np.sum(s.m[:, None] * s.v, 0), m0, atol=1e-10 * np.abs(m0).max())
