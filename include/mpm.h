@@ -1,0 +1,230 @@
+/*
+ * mpm.h -- C ABI of the GB300 implicit APIC-MPM surface-energy library.
+ *
+ * The library advances one or more independent scenes through the time step of
+ * "A Momentum-Conserving Implicit Material Point Method for Surface Energies
+ * with Spatial Gradients" (arXiv 2101.12408), section "Discretization":
+ *   (1) resample the surface (surface + balance particles, mass split),
+ *   (2) P2G of momentum and temperature,
+ *   (3) grid update: implicit heat solve and backward-Euler Newton-Krylov solve,
+ *   (4) G2P with the conservative merge, particle update and phase change.
+ * Every step of that path runs in the library's CUDA kernels (sm_103a).
+ *
+ * Conventions shared by all entry points
+ *   - Units and layout: positions in the scene's length unit; the grid of a scene
+ *     has n[0] x n[1] x n[2] cells of edge dx starting at `origin`, and one node at
+ *     every cell centre (section "Transfer: P2G": nodes at cell centres).
+ *     Dense grid arrays are node-major with x fastest: node (i, j, k) has flat index
+ *     i + n0 (j + n1 k); vector fields store 3 consecutive components per node.
+ *   - Particle arrays are row-major: x is N x 3, A and F are N x 3 x 3 (row = first
+ *     index), all float64.
+ *   - Pointers: a pointer argument may be host memory or device memory of the
+ *     context's device (the CUDA runtime resolves which); the caller owns it and it
+ *     only needs to stay valid until the call returns (calls that read or write it
+ *     synchronise the context's stream before returning).
+ *   - Particles must lie in cells 1 .. n-2 of every axis (their 27-node stencil
+ *     stays inside the grid); violations are reported as MPM_ERR_DOMAIN.
+ *   - Errors: every entry point returns an mpm_status; mpm_last_error() gives a
+ *     one-line reason. Device-side failures (a particle leaving the grid, a surface
+ *     sample with no particle within dx, a non-finite value) are recorded in a
+ *     device status word and reported by the next call that synchronises.
+ *   - Thread safety: one context per host thread; calls on a context are ordered
+ *     on its stream.
+ */
+#ifndef MPM_GB300_H
+#define MPM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_ctx mpm_ctx;
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or parameter */
+    MPM_ERR_CAPACITY = 2,      /* more particles / surface samples than created for */
+    MPM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    MPM_ERR_NOT_CONVERGED = 4, /* Newton stopped at max_newton above tolerance */
+    MPM_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    MPM_ERR_NUMERIC = 6,       /* non-finite value met on the device */
+    MPM_ERR_DOMAIN = 7         /* particle or sample outside the valid cells */
+} mpm_status;
+
+typedef enum {
+    MPM_PREC_FP64 = 0,          /* every operator and vector in float64 */
+    MPM_PREC_FP32_FP64RED = 1   /* particle stress / Hessian / heat operators and Krylov
+                                   vectors in float32; transfers, grid state, Krylov dot
+                                   products, residual norms, line-search energy sums and the
+                                   final force evaluation in float64 */
+} mpm_precision;
+
+typedef enum {
+    MPM_HESS_EXACT = 0,      /* exact second derivative of the objective */
+    MPM_HESS_PROJECTED = 1   /* the operator the Newton-CG uses: surface term reduced to
+                                its positive semi-definite Gauss-Newton part */
+} mpm_hess_mode;
+
+typedef enum { MPM_WALL_NONE = 0, MPM_WALL_SLIP = 1, MPM_WALL_STICKY = 2 } mpm_wall;
+typedef enum { MPM_GAMMA_CONST = 0, MPM_GAMMA_LINEAR = 1 } mpm_gamma_law;
+
+/* Grid of one scene. Dirichlet velocity conditions (Eq. vbc): the two outer node
+ * layers of face f (order x-, x+, y-, y+, z-, z+) follow walls[f]; nodes where the
+ * plane's signed distance plane_n . x - plane_d is negative follow plane_mode. */
+typedef struct {
+    int32_t n[3];
+    double dx;
+    double origin[3];
+    int32_t walls[6];
+    double plane_n[3];
+    double plane_d;
+    int32_t plane_mode;
+    int32_t pad_;
+} mpm_grid_desc;
+
+/* Physical and solver parameters of one scene (sections "Constitutive Models",
+ * "Thermomechanical Material Dependence and Phase Change", "Contact Angle",
+ * "Temperature Update"). */
+typedef struct {
+    double dt;
+    double gravity[3];
+    double rho;
+    double lambda_l;            /* liquid bulk modulus: Psi = lambda/2 (J - 1)^2 */
+    double mu_l;                /* liquid viscosity */
+    double E0, nu;              /* solid Young's modulus at T <= T0, Poisson ratio */
+    double T0, T_melt;          /* E(T) = E0 max(0, (T_melt - T)/(T_melt - T0)) */
+    double cp, K, h, H;         /* heat capacity, diffusivity, Robin coefficient, source */
+    int32_t gamma_law;          /* MPM_GAMMA_CONST: gamma_lg; MPM_GAMMA_LINEAR:
+                                   clamp(gamma_p[0] + gamma_p[1] (T - T0), gamma_p[2], gamma_p[3]) */
+    int32_t thermal;            /* 1: heat solve and gamma(T) */
+    double gamma_p[4];
+    double gamma_lg;            /* liquid-gas coefficient (constant law) */
+    double gamma_sl;            /* effective solid-liquid coefficient k_SL - k_SG */
+    double newton_tol;          /* stop when |P r| <= newton_tol * max(|P r_0|, 1e-12) */
+    double cg_rtol;             /* inner CG relative tolerance */
+    double heat_rtol;           /* heat CG tolerance relative to |rhs| */
+    int32_t max_newton, max_cg, max_ls;
+    int32_t phase_change;       /* 1: melt / freeze at T_melt after G2P */
+} mpm_params;
+
+typedef struct {
+    mpm_grid_desc grid;
+    mpm_params params;
+    int64_t max_particles;      /* capacity of interior particles for this scene */
+    int64_t max_surface;        /* capacity of surface samples for this scene */
+} mpm_scene_desc;
+
+/* Per-scene statistics of the last mpm_newton_step. */
+typedef struct {
+    int32_t newton_iters;
+    int32_t cg_iters;           /* summed over Newton iterations */
+    int32_t heat_iters;
+    int32_t status;             /* mpm_status of this scene */
+    double residual0;           /* |P r| at the first Newton iterate */
+    double residual;            /* |P r| at the last Newton iterate */
+    double momentum[3];         /* sum_i m_i v_i of the end-of-step grid velocity (float64) */
+    double pad_;
+} mpm_stats;
+
+/* Creates a context for `n_scenes` independent scenes advanced together.
+ * Allocates every device buffer once (particle state, grid, solver vectors,
+ * scratch); no later call allocates. `stream` is a cudaStream_t (NULL: the
+ * legacy default stream). precision: mpm_precision. */
+mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t precision,
+                      void* stream, mpm_ctx** out);
+mpm_status mpm_destroy(mpm_ctx* ctx);
+const char* mpm_last_error(const mpm_ctx* ctx);
+
+/* Interior particles of one scene (section "Discretization": x, J, v, A, V0, m,
+ * T, grad T, plus F and the phase for solids). phase: 0 liquid, 1 solid.
+ * Any pointer except x, m, V0 may be NULL (zeros; J = 1, F = I, phase liquid). */
+mpm_status mpm_set_particles(mpm_ctx* ctx, int32_t scene, int64_t n, const double* x,
+                             const double* v, const double* A, const double* m,
+                             const double* V0, const double* J, const double* F,
+                             const double* T, const double* gradT, const uint8_t* phase);
+/* Reads the particles back in the order they were set. NULL pointers are skipped. */
+mpm_status mpm_get_particles(mpm_ctx* ctx, int32_t scene, int64_t n, double* x, double* v,
+                             double* A, double* J, double* F, double* T, double* gradT,
+                             uint8_t* phase);
+
+/* Surface quadrature samples s_r with area-weighted normals dA_r (section
+ * "Surface Particle Sampling"), interface kind (0 liquid-gas, 1 solid-liquid),
+ * boundary heating b_r and ambient temperature Tbar_r (Eq. heat). kind, b, Tbar
+ * may be NULL (zeros). With a solid plane the kind is recomputed by
+ * mpm_resample: solid-liquid where the plane distance is below dx. */
+mpm_status mpm_set_surface(mpm_ctx* ctx, int32_t scene, int64_t n, const double* s,
+                           const double* dA, const uint8_t* kind, const double* b,
+                           const double* Tbar);
+/* Reads samples back in set order: positions, area normals (carried through the
+ * step), kind, surface coefficient gamma_r, the parent particle p(r) (index in
+ * mpm_set_particles order) and the balance position b_r. NULL pointers skipped. */
+mpm_status mpm_get_surface(mpm_ctx* ctx, int32_t scene, int64_t n, double* s, double* dA,
+                           uint8_t* kind, double* gamma, int32_t* parent, double* bpos);
+
+/* (1) Resample: sort by cell, closest interior particle p(r) of each sample
+ * (smallest squared distance, ties to the smaller particle index), balance
+ * particles b_r = s_r + 2 (x_p(r) - s_r) (Eq. pbal), group sizes |Pi_p| and split
+ * masses m~_p = m_p / (2 |Pi_p| + 1) (Eq. cons_mom). */
+mpm_status mpm_resample(mpm_ctx* ctx);
+
+/* (2) P2G (section "Transfer: P2G"): grid mass and APIC momentum from interior,
+ * surface and balance particles; thermal mass and temperature from interior
+ * particles; grid velocity v^n; gamma_r from the grid temperature. */
+mpm_status mpm_p2g(mpm_ctx* ctx);
+
+/* Dense float64 copy of one grid field of one scene (length nodes * comps). */
+typedef enum {
+    MPM_FIELD_MASS = 0, MPM_FIELD_MOMENTUM = 1, MPM_FIELD_VN = 2, MPM_FIELD_THERMAL_MASS = 3,
+    MPM_FIELD_TN = 4, MPM_FIELD_VHAT = 5, MPM_FIELD_THAT = 6, MPM_FIELD_ITERATE = 7
+} mpm_field;
+mpm_status mpm_get_grid(mpm_ctx* ctx, int32_t scene, int32_t field, double* out);
+
+/* Sets the Newton iterate v of one scene (dense float64, nodes x 3) and caches
+ * the per-particle state at y = x + dt v (section "Momentum Update"). */
+mpm_status mpm_set_velocity(mpm_ctx* ctx, int32_t scene, const double* v);
+
+/* Objective Phi(v) of the backward-Euler system and its gradient dPhi/dv
+ * (Eq. disc_force, Eq. fe) at the current iterate: dense float64, nodes x 3,
+ * not projected. `energy` (one double) may be NULL. */
+mpm_status mpm_energy_gradient(mpm_ctx* ctx, int32_t scene, double* grad, double* energy);
+
+/* Hessian-vector product at the current iterate: out = P H P dv with P the
+ * Dirichlet / massless-node projection and H = M + dt^2 d2e/dy2 + dt mu Visc
+ * (the linearisation of Eq. fe). dv and out are dense arrays (nodes x 3) of
+ * float32 in MPM_PREC_FP32_FP64RED and float64 in MPM_PREC_FP64. mode:
+ * mpm_hess_mode. */
+mpm_status mpm_apply_hessian(mpm_ctx* ctx, int32_t scene, const void* dv, void* out, int32_t mode);
+
+/* Heat operator (section "Temperature Update"): out = A T with
+ * A = c_p m^T/dt + Laplacian (particle quadrature) + Robin (surface quadrature),
+ * restricted to nodes with thermal mass. T, out: dense, float32 / float64 as above. */
+mpm_status mpm_heat_apply(mpm_ctx* ctx, int32_t scene, const void* T, void* out);
+
+/* (3) Grid update of every scene: heat CG (thermal scenes), then Newton-CG with
+ * Armijo line search on Phi, then one explicit force evaluation at the converged
+ * iterate. stats: host array of n_scenes entries, or NULL. Returns the worst
+ * per-scene status. */
+mpm_status mpm_newton_step(mpm_ctx* ctx, mpm_stats* stats);
+
+/* (4) G2P with the conservative merge (section "Transfer: G2P"), particle
+ * update x += dt v_p, J / F update, temperature transfer, phase change, and the
+ * carried surface samples s += dt v(s), dA <- cof(I + dt grad v(s)) dA. */
+mpm_status mpm_g2p(mpm_ctx* ctx);
+
+/* mpm_resample + mpm_p2g + mpm_newton_step + mpm_g2p. */
+mpm_status mpm_step(mpm_ctx* ctx, mpm_stats* stats);
+
+/* Waits for the context's stream and reports any device-side error. */
+mpm_status mpm_sync(mpm_ctx* ctx);
+
+/* Counts: interior particles, surface samples, active grid blocks (4x4x4 nodes)
+ * and blocks holding particles, over all scenes, after the last mpm_resample. */
+mpm_status mpm_counts(mpm_ctx* ctx, int64_t* n_particles, int64_t* n_surface,
+                      int64_t* n_blocks, int64_t* n_work_blocks);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPM_GB300_H */

@@ -1,0 +1,134 @@
+// Host-side context of the library and the launchers of its kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "common.cuh"
+
+namespace mpm {
+
+// Node projection codes (grid Dirichlet conditions, massless nodes).
+enum : uint8_t { PC_FIXED = 1, PC_SLIPX = 2, PC_SLIPY = 4, PC_SLIPZ = 8, PC_PLANE = 16 };
+
+struct Dev {
+    // ---- interior particles, float64, sorted by cell (SoA) ----
+    double *x[3], *v[3], *A[9], *m, *V0, *J, *F[9], *T, *gT[3];
+    uint8_t* phase;
+    int *pid, *psc;                 // original index within its scene, scene
+    // second set for the permutation
+    double *x2[3], *v2[3], *A2[9], *m2, *V02, *J2, *F2[9], *T2, *gT22[3];
+    uint8_t* phase2;
+    int *pid2, *psc2;
+    // per-step interior data
+    int* gcount;                    // |Pi_p|
+    double* mt;                     // split mass
+    double* acc[12];                // merged momentum (3) and affine moments (9)
+    // operator packs (type R of the context: float or double)
+    void* pu[3];                    // position relative to the block origin, in cells
+    void* kappa;                    // dt^2 lambda (J^n)^2 V0 (liquid), 0 solid
+    void* cvisc;                    // dt mu V^n (liquid), 0 solid
+    void* Fn[9];                    // F^n (solid)
+    void* lame[2];                  // mu, lambda (solid)
+    void* scache[24];               // solid per-iterate: F (9), R (9), (tr S I - S)^-1 (6)
+    void* Vn;                       // V^n for heat (R)
+    // ---- surface samples ----
+    double *s[3], *dA[3], *bheat, *Tbar, *gamma, *bpos[3], *Tr;
+    uint8_t* kind;
+    int *sid, *ssc, *parent;        // parent: sorted interior index
+    double *s2[3], *dA2[3], *bheat2, *Tbar2;
+    uint8_t* kind2;
+    int *sid2, *ssc2;
+    void* su[3];                    // sample position relative to its block (R)
+    void* sa[3];                    // dA (R)
+    void* sg;                       // gamma (R)
+    void* sF[9];                    // F^ at the iterate (R)
+    void* sn[3];                    // unit c (R)
+    void* sic;                      // 1/|c| (R)
+    void* swn;                      // Robin normaliser 1/sum_j N_j [m^T_j > 0] (R)
+    // ---- sort / blocks ----
+    long long* key;                 // interior cell keys
+    int* rank;
+    int* perm;
+    long long* skey;
+    int* srank;
+    int* sperm;
+    int *cell_count, *cell_start;   // interior, over all cells (+1)
+    int *scell_count, *scell_start; // surface
+    int* bflag;                     // per global block: 1 active
+    int* bwork;                     // per global block: 1 holds particles
+    int* bslot;                     // per global block: slot or -1
+    int* bscan;
+    int4* slot_coord;               // bx, by, bz, scene
+    int* nbr;                       // 27 neighbour slots per slot
+    int* work;                      // work slot list
+    int* work_gb;
+    int* counts;                    // [0] NB, [1] NW
+    int* scan_tmp;
+    // ---- grid (float64) ----
+    double *gm, *gmv, *gvn, *gmT, *gmTT, *gTn, *gv, *gvhat, *gThat, *ggrad;
+    uint8_t* pcode;
+    // ---- solver vectors (R) ----
+    void *cx, *cr, *cp, *cu, *invm;
+    void *hx, *hr, *hp, *hu, *hinvd, *hT;   // heat CG (scalar fields)
+    double* hrhs;
+    // dense staging for the C ABI
+    void* dense_a;
+    void* dense_b;
+    // ---- scalars ----
+    SceneDev* sc;
+    SceneScal* scal;
+    int* err;
+};
+
+}  // namespace mpm
+
+struct mpm_ctx {
+    int nsc = 0;
+    int prec = 0;
+    int rsize = 8;                  // sizeof(R)
+    cudaStream_t st = nullptr;
+    std::vector<mpm::SceneDev> hsc;
+    long long Pcap = 0, Scap = 0, total_blocks = 0, total_cells = 0;
+    long long np = 0, ns = 0;       // current totals
+    int NB = 0, NW = 0;
+    bool resampled = false, p2g_done = false, step_ready = false;
+    mpm::Dev d{};
+    mpm::SceneScal* hscal = nullptr;   // pinned mirror
+    int* herr = nullptr;               // pinned
+    int* hcounts = nullptr;            // pinned
+    std::string last_error;
+    std::vector<void*> allocs;
+};
+
+namespace mpm {
+
+// ---- sort.cu ----
+cudaError_t launch_sort_particles(mpm_ctx* c);
+cudaError_t launch_sort_surface(mpm_ctx* c);
+cudaError_t launch_build_blocks(mpm_ctx* c);   // needs parents (balance particles)
+cudaError_t launch_exclusive_scan(const int* in, int* out, long long n, int* tmp, cudaStream_t st);
+
+// ---- transfer.cu ----
+cudaError_t launch_nearest_parent(mpm_ctx* c);
+cudaError_t launch_p2g(mpm_ctx* c);
+cudaError_t launch_g2p(mpm_ctx* c);
+
+// ---- newton.cu ----
+cudaError_t launch_pack_step(mpm_ctx* c);
+cudaError_t launch_eval(mpm_ctx* c, bool fp64_math, bool want_cache);
+cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode);
+cudaError_t run_newton(mpm_ctx* c);
+cudaError_t launch_dense_to_grid(mpm_ctx* c, int scene, const void* dense, void* grid, int comps, int rsize);
+cudaError_t launch_grid_to_dense(mpm_ctx* c, int scene, const void* grid, void* dense, int comps, int rsize_in, int rsize_out);
+cudaError_t launch_project_vec(mpm_ctx* c, void* vec, int rsize);
+cudaError_t launch_mass_term(mpm_ctx* c, const void* p, void* u);
+
+// ---- heat.cu ----
+cudaError_t run_heat(mpm_ctx* c);
+cudaError_t launch_heat_apply(mpm_ctx* c, const void* T, void* out);
+
+}  // namespace mpm

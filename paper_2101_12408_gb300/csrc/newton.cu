@@ -1,0 +1,1507 @@
+// Backward-Euler momentum solve: objective / gradient, Hessian-vector operator,
+// Jacobi-preconditioned CG, one-pass Armijo line search, Newton control.
+//
+// Paper section "Momentum Update" (Eq. disc_force, the discrete energy e(y),
+// Eq. fe). With y = x + dt v the backward-Euler equations are the stationarity
+// conditions of
+//   Phi(v) = sum_i m_i/2 |v_i - v^n_i|^2 - dt sum_i m_i g.v_i + e(x + dt v)
+//            + dt mu/2 sum_p V^n_p |sym L_p|^2,     L_p = sum_i v_i gradN_i(x_p)^T,
+// liquid J_p = (1 + dt tr L_p) J^n_p, solid F_p = (I + dt L_p) F^n_p, surface
+// F^_r = I + dt L(s_r) with energy k_r |cof(F^_r) dA_r|.
+// Hessian-vector (the linearisation the paper refers to earlier work for):
+//   liquid  dt^2 lambda (J^n)^2 V^0 gradN_i tr(dL)    viscous  dt mu V^n sym(dL) gradN_i
+//   solid   dt^2 V^0 dP(F; dL F^n) F^nT gradN_i
+//   surface dt^2 dG gradN_i(s_r), dG = -k [dn]x F^ [a]x  (+ -k [n]x dF^ [a]x exact),
+//           dn = (I - n n^T) dc/|c|, dc = dcof(F^)[dF^] a, with G = -k [n]x F^ [a]x the
+//           gradient of k |cof(F^) a| (the projected mode keeps the PSD Gauss-Newton part).
+#include "ctx.h"
+#include "polar.cuh"
+
+namespace mpm {
+
+namespace {
+
+constexpr int NT = 128;
+
+struct Ptrs3 { const double* a[3]; };
+struct Ptrs9 { const double* a[9]; };
+template <typename R> struct RPtr3 { R* a[3]; };
+template <typename R> struct RPtr9 { R* a[9]; };
+template <typename R> struct RPtr24 { R* a[24]; };
+
+template <typename R>
+__device__ __forceinline__ void cross_mat(const R* a, R* M) {
+    M[0] = 0; M[1] = -a[2]; M[2] = a[1];
+    M[3] = a[2]; M[4] = 0; M[5] = -a[0];
+    M[6] = -a[1]; M[7] = a[0]; M[8] = 0;
+}
+
+// G = -k [n]x F [a]x
+template <typename R>
+__device__ __forceinline__ void surf_G(R k, const R* n, const R* F, const R* a, R* G) {
+    R An[9], Aa[9], T1[9];
+    cross_mat<R>(a, Aa);
+    cross_mat<R>(n, An);
+    matmul3<R>(F, Aa, T1);
+    matmul3<R>(An, T1, G);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) G[q] *= -k;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_halo_vec(const int* __restrict__ nbr, int slot, const R* __restrict__ vec, R (*sh)[HN]) {
+    for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
+        int c = t / HN, h = t % HN;
+        int ns, loc;
+        halo_source(nbr, slot, h, ns, loc);
+        sh[c][h] = ns < 0 ? R(0) : vec[ns * 192 + c * 64 + loc];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void load_halo_vec_d(const int* __restrict__ nbr, int slot, const double* __restrict__ vec, R (*sh)[HN]) {
+    for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
+        int c = t / HN, h = t % HN;
+        int ns, loc;
+        halo_source(nbr, slot, h, ns, loc);
+        sh[c][h] = ns < 0 ? R(0) : (R)vec[ns * 192 + c * 64 + loc];
+    }
+}
+
+template <typename A>
+__device__ __forceinline__ void flush_halo_vec(const int* __restrict__ nbr, int slot, A (*sh)[HN], A* __restrict__ vec) {
+    for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
+        int c = t / HN, h = t % HN;
+        A val = sh[c][h];
+        if (val == A(0)) continue;
+        int ns, loc;
+        halo_source(nbr, slot, h, ns, loc);
+        if (ns >= 0) atomicAdd(&vec[ns * 192 + c * 64 + loc], val);
+    }
+}
+
+// local stencil of a point: cell relative to the block origin, weights, gradients
+template <typename R>
+__device__ __forceinline__ void stencil_in_block(const double* p, const SceneDev& S, int4 bc, int lc[3], R w[3][3], R dw[3][3], R f[3]) {
+    int ob[3] = {bc.x * BS, bc.y * BS, bc.z * BS};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double u = (p[a] - S.origin[a]) * S.inv_dx;
+        double fl = floor(u);
+        lc[a] = (int)fl - ob[a];
+        f[a] = (R)(u - 0.5 - (fl - 1.0));
+        bspline<R>(f[a], w[a], dw[a]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dw[a][k] *= (R)S.inv_dx;
+    }
+}
+
+// ======================================================================
+// per-step packs for the operator (constant over the Newton iterations)
+// ======================================================================
+template <typename R>
+__global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptrs9 F, const double* __restrict__ V0,
+                              const double* __restrict__ T, const uint8_t* __restrict__ phase, const int* __restrict__ psc,
+                              const SceneDev* __restrict__ sc, RPtr3<R> pu, R* __restrict__ kappa, R* __restrict__ cvisc,
+                              RPtr9<R> Fn, R* __restrict__ lmu, R* __restrict__ llam, R* __restrict__ Vn) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const SceneDev& S = sc[psc[i]];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double u = (x.a[a][i] - S.origin[a]) * S.inv_dx;
+        int c = (int)floor(u);
+        pu.a[a][i] = (R)(u - (double)((c >> 2) * BS));
+    }
+    double dt = S.dt;
+    double Jn = J[i], v0 = V0[i];
+    bool liq = phase[i] == 0;
+    double Fd[9];
+    for (int q = 0; q < 9; ++q) Fd[q] = F.a[q][i];
+    double detF = det3<double>(Fd);
+    Vn[i] = (R)((liq ? Jn : detF) * v0);
+    kappa[i] = liq ? (R)(dt * dt * S.lambda_l * Jn * Jn * v0) : R(0);
+    cvisc[i] = liq ? (R)(dt * S.mu_l * Jn * v0) : R(0);
+    if (!liq) {
+        for (int q = 0; q < 9; ++q) Fn.a[q][i] = (R)Fd[q];
+        double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - T[i]) / (S.T_melt - S.T0));
+        lmu[i] = (R)(E / (2.0 * (1.0 + S.nu)));
+        llam[i] = (R)(E * S.nu / ((1.0 + S.nu) * (1.0 - 2.0 * S.nu)));
+    }
+}
+
+template <typename R>
+__global__ void k_pack_surface(int ns, Ptrs3 s, Ptrs3 dA, const double* __restrict__ gamma, const int* __restrict__ ssc,
+                               const SceneDev* __restrict__ sc, RPtr3<R> su, RPtr3<R> sa, R* __restrict__ sg) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    const SceneDev& S = sc[ssc[j]];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double u = (s.a[a][j] - S.origin[a]) * S.inv_dx;
+        int c = (int)floor(u);
+        su.a[a][j] = (R)(u - (double)((c >> 2) * BS));
+        sa.a[a][j] = (R)dA.a[a][j];
+    }
+    sg[j] = (R)gamma[j];
+}
+
+// ======================================================================
+// objective + gradient (+ per-iterate caches) at the Newton iterate
+// ======================================================================
+template <typename R>
+struct EvalArgs {
+    const int *work, *work_gb, *nbr, *cell_start, *scell_start;
+    const int4* coord;
+    const SceneDev* sc;
+    SceneScal* scal;
+    const double* gv;          // iterate (double grid)
+    double* grad;              // gradient accumulator (double grid)
+    Ptrs3 x;
+    const double *J, *V0, *T;
+    Ptrs9 F;
+    const uint8_t* phase;
+    Ptrs3 s, dA;
+    const double* gamma;
+    int want_grad, want_cache, skip_done;
+    RPtr24<R> scache;          // solid: F (9), R (9), Kinv (6)
+    RPtr9<R> sF;               // surface F^
+    RPtr3<R> sn;               // surface unit c
+    R* sic;                    // 1/|c|
+};
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_eval(EvalArgs<R> a) {
+    __shared__ R vh[3][HN];
+    __shared__ double ga[3][HN];
+    __shared__ double red[NT / 32];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    if (a.skip_done && a.scal[bc.w].newton_done) return;
+    load_halo_vec_d<R>(a.nbr, slot, a.gv, vh);
+    for (int t = threadIdx.x; t < 3 * HN; t += NT) (&ga[0][0])[t] = 0.0;
+    __syncthreads();
+    const R dt = (R)S.dt;
+    double esum = 0.0;
+    int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
+    for (int i = beg + threadIdx.x; i < end; i += NT) {
+        double p[3] = {a.x.a[0][i], a.x.a[1][i], a.x.a[2][i]};
+        int lc[3];
+        R wgt[3][3], dw[3][3], f[3];
+        stencil_in_block<R>(p, S, bc, lc, wgt, dw, f);
+        R L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        R vq = vh[q][h];
+                        L[3 * q] += vq * dN[0];
+                        L[3 * q + 1] += vq * dN[1];
+                        L[3 * q + 2] += vq * dN[2];
+                    }
+                }
+        R M[9];
+        double v0 = a.V0[i];
+        if (a.phase[i] == 0) {
+            R Jn = (R)a.J[i];
+            R jm1n = (R)(a.J[i] - 1.0);
+            R trL = L[0] + L[4] + L[8];
+            R jm1 = jm1n + dt * trL * (R(1) + jm1n);
+            R lam = (R)S.lambda_l;
+            esum += 0.5 * (double)lam * (double)jm1 * (double)jm1 * v0;
+            R Vn = (R)(a.J[i] * v0);
+            R mu = (R)S.mu_l;
+            R eps[9];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) eps[3 * q + e] = R(0.5) * (L[3 * q + e] + L[3 * e + q]);
+            R e2 = 0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) e2 += eps[q] * eps[q];
+            esum += 0.5 * (double)dt * (double)mu * (double)Vn * (double)e2;
+            R pr = dt * lam * jm1 * Jn * (R)v0;
+            R cv = dt * mu * Vn;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) M[q] = cv * eps[q] + ((q % 4 == 0) ? pr : R(0));
+        } else {
+            R Fo[9], A1[9], Fc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                Fo[q] = (R)a.F.a[q][i];
+                A1[q] = dt * L[q] + ((q % 4 == 0) ? R(1) : R(0));
+            }
+            matmul3<R>(A1, Fo, Fc);
+            R Rm[9], K[6], sg[3];
+            polar3<R>(Fc, Rm, K, sg);
+            double Tn = a.T[i];
+            double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - Tn) / (S.T_melt - S.T0));
+            R mu = (R)(E / (2.0 * (1.0 + S.nu)));
+            R lam = (R)(E * S.nu / ((1.0 + S.nu) * (1.0 - 2.0 * S.nu)));
+            R J = det3<R>(Fc);
+            esum += ((double)mu * ((double)(sg[0] - 1) * (sg[0] - 1) + (double)(sg[1] - 1) * (sg[1] - 1) +
+                                   (double)(sg[2] - 1) * (sg[2] - 1)) +
+                     0.5 * (double)lam * (double)(J - 1) * (double)(J - 1)) * v0;
+            R C[9], P[9];
+            cofactor<R>(Fc, C);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) P[q] = R(2) * mu * (Fc[q] - Rm[q]) + lam * (J - 1) * C[q];
+            matmul3_bt<R>(P, Fo, M);
+            R sc = dt * (R)v0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) M[q] *= sc;
+            if (a.want_cache) {
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    a.scache.a[q][i] = Fc[q];
+                    a.scache.a[9 + q][i] = Rm[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) a.scache.a[18 + q][i] = K[q];
+            }
+        }
+        if (a.want_grad) {
+            for (int cz = 0; cz < 3; ++cz)
+                for (int cy = 0; cy < 3; ++cy)
+                    for (int cx = 0; cx < 3; ++cx) {
+                        int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                        R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                                   wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            atomicAdd(&ga[q][h], (double)(M[3 * q] * dN[0] + M[3 * q + 1] * dN[1] + M[3 * q + 2] * dN[2]));
+                    }
+        }
+    }
+    int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    for (int j = sbeg + threadIdx.x; j < send; j += NT) {
+        double p[3] = {a.s.a[0][j], a.s.a[1][j], a.s.a[2][j]};
+        int lc[3];
+        R wgt[3][3], dw[3][3], f[3];
+        stencil_in_block<R>(p, S, bc, lc, wgt, dw, f);
+        R Fh[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        R vq = dt * vh[q][h];
+                        Fh[3 * q] += vq * dN[0];
+                        Fh[3 * q + 1] += vq * dN[1];
+                        Fh[3 * q + 2] += vq * dN[2];
+                    }
+                }
+        R av[3] = {(R)a.dA.a[0][j], (R)a.dA.a[1][j], (R)a.dA.a[2][j]};
+        R C[9];
+        cofactor<R>(Fh, C);
+        R cv[3] = {C[0] * av[0] + C[1] * av[1] + C[2] * av[2], C[3] * av[0] + C[4] * av[1] + C[5] * av[2],
+                   C[6] * av[0] + C[7] * av[1] + C[8] * av[2]};
+        R cn = sqrt(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]);
+        R k = (R)a.gamma[j];
+        esum += (double)k * (double)cn;
+        R nv[3] = {cv[0] / cn, cv[1] / cn, cv[2] / cn};
+        if (a.want_cache) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) a.sF.a[q][j] = Fh[q];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) a.sn.a[q][j] = nv[q];
+            a.sic[j] = R(1) / cn;
+        }
+        if (a.want_grad) {
+            R G[9];
+            surf_G<R>(k * dt, nv, Fh, av, G);
+            for (int cz = 0; cz < 3; ++cz)
+                for (int cy = 0; cy < 3; ++cy)
+                    for (int cx = 0; cx < 3; ++cx) {
+                        int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                        R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                                   wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            atomicAdd(&ga[q][h], (double)(G[3 * q] * dN[0] + G[3 * q + 1] * dN[1] + G[3 * q + 2] * dN[2]));
+                    }
+        }
+    }
+    block_atomic_sum<NT>(esum, &a.scal[bc.w].phi_part, red);
+    if (a.want_grad) {
+        __syncthreads();
+        flush_halo_vec<double>(a.nbr, slot, ga, a.grad);
+    }
+}
+
+// node part of the gradient: m (v - v^n) - dt m g; |P grad|^2 and the kinetic energy
+__device__ __forceinline__ void project3(double* v, uint8_t code, const SceneDev& S) {
+    if (code & PC_FIXED) {
+        v[0] = v[1] = v[2] = 0.0;
+        return;
+    }
+    if (code & PC_SLIPX) v[0] = 0.0;
+    if (code & PC_SLIPY) v[1] = 0.0;
+    if (code & PC_SLIPZ) v[2] = 0.0;
+    if (code & PC_PLANE) {
+        double d = v[0] * S.plane_n[0] + v[1] * S.plane_n[1] + v[2] * S.plane_n[2];
+        for (int q = 0; q < 3; ++q) v[q] -= d * S.plane_n[q];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void project3r(R* v, uint8_t code, const SceneDev& S) {
+    if (code & PC_FIXED) {
+        v[0] = v[1] = v[2] = R(0);
+        return;
+    }
+    if (code & PC_SLIPX) v[0] = R(0);
+    if (code & PC_SLIPY) v[1] = R(0);
+    if (code & PC_SLIPZ) v[2] = R(0);
+    if (code & PC_PLANE) {
+        R n0 = (R)S.plane_n[0], n1 = (R)S.plane_n[1], n2 = (R)S.plane_n[2];
+        R d = v[0] * n0 + v[1] * n1 + v[2] * n2;
+        v[0] -= d * n0;
+        v[1] -= d * n1;
+        v[2] -= d * n2;
+    }
+}
+
+__global__ void k_node_grad(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, SceneScal* __restrict__ scal,
+                            const double* __restrict__ gm, const double* __restrict__ gvn, const double* __restrict__ gv,
+                            const uint8_t* __restrict__ pcode, double* __restrict__ grad, int skip_done) {
+    __shared__ double red[2];
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = coord[slot];
+    const SceneDev& S = sc[bc.w];
+    if (skip_done && scal[bc.w].newton_done) return;
+    int t = slot * 64 + l;
+    double m = gm[t];
+    double rr = 0.0, ek = 0.0;
+    if (m > 0.0) {
+        double gr[3];
+        for (int q = 0; q < 3; ++q) {
+            int k = slot * 192 + q * 64 + l;
+            double v = gv[k], dv = v - gvn[k];
+            gr[q] = grad[k] + m * dv - S.dt * m * S.g[q];
+            grad[k] = gr[q];
+            ek += 0.5 * m * dv * dv - S.dt * m * S.g[q] * v;
+        }
+        project3(gr, pcode[t], S);
+        rr = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+    }
+    rr = warp_sum(rr);
+    ek = warp_sum(ek);
+    if ((l & 31) == 0) {
+        // 2 warps per block
+        atomicAdd(&scal[bc.w].rr, rr);
+        atomicAdd(&scal[bc.w].phi_kin, ek);
+    }
+    (void)red;
+}
+
+// ======================================================================
+// Hessian-vector operator (the hot kernel): u += K p (stiffness part)
+// ======================================================================
+template <typename R>
+struct ApplyArgs {
+    const int *work, *work_gb, *nbr, *cell_start, *scell_start;
+    const int4* coord;
+    const SceneDev* sc;
+    const SceneScal* scal;
+    const R* p;
+    R* u;
+    const uint8_t* phase;
+    const double* V0;
+    RPtr3<R> pu;
+    const R *kappa, *cvisc;
+    RPtr9<R> Fn;
+    const R *lmu, *llam;
+    RPtr24<R> scache;
+    RPtr3<R> su, sa;
+    const R* sg;
+    RPtr9<R> sF;
+    RPtr3<R> sn;
+    const R* sic;
+    int mode;
+    int check_done;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_apply(ApplyArgs<R> a) {
+    __shared__ R ph[3][HN];
+    __shared__ R ua[3][HN];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    if (a.check_done && a.scal[bc.w].cg_done) return;
+    load_halo_vec<R>(a.nbr, slot, a.p, ph);
+    for (int t = threadIdx.x; t < 3 * HN; t += NT) (&ua[0][0])[t] = R(0);
+    __syncthreads();
+    const R dt = (R)S.dt;
+    const R inv_dx = (R)S.inv_dx;
+    int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
+    for (int i = beg + threadIdx.x; i < end; i += NT) {
+        int lc[3];
+        R wgt[3][3], dw[3][3];
+        make_stencil_local<R>(a.pu.a[0][i], a.pu.a[1][i], a.pu.a[2][i], inv_dx, lc, wgt, dw);
+        bool liq = a.phase[i] == 0;
+        R cv = liq ? a.cvisc[i] : R(0);
+        bool full = !liq || cv != R(0);
+        R dL[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        R tr = 0;
+        if (full) {
+            for (int cz = 0; cz < 3; ++cz)
+                for (int cy = 0; cy < 3; ++cy)
+                    for (int cx = 0; cx < 3; ++cx) {
+                        int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                        R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                                   wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            R pq = ph[q][h];
+                            dL[3 * q] += pq * dN[0];
+                            dL[3 * q + 1] += pq * dN[1];
+                            dL[3 * q + 2] += pq * dN[2];
+                        }
+                    }
+            tr = dL[0] + dL[4] + dL[8];
+        } else {
+            for (int cz = 0; cz < 3; ++cz)
+                for (int cy = 0; cy < 3; ++cy)
+                    for (int cx = 0; cx < 3; ++cx) {
+                        int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                        tr += ph[0][h] * dw[0][cx] * wgt[1][cy] * wgt[2][cz] + ph[1][h] * wgt[0][cx] * dw[1][cy] * wgt[2][cz] +
+                              ph[2][h] * wgt[0][cx] * wgt[1][cy] * dw[2][cz];
+                    }
+        }
+        R M[9];
+        if (liq) {
+            R s = a.kappa[i] * tr;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) M[3 * q + e] = cv * R(0.5) * (dL[3 * q + e] + dL[3 * e + q]) + (q == e ? s : R(0));
+        } else {
+            R Fo[9], Fc[9], Rm[9], K[6], dF[9], dP[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                Fo[q] = a.Fn.a[q][i];
+                Fc[q] = a.scache.a[q][i];
+                Rm[q] = a.scache.a[9 + q][i];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) K[q] = a.scache.a[18 + q][i];
+            matmul3<R>(dL, Fo, dF);
+            fcr_dP<R>(Fc, Rm, K, a.lmu[i], a.llam[i], dF, dP);
+            matmul3_bt<R>(dP, Fo, M);
+            R sc = dt * dt * (R)a.V0[i];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) M[q] *= sc;
+        }
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], M[3 * q] * dN[0] + M[3 * q + 1] * dN[1] + M[3 * q + 2] * dN[2]);
+                }
+    }
+    int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    for (int j = sbeg + threadIdx.x; j < send; j += NT) {
+        int lc[3];
+        R wgt[3][3], dw[3][3];
+        make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
+        R dFh[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        R pq = ph[q][h];
+                        dFh[3 * q] += pq * dN[0];
+                        dFh[3 * q + 1] += pq * dN[1];
+                        dFh[3 * q + 2] += pq * dN[2];
+                    }
+                }
+        R Fh[9], av[3], nv[3];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Fh[q] = a.sF.a[q][j];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            av[q] = a.sa.a[q][j];
+            nv[q] = a.sn.a[q][j];
+        }
+        R k = a.sg[j], ic = a.sic[j];
+        R dC[9];
+        dcofactor<R>(Fh, dFh, dC);
+        R dc[3] = {dC[0] * av[0] + dC[1] * av[1] + dC[2] * av[2], dC[3] * av[0] + dC[4] * av[1] + dC[5] * av[2],
+                   dC[6] * av[0] + dC[7] * av[1] + dC[8] * av[2]};
+        R nd = nv[0] * dc[0] + nv[1] * dc[1] + nv[2] * dc[2];
+        R dn[3] = {(dc[0] - nd * nv[0]) * ic, (dc[1] - nd * nv[1]) * ic, (dc[2] - nd * nv[2]) * ic};
+        R G[9];
+        surf_G<R>(k * dt * dt, dn, Fh, av, G);
+        if (a.mode == MPM_HESS_EXACT) {
+            R G2[9];
+            surf_G<R>(k * dt * dt, nv, dFh, av, G2);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) G[q] += G2[q];
+        }
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], G[3 * q] * dN[0] + G[3 * q + 1] * dN[1] + G[3 * q + 2] * dN[2]);
+                }
+    }
+    __syncthreads();
+    flush_halo_vec<R>(a.nbr, slot, ua, a.u);
+}
+
+// ======================================================================
+// CG vector kernels (one 64-thread CTA per slot; NC = 3 momentum, 1 heat)
+// ======================================================================
+template <typename R, int NC>
+struct CGArgs {
+    const int4* coord;
+    const SceneDev* sc;
+    SceneScal* scal;
+    const uint8_t* pcode;     // NC == 3
+    const R* inv;             // inverse diagonal (0 = not an unknown)
+    const double* gm;         // NC == 3: mass diagonal
+    R *x, *r, *p, *u;
+    const double* rhs_d;      // for init: b = sign * rhs (double)
+    double rhs_sign;
+};
+
+template <typename R, int NC>
+__device__ __forceinline__ void cg_proj(R* v, const CGArgs<R, NC>& a, int t, const SceneDev& S) {
+    if (NC == 3) project3r<R>(v, a.pcode[t], S);
+    else if (a.inv[t] == R(0)) v[0] = R(0);
+}
+
+template <typename R, int NC>
+__device__ __forceinline__ int vidx(int slot, int q, int l) { return NC == 3 ? slot * 192 + q * 64 + l : slot * 64 + l; }
+
+template <typename R, int NC>
+__device__ __forceinline__ void scal_add2(SceneScal* sc, double* f1, double v1, double* f2, double v2) {
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    if ((threadIdx.x & 31) == 0) {
+        if (v1 != 0.0) atomicAdd(f1, v1);
+        if (f2 && v2 != 0.0) atomicAdd(f2, v2);
+    }
+}
+
+// r = P b, x = 0, z = P(inv r), p = z, u = 0; rz, bnorm (if requested)
+template <typename R, int NC>
+__global__ void k_cg_init(CGArgs<R, NC> a, int set_bnorm) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    SceneScal& sc = a.scal[bc.w];
+    if (sc.cg_done) return;
+    int t = slot * 64 + l;
+    R r[NC];
+    double bb = 0.0, rz = 0.0;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) r[q] = (R)(a.rhs_sign * a.rhs_d[vidx<R, NC>(slot, q, l)]);
+    cg_proj<R, NC>(r, a, t, S);
+    R z[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) z[q] = r[q] * a.inv[t];
+    cg_proj<R, NC>(z, a, t, S);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+        int k = vidx<R, NC>(slot, q, l);
+        a.r[k] = r[q];
+        a.x[k] = R(0);
+        a.p[k] = z[q];
+        a.u[k] = R(0);
+        bb += (double)r[q] * (double)r[q];
+        rz += (double)r[q] * (double)z[q];
+    }
+    scal_add2<R, NC>(&sc, &sc.rz, rz, set_bnorm ? &sc.bnorm : nullptr, bb);
+}
+
+// q = P (D p + u) -> u ; pAp
+template <typename R, int NC>
+__global__ void k_cg_pq(CGArgs<R, NC> a) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    SceneScal& sc = a.scal[bc.w];
+    if (sc.cg_done) return;
+    int t = slot * 64 + l;
+    R q[NC], pv[NC];
+    double diag;
+    if (NC == 3) diag = a.gm[t];
+    else diag = a.inv[t] == R(0) ? 0.0 : 1.0 / (double)a.inv[t];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        int k = vidx<R, NC>(slot, c, l);
+        pv[c] = a.p[k];
+        q[c] = (R)diag * pv[c] + a.u[k];
+    }
+    cg_proj<R, NC>(q, a, t, S);
+    double pq = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        a.u[vidx<R, NC>(slot, c, l)] = q[c];
+        pq += (double)pv[c] * (double)q[c];
+    }
+    scal_add2<R, NC>(&sc, &sc.pAp, pq, nullptr, 0.0);
+}
+
+// x += alpha p, r -= alpha q, u = 0; rz_new, rr   (negative curvature: x = p on the first iteration)
+template <typename R, int NC>
+__global__ void k_cg_update(CGArgs<R, NC> a) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    SceneScal& sc = a.scal[bc.w];
+    if (sc.cg_done) return;
+    int t = slot * 64 + l;
+    double pAp = sc.pAp;
+    double rz_new = 0.0, rr = 0.0;
+    if (!(pAp > 0.0)) {
+        if (sc.cg_it == 0) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                int k = vidx<R, NC>(slot, c, l);
+                a.x[k] = a.p[k];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) a.u[vidx<R, NC>(slot, c, l)] = R(0);
+        return;
+    }
+    R alpha = (R)(sc.rz / pAp);
+    R r[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        int k = vidx<R, NC>(slot, c, l);
+        a.x[k] += alpha * a.p[k];
+        r[c] = a.r[k] - alpha * a.u[k];
+        a.r[k] = r[c];
+        a.u[k] = R(0);
+    }
+    R z[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) z[c] = r[c] * a.inv[t];
+    cg_proj<R, NC>(z, a, t, S);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        rz_new += (double)r[c] * (double)z[c];
+        rr += (double)r[c] * (double)r[c];
+    }
+    scal_add2<R, NC>(&sc, &sc.rz_new, rz_new, &sc.rr, rr);
+}
+
+// p = z + beta p
+template <typename R, int NC>
+__global__ void k_cg_p(CGArgs<R, NC> a) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    SceneScal& sc = a.scal[bc.w];
+    if (sc.cg_done) return;
+    int t = slot * 64 + l;
+    R beta = (R)sc.alpha;   // holds beta here (set by k_cg_check)
+    R z[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) z[c] = a.r[vidx<R, NC>(slot, c, l)] * a.inv[t];
+    cg_proj<R, NC>(z, a, t, S);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        int k = vidx<R, NC>(slot, c, l);
+        a.p[k] = z[c] + beta * a.p[k];
+    }
+}
+
+// per-scene CG control: count, test, beta
+__global__ void k_cg_check(SceneScal* scal, const SceneDev* sc, int nsc, int heat) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsc) return;
+    SceneScal& c = scal[s];
+    if (c.cg_done) return;
+    c.cg_it += 1;
+    double rtol = heat ? sc[s].heat_rtol : sc[s].cg_rtol;
+    int maxit = sc[s].max_cg;
+    bool done = !(c.pAp > 0.0) || c.rr <= rtol * rtol * c.bnorm || c.cg_it >= maxit;
+    if (done) {
+        c.cg_done = 1;
+    } else {
+        c.alpha = c.rz_new / c.rz;
+        c.rz = c.rz_new;
+    }
+    c.rz_new = 0.0;
+    c.rr = 0.0;
+    c.pAp = 0.0;
+}
+
+__global__ void k_cg_begin(SceneScal* scal, int nsc, int from_newton) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsc) return;
+    SceneScal& c = scal[s];
+    c.cg_done = from_newton ? c.newton_done : 0;
+    c.cg_it = 0;
+    c.rz = c.rz_new = c.rr = c.pAp = c.bnorm = 0.0;
+}
+
+// ======================================================================
+// Newton control
+// ======================================================================
+__global__ void k_newton_begin(SceneScal* scal, int nsc) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsc) return;
+    SceneScal& c = scal[s];
+    c.newton_it = 0;
+    c.newton_done = 0;
+    c.cg_total = 0;
+    c.status = 0;
+    c.r0 = -1.0;
+    c.rnorm = 0.0;
+}
+
+__global__ void k_newton_iter_begin(SceneScal* scal, int nsc) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsc) return;
+    SceneScal& c = scal[s];
+    if (c.newton_done) return;
+    c.rr = 0.0;
+    c.phi_kin = 0.0;
+    c.phi_part = 0.0;
+    c.slope = 0.0;
+    for (int k = 0; k < MAX_LS; ++k) c.dphi[k] = 0.0;
+}
+
+__global__ void k_newton_check(SceneScal* scal, const SceneDev* sc, int nsc) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsc) return;
+    SceneScal& c = scal[s];
+    if (c.newton_done) return;
+    c.rnorm = sqrt(c.rr);
+    if (c.r0 < 0.0) c.r0 = c.rnorm;
+    if (c.rnorm <= sc[s].newton_tol * fmax(c.r0, 1e-12)) c.newton_done = 1;
+    else if (c.newton_it >= sc[s].max_newton) {
+        c.newton_done = 1;
+        c.status = MPM_ERR_NOT_CONVERGED;
+    }
+    if (!isfinite(c.rnorm)) {
+        c.newton_done = 1;
+        c.status = MPM_ERR_NUMERIC;
+    }
+}
+
+// v = P (v^n + dt g)
+__global__ void k_newton_init_v(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, const double* __restrict__ gvn,
+                                const uint8_t* __restrict__ pcode, double* __restrict__ gv) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = coord[slot];
+    const SceneDev& S = sc[bc.w];
+    int t = slot * 64 + l;
+    double v[3];
+    for (int q = 0; q < 3; ++q) v[q] = gvn[slot * 192 + q * 64 + l] + S.dt * S.g[q];
+    project3(v, pcode[t], S);
+    for (int q = 0; q < 3; ++q) gv[slot * 192 + q * 64 + l] = v[q];
+}
+
+// line search: per-particle energy differences for alpha_k = 2^-k in one pass
+template <typename R>
+struct LSArgs {
+    const int *work, *work_gb, *nbr, *cell_start, *scell_start;
+    const int4* coord;
+    const SceneDev* sc;
+    SceneScal* scal;
+    const double* gv;
+    const R* d;
+    Ptrs3 x;
+    const double *J, *V0, *T;
+    Ptrs9 F;
+    const uint8_t* phase;
+    Ptrs3 s, dA;
+    const double* gamma;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_linesearch(LSArgs<R> a) {
+    __shared__ R vh[3][HN];
+    __shared__ R dh[3][HN];
+    __shared__ double red[NT / 32];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    SceneScal& scl = a.scal[bc.w];
+    if (scl.newton_done) return;
+    load_halo_vec_d<R>(a.nbr, slot, a.gv, vh);
+    load_halo_vec<R>(a.nbr, slot, a.d, dh);
+    __syncthreads();
+    const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
+    const R dt = (R)S.dt;
+    double de[MAX_LS];
+#pragma unroll
+    for (int k = 0; k < MAX_LS; ++k) de[k] = 0.0;
+    int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
+    for (int i = beg + threadIdx.x; i < end; i += NT) {
+        double p[3] = {a.x.a[0][i], a.x.a[1][i], a.x.a[2][i]};
+        int lc[3];
+        R wgt[3][3], dw[3][3], f[3];
+        stencil_in_block<R>(p, S, bc, lc, wgt, dw, f);
+        R L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, D[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) {
+                            L[3 * q + e] += vh[q][h] * dN[e];
+                            D[3 * q + e] += dh[q][h] * dN[e];
+                        }
+                }
+        double v0 = a.V0[i];
+        if (a.phase[i] == 0) {
+            double Jn = a.J[i];
+            R jm1n = (R)(Jn - 1.0);
+            R trL = L[0] + L[4] + L[8], trD = D[0] + D[4] + D[8];
+            R jm1 = jm1n + dt * trL * (R(1) + jm1n);
+            double lam = S.lambda_l;
+            double Vn = Jn * v0;
+            R el = 0, ed = 0, dd = 0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    R sl = R(0.5) * (L[3 * q + e] + L[3 * e + q]);
+                    R sd = R(0.5) * (D[3 * q + e] + D[3 * e + q]);
+                    ed += sl * sd;
+                    dd += sd * sd;
+                }
+            (void)el;
+            double cvis = 0.5 * S.dt * S.mu_l * Vn;
+            double alpha = 1.0;
+            for (int k = 0; k < nls; ++k) {
+                R dJ = (R)alpha * dt * trD * (R)Jn;
+                double dE = 0.5 * lam * v0 * (double)dJ * (double)(R(2) * jm1 + dJ);
+                dE += cvis * (2.0 * alpha * (double)ed + alpha * alpha * (double)dd);
+                de[k] += dE;
+                alpha *= 0.5;
+            }
+        } else {
+            R Fo[9], A1[9], Fc[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                Fo[q] = (R)a.F.a[q][i];
+                A1[q] = dt * L[q] + ((q % 4 == 0) ? R(1) : R(0));
+            }
+            matmul3<R>(A1, Fo, Fc);
+            double Tn = a.T[i];
+            double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - Tn) / (S.T_melt - S.T0));
+            R mu = (R)(E / (2.0 * (1.0 + S.nu)));
+            R lam = (R)(E * S.nu / ((1.0 + S.nu) * (1.0 - 2.0 * S.nu)));
+            R psi0 = fcr_psi<R>(Fc, mu, lam);
+            R alpha = 1;
+            for (int k = 0; k < nls; ++k) {
+                R Fa[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) A1[q] = dt * (L[q] + alpha * D[q]) + ((q % 4 == 0) ? R(1) : R(0));
+                matmul3<R>(A1, Fo, Fa);
+                de[k] += v0 * ((double)fcr_psi<R>(Fa, mu, lam) - (double)psi0);
+                alpha *= R(0.5);
+            }
+        }
+    }
+    int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    for (int j = sbeg + threadIdx.x; j < send; j += NT) {
+        double p[3] = {a.s.a[0][j], a.s.a[1][j], a.s.a[2][j]};
+        int lc[3];
+        R wgt[3][3], dw[3][3], f[3];
+        stencil_in_block<R>(p, S, bc, lc, wgt, dw, f);
+        R Fh[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, Dh[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) {
+                            Fh[3 * q + e] += dt * vh[q][h] * dN[e];
+                            Dh[3 * q + e] += dt * dh[q][h] * dN[e];
+                        }
+                }
+        R av[3] = {(R)a.dA.a[0][j], (R)a.dA.a[1][j], (R)a.dA.a[2][j]};
+        R C[9], dC[9], CD[9];
+        cofactor<R>(Fh, C);
+        dcofactor<R>(Fh, Dh, dC);
+        cofactor<R>(Dh, CD);
+        R c0[3], c1[3], c2[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            c0[q] = C[3 * q] * av[0] + C[3 * q + 1] * av[1] + C[3 * q + 2] * av[2];
+            c1[q] = dC[3 * q] * av[0] + dC[3 * q + 1] * av[1] + dC[3 * q + 2] * av[2];
+            c2[q] = CD[3 * q] * av[0] + CD[3 * q + 1] * av[1] + CD[3 * q + 2] * av[2];
+        }
+        R n0 = sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
+        double k = a.gamma[j];
+        R alpha = 1;
+        for (int kk = 0; kk < nls; ++kk) {
+            R dc[3], cn[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                dc[q] = alpha * c1[q] + alpha * alpha * c2[q];
+                cn[q] = c0[q] + dc[q];
+            }
+            R n1 = sqrt(cn[0] * cn[0] + cn[1] * cn[1] + cn[2] * cn[2]);
+            R num = R(2) * (c0[0] * dc[0] + c0[1] * dc[1] + c0[2] * dc[2]) + dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2];
+            de[kk] += k * (double)num / ((double)n1 + (double)n0);
+            alpha *= R(0.5);
+        }
+    }
+    for (int k = 0; k < nls; ++k) block_atomic_sum<NT>(de[k], &scl.dphi[k], red);
+}
+
+// node part of the line search: kinetic + gravity differences, slope = grad . d
+template <typename R>
+__global__ void k_ls_nodes(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, SceneScal* __restrict__ scal,
+                           const double* __restrict__ gm, const double* __restrict__ gvn, const double* __restrict__ gv,
+                           const double* __restrict__ grad, const R* __restrict__ d) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = coord[slot];
+    const SceneDev& S = sc[bc.w];
+    SceneScal& c = scal[bc.w];
+    if (c.newton_done) return;
+    int t = slot * 64 + l;
+    double m = gm[t];
+    double dv = 0.0, dd = 0.0, gd = 0.0, sl = 0.0;
+    if (m > 0.0) {
+        for (int q = 0; q < 3; ++q) {
+            int k = slot * 192 + q * 64 + l;
+            double dq = (double)d[k];
+            dv += dq * (gv[k] - gvn[k]);
+            dd += dq * dq;
+            gd += S.g[q] * dq;
+            sl += grad[k] * dq;
+        }
+    }
+    const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
+    double alpha = 1.0;
+    for (int k = 0; k < nls; ++k) {
+        double e = 0.5 * m * (2.0 * alpha * dv + alpha * alpha * dd) - S.dt * alpha * m * gd;
+        e = warp_sum(e);
+        if ((l & 31) == 0 && e != 0.0) atomicAdd(&c.dphi[k], e);
+        alpha *= 0.5;
+    }
+    sl = warp_sum(sl);
+    if ((l & 31) == 0 && sl != 0.0) atomicAdd(&c.slope, sl);
+}
+
+__global__ void k_ls_pick(SceneScal* scal, const SceneDev* sc, int nsc) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsc) return;
+    SceneScal& c = scal[s];
+    if (c.newton_done) return;
+    const int nls = sc[s].max_ls < MAX_LS ? sc[s].max_ls : MAX_LS;
+    double alpha = 1.0;
+    int pick = nls;
+    for (int k = 0; k < nls; ++k) {
+        if (c.dphi[k] <= 1e-4 * alpha * c.slope) {
+            pick = k;
+            break;
+        }
+        alpha *= 0.5;
+    }
+    c.alpha = alpha;   // 2^-nls when no trial passed
+    c.ls_pick = pick;
+    c.cg_total += c.cg_it;
+    c.newton_it += 1;
+}
+
+template <typename R>
+__global__ void k_newton_update(const int4* __restrict__ coord, const SceneScal* __restrict__ scal, const R* __restrict__ d,
+                                double* __restrict__ gv) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = coord[slot];
+    const SceneScal& c = scal[bc.w];
+    if (c.newton_done) return;
+    double alpha = c.alpha;
+    for (int q = 0; q < 3; ++q) {
+        int k = slot * 192 + q * 64 + l;
+        gv[k] += alpha * (double)d[k];
+    }
+}
+
+// final explicit force evaluation: vhat = P (v - grad / m); momentum sums
+__global__ void k_newton_final(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, SceneScal* __restrict__ scal,
+                               const double* __restrict__ gm, const double* __restrict__ gv, const double* __restrict__ grad,
+                               const uint8_t* __restrict__ pcode, double* __restrict__ gvhat) {
+    int slot = blockIdx.x, l = threadIdx.x;
+    int4 bc = coord[slot];
+    const SceneDev& S = sc[bc.w];
+    int t = slot * 64 + l;
+    double m = gm[t];
+    double v[3] = {0, 0, 0};
+    if (m > 0.0) {
+        for (int q = 0; q < 3; ++q) {
+            int k = slot * 192 + q * 64 + l;
+            v[q] = gv[k] - grad[k] / m;
+        }
+        project3(v, pcode[t], S);
+    }
+    for (int q = 0; q < 3; ++q) {
+        gvhat[slot * 192 + q * 64 + l] = v[q];
+        double mv = warp_sum(m * v[q]);
+        if ((l & 31) == 0 && mv != 0.0) atomicAdd(&scal[bc.w].mom[q], mv);
+    }
+}
+
+__global__ void k_zero_mom(SceneScal* scal, int nsc) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsc) return;
+    scal[s].mom[0] = scal[s].mom[1] = scal[s].mom[2] = 0.0;
+    scal[s].phi_part = 0.0;
+}
+
+// dense <-> grid copies for the C ABI
+template <typename Tin, typename Tout>
+__global__ void k_dense_to_grid(int nb, const int4* __restrict__ coord, int scene, const SceneDev* __restrict__ sc,
+                                const Tin* __restrict__ dense, Tout* __restrict__ grid, int comps) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * 64) return;
+    int slot = t >> 6, l = t & 63;
+    int4 bc = coord[slot];
+    const SceneDev& S = sc[bc.w];
+    int g[3] = {bc.x * 4 + (l & 3), bc.y * 4 + ((l >> 2) & 3), bc.z * 4 + (l >> 4)};
+    bool in = bc.w == scene && g[0] < S.n[0] && g[1] < S.n[1] && g[2] < S.n[2];
+    long long node = g[0] + (long long)S.n[0] * (g[1] + (long long)S.n[1] * g[2]);
+    for (int q = 0; q < comps; ++q) {
+        int k = comps == 1 ? t : slot * 192 + q * 64 + l;
+        grid[k] = in ? (Tout)dense[node * comps + q] : Tout(0);
+    }
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_grid_to_dense(int nb, const int4* __restrict__ coord, int scene, const SceneDev* __restrict__ sc,
+                                const Tin* __restrict__ grid, Tout* __restrict__ dense, int comps) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * 64) return;
+    int slot = t >> 6, l = t & 63;
+    int4 bc = coord[slot];
+    if (bc.w != scene) return;
+    const SceneDev& S = sc[bc.w];
+    int g[3] = {bc.x * 4 + (l & 3), bc.y * 4 + ((l >> 2) & 3), bc.z * 4 + (l >> 4)};
+    if (g[0] >= S.n[0] || g[1] >= S.n[1] || g[2] >= S.n[2]) return;
+    long long node = g[0] + (long long)S.n[0] * (g[1] + (long long)S.n[1] * g[2]);
+    for (int q = 0; q < comps; ++q) {
+        int k = comps == 1 ? t : slot * 192 + q * 64 + l;
+        dense[node * comps + q] = (Tout)grid[k];
+    }
+}
+
+template <typename R>
+__global__ void k_project_vec(int nb, const int4* __restrict__ coord, const SceneDev* __restrict__ sc,
+                              const uint8_t* __restrict__ pcode, R* __restrict__ vec) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * 64) return;
+    int slot = t >> 6, l = t & 63;
+    const SceneDev& S = sc[coord[slot].w];
+    R v[3];
+    for (int q = 0; q < 3; ++q) v[q] = vec[slot * 192 + q * 64 + l];
+    project3r<R>(v, pcode[t], S);
+    for (int q = 0; q < 3; ++q) vec[slot * 192 + q * 64 + l] = v[q];
+}
+
+// u = P (m p + u)
+template <typename R>
+__global__ void k_mass_term(int nb, const int4* __restrict__ coord, const SceneDev* __restrict__ sc,
+                            const uint8_t* __restrict__ pcode, const double* __restrict__ gm, const R* __restrict__ p,
+                            R* __restrict__ u) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * 64) return;
+    int slot = t >> 6, l = t & 63;
+    const SceneDev& S = sc[coord[slot].w];
+    R v[3];
+    R m = (R)gm[t];
+    for (int q = 0; q < 3; ++q) {
+        int k = slot * 192 + q * 64 + l;
+        v[q] = m * p[k] + u[k];
+    }
+    project3r<R>(v, pcode[t], S);
+    for (int q = 0; q < 3; ++q) u[slot * 192 + q * 64 + l] = v[q];
+}
+
+inline unsigned nblk(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
+
+template <typename R>
+EvalArgs<R> make_eval_args(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) {
+    Dev& d = c->d;
+    EvalArgs<R> a;
+    a.work = d.work;
+    a.work_gb = d.work_gb;
+    a.nbr = d.nbr;
+    a.cell_start = d.cell_start;
+    a.scell_start = d.scell_start;
+    a.coord = d.slot_coord;
+    a.sc = d.sc;
+    a.scal = d.scal;
+    a.gv = d.gv;
+    a.grad = d.ggrad;
+    for (int q = 0; q < 3; ++q) {
+        a.x.a[q] = d.x[q];
+        a.s.a[q] = d.s[q];
+        a.dA.a[q] = d.dA[q];
+        a.sn.a[q] = (R*)d.sn[q];
+    }
+    a.J = d.J;
+    a.V0 = d.V0;
+    a.T = d.T;
+    for (int q = 0; q < 9; ++q) {
+        a.F.a[q] = d.F[q];
+        a.sF.a[q] = (R*)d.sF[q];
+    }
+    a.phase = d.phase;
+    a.gamma = d.gamma;
+    a.want_grad = want_grad;
+    a.want_cache = want_cache;
+    a.skip_done = skip_done;
+    for (int q = 0; q < 24; ++q) a.scache.a[q] = (R*)d.scache[q];
+    a.sic = (R*)d.sic;
+    return a;
+}
+
+template <typename R>
+ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int check_done) {
+    Dev& d = c->d;
+    ApplyArgs<R> a;
+    a.work = d.work;
+    a.work_gb = d.work_gb;
+    a.nbr = d.nbr;
+    a.cell_start = d.cell_start;
+    a.scell_start = d.scell_start;
+    a.coord = d.slot_coord;
+    a.sc = d.sc;
+    a.scal = d.scal;
+    a.p = (const R*)p;
+    a.u = (R*)u;
+    a.phase = d.phase;
+    a.V0 = d.V0;
+    for (int q = 0; q < 3; ++q) {
+        a.pu.a[q] = (R*)d.pu[q];
+        a.su.a[q] = (R*)d.su[q];
+        a.sa.a[q] = (R*)d.sa[q];
+        a.sn.a[q] = (R*)d.sn[q];
+    }
+    a.kappa = (const R*)d.kappa;
+    a.cvisc = (const R*)d.cvisc;
+    for (int q = 0; q < 9; ++q) {
+        a.Fn.a[q] = (R*)d.Fn[q];
+        a.sF.a[q] = (R*)d.sF[q];
+    }
+    a.lmu = (const R*)d.lame[0];
+    a.llam = (const R*)d.lame[1];
+    for (int q = 0; q < 24; ++q) a.scache.a[q] = (R*)d.scache[q];
+    a.sg = (const R*)d.sg;
+    a.sic = (const R*)d.sic;
+    a.mode = mode;
+    a.check_done = check_done;
+    return a;
+}
+
+template <typename R, int NC>
+CGArgs<R, NC> make_cg_args(mpm_ctx* c) {
+    Dev& d = c->d;
+    CGArgs<R, NC> a;
+    a.coord = d.slot_coord;
+    a.sc = d.sc;
+    a.scal = d.scal;
+    a.pcode = d.pcode;
+    a.gm = d.gm;
+    if (NC == 3) {
+        a.inv = (const R*)d.invm;
+        a.x = (R*)d.cx;
+        a.r = (R*)d.cr;
+        a.p = (R*)d.cp;
+        a.u = (R*)d.cu;
+        a.rhs_d = d.ggrad;
+        a.rhs_sign = -1.0;
+    } else {
+        a.inv = (const R*)d.hinvd;
+        a.x = (R*)d.hx;
+        a.r = (R*)d.hr;
+        a.p = (R*)d.hp;
+        a.u = (R*)d.hu;
+        a.rhs_d = d.hrhs;
+        a.rhs_sign = 1.0;
+    }
+    return a;
+}
+
+template <typename R>
+cudaError_t pack_step_t(mpm_ctx* c) {
+    Dev& d = c->d;
+    cudaStream_t st = c->st;
+    if (c->np > 0) {
+        RPtr3<R> pu;
+        RPtr9<R> Fn;
+        for (int q = 0; q < 3; ++q) pu.a[q] = (R*)d.pu[q];
+        for (int q = 0; q < 9; ++q) Fn.a[q] = (R*)d.Fn[q];
+        Ptrs9 F;
+        for (int q = 0; q < 9; ++q) F.a[q] = d.F[q];
+        k_pack_volume<R><<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, Ptrs3{{d.x[0], d.x[1], d.x[2]}}, d.J, F, d.V0, d.T,
+                                                           d.phase, d.psc, d.sc, pu, (R*)d.kappa, (R*)d.cvisc, Fn,
+                                                           (R*)d.lame[0], (R*)d.lame[1], (R*)d.Vn);
+    }
+    if (c->ns > 0) {
+        RPtr3<R> su, sa;
+        for (int q = 0; q < 3; ++q) {
+            su.a[q] = (R*)d.su[q];
+            sa.a[q] = (R*)d.sa[q];
+        }
+        k_pack_surface<R><<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, Ptrs3{{d.s[0], d.s[1], d.s[2]}},
+                                                            Ptrs3{{d.dA[0], d.dA[1], d.dA[2]}}, d.gamma, d.ssc, d.sc, su,
+                                                            sa, (R*)d.sg);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
+    // runs CG to completion on every scene that is not done; returns after the host saw all done
+    cudaStream_t st = c->st;
+    int nb = c->NB;
+    int ns = c->nsc;
+    Dev& d = c->d;
+    int maxit = 0;
+    for (auto& S : c->hsc) maxit = maxit > S.max_cg ? maxit : S.max_cg;
+    const int chunk = 8;
+    if (NC_is_heat) {
+        auto a = make_cg_args<R, 1>(c);
+        k_cg_init<R, 1><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
+        for (int it = 0; it < maxit; it += chunk) {
+            for (int k = 0; k < chunk; ++k) {
+                launch_heat_apply(c, d.hp, d.hu);
+                k_cg_pq<R, 1><<<nb, 64, 0, st>>>(a);
+                k_cg_update<R, 1><<<nb, 64, 0, st>>>(a);
+                k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 1);
+                k_cg_p<R, 1><<<nb, 64, 0, st>>>(a);
+            }
+            cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            bool all = true;
+            for (int s = 0; s < ns; ++s) all = all && c->hscal[s].cg_done;
+            if (all) break;
+        }
+    } else {
+        auto a = make_cg_args<R, 3>(c);
+        auto ap = make_apply_args<R>(c, d.cp, d.cu, MPM_HESS_PROJECTED, 1);
+        k_cg_init<R, 3><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
+        for (int it = 0; it < maxit; it += chunk) {
+            for (int k = 0; k < chunk; ++k) {
+                if (c->NW > 0) k_apply<R><<<c->NW, NT, 0, st>>>(ap);
+                k_cg_pq<R, 3><<<nb, 64, 0, st>>>(a);
+                k_cg_update<R, 3><<<nb, 64, 0, st>>>(a);
+                k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 0);
+                k_cg_p<R, 3><<<nb, 64, 0, st>>>(a);
+            }
+            cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            bool all = true;
+            for (int s = 0; s < ns; ++s) all = all && c->hscal[s].cg_done;
+            if (all) break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) {
+    if (c->NW == 0) return cudaSuccess;
+    auto a = make_eval_args<R>(c, want_grad, want_cache, skip_done);
+    k_eval<R><<<c->NW, NT, 0, c->st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t eval_any(mpm_ctx* c, bool fp64, bool want_grad, bool want_cache, bool skip_done) {
+    if (fp64 || c->rsize == 8) return eval_t<double>(c, want_grad, want_cache, skip_done);
+    return eval_t<float>(c, want_grad, want_cache, skip_done);
+}
+
+template <typename R>
+cudaError_t newton_t(mpm_ctx* c) {
+    Dev& d = c->d;
+    cudaStream_t st = c->st;
+    int nb = c->NB, ns = c->nsc;
+    unsigned gs = nblk(ns, 128);
+    k_newton_begin<<<gs, 128, 0, st>>>(d.scal, ns);
+    k_newton_init_v<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.gvn, d.pcode, d.gv);
+    int maxn = 0;
+    for (auto& S : c->hsc) maxn = maxn > S.max_newton ? maxn : S.max_newton;
+    for (int it = 0; it <= maxn; ++it) {
+        k_newton_iter_begin<<<gs, 128, 0, st>>>(d.scal, ns);
+        cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
+        eval_any(c, false, true, true, true);
+        k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 1);
+        k_newton_check<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
+        cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        bool all = true;
+        for (int s = 0; s < ns; ++s) all = all && c->hscal[s].newton_done;
+        if (all) break;
+        k_cg_begin<<<gs, 128, 0, st>>>(d.scal, ns, 1);
+        e = cg_solve_t<R>(c, 0, 1);
+        if (e != cudaSuccess) return e;
+        if (c->NW > 0) {
+            LSArgs<R> a;
+            a.work = d.work;
+            a.work_gb = d.work_gb;
+            a.nbr = d.nbr;
+            a.cell_start = d.cell_start;
+            a.scell_start = d.scell_start;
+            a.coord = d.slot_coord;
+            a.sc = d.sc;
+            a.scal = d.scal;
+            a.gv = d.gv;
+            a.d = (const R*)d.cx;
+            for (int q = 0; q < 3; ++q) {
+                a.x.a[q] = d.x[q];
+                a.s.a[q] = d.s[q];
+                a.dA.a[q] = d.dA[q];
+            }
+            a.J = d.J;
+            a.V0 = d.V0;
+            a.T = d.T;
+            for (int q = 0; q < 9; ++q) a.F.a[q] = d.F[q];
+            a.phase = d.phase;
+            a.gamma = d.gamma;
+            k_linesearch<R><<<c->NW, NT, 0, st>>>(a);
+        }
+        k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, (const R*)d.cx);
+        k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
+        k_newton_update<R><<<nb, 64, 0, st>>>(d.slot_coord, d.scal, (const R*)d.cx, d.gv);
+    }
+    // final explicit force evaluation in float64
+    k_zero_mom<<<gs, 128, 0, st>>>(d.scal, ns);
+    cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
+    eval_any(c, true, true, false, false);
+    k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
+    k_newton_final<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gv, d.ggrad, d.pcode, d.gvhat);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pack_step(mpm_ctx* c) {
+    if (c->rsize == 4) return pack_step_t<float>(c);
+    return pack_step_t<double>(c);
+}
+
+cudaError_t launch_eval(mpm_ctx* c, bool fp64_math, bool want_cache) {
+    Dev& d = c->d;
+    int ns = c->nsc;
+    k_newton_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
+    k_newton_iter_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
+    cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)c->NB * 192, c->st);
+    eval_any(c, fp64_math, true, want_cache, false);
+    if (c->NB > 0) k_node_grad<<<c->NB, 64, 0, c->st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
+    if (c->NW == 0) return cudaSuccess;
+    if (c->rsize == 4) {
+        auto a = make_apply_args<float>(c, p, u, mode, 0);
+        k_apply<float><<<c->NW, NT, 0, c->st>>>(a);
+    } else {
+        auto a = make_apply_args<double>(c, p, u, mode, 0);
+        k_apply<double><<<c->NW, NT, 0, c->st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t run_newton(mpm_ctx* c) {
+    if (c->NB == 0) return cudaSuccess;
+    if (c->rsize == 4) return newton_t<float>(c);
+    return newton_t<double>(c);
+}
+
+cudaError_t launch_cg(mpm_ctx* c, int heat) {
+    if (c->rsize == 4) return cg_solve_t<float>(c, heat, 0);
+    return cg_solve_t<double>(c, heat, 0);
+}
+
+cudaError_t launch_cg_begin(mpm_ctx* c) {
+    k_cg_begin<<<nblk(c->nsc, 128), 128, 0, c->st>>>(c->d.scal, c->nsc, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_to_grid(mpm_ctx* c, int scene, const void* dense, void* grid, int comps, int rsize) {
+    if (c->NB == 0) return cudaSuccess;
+    unsigned g = nblk((long long)c->NB * 64, 256);
+    Dev& d = c->d;
+    if (rsize == 8)
+        k_dense_to_grid<double, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)dense, (double*)grid, comps);
+    else
+        k_dense_to_grid<float, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)dense, (float*)grid, comps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_to_dense(mpm_ctx* c, int scene, const void* grid, void* dense, int comps, int rsize_in, int rsize_out) {
+    if (c->NB == 0) return cudaSuccess;
+    unsigned g = nblk((long long)c->NB * 64, 256);
+    Dev& d = c->d;
+    if (rsize_in == 8 && rsize_out == 8)
+        k_grid_to_dense<double, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)grid, (double*)dense, comps);
+    else if (rsize_in == 4 && rsize_out == 4)
+        k_grid_to_dense<float, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)grid, (float*)dense, comps);
+    else if (rsize_in == 4 && rsize_out == 8)
+        k_grid_to_dense<float, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)grid, (double*)dense, comps);
+    else
+        k_grid_to_dense<double, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)grid, (float*)dense, comps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_vec(mpm_ctx* c, void* vec, int rsize) {
+    if (c->NB == 0) return cudaSuccess;
+    unsigned g = nblk((long long)c->NB * 64, 256);
+    Dev& d = c->d;
+    if (rsize == 8) k_project_vec<double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, (double*)vec);
+    else k_project_vec<float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, (float*)vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_term(mpm_ctx* c, const void* p, void* u) {
+    if (c->NB == 0) return cudaSuccess;
+    unsigned g = nblk((long long)c->NB * 64, 256);
+    Dev& d = c->d;
+    if (c->rsize == 8) k_mass_term<double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, d.gm, (const double*)p, (double*)u);
+    else k_mass_term<float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, d.gm, (const float*)p, (float*)u);
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

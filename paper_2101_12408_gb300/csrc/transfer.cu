@@ -1,0 +1,563 @@
+// Resampling (closest parent, balance particles, split), P2G, grid finalisation,
+// gamma(T), and G2P with the conservative merge. All float64: these run once per
+// step and carry the momentum bookkeeping that must close to round-off.
+//
+// Paper sections: "Conservative Surface Particle Resampling" (Eq. pbal,
+// Eq. cons_mom), "Transfer: P2G", "Transfer: G2P", "Thermomechanical Material
+// Dependence and Phase Change", "Contact Angle".
+#include "ctx.h"
+
+namespace mpm {
+
+namespace {
+
+constexpr int NT = 128;
+
+__device__ __forceinline__ int node_slot_index(const SceneDev& S, const int* __restrict__ bslot, int gx, int gy, int gz) {
+    long long gb = S.block_base + (gx >> 2) + (long long)S.nb[0] * ((gy >> 2) + (long long)S.nb[1] * (gz >> 2));
+    int slot = bslot[gb];
+    return slot < 0 ? -1 : slot * 64 + ((gx & 3) + 4 * (gy & 3) + 16 * (gz & 3));
+}
+
+__device__ __forceinline__ void load_pos(const double* const* x, int i, double p[3]) {
+    p[0] = x[0][i];
+    p[1] = x[1][i];
+    p[2] = x[2][i];
+}
+
+struct P3 { const double* a[3]; };
+struct P9 { const double* a[9]; };
+struct W3 { double* a[3]; };
+struct W9 { double* a[9]; };
+struct W12 { double* a[12]; };
+
+// ---------------------------------------------------------------- resample
+
+__global__ void k_nearest(int ns, P3 s, const int* __restrict__ ssc, P3 x, const int* __restrict__ pid,
+                          const int* __restrict__ cell_start, const SceneDev* __restrict__ sc, int* __restrict__ parent,
+                          W3 bpos, int* __restrict__ gcount, uint8_t* __restrict__ kind, int* err) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    const SceneDev& S = sc[ssc[j]];
+    double q[3] = {s.a[0][j], s.a[1][j], s.a[2][j]};
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int ci = (int)floor((q[a] - S.origin[a]) * S.inv_dx);
+        c[a] = ci < 1 ? 1 : (ci > S.n[a] - 2 ? S.n[a] - 2 : ci);
+    }
+    double best = 1e300;
+    int bi = -1, bid = 0x7fffffff;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dxx = -1; dxx <= 1; ++dxx) {
+                long long k = cell_key(S, c[0] + dxx, c[1] + dy, c[2] + dz);
+                int e = cell_start[k + 1];
+                for (int i = cell_start[k]; i < e; ++i) {
+                    double d0 = __dsub_rn(q[0], x.a[0][i]);
+                    double d1 = __dsub_rn(q[1], x.a[1][i]);
+                    double d2 = __dsub_rn(q[2], x.a[2][i]);
+                    double dist = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+                    int id = pid[i];
+                    if (dist < best || (dist == best && id < bid)) {
+                        best = dist;
+                        bi = i;
+                        bid = id;
+                    }
+                }
+            }
+    if (bi < 0 || best > S.dx * S.dx) {
+        atomicOr(err, ERR_FAR_SURFACE);
+        parent[j] = -1;
+        for (int a = 0; a < 3; ++a) bpos.a[a][j] = q[a];
+        return;
+    }
+    parent[j] = bi;
+    atomicAdd(&gcount[bi], 1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bpos.a[a][j] = __dadd_rn(q[a], 2.0 * __dsub_rn(x.a[a][bi], q[a]));
+    if (S.plane_mode) {
+        double phi = S.plane_n[0] * q[0] + S.plane_n[1] * q[1] + S.plane_n[2] * q[2] - S.plane_d;
+        kind[j] = phi < S.dx ? 1 : 0;
+    }
+}
+
+__global__ void k_split(int np, const double* __restrict__ m, const int* __restrict__ gcount, double* __restrict__ mt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    mt[i] = m[i] / (2.0 * gcount[i] + 1.0);
+}
+
+// ---------------------------------------------------------------- P2G
+
+struct P2GArgs {
+    P3 x, v;
+    P9 A;
+    const double *mt, *m, *T;
+    P3 gT;
+    const int* cell_start;
+    const int* work;
+    const int* work_gb;
+    const int4* coord;
+    const int* nbr;
+    const SceneDev* sc;
+    double *gm, *gmv, *gmT, *gmTT;
+};
+
+__global__ void __launch_bounds__(NT) k_p2g_volume(P2GArgs a) {
+    __shared__ double acc[6][HN];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    for (int t = threadIdx.x; t < 6 * HN; t += NT) (&acc[0][0])[t] = 0.0;
+    __syncthreads();
+    int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
+    int ob[3] = {bc.x * BS, bc.y * BS, bc.z * BS};
+    for (int i = beg + threadIdx.x; i < end; i += NT) {
+        double u[3];
+        for (int q = 0; q < 3; ++q) u[q] = (a.x.a[q][i] - S.origin[q]) * S.inv_dx;
+        Stencil<double> st;
+        make_stencil<double>(u, S.inv_dx, st);
+        double f[3];
+        for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
+        double mt = a.mt[i], mp = a.m[i];
+        double vp[3] = {a.v.a[0][i], a.v.a[1][i], a.v.a[2][i]};
+        double Ap[9];
+        for (int q = 0; q < 9; ++q) Ap[q] = a.A.a[q][i];
+        double Tp = S.thermal ? a.T[i] : 0.0;
+        double gTp[3] = {0, 0, 0};
+        if (S.thermal)
+            for (int q = 0; q < 3; ++q) gTp[q] = a.gT.a[q][i];
+        int lx = st.c[0] - ob[0], ly = st.c[1] - ob[1], lz = st.c[2] - ob[2];
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    double N = st.w[0][cx] * st.w[1][cy] * st.w[2][cz];
+                    double r[3] = {(cx - f[0]) * S.dx, (cy - f[1]) * S.dx, (cz - f[2]) * S.dx};
+                    int h = halo_index(lx + cx, ly + cy, lz + cz);
+                    double wm = mt * N;
+                    atomicAdd(&acc[0][h], wm);
+                    for (int q = 0; q < 3; ++q)
+                        atomicAdd(&acc[1 + q][h], wm * (vp[q] + Ap[3 * q] * r[0] + Ap[3 * q + 1] * r[1] + Ap[3 * q + 2] * r[2]));
+                    if (S.thermal) {
+                        double wT = mp * N;
+                        atomicAdd(&acc[4][h], wT);
+                        atomicAdd(&acc[5][h], wT * (Tp + r[0] * gTp[0] + r[1] * gTp[1] + r[2] * gTp[2]));
+                    }
+                }
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < HN; h += NT) {
+        if (acc[0][h] == 0.0 && acc[4][h] == 0.0) continue;
+        int ns, loc;
+        halo_source(a.nbr, slot, h, ns, loc);
+        if (ns < 0) continue;
+        atomicAdd(&a.gm[ns * 64 + loc], acc[0][h]);
+        for (int q = 0; q < 3; ++q) atomicAdd(&a.gmv[ns * 192 + q * 64 + loc], acc[1 + q][h]);
+        if (S.thermal) {
+            atomicAdd(&a.gmT[ns * 64 + loc], acc[4][h]);
+            atomicAdd(&a.gmTT[ns * 64 + loc], acc[5][h]);
+        }
+    }
+}
+
+__global__ void k_p2g_surface(int ns, P3 s, P3 bpos, const int* __restrict__ ssc, const int* __restrict__ parent,
+                              P3 x, P3 v, P9 A, const double* __restrict__ mt, const int* __restrict__ bslot,
+                              const SceneDev* __restrict__ sc, double* __restrict__ gm, double* __restrict__ gmv) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    int p = parent[j];
+    if (p < 0) return;
+    const SceneDev& S = sc[ssc[j]];
+    double mp = mt[p];
+    double vp[3] = {v.a[0][p], v.a[1][p], v.a[2][p]};
+    double Ap[9];
+    for (int q = 0; q < 9; ++q) Ap[q] = A.a[q][p];
+    for (int which = 0; which < 2; ++which) {
+        const P3& P = which ? bpos : s;
+        double u[3];
+        for (int q = 0; q < 3; ++q) u[q] = (P.a[q][j] - S.origin[q]) * S.inv_dx;
+        Stencil<double> st;
+        make_stencil<double>(u, S.inv_dx, st);
+        double f[3];
+        for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int idx = node_slot_index(S, bslot, st.c[0] - 1 + cx, st.c[1] - 1 + cy, st.c[2] - 1 + cz);
+                    if (idx < 0) continue;
+                    double N = st.w[0][cx] * st.w[1][cy] * st.w[2][cz];
+                    double r[3] = {(cx - f[0]) * S.dx, (cy - f[1]) * S.dx, (cz - f[2]) * S.dx};
+                    double wm = mp * N;
+                    int slot = idx >> 6, loc = idx & 63;
+                    atomicAdd(&gm[idx], wm);
+                    for (int q = 0; q < 3; ++q)
+                        atomicAdd(&gmv[slot * 192 + q * 64 + loc],
+                                  wm * (vp[q] + Ap[3 * q] * r[0] + Ap[3 * q + 1] * r[1] + Ap[3 * q + 2] * r[2]));
+                }
+    }
+}
+
+// Node finalisation: v^n, T^n, projection codes, inverse masses.
+template <typename R>
+__global__ void k_grid_final(int nb, const int4* __restrict__ coord, const SceneDev* __restrict__ sc,
+                             const double* __restrict__ gm, const double* __restrict__ gmv, const double* __restrict__ gmT,
+                             const double* __restrict__ gmTT, double* __restrict__ gvn, double* __restrict__ gTn,
+                             uint8_t* __restrict__ pcode, R* __restrict__ invm, R* __restrict__ hinvd) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * 64) return;
+    int slot = t >> 6, l = t & 63;
+    int4 bc = coord[slot];
+    const SceneDev& S = sc[bc.w];
+    int g[3] = {bc.x * 4 + (l & 3), bc.y * 4 + ((l >> 2) & 3), bc.z * 4 + (l >> 4)};
+    double m = gm[t];
+    for (int q = 0; q < 3; ++q) gvn[slot * 192 + q * 64 + l] = m > 0.0 ? gmv[slot * 192 + q * 64 + l] / m : 0.0;
+    double mT = S.thermal ? gmT[t] : 0.0;
+    gTn[t] = mT > 0.0 ? gmTT[t] / mT : 0.0;
+    hinvd[t] = mT > 0.0 ? (R)(S.dt / (S.cp * mT)) : R(0);
+    // Dirichlet reading: outer two node layers per face, plus the solid plane
+    bool sticky = false, on_plane = false;
+    int slip = 0;
+    for (int f = 0; f < 6; ++f) {
+        int ax = f >> 1, side = f & 1, mode = S.walls[f];
+        if (mode == 0) continue;
+        bool on = side == 0 ? (g[ax] <= 1) : (g[ax] >= S.n[ax] - 2);
+        if (!on) continue;
+        if (mode == 2) sticky = true; else slip |= 1 << ax;
+    }
+    if (S.plane_mode) {
+        double xn = 0.0;
+        for (int q = 0; q < 3; ++q) xn += S.plane_n[q] * ((g[q] + 0.5) * S.dx + S.origin[q]);
+        on_plane = xn - S.plane_d < 0.0;
+        if (on_plane && S.plane_mode == 2) sticky = true;
+    }
+    int nslip = __popc(slip);
+    uint8_t code = 0;
+    if (sticky || (on_plane && nslip > 0) || nslip == 3 || !(m > 0.0)) code = PC_FIXED;
+    else {
+        if (slip & 1) code |= PC_SLIPX;
+        if (slip & 2) code |= PC_SLIPY;
+        if (slip & 4) code |= PC_SLIPZ;
+        if (on_plane) code |= PC_PLANE;
+    }
+    pcode[t] = code;
+    invm[t] = (m > 0.0 && code != PC_FIXED) ? (R)(1.0 / m) : R(0);
+}
+
+// gamma_r from the grid temperature (normalised over nodes with thermal mass)
+template <typename R>
+__global__ void k_gamma(int ns, P3 s, const int* __restrict__ ssc, const uint8_t* __restrict__ kind,
+                        const int* __restrict__ bslot, const SceneDev* __restrict__ sc, const double* __restrict__ gmT,
+                        const double* __restrict__ gTn, double* __restrict__ gamma, double* __restrict__ Tr,
+                        R* __restrict__ swn) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    const SceneDev& S = sc[ssc[j]];
+    double T = S.T0, wsum = 0.0;
+    if (S.thermal) {
+        double u[3];
+        for (int q = 0; q < 3; ++q) u[q] = (s.a[q][j] - S.origin[q]) * S.inv_dx;
+        Stencil<double> st;
+        make_stencil<double>(u, S.inv_dx, st);
+        double tw = 0.0;
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int idx = node_slot_index(S, bslot, st.c[0] - 1 + cx, st.c[1] - 1 + cy, st.c[2] - 1 + cz);
+                    if (idx < 0 || !(gmT[idx] > 0.0)) continue;
+                    double N = st.w[0][cx] * st.w[1][cy] * st.w[2][cz];
+                    wsum += N;
+                    tw += N * gTn[idx];
+                }
+        if (wsum > 0.0) T = tw / wsum;
+    }
+    Tr[j] = T;
+    swn[j] = wsum > 0.0 ? (R)(1.0 / wsum) : R(0);
+    double g;
+    if (kind[j] == 1) g = S.gamma_sl;
+    else if (S.gamma_law == 0) g = S.gamma_lg;
+    else {
+        g = S.gamma_p[0] + S.gamma_p[1] * (T - S.T0);
+        g = fmin(fmax(g, S.gamma_p[2]), S.gamma_p[3]);
+    }
+    gamma[j] = g;
+}
+
+// ---------------------------------------------------------------- G2P
+
+struct G2PArgs {
+    int np;
+    P3 x;
+    const double *mt;
+    const int* psc;
+    const uint8_t* phase;
+    const int* bslot;
+    const SceneDev* sc;
+    const double *gvhat, *gThat;
+    W12 acc;
+    double *J, *T;
+    W9 F;
+    W3 gT;
+};
+
+__global__ void k_g2p_volume(G2PArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.np) return;
+    const SceneDev& S = a.sc[a.psc[i]];
+    double u[3];
+    for (int q = 0; q < 3; ++q) u[q] = (a.x.a[q][i] - S.origin[q]) * S.inv_dx;
+    Stencil<double> st;
+    make_stencil<double>(u, S.inv_dx, st);
+    double f[3];
+    for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
+    double pv[3] = {0, 0, 0}, tv[9] = {0}, L[9] = {0}, T = 0.0, gT[3] = {0, 0, 0};
+    for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+            for (int cx = 0; cx < 3; ++cx) {
+                int idx = node_slot_index(S, a.bslot, st.c[0] - 1 + cx, st.c[1] - 1 + cy, st.c[2] - 1 + cz);
+                if (idx < 0) continue;
+                int slot = idx >> 6, loc = idx & 63;
+                double N = st.w[0][cx] * st.w[1][cy] * st.w[2][cz];
+                double dN[3] = {st.dw[0][cx] * st.w[1][cy] * st.w[2][cz], st.w[0][cx] * st.dw[1][cy] * st.w[2][cz],
+                                st.w[0][cx] * st.w[1][cy] * st.dw[2][cz]};
+                double r[3] = {(cx - f[0]) * S.dx, (cy - f[1]) * S.dx, (cz - f[2]) * S.dx};
+                double vh[3];
+                for (int q = 0; q < 3; ++q) vh[q] = a.gvhat[slot * 192 + q * 64 + loc];
+                for (int q = 0; q < 3; ++q) {
+                    pv[q] += N * vh[q];
+                    for (int e = 0; e < 3; ++e) {
+                        tv[3 * q + e] += N * vh[q] * r[e];
+                        L[3 * q + e] += vh[q] * dN[e];
+                    }
+                }
+                if (S.thermal) {
+                    double Th = a.gThat[idx];
+                    T += N * Th;
+                    for (int e = 0; e < 3; ++e) gT[e] += Th * dN[e];
+                }
+            }
+    double mt = a.mt[i];
+    for (int q = 0; q < 3; ++q) a.acc.a[q][i] = mt * pv[q];
+    for (int q = 0; q < 9; ++q) a.acc.a[3 + q][i] = mt * tv[q];
+    double dt = S.dt;
+    if (a.phase[i] == 0) {
+        a.J[i] = (1.0 + dt * (L[0] + L[4] + L[8])) * a.J[i];
+    } else {
+        double Fo[9], M[9], Fnew[9];
+        for (int q = 0; q < 9; ++q) Fo[q] = a.F.a[q][i];
+        for (int q = 0; q < 9; ++q) M[q] = dt * L[q] + ((q % 4 == 0) ? 1.0 : 0.0);
+        matmul3<double>(M, Fo, Fnew);
+        for (int q = 0; q < 9; ++q) a.F.a[q][i] = Fnew[q];
+    }
+    if (S.thermal) {
+        a.T[i] = T;
+        for (int e = 0; e < 3; ++e) a.gT.a[e][i] = gT[e];
+    }
+}
+
+__global__ void k_g2p_surface(int ns, W3 s, W3 dA, P3 bpos, const int* __restrict__ ssc, const int* __restrict__ parent,
+                              P3 x, const double* __restrict__ mt, const int* __restrict__ bslot,
+                              const SceneDev* __restrict__ sc, const double* __restrict__ gvhat, W12 acc) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    int p = parent[j];
+    const SceneDev& S = sc[ssc[j]];
+    double xp[3] = {x.a[0][p < 0 ? 0 : p], x.a[1][p < 0 ? 0 : p], x.a[2][p < 0 ? 0 : p]};
+    double mp = p < 0 ? 0.0 : mt[p];
+    double sv[3] = {0, 0, 0}, Ls[9] = {0};
+    for (int which = 0; which < 2; ++which) {
+        const double* P[3] = {which ? bpos.a[0] : s.a[0], which ? bpos.a[1] : s.a[1], which ? bpos.a[2] : s.a[2]};
+        double pos[3] = {P[0][j], P[1][j], P[2][j]};
+        double u[3];
+        for (int q = 0; q < 3; ++q) u[q] = (pos[q] - S.origin[q]) * S.inv_dx;
+        Stencil<double> st;
+        make_stencil<double>(u, S.inv_dx, st);
+        double f[3];
+        for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
+        double pv[3] = {0, 0, 0}, tv[9] = {0};
+        for (int cz = 0; cz < 3; ++cz)
+            for (int cy = 0; cy < 3; ++cy)
+                for (int cx = 0; cx < 3; ++cx) {
+                    int idx = node_slot_index(S, bslot, st.c[0] - 1 + cx, st.c[1] - 1 + cy, st.c[2] - 1 + cz);
+                    if (idx < 0) continue;
+                    int slot = idx >> 6, loc = idx & 63;
+                    double N = st.w[0][cx] * st.w[1][cy] * st.w[2][cz];
+                    // r = x_i - x_p (relative to the parent, the centre of mass of the group)
+                    double r[3] = {(cx - f[0]) * S.dx + pos[0] - xp[0], (cy - f[1]) * S.dx + pos[1] - xp[1],
+                                   (cz - f[2]) * S.dx + pos[2] - xp[2]};
+                    double vh[3];
+                    for (int q = 0; q < 3; ++q) vh[q] = gvhat[slot * 192 + q * 64 + loc];
+                    for (int q = 0; q < 3; ++q) {
+                        pv[q] += N * vh[q];
+                        for (int e = 0; e < 3; ++e) tv[3 * q + e] += N * vh[q] * r[e];
+                    }
+                    if (which == 0) {
+                        double dN[3] = {st.dw[0][cx] * st.w[1][cy] * st.w[2][cz], st.w[0][cx] * st.dw[1][cy] * st.w[2][cz],
+                                        st.w[0][cx] * st.w[1][cy] * st.dw[2][cz]};
+                        for (int q = 0; q < 3; ++q) {
+                            sv[q] += N * vh[q];
+                            for (int e = 0; e < 3; ++e) Ls[3 * q + e] += vh[q] * dN[e];
+                        }
+                    }
+                }
+        if (p >= 0) {
+            for (int q = 0; q < 3; ++q) atomicAdd(&acc.a[q][p], mp * pv[q]);
+            for (int q = 0; q < 9; ++q) atomicAdd(&acc.a[3 + q][p], mp * tv[q]);
+        }
+    }
+    // carry the sample: s += dt v(s), dA <- cof(I + dt grad v(s)) dA
+    double dt = S.dt;
+    double M[9], C[9];
+    for (int q = 0; q < 9; ++q) M[q] = dt * Ls[q] + ((q % 4 == 0) ? 1.0 : 0.0);
+    cofactor<double>(M, C);
+    double a0[3] = {dA.a[0][j], dA.a[1][j], dA.a[2][j]};
+    for (int q = 0; q < 3; ++q) dA.a[q][j] = C[3 * q] * a0[0] + C[3 * q + 1] * a0[1] + C[3 * q + 2] * a0[2];
+    for (int q = 0; q < 3; ++q) s.a[q][j] = s.a[q][j] + dt * sv[q];
+}
+
+__global__ void k_g2p_final(int np, W3 x, W3 v, W9 A, const double* __restrict__ m, const int* __restrict__ psc,
+                            const SceneDev* __restrict__ sc, W12 acc, uint8_t* __restrict__ phase,
+                            double* __restrict__ J, W9 F, const double* __restrict__ T) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const SceneDev& S = sc[psc[i]];
+    double mp = m[i];
+    double vp[3];
+    for (int q = 0; q < 3; ++q) vp[q] = acc.a[q][i] / mp;
+    double sA = 4.0 / (mp * S.dx * S.dx);
+    for (int q = 0; q < 9; ++q) A.a[q][i] = acc.a[3 + q][i] * sA;
+    for (int q = 0; q < 3; ++q) {
+        v.a[q][i] = vp[q];
+        x.a[q][i] = x.a[q][i] + S.dt * vp[q];
+    }
+    if (S.phase_change) {
+        uint8_t ph = phase[i];
+        double Tp = T[i];
+        bool melt = ph == 1 && Tp > S.T_melt;
+        bool freeze = ph == 0 && Tp < S.T_melt;
+        if (melt || freeze) {
+            phase[i] = melt ? 0 : 1;
+            J[i] = 1.0;
+            for (int q = 0; q < 9; ++q) F.a[q][i] = (q % 4 == 0) ? 1.0 : 0.0;
+        }
+    }
+}
+
+inline unsigned nblk(long long n, int nt) { return (unsigned)((n + nt - 1) / nt); }
+
+}  // namespace
+
+cudaError_t launch_nearest_parent(mpm_ctx* c) {
+    Dev& d = c->d;
+    cudaStream_t st = c->st;
+    cudaMemsetAsync(d.gcount, 0, sizeof(int) * (c->np > 0 ? c->np : 1), st);
+    if (c->ns > 0) {
+        k_nearest<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc,
+                                                    P3{{d.x[0], d.x[1], d.x[2]}}, d.pid, d.cell_start, d.sc, d.parent,
+                                                    W3{{d.bpos[0], d.bpos[1], d.bpos[2]}}, d.gcount, d.kind, d.err);
+    }
+    if (c->np > 0) k_split<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, d.m, d.gcount, d.mt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2g(mpm_ctx* c) {
+    Dev& d = c->d;
+    cudaStream_t st = c->st;
+    size_t nn = (size_t)c->NB * 64;
+    cudaMemsetAsync(d.gm, 0, sizeof(double) * nn, st);
+    cudaMemsetAsync(d.gmv, 0, sizeof(double) * nn * 3, st);
+    cudaMemsetAsync(d.gmT, 0, sizeof(double) * nn, st);
+    cudaMemsetAsync(d.gmTT, 0, sizeof(double) * nn, st);
+    if (c->NW > 0) {
+        P2GArgs a;
+        a.x = P3{{d.x[0], d.x[1], d.x[2]}};
+        a.v = P3{{d.v[0], d.v[1], d.v[2]}};
+        for (int q = 0; q < 9; ++q) a.A.a[q] = d.A[q];
+        a.mt = d.mt;
+        a.m = d.m;
+        a.T = d.T;
+        a.gT = P3{{d.gT[0], d.gT[1], d.gT[2]}};
+        a.cell_start = d.cell_start;
+        a.work = d.work;
+        a.work_gb = d.work_gb;
+        a.coord = d.slot_coord;
+        a.nbr = d.nbr;
+        a.sc = d.sc;
+        a.gm = d.gm;
+        a.gmv = d.gmv;
+        a.gmT = d.gmT;
+        a.gmTT = d.gmTT;
+        k_p2g_volume<<<c->NW, NT, 0, st>>>(a);
+    }
+    if (c->ns > 0) {
+        P9 A;
+        for (int q = 0; q < 9; ++q) A.a[q] = d.A[q];
+        k_p2g_surface<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}},
+                                                        P3{{d.bpos[0], d.bpos[1], d.bpos[2]}}, d.ssc, d.parent,
+                                                        P3{{d.x[0], d.x[1], d.x[2]}}, P3{{d.v[0], d.v[1], d.v[2]}}, A,
+                                                        d.mt, d.bslot, d.sc, d.gm, d.gmv);
+    }
+    if (c->NB > 0) {
+        if (c->rsize == 4)
+            k_grid_final<float><<<nblk(nn, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.gmv, d.gmT, d.gmTT,
+                                                              d.gvn, d.gTn, d.pcode, (float*)d.invm, (float*)d.hinvd);
+        else
+            k_grid_final<double><<<nblk(nn, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.gmv, d.gmT, d.gmTT,
+                                                               d.gvn, d.gTn, d.pcode, (double*)d.invm, (double*)d.hinvd);
+    }
+    if (c->ns > 0) {
+        if (c->rsize == 4)
+            k_gamma<float><<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc, d.kind,
+                                                             d.bslot, d.sc, d.gmT, d.gTn, d.gamma, d.Tr, (float*)d.swn);
+        else
+            k_gamma<double><<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc, d.kind,
+                                                              d.bslot, d.sc, d.gmT, d.gTn, d.gamma, d.Tr, (double*)d.swn);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_g2p(mpm_ctx* c) {
+    Dev& d = c->d;
+    cudaStream_t st = c->st;
+    if (c->np > 0) {
+        G2PArgs a;
+        a.np = (int)c->np;
+        a.x = P3{{d.x[0], d.x[1], d.x[2]}};
+        a.mt = d.mt;
+        a.psc = d.psc;
+        a.phase = d.phase;
+        a.bslot = d.bslot;
+        a.sc = d.sc;
+        a.gvhat = d.gvhat;
+        a.gThat = d.gThat;
+        for (int q = 0; q < 12; ++q) a.acc.a[q] = d.acc[q];
+        a.J = d.J;
+        a.T = d.T;
+        for (int q = 0; q < 9; ++q) a.F.a[q] = d.F[q];
+        for (int q = 0; q < 3; ++q) a.gT.a[q] = d.gT[q];
+        k_g2p_volume<<<nblk(c->np, 128), 128, 0, st>>>(a);
+    }
+    W12 acc;
+    for (int q = 0; q < 12; ++q) acc.a[q] = d.acc[q];
+    if (c->ns > 0) {
+        k_g2p_surface<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, W3{{d.s[0], d.s[1], d.s[2]}},
+                                                        W3{{d.dA[0], d.dA[1], d.dA[2]}},
+                                                        P3{{d.bpos[0], d.bpos[1], d.bpos[2]}}, d.ssc, d.parent,
+                                                        P3{{d.x[0], d.x[1], d.x[2]}}, d.mt, d.bslot, d.sc, d.gvhat, acc);
+    }
+    if (c->np > 0) {
+        W9 A, F;
+        for (int q = 0; q < 9; ++q) {
+            A.a[q] = d.A[q];
+            F.a[q] = d.F[q];
+        }
+        k_g2p_final<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, W3{{d.x[0], d.x[1], d.x[2]}},
+                                                      W3{{d.v[0], d.v[1], d.v[2]}}, A, d.m, d.psc, d.sc, acc, d.phase,
+                                                      d.J, F, d.T);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mpm

@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, phase by phase.
+
+Tolerances: float64 form 1e-9 relative (atomics reorder sums); the
+float32-operator form 1e-5 relative for the step's grid velocity (the target
+of the workload) and 2e-5 for single operator applications, relative to the
+largest entry of the oracle's result. Index work (closest parent) is bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.energy import HESS_EXACT, HESS_PROJECTED
+from paper_2101_12408_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+mpm = pytest.importorskip("paper_2101_12408_gb300.mpm")
+
+
+def relerr(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+TOL = {mpm.PREC_FP64: 1e-9, mpm.PREC_FP32_FP64RED: 2e-5}
+PRECS = [mpm.PREC_FP64, mpm.PREC_FP32_FP64RED]
+
+
+def _mixed_scene(seed=9):
+    """Liquid + solid + viscosity + heat + gamma(T) in one small scene."""
+    sc = scenes.droplet(n=16, r_cells=4.5, seed=seed, gravity=(0.0, -3.0, 0.5), mu_l=0.05, lambda_l=40.0,
+                        thermal=True)
+    rng = np.random.default_rng(seed)
+    half = sc.x[:, 0] > 0.5
+    sc.phase[half] = scenes.PHASE_SOLID
+    sc.F[half] = np.eye(3) + 0.02 * rng.standard_normal((half.sum(), 3, 3))
+    sc.J = rng.uniform(0.97, 1.03, sc.J.shape)
+    sc.v = rng.standard_normal(sc.v.shape) * 0.2
+    sc.A = rng.standard_normal(sc.A.shape) * 0.5
+    p = sc.params
+    p.E0 = 30.0
+    p.T0 = 0.0
+    p.T_melt = 10.0
+    p.dt = 0.01
+    p.gamma_law = scenes.GAMMA_LINEAR
+    p.gamma_p = (1.0, -0.2, 0.1, 2.0)
+    p.h = 2.0
+    p.H = 0.3
+    p.K = 0.2
+    sc.T = rng.uniform(0.0, 4.0, sc.T.shape)
+    sc.gradT = rng.standard_normal(sc.gradT.shape) * 0.5
+    sc.b = rng.uniform(0, 1, sc.n_surface)
+    sc.Tbar = rng.uniform(0, 1, sc.n_surface)
+    return sc
+
+
+SCENES = {
+    "droplet": lambda: scenes.config(0),
+    "mixed": _mixed_scene,
+}
+
+
+def _setup(sc, prec):
+    ctx = mpm.Context(sc, precision=prec)
+    ctx.load_scene(0)
+    ctx.resample()
+    ctx.p2g()
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    return ctx, sim
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_resample_parents_bitexact(name):
+    sc = SCENES[name]()
+    ctx, sim = _setup(sc, mpm.PREC_FP64)
+    out = ctx.get_surface(0)
+    np.testing.assert_array_equal(out["parent"], sim.parent)
+    np.testing.assert_array_equal(out["b"], sim.bpos)
+    np.testing.assert_allclose(out["gamma"], sim.gamma, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_p2g_matches_oracle(name):
+    sc = SCENES[name]()
+    ctx, sim = _setup(sc, mpm.PREC_FP64)
+    g = sim.grid
+    assert relerr(ctx.get_grid(0, mpm.FIELD_MASS), g["m"]) < 1e-12
+    assert relerr(ctx.get_grid(0, mpm.FIELD_MOMENTUM), g["mv"]) < 1e-12
+    assert relerr(ctx.get_grid(0, mpm.FIELD_VN), sim.vn) < 1e-12
+    if sc.params.thermal:
+        assert relerr(ctx.get_grid(0, mpm.FIELD_THERMAL_MASS), g["mT"]) < 1e-12
+        assert relerr(ctx.get_grid(0, mpm.FIELD_TN), sim.Tn) < 1e-12
+    # conservation in float64 sums
+    np.testing.assert_allclose(ctx.get_grid(0, mpm.FIELD_MOMENTUM).sum(0), np.sum(sc.m[:, None] * sc.v, 0),
+                               rtol=1e-12, atol=1e-15)
+
+
+def _iterate(sim, seed=1, scale=0.3):
+    st = sim.newton_state()
+    rng = np.random.default_rng(seed)
+    v = (st.vn + scale * rng.standard_normal(st.vn.shape)) * st.active[:, None]
+    return st, v
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(SCENES))
+def test_energy_gradient_matches_oracle(name, prec):
+    sc = SCENES[name]()
+    ctx, sim = _setup(sc, prec)
+    st, v = _iterate(sim)
+    ctx.set_velocity(0, v)
+    e, g = ctx.energy_gradient(0)
+    ge = st.gradient(v)
+    eo = st.energy(v)
+    tol = 1e-10 if prec == mpm.PREC_FP64 else 2e-5
+    assert relerr(g, ge) < tol
+    assert abs(e - eo) <= tol * abs(eo)
+
+
+@pytest.mark.parametrize("mode", [HESS_PROJECTED, HESS_EXACT])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(SCENES))
+def test_apply_hessian_matches_oracle(name, prec, mode):
+    sc = SCENES[name]()
+    ctx, sim = _setup(sc, prec)
+    st, v = _iterate(sim)
+    ctx.set_velocity(0, v)
+    act = st.active[:, None]
+    rng = np.random.default_rng(4)
+    dv = rng.standard_normal(v.shape) * act
+
+    def proj(u):
+        return oracle.apply_projector(sim.P, u) * act
+
+    ref = proj(st.hessvec(v, proj(dv), mode))
+    out = ctx.apply_hessian(0, dv, mode=mode)
+    assert relerr(out, ref) < TOL[prec]
+    # stiffness part on its own (the mass term dominates the total)
+    stiff_ref = ref - proj(st.m[:, None] * proj(dv))
+    stiff = out - proj(st.m[:, None] * proj(dv))
+    assert relerr(stiff, stiff_ref) < (1e-9 if prec == mpm.PREC_FP64 else 1e-4)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_heat_apply_matches_oracle(prec):
+    sc = _mixed_scene()
+    ctx, sim = _setup(sc, prec)
+    hs = sim.heat_system()
+    rng = np.random.default_rng(6)
+    T = rng.standard_normal(hs.G) * hs.unknown
+    ref = hs.apply(T)
+    out = ctx.heat_apply(0, T)
+    assert relerr(out, ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(SCENES))
+def test_step_grid_velocity_matches_oracle(name, prec):
+    sc = SCENES[name]()
+    if prec == mpm.PREC_FP64:
+        # both sides converge tightly, so the comparison is not at the solver tolerance
+        sc.params.newton_tol = 1e-11
+        sc.params.cg_rtol = 1e-11
+        sc.params.heat_rtol = 1e-12
+        sc.params.max_cg = 5000
+    ctx, sim = _setup(sc, prec)
+    stats = ctx.newton_step()
+    sim.grid_update()
+    vgpu = ctx.get_grid(0, mpm.FIELD_VHAT)
+    tol = 1e-9 if prec == mpm.PREC_FP64 else 1e-5
+    assert relerr(vgpu, sim.vhat) < tol, stats
+    if sc.params.thermal:
+        assert relerr(ctx.get_grid(0, mpm.FIELD_THAT), sim.That) < (1e-9 if prec == mpm.PREC_FP64 else 1e-5)
+    # G2P
+    ctx.g2p()
+    sim.g2p()
+    p = ctx.get_particles(0)
+    for f in ("x", "v", "A", "J", "F"):
+        ref = getattr(sim.sc, f)
+        assert relerr(p[f], ref) < (1e-9 if prec == mpm.PREC_FP64 else 1e-5), f
+    s = ctx.get_surface(0)
+    assert relerr(s["s"], sim.sc.s) < 1e-9
+    assert relerr(s["dA"], sim.sc.dA) < (1e-9 if prec == mpm.PREC_FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_momentum_conserved_in_fp64_sums(prec):
+    sc = scenes.droplet(n=32, r_cells=8.0, seed=12, v0=(0.3, -0.1, 0.2), spin=1.5, lambda_l=100.0)
+    ctx = mpm.Context(sc, precision=prec)
+    ctx.load_scene(0)
+    m0 = np.sum(sc.m[:, None] * sc.v, 0)
+    for _ in range(2):
+        stats = ctx.step()
+        np.testing.assert_allclose(stats[0]["momentum"], m0, rtol=0, atol=1e-10 * np.abs(m0).max())
+    p = ctx.get_particles(0)
+    np.testing.assert_allclose(np.sum(sc.m[:, None] * p["v"], 0), m0, rtol=0, atol=1e-10 * np.abs(m0).max())
+
+
+def test_two_steps_match_oracle_fp32():
+    sc = scenes.config(0)
+    ctx = mpm.Context(sc, precision=mpm.PREC_FP32_FP64RED)
+    ctx.load_scene(0)
+    sim = oracle.OracleSim(sc)
+    for _ in range(2):
+        ctx.step()
+        sim.step()
+    p = ctx.get_particles(0)
+    assert relerr(p["v"], sim.sc.v) < 2e-5
+    assert relerr(p["x"], sim.sc.x) < 1e-9
+
+
+def test_domain_error_is_reported():
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=1)
+    sc.x[0] = [0.01, 0.5, 0.5]   # cell 0: outside cells 1..n-2
+    ctx = mpm.Context(sc)
+    ctx.load_scene(0)
+    with pytest.raises(mpm.MPMError) as ei:
+        ctx.resample()
+    assert ei.value.status == mpm.MPM_ERR_DOMAIN
+
+
+def test_nonfinite_input_rejected():
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=1)
+    sc.v[3, 1] = np.nan
+    ctx = mpm.Context(sc)
+    with pytest.raises(mpm.MPMError) as ei:
+        ctx.load_scene(0)
+    assert ei.value.status == mpm.MPM_ERR_NUMERIC
