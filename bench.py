@@ -1,0 +1,351 @@
+"""Benchmark: implicit backward-Euler steps per second of the surface-energy APIC-MPM
+path on one GB300, plus the Hessian-vector operator's roofline.
+
+Workload (default ``incline``): 256^3 grid, dx = 1/256, 40 droplets above a
+30-degree slip plane, radii uniform in [9.3, 24.8] cells (about 8M interior
+particles at 8 per cell, ~0.3M surface samples), gravity -9.8, interface
+dependent surface coefficients (liquid-gas 1.0, effective solid-liquid 0.5 for a
+120-degree contact angle), dt = 1e-3, Newton tolerance 1e-6 with CG. Seeded
+synthetic input (no dataset exists for this path).
+
+A step is one full pass of the method: resample (sort, closest parent, balance
+particles, split) + P2G + heat solve (thermal scenes) + Newton-CG + G2P/merge.
+
+Reported (one JSON line on rank 0):
+  value        implicit steps/s, float32 operator + float64 reductions, inputs
+               resident in HBM; the state (~2 GB) exceeds L2 between steps
+  roofline     the Hessian-vector kernel: algorithmic bytes per launch / its mean
+               CUDA-event duration inside the timed steps, against measured HBM
+  e2e          the same steps/s through the C ABI with host buffers: particle and
+               surface state copied in from host memory and back out every step
+  fp64_form    the all-float64 GPU form on the same workload (fewer steps)
+  cpu_baseline the FP64 numpy oracle on one droplet of the workload (a bounded
+               sample), scaled per particle to the full workload
+  --impl reference: the oracle alone, timed on the host, same metric.
+Multi-GPU (torchrun): replicas only -- every rank advances its own copy of the
+workload; value is the sum over ranks (weak scaling, no collective on the path).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2101_12408_gb300 import scenes  # noqa: E402
+
+METRIC = "implicit steps/sec (float32 operator + float64 reductions)"
+UNIT = "steps/s"
+# ncu traffic of one Hessian-operator launch (dram read + write bytes) from the
+# capture summarised in profiles/apply_hessian_incline.md; None until captured
+NCU_TRAFFIC_BYTES = None
+
+
+def make_workload(name):
+    if name == "incline":
+        return scenes.incline()
+    if name == "film":
+        return scenes.film()
+    if name == "droplet":
+        return scenes.droplet()
+    if name == "wax":
+        return scenes.wax()
+    raise ValueError(name)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        v = pk.get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(ctx, sc, rsize):
+    """Bytes one Hessian-operator launch must move: per liquid particle its
+    position and two coefficients, per solid particle position, F^n, Lame pair
+    and the iterate's F, R, (tr S I - S)^-1, per surface sample position, dA,
+    F^, n, 1/|c|, gamma, per active node the direction read and the product
+    written (3 components each)."""
+    p = ctx.get_particles(0)
+    nsol = int(np.sum(p["phase"] == 1))
+    nliq = ctx.np[0] - nsol
+    m = ctx.get_grid(0, 0)
+    g_active = int(np.sum(m > 0))
+    b = rsize * (nliq * 5 + nsol * (3 + 9 + 2 + 24) + ctx.ns[0] * 20 + g_active * 6)
+    return b, dict(liquid=nliq, solid=nsol, surface=ctx.ns[0], active_nodes=g_active)
+
+
+def run_oracle_sample(sc, steps):
+    """FP64 oracle on one droplet of the workload; returns seconds per step and the sample size."""
+    import oracle
+    # the smallest droplet: its particles and samples in a window of the same grid
+    from scipy.spatial import cKDTree  # noqa: F401  (scipy present on both machines)
+    sample = sample_scene(sc)
+    sim = oracle.OracleSim(sample)
+    times = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        sim.step()
+        times.append(time.perf_counter() - t)
+    return times, sample
+
+
+SAMPLE_CELLS = 16
+
+
+def sample_scene(sc, size=SAMPLE_CELLS):
+    """A bounded piece of the workload for the CPU oracle: the particles and
+    surface samples in a `size`^3-cell window (same dx, parameters and plane)
+    around the lower surface of the smallest droplet."""
+    if "radii" in sc.meta:
+        k = int(np.argmin(sc.meta["radii"]))
+        c = sc.meta["centers"][k] - np.array([0.0, sc.meta["radii"][k] - 3 * sc.dx, 0.0])
+        return scenes.window(sc, c, size, name=f"incline_window{size}")
+    c = sc.x.mean(0)
+    return scenes.window(sc, c, size, name=f"{sc.name}_window{size}")
+
+
+def bench_ours(args, rank, world):
+    import torch
+    from paper_2101_12408_gb300 import mpm
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    sc = make_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    prec = mpm.PREC_FP32_FP64RED if args.precision == "fp32" else mpm.PREC_FP64
+    ctx = mpm.Context(sc, precision=prec, stream=stream.cuda_stream)
+    ctx.load_scene(0)
+    for _ in range(args.warmup):
+        ctx.step()
+    dist = world > 1
+    if dist:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    ctx.profile_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(ctx.step()[0])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        torch.distributed.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    prof = ctx.profile()
+    ctx.profile_enable(False)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    rsize = 4 if prec == mpm.PREC_FP32_FP64RED else 8
+    abytes, counts = algorithmic_bytes(ctx, sc, rsize)
+    apply_avg_ms = prof["apply_ms"] / max(prof["apply_launches"], 1)
+    peak, peak_kind = measured_peak()
+    achieved = abytes / (apply_avg_ms * 1e-3) / 1e9
+    out = {
+        "steps_per_s": world * args.steps / (elapsed_ms * 1e-3),
+        "ms_per_step": elapsed_ms / args.steps,
+        "prof": prof,
+        "stats": stats,
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC_BYTES, "peak_source": peak_kind, "kernel": "k_apply (Hessian-vector)",
+                     "bytes_per_launch": abytes, "launch_ms": apply_avg_ms,
+                     "launches": prof["apply_launches"]},
+        "counts": counts,
+        "applies_per_s": prof["apply_launches"] / (elapsed_ms * 1e-3),
+    }
+    # end to end through host buffers: state in from host memory, step, state back out
+    if args.e2e_steps > 0:
+        cur = sc.copy()
+        p = ctx.get_particles(0)
+        srf = ctx.get_surface(0)
+        for f in ("x", "v", "A", "J", "F", "T", "gradT", "phase"):
+            setattr(cur, f, p[f])
+        cur.s, cur.dA, cur.kind = srf["s"], srf["dA"], srf["kind"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.load_scene(0, cur)
+            ctx.step()
+            p = ctx.get_particles(0)
+            srf = ctx.get_surface(0)
+            for f in ("x", "v", "A", "J", "F", "T", "gradT", "phase"):
+                setattr(cur, f, p[f])
+            cur.s, cur.dA, cur.kind = srf["s"], srf["dA"], srf["kind"]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        n, ns = ctx.np[0], ctx.ns[0]
+        h2d = n * (3 + 3 + 9 + 1 + 1 + 1 + 9 + 1 + 3) * 8 + n + ns * (3 + 3 + 1 + 1) * 8 + ns
+        d2h = n * (3 + 3 + 9 + 1 + 9 + 1 + 3) * 8 + n + ns * (3 + 3 + 1 + 3) * 8 + ns + ns * 4
+        out["e2e"] = {"value": world * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h)}
+    ctx.close()
+    # all-float64 form on the same workload
+    if args.fp64_steps > 0 and prec == mpm.PREC_FP32_FP64RED:
+        ctx = mpm.Context(sc, precision=mpm.PREC_FP64, stream=stream.cuda_stream)
+        ctx.load_scene(0)
+        ctx.step()
+        ctx.profile_enable(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64 = [ctx.step()[0] for _ in range(args.fp64_steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        p64 = ctx.profile()
+        out["fp64_form"] = {"steps_per_s": args.fp64_steps / (ms * 1e-3), "ms_per_step": ms / args.fp64_steps,
+                            "apply_launch_ms": p64["apply_ms"] / max(p64["apply_launches"], 1),
+                            "newton_iters": [s["newton_iters"] for s in st64],
+                            "cg_iters": [s["cg_iters"] for s in st64],
+                            "residual_rel": [s["residual"] / max(s["residual0"], 1e-300) for s in st64]}
+        ctx.close()
+    return out, sc
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="incline")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sc = make_workload(args.workload)
+        times, sample = run_oracle_sample(sc, args.warmup + args.steps)
+        t = float(np.mean(times[args.warmup:])) if args.steps > 0 else float("nan")
+        scale = sample.n_particles / sc.n_particles
+        val = scale / t
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "particles": sc.n_particles},
+                "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"one droplet ({sample.n_particles} particles, {sample.n_surface} samples, "
+                                           f"{sample.n[0]}^3 window) of the workload per step, scaled by particle "
+                                           f"count {scale:.5f}"},
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res, sc = bench_ours(args, rank, world)
+    if rank != 0:
+        return
+    cpu = None
+    if args.cpu_steps > 0:
+        times, sample = run_oracle_sample(sc, args.cpu_steps)
+        t = float(np.mean(times))
+        scale = sample.n_particles / sc.n_particles
+        cpu = {"value": scale / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one droplet of the workload ({sample.n_particles} of {sc.n_particles} particles, "
+                         f"{sample.n[0]}^3 window, {args.cpu_steps} step), seconds per step scaled by particle count"}
+    prof = res["prof"]
+    line = {
+        "metric": METRIC, "value": res["steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(sc.n), "dx": sc.dx, "particles": sc.n_particles,
+                   "surface_samples": sc.n_surface, "dt": sc.params.dt, "newton_tol": sc.params.newton_tol,
+                   "l2": "inputs larger than L2 (particle state ~2 GB)", "parallelism": "replicas"},
+        "roofline": res["roofline"],
+        "cpu_baseline": cpu,
+        "e2e": res.get("e2e"),
+        "gpu_launches": prof["kernel_launches"],
+        "clocks": res["clocks"],
+        "hessian_applies_per_s": res["applies_per_s"],
+        "fp64_form": res.get("fp64_form"),
+        "phases_ms_per_step": {k: v / args.steps for k, v in prof["phase_ms"].items()},
+        "newton_iters": [s["newton_iters"] for s in res["stats"]],
+        "cg_iters": [s["cg_iters"] for s in res["stats"]],
+        "residual_rel": [s["residual"] / max(s["residual0"], 1e-300) for s in res["stats"]],
+        "counts": res["counts"],
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

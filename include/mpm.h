@@ -224,6 +224,23 @@ mpm_status mpm_sync(mpm_ctx* ctx);
 mpm_status mpm_counts(mpm_ctx* ctx, int64_t* n_particles, int64_t* n_surface,
                       int64_t* n_blocks, int64_t* n_work_blocks);
 
+/* Profiling counters, accumulated while enabled (not part of the paper's method).
+ * Kernel durations come from CUDA events recorded on the context's stream around
+ * each launch; phase times around each phase call. */
+typedef struct {
+    int64_t kernel_launches;      /* every kernel the library launched */
+    int64_t apply_launches;       /* Hessian-vector operator launches inside Newton-CG */
+    double apply_ms;              /* their summed device time */
+    int64_t heat_apply_launches;  /* heat operator launches inside the heat CG */
+    double heat_apply_ms;
+    double phase_ms[5];           /* resample, p2g, heat solve, Newton solve, g2p */
+    int64_t newton_iters, cg_iters, heat_iters;
+} mpm_profile;
+
+/* enable != 0 resets the counters and starts accumulating; 0 stops. */
+mpm_status mpm_profile_enable(mpm_ctx* ctx, int32_t enable);
+mpm_status mpm_get_profile(mpm_ctx* ctx, mpm_profile* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,8 +28,16 @@ Hessian-vector products (the linearisation the paper defers to earlier work):
   surface   dt^2 dG gradN_i(s_r) with, for c = cof(F^) a, n = c/|c|, C = dc/dF^,
             dc = C : dF, dn = (I - n n^T) dc / |c|,
             dG_gd = k (dn_a C_agd + n_a dC_agd)         EXACT
-            dG_gd = k  dn_a C_agd                        PROJECTED (Gauss-Newton part,
-            PSD; the reading of the paper's deferred "definiteness fix")
+            dG_gd = k (dn_a C_agd + Q+[dF^])             PROJECTED
+  Reading of the paper's deferred "definiteness fix": the exact surface Hessian
+  is the Gauss-Newton term k dc^T (I - n n^T) dc / |c| (PSD) plus the curvature of
+  the cofactor, n . cof(dF) a, which does not depend on F^. In right-handed frames
+  (t1, t2, n) and (s1, s2, a/|a|) it equals |a| det of the 2x2 tangential block
+  x_ij = t_i . dF s_j, an indefinite form with eigenvalues +|a| on the conformal
+  directions (x11 + x22, x12 - x21) and -|a| on the anti-conformal ones. The
+  projected Hessian keeps the Gauss-Newton term and the positive (conformal)
+  part Q+, so it stays PSD and keeps the surface's stiffness against in-plane
+  dilation (dropping the whole curvature term loses it and stalls Newton).
 """
 import numpy as np
 
@@ -41,6 +49,18 @@ HESS_EXACT, HESS_PROJECTED = 0, 1
 
 def _L(st, v):
     return np.einsum("pqa,pqb->pab", v[st.node], st.dN)
+
+
+def _frame(u):
+    """Unit vectors t1, t2 with (t1, t2, u) right-handed, for unit rows u."""
+    # helper axis: the coordinate axis least aligned with u
+    k = np.argmin(np.abs(u), axis=1)
+    e = np.zeros_like(u)
+    e[np.arange(u.shape[0]), k] = 1.0
+    t1 = e - u * np.sum(e * u, 1, keepdims=True)
+    t1 /= np.linalg.norm(t1, axis=1, keepdims=True)
+    t2 = np.cross(u, t1)
+    return t1, t2
 
 
 class NewtonState:
@@ -94,6 +114,24 @@ class NewtonState:
             e_sol = np.sum(fcr_energy(F[sol], self.mu_h[sol], self.lam_h[sol]) * self.V0[sol])
         e_surf = np.sum(self.gamma * np.linalg.norm(c, axis=1))
         return kin + e + e_visc + e_sol + e_surf
+
+    def _conformal_part(self, nrm, X):
+        """Positive part of the cofactor curvature n . cof(X) a (see module doc).
+
+        With right-handed frames (t1, t2, n) and (s1, s2, a/|a|) and x_ij = t_i . X s_j,
+        n . cof(X) a = |a| (x11 x22 - x12 x21); its positive part as a quadratic form
+        is |a|/2 [(x11 + x22)^2 + (x12 - x21)^2], whose Hessian-vector product is
+        |a|/2 [(x11 + x22) (t1 s1^T + t2 s2^T) + (x12 - x21) (t1 s2^T - t2 s1^T)].
+        """
+        a = self.dA
+        an = np.linalg.norm(a, axis=1)
+        t1, t2 = _frame(nrm)
+        s1, s2 = _frame(a / an[:, None])
+        x = lambda t, s: np.einsum("ra,rab,rb->r", t, X, s)
+        x11, x22, x12, x21 = x(t1, s1), x(t2, s2), x(t1, s2), x(t2, s1)
+        out = ((x11 + x22)[:, None, None] * (np.einsum("ra,rb->rab", t1, s1) + np.einsum("ra,rb->rab", t2, s2))
+               + (x12 - x21)[:, None, None] * (np.einsum("ra,rb->rab", t1, s2) - np.einsum("ra,rb->rab", t2, s1)))
+        return 0.5 * an[:, None, None] * out
 
     def _surface_C(self, Fh):
         # C_agd = dc_a / dF_gd = eps_agk eps_bdl a_b F_kl
@@ -158,6 +196,8 @@ class NewtonState:
             if mode == HESS_EXACT:
                 dC = np.einsum("agk,bdl,rb,rkl->ragd", EPS, EPS, self.dA, dFh)
                 dG = dG + np.einsum("ra,ragd->rgd", nrm, dC)
+            else:
+                dG = dG + self._conformal_part(nrm, dFh)
             dG = self.gamma[:, None, None] * dG
             out += scatter(G, ss.node, dt * dt * np.einsum("rgd,rqd->rqg", dG, ss.dN))
         return out

@@ -119,8 +119,8 @@ class OracleSim:
         self.That = None
         self.heat_its = 0
         if prm.thermal:
-            # solved to 1e-10 relative to |rhs|, tighter than any tolerance the GPU path runs at
-            self.That, self.heat_its = heat_solve(self.heat_system(), 1e-10, 20000)
+            # solved to 1e-13 relative to |rhs| (near round-off), tighter than any GPU tolerance
+            self.That, self.heat_its = heat_solve(self.heat_system(), 1e-13, 20000)
         self.state = self.newton_state()
         self.vhat, self.stats = newton_solve(self.state, self.P, prm, self.hess_mode, self.explicit)
 

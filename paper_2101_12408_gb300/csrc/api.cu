@@ -11,7 +11,56 @@ namespace mpm {
 cudaError_t launch_heat_full(mpm_ctx* c, const void* T, void* out);
 }
 
+namespace mpm {
+
+void prof_mark_apply(mpm_ctx* c, bool begin) {
+    if (!c->prof || c->nev >= 16) return;
+    cudaEventRecord(c->ev[2 * c->nev + (begin ? 0 : 1)], c->st);
+    if (!begin) c->nev++;
+}
+
+// called after the stream was synchronised
+void prof_collect_applies(mpm_ctx* c, bool heat) {
+    if (c->prof) {
+        for (int i = 0; i < c->nev; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) != cudaSuccess) continue;
+            if (heat) {
+                c->pr.heat_apply_ms += ms;
+                c->pr.heat_apply_launches++;
+            } else {
+                c->pr.apply_ms += ms;
+                c->pr.apply_launches++;
+            }
+        }
+    }
+    c->nev = 0;
+}
+
+}  // namespace mpm
+
 using namespace mpm;
+
+namespace {
+
+// device time of one phase call (events on the context's stream)
+struct PhaseTimer {
+    mpm_ctx* c;
+    int k;
+    PhaseTimer(mpm_ctx* c_, int k_) : c(c_), k(k_) {
+        if (c->prof) cudaEventRecord(c->ev[32], c->st);
+    }
+    ~PhaseTimer() {
+        if (!c->prof) return;
+        cudaEventRecord(c->ev[33], c->st);
+        if (cudaEventSynchronize(c->ev[33]) == cudaSuccess) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev[32], c->ev[33]) == cudaSuccess) c->pr.phase_ms[k] += ms;
+        }
+    }
+};
+
+}  // namespace
 
 namespace {
 
@@ -298,6 +347,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.sc, SceneDev, n_scenes); A_(d.scal, SceneScal, n_scenes); A_(d.err, int, 1);
 #undef A_
 #undef R_
+    for (int k = 0; k < 34 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     if (e == cudaSuccess) e = cudaMallocHost(&c->hscal, sizeof(SceneScal) * n_scenes);
     if (e == cudaSuccess) e = cudaMallocHost(&c->herr, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->hcounts, sizeof(int) * 4);
@@ -317,6 +367,8 @@ mpm_status mpm_destroy(mpm_ctx* c) {
     if (!c) return MPM_ERR_INVALID_ARG;
     if (c->st) cudaStreamSynchronize(c->st); else cudaDeviceSynchronize();
     for (void* p : c->allocs) cudaFree(p);
+    for (int k = 0; k < 34; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->hscal) cudaFreeHost(c->hscal);
     if (c->herr) cudaFreeHost(c->herr);
     if (c->hcounts) cudaFreeHost(c->hcounts);
@@ -336,7 +388,7 @@ mpm_status mpm_set_particles(mpm_ctx* c, int32_t scene, int64_t n, const double*
     if (n > S.p_end - S.p_begin) return fail(c, MPM_ERR_CAPACITY, "mpm_set_particles: more particles than max_particles");
     cudaStream_t st = c->st;
     Dev& d = c->d;
-    if (c->np > 0) k_kill_scene<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, d.psc);
+    if (c->np > 0) MPM_LAUNCH k_kill_scene<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, d.psc);
     if (c->np + n > c->Pcap) MPM_CUDA(launch_sort_particles(c));   // drops removed particles
     if (n > 0) {
         // every field is copied (from host or device memory) into the two staging
@@ -365,12 +417,12 @@ mpm_status mpm_set_particles(mpm_ctx* c, int32_t scene, int64_t n, const double*
             ph = (uint8_t*)d.perm;
             MPM_CUDA(cudaMemcpyAsync(ph, phase, (size_t)n, cudaMemcpyDefault, st));
         }
-        k_stage_in<<<nblk(n, 256), 256, 0, st>>>((int)n, (int)c->np, scene, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4],
+        MPM_LAUNCH k_stage_in<<<nblk(n, 256), 256, 0, st>>>((int)n, (int)c->np, scene, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4],
                                                   dptr[5], dptr[6], dptr[7], dptr[8], ph, d);
         MPM_CUDA(cudaGetLastError());
         // reject non-finite input before any step
         for (int f = 0; f < 9; ++f)
-            if (dptr[f]) k_check_finite<<<nblk(comps[f] * n, 256), 256, 0, st>>>((int)(comps[f] * n), dptr[f], d.err);
+            if (dptr[f]) MPM_LAUNCH k_check_finite<<<nblk(comps[f] * n, 256), 256, 0, st>>>((int)(comps[f] * n), dptr[f], d.err);
         c->np += n;
     }
     c->resampled = false;
@@ -396,7 +448,7 @@ mpm_status mpm_get_particles(mpm_ctx* c, int32_t scene, int64_t n, double* x, do
         for (int q = 0; q < fd.comps; ++q) srcs[q] = fd.src[q];
         double** dsrc = (double**)d.dense_b;
         MPM_CUDA(cudaMemcpyAsync(dsrc, srcs, sizeof(double*) * fd.comps, cudaMemcpyHostToDevice, st));
-        k_stage_out<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, (int)n, d.psc, d.pid, (const double* const*)dsrc,
+        MPM_LAUNCH k_stage_out<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, (int)n, d.psc, d.pid, (const double* const*)dsrc,
                                                       fd.comps, (double*)d.dense_a);
         MPM_CUDA(cudaMemcpyAsync(fd.out, d.dense_a, sizeof(double) * fd.comps * n, cudaMemcpyDefault, st));
         MPM_CUDA(cudaStreamSynchronize(st));
@@ -407,13 +459,13 @@ mpm_status mpm_get_particles(mpm_ctx* c, int32_t scene, int64_t n, double* x, do
         if (!scal_out[f]) continue;
         double** dsrc = (double**)d.dense_b;
         MPM_CUDA(cudaMemcpyAsync(dsrc, &scal_src[f], sizeof(double*), cudaMemcpyHostToDevice, st));
-        k_stage_out<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, (int)n, d.psc, d.pid, (const double* const*)dsrc, 1,
+        MPM_LAUNCH k_stage_out<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, (int)n, d.psc, d.pid, (const double* const*)dsrc, 1,
                                                       (double*)d.dense_a);
         MPM_CUDA(cudaMemcpyAsync(scal_out[f], d.dense_a, sizeof(double) * n, cudaMemcpyDefault, st));
         MPM_CUDA(cudaStreamSynchronize(st));
     }
     if (phase) {
-        k_stage_out_u8<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, (int)n, d.psc, d.pid, d.phase, (uint8_t*)d.dense_a);
+        MPM_LAUNCH k_stage_out_u8<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, scene, (int)n, d.psc, d.pid, d.phase, (uint8_t*)d.dense_a);
         MPM_CUDA(cudaMemcpyAsync(phase, d.dense_a, (size_t)n, cudaMemcpyDefault, st));
         MPM_CUDA(cudaStreamSynchronize(st));
     }
@@ -429,7 +481,7 @@ mpm_status mpm_set_surface(mpm_ctx* c, int32_t scene, int64_t n, const double* s
     if (n > S.s_end - S.s_begin) return fail(c, MPM_ERR_CAPACITY, "mpm_set_surface: more samples than max_surface");
     cudaStream_t st = c->st;
     Dev& d = c->d;
-    if (c->ns > 0) k_kill_scene<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, d.ssc);
+    if (c->ns > 0) MPM_LAUNCH k_kill_scene<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, d.ssc);
     if (c->ns + n > c->Scap) MPM_CUDA(launch_sort_surface(c));   // drops removed samples
     if (n > 0) {
         double* a = (double*)d.dense_a;
@@ -451,9 +503,9 @@ mpm_status mpm_set_surface(mpm_ctx* c, int32_t scene, int64_t n, const double* s
             dk = (uint8_t*)(bb + 2 * n);
             MPM_CUDA(cudaMemcpyAsync(dk, kind, (size_t)n, cudaMemcpyDefault, st));
         }
-        k_stage_surf_in<<<nblk(n, 256), 256, 0, st>>>((int)n, (int)c->ns, scene, a, a + 3 * n, dk, db, dT, d);
+        MPM_LAUNCH k_stage_surf_in<<<nblk(n, 256), 256, 0, st>>>((int)n, (int)c->ns, scene, a, a + 3 * n, dk, db, dT, d);
         MPM_CUDA(cudaGetLastError());
-        k_check_finite<<<nblk(6 * n, 256), 256, 0, st>>>((int)(6 * n), a, d.err);
+        MPM_LAUNCH k_check_finite<<<nblk(6 * n, 256), 256, 0, st>>>((int)(6 * n), a, d.err);
         c->ns += n;
     }
     c->resampled = false;
@@ -476,18 +528,18 @@ mpm_status mpm_get_surface(mpm_ctx* c, int32_t scene, int64_t n, double* s, doub
         if (!fd.out) continue;
         double** dsrc = (double**)d.dense_b;
         MPM_CUDA(cudaMemcpyAsync(dsrc, fd.src, sizeof(double*) * fd.comps, cudaMemcpyHostToDevice, st));
-        k_stage_out<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, (int)n, d.ssc, d.sid, (const double* const*)dsrc,
+        MPM_LAUNCH k_stage_out<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, (int)n, d.ssc, d.sid, (const double* const*)dsrc,
                                                       fd.comps, (double*)d.dense_a);
         MPM_CUDA(cudaMemcpyAsync(fd.out, d.dense_a, sizeof(double) * fd.comps * n, cudaMemcpyDefault, st));
         MPM_CUDA(cudaStreamSynchronize(st));
     }
     if (kind) {
-        k_stage_out_u8<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, (int)n, d.ssc, d.sid, d.kind, (uint8_t*)d.dense_a);
+        MPM_LAUNCH k_stage_out_u8<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, (int)n, d.ssc, d.sid, d.kind, (uint8_t*)d.dense_a);
         MPM_CUDA(cudaMemcpyAsync(kind, d.dense_a, (size_t)n, cudaMemcpyDefault, st));
         MPM_CUDA(cudaStreamSynchronize(st));
     }
     if (parent) {
-        k_stage_parent<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, (int)n, d.ssc, d.sid, d.parent, d.pid,
+        MPM_LAUNCH k_stage_parent<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, (int)n, d.ssc, d.sid, d.parent, d.pid,
                                                          (int32_t*)d.dense_a);
         MPM_CUDA(cudaMemcpyAsync(parent, d.dense_a, sizeof(int32_t) * n, cudaMemcpyDefault, st));
         MPM_CUDA(cudaStreamSynchronize(st));
@@ -497,6 +549,7 @@ mpm_status mpm_get_surface(mpm_ctx* c, int32_t scene, int64_t n, double* s, doub
 
 mpm_status mpm_resample(mpm_ctx* c) {
     if (!c) return MPM_ERR_INVALID_ARG;
+    PhaseTimer timer(c, 0);
     cudaStream_t st = c->st;
     Dev& d = c->d;
     MPM_CUDA(launch_sort_particles(c));
@@ -516,6 +569,7 @@ mpm_status mpm_resample(mpm_ctx* c) {
 mpm_status mpm_p2g(mpm_ctx* c) {
     if (!c) return MPM_ERR_INVALID_ARG;
     if (!c->resampled) return fail(c, MPM_ERR_INVALID_ARG, "mpm_p2g: call mpm_resample first");
+    PhaseTimer timer(c, 1);
     MPM_CUDA(launch_p2g(c));
     MPM_CUDA(launch_pack_step(c));
     c->p2g_done = true;
@@ -633,8 +687,14 @@ mpm_status mpm_newton_step(mpm_ctx* c, mpm_stats* stats) {
     if (!c) return MPM_ERR_INVALID_ARG;
     if (!c->p2g_done) return fail(c, MPM_ERR_INVALID_ARG, "mpm_newton_step: call mpm_p2g first");
     cudaStream_t st = c->st;
-    MPM_CUDA(run_heat(c));
-    MPM_CUDA(run_newton(c));
+    {
+        PhaseTimer timer(c, 2);
+        MPM_CUDA(run_heat(c));
+    }
+    {
+        PhaseTimer timer(c, 3);
+        MPM_CUDA(run_newton(c));
+    }
     MPM_CUDA(cudaMemcpyAsync(c->hscal, c->d.scal, sizeof(SceneScal) * c->nsc, cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     mpm_status worst = MPM_OK;
@@ -650,6 +710,11 @@ mpm_status mpm_newton_step(mpm_ctx* c, mpm_stats* stats) {
             for (int q = 0; q < 3; ++q) stats[s].momentum[q] = h.mom[q];
         }
         if (h.status != 0 && worst == MPM_OK) worst = (mpm_status)h.status;
+        if (c->prof) {
+            c->pr.newton_iters += h.newton_it;
+            c->pr.cg_iters += h.cg_total;
+            c->pr.heat_iters += h.heat_it;
+        }
     }
     c->step_ready = true;
     mpm_status e = check_device_error(c);
@@ -661,6 +726,7 @@ mpm_status mpm_newton_step(mpm_ctx* c, mpm_stats* stats) {
 mpm_status mpm_g2p(mpm_ctx* c) {
     if (!c) return MPM_ERR_INVALID_ARG;
     if (!c->p2g_done) return fail(c, MPM_ERR_INVALID_ARG, "mpm_g2p: call mpm_newton_step first");
+    PhaseTimer timer(c, 4);
     MPM_CUDA(launch_g2p(c));
     c->resampled = false;
     c->p2g_done = false;
@@ -693,6 +759,24 @@ mpm_status mpm_counts(mpm_ctx* c, int64_t* n_particles, int64_t* n_surface, int6
     if (n_surface) *n_surface = c->ns;
     if (n_blocks) *n_blocks = c->NB;
     if (n_work_blocks) *n_work_blocks = c->NW;
+    return MPM_OK;
+}
+
+mpm_status mpm_profile_enable(mpm_ctx* c, int32_t enable) {
+    if (!c) return MPM_ERR_INVALID_ARG;
+    c->prof = enable != 0;
+    if (c->prof) {
+        memset(&c->pr, 0, sizeof(c->pr));
+        c->pr.kernel_launches = -c->launches;   // counts from here
+    }
+    c->nev = 0;
+    return MPM_OK;
+}
+
+mpm_status mpm_get_profile(mpm_ctx* c, mpm_profile* out) {
+    if (!c || !out) return MPM_ERR_INVALID_ARG;
+    *out = c->pr;
+    out->kernel_launches = c->pr.kernel_launches + c->launches;
     return MPM_OK;
 }
 

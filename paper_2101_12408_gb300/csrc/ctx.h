@@ -102,7 +102,16 @@ struct mpm_ctx {
     int* hcounts = nullptr;            // pinned
     std::string last_error;
     std::vector<void*> allocs;
+    // profiling
+    long long launches = 0;
+    bool prof = false;
+    mpm_profile pr{};
+    cudaEvent_t ev[2 * 16 + 2] = {};
+    int nev = 0;                       // recorded apply event pairs pending
 };
+
+// counts every kernel launch of a context (`c` in scope); usable as a statement prefix
+#define MPM_LAUNCH for (int once_ = (c->launches++, 1); once_; once_ = 0)
 
 namespace mpm {
 
@@ -110,7 +119,7 @@ namespace mpm {
 cudaError_t launch_sort_particles(mpm_ctx* c);
 cudaError_t launch_sort_surface(mpm_ctx* c);
 cudaError_t launch_build_blocks(mpm_ctx* c);   // needs parents (balance particles)
-cudaError_t launch_exclusive_scan(const int* in, int* out, long long n, int* tmp, cudaStream_t st);
+cudaError_t launch_exclusive_scan(mpm_ctx* c, const int* in, int* out, long long n, int* tmp, cudaStream_t st);
 
 // ---- transfer.cu ----
 cudaError_t launch_nearest_parent(mpm_ctx* c);
@@ -130,5 +139,9 @@ cudaError_t launch_mass_term(mpm_ctx* c, const void* p, void* u);
 // ---- heat.cu ----
 cudaError_t run_heat(mpm_ctx* c);
 cudaError_t launch_heat_apply(mpm_ctx* c, const void* T, void* out);
+
+// ---- profiling helpers (api.cu) ----
+void prof_mark_apply(mpm_ctx* c, bool begin);
+void prof_collect_applies(mpm_ctx* c, bool heat);
 
 }  // namespace mpm

@@ -293,7 +293,7 @@ cudaError_t heat_apply_t(mpm_ctx* c, const void* T, void* out, int check_done) {
     a.sa2 = (const R*)d.sa[2];
     a.swn = (const R*)d.swn;
     a.check_done = check_done;
-    k_heat_apply<R><<<c->NW, NT, 0, c->st>>>(a);
+    MPM_LAUNCH k_heat_apply<R><<<c->NW, NT, 0, c->st>>>(a);
     return cudaGetLastError();
 }
 
@@ -303,8 +303,8 @@ cudaError_t run_heat_t(mpm_ctx* c) {
     cudaStream_t st = c->st;
     int nb = c->NB;
     unsigned g = nblk((long long)nb * 64, 256);
-    k_heat_begin<<<nblk(c->nsc, 128), 128, 0, st>>>(d.scal, d.sc, c->nsc);
-    k_heat_prep<R><<<g, 256, 0, st>>>(nb, d.gTn, (const R*)d.hinvd, (R*)d.hT, (R*)d.hu);
+    MPM_LAUNCH k_heat_begin<<<nblk(c->nsc, 128), 128, 0, st>>>(d.scal, d.sc, c->nsc);
+    MPM_LAUNCH k_heat_prep<R><<<g, 256, 0, st>>>(nb, d.gTn, (const R*)d.hinvd, (R*)d.hT, (R*)d.hu);
     heat_apply_t<R>(c, d.hT, d.hu, 0);
     cudaMemsetAsync(d.hrhs, 0, sizeof(double) * (size_t)nb * 64, st);
     if (c->NW > 0) {
@@ -334,13 +334,13 @@ cudaError_t run_heat_t(mpm_ctx* c) {
         a.Tbar = d.Tbar;
         a.gmT = d.gmT;
         a.rhs = d.hrhs;
-        k_heat_rhs<<<c->NW, NT, 0, st>>>(a);
+        MPM_LAUNCH k_heat_rhs<<<c->NW, NT, 0, st>>>(a);
     }
-    k_heat_b<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gmT, d.gTn, (const R*)d.hu, d.hrhs);
+    MPM_LAUNCH k_heat_b<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gmT, d.gTn, (const R*)d.hu, d.hrhs);
     cudaError_t e = launch_cg(c, 1);
     if (e != cudaSuccess) return e;
-    k_heat_finish<R><<<g, 256, 0, st>>>(nb, d.slot_coord, d.sc, d.gTn, (const R*)d.hinvd, (const R*)d.hx, d.gThat);
-    k_heat_end<<<nblk(c->nsc, 128), 128, 0, st>>>(d.scal, c->nsc);
+    MPM_LAUNCH k_heat_finish<R><<<g, 256, 0, st>>>(nb, d.slot_coord, d.sc, d.gTn, (const R*)d.hinvd, (const R*)d.hx, d.gThat);
+    MPM_LAUNCH k_heat_end<<<nblk(c->nsc, 128), 128, 0, st>>>(d.scal, c->nsc);
     return cudaGetLastError();
 }
 
@@ -356,10 +356,10 @@ cudaError_t launch_heat_full(mpm_ctx* c, const void* T, void* out) {
     unsigned g = nblk((long long)c->NB * 64, 256);
     if (c->rsize == 4) {
         heat_apply_t<float>(c, T, out, 0);
-        k_heat_diag<float><<<g, 256, 0, c->st>>>(c->NB, (const float*)c->d.hinvd, (const float*)T, (float*)out);
+        MPM_LAUNCH k_heat_diag<float><<<g, 256, 0, c->st>>>(c->NB, (const float*)c->d.hinvd, (const float*)T, (float*)out);
     } else {
         heat_apply_t<double>(c, T, out, 0);
-        k_heat_diag<double><<<g, 256, 0, c->st>>>(c->NB, (const double*)c->d.hinvd, (const double*)T, (double*)out);
+        MPM_LAUNCH k_heat_diag<double><<<g, 256, 0, c->st>>>(c->NB, (const double*)c->d.hinvd, (const double*)T, (double*)out);
     }
     return cudaGetLastError();
 }

@@ -13,7 +13,10 @@
 //   solid   dt^2 V^0 dP(F; dL F^n) F^nT gradN_i
 //   surface dt^2 dG gradN_i(s_r), dG = -k [dn]x F^ [a]x  (+ -k [n]x dF^ [a]x exact),
 //           dn = (I - n n^T) dc/|c|, dc = dcof(F^)[dF^] a, with G = -k [n]x F^ [a]x the
-//           gradient of k |cof(F^) a| (the projected mode keeps the PSD Gauss-Newton part).
+//           gradient of k |cof(F^) a|. The projected mode (the definiteness fix) keeps the
+//           Gauss-Newton term and the positive, conformal part of the cofactor curvature
+//           n . cof(dF^) a (which has eigenvalues +-|a|), so it is PSD and still stiff
+//           against in-plane dilation of the surface.
 #include "ctx.h"
 #include "polar.cuh"
 
@@ -46,6 +49,53 @@ __device__ __forceinline__ void surf_G(R k, const R* n, const R* F, const R* a, 
     matmul3<R>(An, T1, G);
 #pragma unroll
     for (int q = 0; q < 9; ++q) G[q] *= -k;
+}
+
+// unit t1, t2 with (t1, t2, u) right-handed
+template <typename R>
+__device__ __forceinline__ void tangent_frame(const R* u, R* t1, R* t2) {
+    R ax = fabs(u[0]), ay = fabs(u[1]), az = fabs(u[2]);
+    int k = ax <= ay ? (ax <= az ? 0 : 2) : (ay <= az ? 1 : 2);
+    R e[3] = {R(0), R(0), R(0)};
+    e[k] = R(1);
+    R d = u[k];
+    R t[3] = {e[0] - d * u[0], e[1] - d * u[1], e[2] - d * u[2]};
+    R inv = R(1) / sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    t1[0] = t[0] * inv;
+    t1[1] = t[1] * inv;
+    t1[2] = t[2] * inv;
+    t2[0] = u[1] * t1[2] - u[2] * t1[1];
+    t2[1] = u[2] * t1[0] - u[0] * t1[2];
+    t2[2] = u[0] * t1[1] - u[1] * t1[0];
+}
+
+// Positive (conformal) part of the cofactor curvature n . cof(X) a, added to G:
+// with x_ij = t_i . X s_j in frames (t1, t2, n), (s1, s2, a/|a|),
+// G += k |a|/2 [(x11 + x22)(t1 s1^T + t2 s2^T) + (x12 - x21)(t1 s2^T - t2 s1^T)].
+template <typename R>
+__device__ __forceinline__ void add_conformal(R k, const R* n, const R* a, const R* X, R* G) {
+    R an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    R ah[3] = {a[0] / an, a[1] / an, a[2] / an};
+    R t1[3], t2[3], s1[3], s2[3];
+    tangent_frame<R>(n, t1, t2);
+    tangent_frame<R>(ah, s1, s2);
+    R Xs1[3], Xs2[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        Xs1[i] = X[3 * i] * s1[0] + X[3 * i + 1] * s1[1] + X[3 * i + 2] * s1[2];
+        Xs2[i] = X[3 * i] * s2[0] + X[3 * i + 1] * s2[1] + X[3 * i + 2] * s2[2];
+    }
+    R x11 = t1[0] * Xs1[0] + t1[1] * Xs1[1] + t1[2] * Xs1[2];
+    R x22 = t2[0] * Xs2[0] + t2[1] * Xs2[1] + t2[2] * Xs2[2];
+    R x12 = t1[0] * Xs2[0] + t1[1] * Xs2[1] + t1[2] * Xs2[2];
+    R x21 = t2[0] * Xs1[0] + t2[1] * Xs1[1] + t2[2] * Xs1[2];
+    R p = R(0.5) * k * an * (x11 + x22);
+    R q = R(0.5) * k * an * (x12 - x21);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            G[3 * i + j] += p * (t1[i] * s1[j] + t2[i] * s2[j]) + q * (t1[i] * s2[j] - t2[i] * s1[j]);
 }
 
 template <typename R>
@@ -558,6 +608,8 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs<R> a) {
             surf_G<R>(k * dt * dt, nv, dFh, av, G2);
 #pragma unroll
             for (int q = 0; q < 9; ++q) G[q] += G2[q];
+        } else {
+            add_conformal<R>(k * dt * dt, nv, av, dFh, G);
         }
         for (int cz = 0; cz < 3; ++cz)
             for (int cy = 0; cy < 3; ++cy)
@@ -1270,7 +1322,7 @@ cudaError_t pack_step_t(mpm_ctx* c) {
         for (int q = 0; q < 9; ++q) Fn.a[q] = (R*)d.Fn[q];
         Ptrs9 F;
         for (int q = 0; q < 9; ++q) F.a[q] = d.F[q];
-        k_pack_volume<R><<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, Ptrs3{{d.x[0], d.x[1], d.x[2]}}, d.J, F, d.V0, d.T,
+        MPM_LAUNCH k_pack_volume<R><<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, Ptrs3{{d.x[0], d.x[1], d.x[2]}}, d.J, F, d.V0, d.T,
                                                            d.phase, d.psc, d.sc, pu, (R*)d.kappa, (R*)d.cvisc, Fn,
                                                            (R*)d.lame[0], (R*)d.lame[1], (R*)d.Vn);
     }
@@ -1280,7 +1332,7 @@ cudaError_t pack_step_t(mpm_ctx* c) {
             su.a[q] = (R*)d.su[q];
             sa.a[q] = (R*)d.sa[q];
         }
-        k_pack_surface<R><<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, Ptrs3{{d.s[0], d.s[1], d.s[2]}},
+        MPM_LAUNCH k_pack_surface<R><<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, Ptrs3{{d.s[0], d.s[1], d.s[2]}},
                                                             Ptrs3{{d.dA[0], d.dA[1], d.dA[2]}}, d.gamma, d.ssc, d.sc, su,
                                                             sa, (R*)d.sg);
     }
@@ -1299,18 +1351,21 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     const int chunk = 8;
     if (NC_is_heat) {
         auto a = make_cg_args<R, 1>(c);
-        k_cg_init<R, 1><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
+        MPM_LAUNCH k_cg_init<R, 1><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
         for (int it = 0; it < maxit; it += chunk) {
             for (int k = 0; k < chunk; ++k) {
+                prof_mark_apply(c, true);
                 launch_heat_apply(c, d.hp, d.hu);
-                k_cg_pq<R, 1><<<nb, 64, 0, st>>>(a);
-                k_cg_update<R, 1><<<nb, 64, 0, st>>>(a);
-                k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 1);
-                k_cg_p<R, 1><<<nb, 64, 0, st>>>(a);
+                prof_mark_apply(c, false);
+                MPM_LAUNCH k_cg_pq<R, 1><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_update<R, 1><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 1);
+                MPM_LAUNCH k_cg_p<R, 1><<<nb, 64, 0, st>>>(a);
             }
             cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return e;
+            prof_collect_applies(c, NC_is_heat != 0);
             bool all = true;
             for (int s = 0; s < ns; ++s) all = all && c->hscal[s].cg_done;
             if (all) break;
@@ -1318,18 +1373,21 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     } else {
         auto a = make_cg_args<R, 3>(c);
         auto ap = make_apply_args<R>(c, d.cp, d.cu, MPM_HESS_PROJECTED, 1);
-        k_cg_init<R, 3><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
+        MPM_LAUNCH k_cg_init<R, 3><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
         for (int it = 0; it < maxit; it += chunk) {
             for (int k = 0; k < chunk; ++k) {
-                if (c->NW > 0) k_apply<R><<<c->NW, NT, 0, st>>>(ap);
-                k_cg_pq<R, 3><<<nb, 64, 0, st>>>(a);
-                k_cg_update<R, 3><<<nb, 64, 0, st>>>(a);
-                k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 0);
-                k_cg_p<R, 3><<<nb, 64, 0, st>>>(a);
+                prof_mark_apply(c, true);
+                if (c->NW > 0) MPM_LAUNCH k_apply<R><<<c->NW, NT, 0, st>>>(ap);
+                prof_mark_apply(c, false);
+                MPM_LAUNCH k_cg_pq<R, 3><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_update<R, 3><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 0);
+                MPM_LAUNCH k_cg_p<R, 3><<<nb, 64, 0, st>>>(a);
             }
             cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return e;
+            prof_collect_applies(c, NC_is_heat != 0);
             bool all = true;
             for (int s = 0; s < ns; ++s) all = all && c->hscal[s].cg_done;
             if (all) break;
@@ -1342,7 +1400,7 @@ template <typename R>
 cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) {
     if (c->NW == 0) return cudaSuccess;
     auto a = make_eval_args<R>(c, want_grad, want_cache, skip_done);
-    k_eval<R><<<c->NW, NT, 0, c->st>>>(a);
+    MPM_LAUNCH k_eval<R><<<c->NW, NT, 0, c->st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1357,23 +1415,23 @@ cudaError_t newton_t(mpm_ctx* c) {
     cudaStream_t st = c->st;
     int nb = c->NB, ns = c->nsc;
     unsigned gs = nblk(ns, 128);
-    k_newton_begin<<<gs, 128, 0, st>>>(d.scal, ns);
-    k_newton_init_v<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.gvn, d.pcode, d.gv);
+    MPM_LAUNCH k_newton_begin<<<gs, 128, 0, st>>>(d.scal, ns);
+    MPM_LAUNCH k_newton_init_v<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.gvn, d.pcode, d.gv);
     int maxn = 0;
     for (auto& S : c->hsc) maxn = maxn > S.max_newton ? maxn : S.max_newton;
     for (int it = 0; it <= maxn; ++it) {
-        k_newton_iter_begin<<<gs, 128, 0, st>>>(d.scal, ns);
+        MPM_LAUNCH k_newton_iter_begin<<<gs, 128, 0, st>>>(d.scal, ns);
         cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
         eval_any(c, false, true, true, true);
-        k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 1);
-        k_newton_check<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
+        MPM_LAUNCH k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 1);
+        MPM_LAUNCH k_newton_check<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
         cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
         bool all = true;
         for (int s = 0; s < ns; ++s) all = all && c->hscal[s].newton_done;
         if (all) break;
-        k_cg_begin<<<gs, 128, 0, st>>>(d.scal, ns, 1);
+        MPM_LAUNCH k_cg_begin<<<gs, 128, 0, st>>>(d.scal, ns, 1);
         e = cg_solve_t<R>(c, 0, 1);
         if (e != cudaSuccess) return e;
         if (c->NW > 0) {
@@ -1399,18 +1457,18 @@ cudaError_t newton_t(mpm_ctx* c) {
             for (int q = 0; q < 9; ++q) a.F.a[q] = d.F[q];
             a.phase = d.phase;
             a.gamma = d.gamma;
-            k_linesearch<R><<<c->NW, NT, 0, st>>>(a);
+            MPM_LAUNCH k_linesearch<R><<<c->NW, NT, 0, st>>>(a);
         }
-        k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, (const R*)d.cx);
-        k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
-        k_newton_update<R><<<nb, 64, 0, st>>>(d.slot_coord, d.scal, (const R*)d.cx, d.gv);
+        MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, (const R*)d.cx);
+        MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
+        MPM_LAUNCH k_newton_update<R><<<nb, 64, 0, st>>>(d.slot_coord, d.scal, (const R*)d.cx, d.gv);
     }
     // final explicit force evaluation in float64
-    k_zero_mom<<<gs, 128, 0, st>>>(d.scal, ns);
+    MPM_LAUNCH k_zero_mom<<<gs, 128, 0, st>>>(d.scal, ns);
     cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
     eval_any(c, true, true, false, false);
-    k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
-    k_newton_final<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gv, d.ggrad, d.pcode, d.gvhat);
+    MPM_LAUNCH k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
+    MPM_LAUNCH k_newton_final<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gv, d.ggrad, d.pcode, d.gvhat);
     return cudaGetLastError();
 }
 
@@ -1424,11 +1482,11 @@ cudaError_t launch_pack_step(mpm_ctx* c) {
 cudaError_t launch_eval(mpm_ctx* c, bool fp64_math, bool want_cache) {
     Dev& d = c->d;
     int ns = c->nsc;
-    k_newton_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
-    k_newton_iter_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
+    MPM_LAUNCH k_newton_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
+    MPM_LAUNCH k_newton_iter_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
     cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)c->NB * 192, c->st);
     eval_any(c, fp64_math, true, want_cache, false);
-    if (c->NB > 0) k_node_grad<<<c->NB, 64, 0, c->st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
+    if (c->NB > 0) MPM_LAUNCH k_node_grad<<<c->NB, 64, 0, c->st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
     return cudaGetLastError();
 }
 
@@ -1436,10 +1494,10 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
     if (c->NW == 0) return cudaSuccess;
     if (c->rsize == 4) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
-        k_apply<float><<<c->NW, NT, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply<float><<<c->NW, NT, 0, c->st>>>(a);
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
-        k_apply<double><<<c->NW, NT, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply<double><<<c->NW, NT, 0, c->st>>>(a);
     }
     return cudaGetLastError();
 }
@@ -1456,7 +1514,7 @@ cudaError_t launch_cg(mpm_ctx* c, int heat) {
 }
 
 cudaError_t launch_cg_begin(mpm_ctx* c) {
-    k_cg_begin<<<nblk(c->nsc, 128), 128, 0, c->st>>>(c->d.scal, c->nsc, 0);
+    MPM_LAUNCH k_cg_begin<<<nblk(c->nsc, 128), 128, 0, c->st>>>(c->d.scal, c->nsc, 0);
     return cudaGetLastError();
 }
 
@@ -1465,9 +1523,9 @@ cudaError_t launch_dense_to_grid(mpm_ctx* c, int scene, const void* dense, void*
     unsigned g = nblk((long long)c->NB * 64, 256);
     Dev& d = c->d;
     if (rsize == 8)
-        k_dense_to_grid<double, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)dense, (double*)grid, comps);
+        MPM_LAUNCH k_dense_to_grid<double, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)dense, (double*)grid, comps);
     else
-        k_dense_to_grid<float, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)dense, (float*)grid, comps);
+        MPM_LAUNCH k_dense_to_grid<float, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)dense, (float*)grid, comps);
     return cudaGetLastError();
 }
 
@@ -1476,13 +1534,13 @@ cudaError_t launch_grid_to_dense(mpm_ctx* c, int scene, const void* grid, void* 
     unsigned g = nblk((long long)c->NB * 64, 256);
     Dev& d = c->d;
     if (rsize_in == 8 && rsize_out == 8)
-        k_grid_to_dense<double, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)grid, (double*)dense, comps);
+        MPM_LAUNCH k_grid_to_dense<double, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)grid, (double*)dense, comps);
     else if (rsize_in == 4 && rsize_out == 4)
-        k_grid_to_dense<float, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)grid, (float*)dense, comps);
+        MPM_LAUNCH k_grid_to_dense<float, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)grid, (float*)dense, comps);
     else if (rsize_in == 4 && rsize_out == 8)
-        k_grid_to_dense<float, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)grid, (double*)dense, comps);
+        MPM_LAUNCH k_grid_to_dense<float, double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const float*)grid, (double*)dense, comps);
     else
-        k_grid_to_dense<double, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)grid, (float*)dense, comps);
+        MPM_LAUNCH k_grid_to_dense<double, float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, scene, d.sc, (const double*)grid, (float*)dense, comps);
     return cudaGetLastError();
 }
 
@@ -1490,8 +1548,8 @@ cudaError_t launch_project_vec(mpm_ctx* c, void* vec, int rsize) {
     if (c->NB == 0) return cudaSuccess;
     unsigned g = nblk((long long)c->NB * 64, 256);
     Dev& d = c->d;
-    if (rsize == 8) k_project_vec<double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, (double*)vec);
-    else k_project_vec<float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, (float*)vec);
+    if (rsize == 8) MPM_LAUNCH k_project_vec<double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, (double*)vec);
+    else MPM_LAUNCH k_project_vec<float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, (float*)vec);
     return cudaGetLastError();
 }
 
@@ -1499,8 +1557,8 @@ cudaError_t launch_mass_term(mpm_ctx* c, const void* p, void* u) {
     if (c->NB == 0) return cudaSuccess;
     unsigned g = nblk((long long)c->NB * 64, 256);
     Dev& d = c->d;
-    if (c->rsize == 8) k_mass_term<double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, d.gm, (const double*)p, (double*)u);
-    else k_mass_term<float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, d.gm, (const float*)p, (float*)u);
+    if (c->rsize == 8) MPM_LAUNCH k_mass_term<double><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, d.gm, (const double*)p, (double*)u);
+    else MPM_LAUNCH k_mass_term<float><<<g, 256, 0, c->st>>>(c->NB, d.slot_coord, d.sc, d.pcode, d.gm, (const float*)p, (float*)u);
     return cudaGetLastError();
 }
 

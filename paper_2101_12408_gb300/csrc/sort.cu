@@ -222,12 +222,12 @@ inline int nblocks(long long n, int nt) { return (int)((n + nt - 1) / nt); }
 
 }  // namespace
 
-cudaError_t launch_exclusive_scan(const int* in, int* out, long long n, int* tmp, cudaStream_t st) {
+cudaError_t launch_exclusive_scan(mpm_ctx* c, const int* in, int* out, long long n, int* tmp, cudaStream_t st) {
     // out[0..n] = exclusive scan of in[0..n-1]; out[n] = total
     long long tiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
-    k_scan_partials<<<(unsigned)tiles, SCAN_NT, 0, st>>>(in, n, tmp);
-    k_scan_top<<<1, SCAN_NT, 0, st>>>(tmp, (int)tiles);
-    k_scan_final<<<(unsigned)tiles, SCAN_NT, 0, st>>>(in, n, tmp, out);
+    MPM_LAUNCH k_scan_partials<<<(unsigned)tiles, SCAN_NT, 0, st>>>(in, n, tmp);
+    MPM_LAUNCH k_scan_top<<<1, SCAN_NT, 0, st>>>(tmp, (int)tiles);
+    MPM_LAUNCH k_scan_final<<<(unsigned)tiles, SCAN_NT, 0, st>>>(in, n, tmp, out);
     return cudaGetLastError();
 }
 
@@ -237,11 +237,11 @@ cudaError_t launch_sort_particles(mpm_ctx* c) {
     int n = (int)c->np;
     cudaMemsetAsync(d.cell_count, 0, sizeof(int) * c->total_cells, st);
     if (n > 0) {
-        k_keys<<<nblocks(n, 256), 256, 0, st>>>(n, d.x[0], d.x[1], d.x[2], d.psc, d.sc, d.key, d.rank, d.cell_count, d.err);
+        MPM_LAUNCH k_keys<<<nblocks(n, 256), 256, 0, st>>>(n, d.x[0], d.x[1], d.x[2], d.psc, d.sc, d.key, d.rank, d.cell_count, d.err);
     }
-    launch_exclusive_scan(d.cell_count, d.cell_start, c->total_cells, d.scan_tmp, st);
+    launch_exclusive_scan(c, d.cell_count, d.cell_start, c->total_cells, d.scan_tmp, st);
     if (n == 0) return cudaGetLastError();
-    k_perm<<<nblocks(n, 256), 256, 0, st>>>(n, d.key, d.rank, d.cell_start, d.perm);
+    MPM_LAUNCH k_perm<<<nblocks(n, 256), 256, 0, st>>>(n, d.key, d.rank, d.cell_start, d.perm);
     cudaMemcpyAsync(c->hcounts + 2, d.cell_start + c->total_cells, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
@@ -250,21 +250,21 @@ cudaError_t launch_sort_particles(mpm_ctx* c) {
     if (n == 0) return cudaGetLastError();
     int g = nblocks(n, 256);
     for (int a = 0; a < 3; ++a) {
-        k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.x[a], d.x2[a]);
-        k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.v[a], d.v2[a]);
-        k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.gT[a], d.gT22[a]);
+        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.x[a], d.x2[a]);
+        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.v[a], d.v2[a]);
+        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.gT[a], d.gT22[a]);
     }
     for (int a = 0; a < 9; ++a) {
-        k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.A[a], d.A2[a]);
-        k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.F[a], d.F2[a]);
+        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.A[a], d.A2[a]);
+        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.F[a], d.F2[a]);
     }
-    k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.m, d.m2);
-    k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.V0, d.V02);
-    k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.J, d.J2);
-    k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.T, d.T2);
-    k_gather<uint8_t><<<g, 256, 0, st>>>(n, d.perm, d.phase, d.phase2);
-    k_gather<int><<<g, 256, 0, st>>>(n, d.perm, d.pid, d.pid2);
-    k_gather<int><<<g, 256, 0, st>>>(n, d.perm, d.psc, d.psc2);
+    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.m, d.m2);
+    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.V0, d.V02);
+    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.J, d.J2);
+    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.T, d.T2);
+    MPM_LAUNCH k_gather<uint8_t><<<g, 256, 0, st>>>(n, d.perm, d.phase, d.phase2);
+    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.perm, d.pid, d.pid2);
+    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.perm, d.psc, d.psc2);
     for (int a = 0; a < 3; ++a) {
         std::swap(d.x[a], d.x2[a]);
         std::swap(d.v[a], d.v2[a]);
@@ -290,11 +290,11 @@ cudaError_t launch_sort_surface(mpm_ctx* c) {
     int n = (int)c->ns;
     cudaMemsetAsync(d.scell_count, 0, sizeof(int) * c->total_cells, st);
     if (n > 0) {
-        k_keys<<<nblocks(n, 256), 256, 0, st>>>(n, d.s[0], d.s[1], d.s[2], d.ssc, d.sc, d.skey, d.srank, d.scell_count, d.err);
+        MPM_LAUNCH k_keys<<<nblocks(n, 256), 256, 0, st>>>(n, d.s[0], d.s[1], d.s[2], d.ssc, d.sc, d.skey, d.srank, d.scell_count, d.err);
     }
-    launch_exclusive_scan(d.scell_count, d.scell_start, c->total_cells, d.scan_tmp, st);
+    launch_exclusive_scan(c, d.scell_count, d.scell_start, c->total_cells, d.scan_tmp, st);
     if (n == 0) return cudaGetLastError();
-    k_perm<<<nblocks(n, 256), 256, 0, st>>>(n, d.skey, d.srank, d.scell_start, d.sperm);
+    MPM_LAUNCH k_perm<<<nblocks(n, 256), 256, 0, st>>>(n, d.skey, d.srank, d.scell_start, d.sperm);
     cudaMemcpyAsync(c->hcounts + 3, d.scell_start + c->total_cells, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
@@ -303,14 +303,14 @@ cudaError_t launch_sort_surface(mpm_ctx* c) {
     if (n == 0) return cudaGetLastError();
     int g = nblocks(n, 256);
     for (int a = 0; a < 3; ++a) {
-        k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.s[a], d.s2[a]);
-        k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.dA[a], d.dA2[a]);
+        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.s[a], d.s2[a]);
+        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.dA[a], d.dA2[a]);
     }
-    k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.bheat, d.bheat2);
-    k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.Tbar, d.Tbar2);
-    k_gather<uint8_t><<<g, 256, 0, st>>>(n, d.sperm, d.kind, d.kind2);
-    k_gather<int><<<g, 256, 0, st>>>(n, d.sperm, d.sid, d.sid2);
-    k_gather<int><<<g, 256, 0, st>>>(n, d.sperm, d.ssc, d.ssc2);
+    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.bheat, d.bheat2);
+    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.Tbar, d.Tbar2);
+    MPM_LAUNCH k_gather<uint8_t><<<g, 256, 0, st>>>(n, d.sperm, d.kind, d.kind2);
+    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.sperm, d.sid, d.sid2);
+    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.sperm, d.ssc, d.ssc2);
     for (int a = 0; a < 3; ++a) {
         std::swap(d.s[a], d.s2[a]);
         std::swap(d.dA[a], d.dA2[a]);
@@ -330,21 +330,21 @@ cudaError_t launch_build_blocks(mpm_ctx* c) {
     cudaMemsetAsync(d.bflag, 0, sizeof(int) * nblk, st);
     cudaMemsetAsync(d.bwork, 0, sizeof(int) * nblk, st);
     if (c->np > 0)
-        k_mark<<<nblocks(c->np, 256), 256, 0, st>>>((int)c->np, d.x[0], d.x[1], d.x[2], d.psc, nullptr, d.sc, d.bflag, d.bwork, d.err);
+        MPM_LAUNCH k_mark<<<nblocks(c->np, 256), 256, 0, st>>>((int)c->np, d.x[0], d.x[1], d.x[2], d.psc, nullptr, d.sc, d.bflag, d.bwork, d.err);
     if (c->ns > 0) {
-        k_mark<<<nblocks(c->ns, 256), 256, 0, st>>>((int)c->ns, d.s[0], d.s[1], d.s[2], d.ssc, nullptr, d.sc, d.bflag, d.bwork, d.err);
-        k_mark<<<nblocks(c->ns, 256), 256, 0, st>>>((int)c->ns, d.bpos[0], d.bpos[1], d.bpos[2], d.ssc, nullptr, d.sc, d.bflag, nullptr, d.err);
+        MPM_LAUNCH k_mark<<<nblocks(c->ns, 256), 256, 0, st>>>((int)c->ns, d.s[0], d.s[1], d.s[2], d.ssc, nullptr, d.sc, d.bflag, d.bwork, d.err);
+        MPM_LAUNCH k_mark<<<nblocks(c->ns, 256), 256, 0, st>>>((int)c->ns, d.bpos[0], d.bpos[1], d.bpos[2], d.ssc, nullptr, d.sc, d.bflag, nullptr, d.err);
     }
-    launch_exclusive_scan(d.bflag, d.bscan, nblk, d.scan_tmp, st);
-    k_slots<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bflag, d.bscan, d.sc, c->nsc, d.bslot, d.slot_coord, d.counts);
-    launch_exclusive_scan(d.bwork, d.bscan, nblk, d.scan_tmp, st);
-    k_work<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bwork, d.bscan, d.bslot, d.work, d.work_gb, d.counts);
+    launch_exclusive_scan(c, d.bflag, d.bscan, nblk, d.scan_tmp, st);
+    MPM_LAUNCH k_slots<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bflag, d.bscan, d.sc, c->nsc, d.bslot, d.slot_coord, d.counts);
+    launch_exclusive_scan(c, d.bwork, d.bscan, nblk, d.scan_tmp, st);
+    MPM_LAUNCH k_work<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bwork, d.bscan, d.bslot, d.work, d.work_gb, d.counts);
     cudaMemcpyAsync(c->hcounts, d.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     c->NB = c->hcounts[0];
     c->NW = c->hcounts[1];
-    if (c->NB > 0) k_nbr<<<nblocks((long long)c->NB * 27, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.bslot, d.nbr);
+    if (c->NB > 0) MPM_LAUNCH k_nbr<<<nblocks((long long)c->NB * 27, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.bslot, d.nbr);
     return cudaGetLastError();
 }
 

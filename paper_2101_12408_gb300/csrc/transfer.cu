@@ -454,11 +454,11 @@ cudaError_t launch_nearest_parent(mpm_ctx* c) {
     cudaStream_t st = c->st;
     cudaMemsetAsync(d.gcount, 0, sizeof(int) * (c->np > 0 ? c->np : 1), st);
     if (c->ns > 0) {
-        k_nearest<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc,
+        MPM_LAUNCH k_nearest<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc,
                                                     P3{{d.x[0], d.x[1], d.x[2]}}, d.pid, d.cell_start, d.sc, d.parent,
                                                     W3{{d.bpos[0], d.bpos[1], d.bpos[2]}}, d.gcount, d.kind, d.err);
     }
-    if (c->np > 0) k_split<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, d.m, d.gcount, d.mt);
+    if (c->np > 0) MPM_LAUNCH k_split<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, d.m, d.gcount, d.mt);
     return cudaGetLastError();
 }
 
@@ -489,30 +489,30 @@ cudaError_t launch_p2g(mpm_ctx* c) {
         a.gmv = d.gmv;
         a.gmT = d.gmT;
         a.gmTT = d.gmTT;
-        k_p2g_volume<<<c->NW, NT, 0, st>>>(a);
+        MPM_LAUNCH k_p2g_volume<<<c->NW, NT, 0, st>>>(a);
     }
     if (c->ns > 0) {
         P9 A;
         for (int q = 0; q < 9; ++q) A.a[q] = d.A[q];
-        k_p2g_surface<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}},
+        MPM_LAUNCH k_p2g_surface<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}},
                                                         P3{{d.bpos[0], d.bpos[1], d.bpos[2]}}, d.ssc, d.parent,
                                                         P3{{d.x[0], d.x[1], d.x[2]}}, P3{{d.v[0], d.v[1], d.v[2]}}, A,
                                                         d.mt, d.bslot, d.sc, d.gm, d.gmv);
     }
     if (c->NB > 0) {
         if (c->rsize == 4)
-            k_grid_final<float><<<nblk(nn, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.gmv, d.gmT, d.gmTT,
+            MPM_LAUNCH k_grid_final<float><<<nblk(nn, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.gmv, d.gmT, d.gmTT,
                                                               d.gvn, d.gTn, d.pcode, (float*)d.invm, (float*)d.hinvd);
         else
-            k_grid_final<double><<<nblk(nn, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.gmv, d.gmT, d.gmTT,
+            MPM_LAUNCH k_grid_final<double><<<nblk(nn, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.gmv, d.gmT, d.gmTT,
                                                                d.gvn, d.gTn, d.pcode, (double*)d.invm, (double*)d.hinvd);
     }
     if (c->ns > 0) {
         if (c->rsize == 4)
-            k_gamma<float><<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc, d.kind,
+            MPM_LAUNCH k_gamma<float><<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc, d.kind,
                                                              d.bslot, d.sc, d.gmT, d.gTn, d.gamma, d.Tr, (float*)d.swn);
         else
-            k_gamma<double><<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc, d.kind,
+            MPM_LAUNCH k_gamma<double><<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, P3{{d.s[0], d.s[1], d.s[2]}}, d.ssc, d.kind,
                                                               d.bslot, d.sc, d.gmT, d.gTn, d.gamma, d.Tr, (double*)d.swn);
     }
     return cudaGetLastError();
@@ -537,12 +537,12 @@ cudaError_t launch_g2p(mpm_ctx* c) {
         a.T = d.T;
         for (int q = 0; q < 9; ++q) a.F.a[q] = d.F[q];
         for (int q = 0; q < 3; ++q) a.gT.a[q] = d.gT[q];
-        k_g2p_volume<<<nblk(c->np, 128), 128, 0, st>>>(a);
+        MPM_LAUNCH k_g2p_volume<<<nblk(c->np, 128), 128, 0, st>>>(a);
     }
     W12 acc;
     for (int q = 0; q < 12; ++q) acc.a[q] = d.acc[q];
     if (c->ns > 0) {
-        k_g2p_surface<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, W3{{d.s[0], d.s[1], d.s[2]}},
+        MPM_LAUNCH k_g2p_surface<<<nblk(c->ns, 128), 128, 0, st>>>((int)c->ns, W3{{d.s[0], d.s[1], d.s[2]}},
                                                         W3{{d.dA[0], d.dA[1], d.dA[2]}},
                                                         P3{{d.bpos[0], d.bpos[1], d.bpos[2]}}, d.ssc, d.parent,
                                                         P3{{d.x[0], d.x[1], d.x[2]}}, d.mt, d.bslot, d.sc, d.gvhat, acc);
@@ -553,7 +553,7 @@ cudaError_t launch_g2p(mpm_ctx* c) {
             A.a[q] = d.A[q];
             F.a[q] = d.F[q];
         }
-        k_g2p_final<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, W3{{d.x[0], d.x[1], d.x[2]}},
+        MPM_LAUNCH k_g2p_final<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, W3{{d.x[0], d.x[1], d.x[2]}},
                                                       W3{{d.v[0], d.v[1], d.v[2]}}, A, d.m, d.psc, d.sc, acc, d.phase,
                                                       d.J, F, d.T);
     }

@@ -32,7 +32,7 @@ FIELD_COMPS = {FIELD_MASS: 1, FIELD_MOMENTUM: 3, FIELD_VN: 3, FIELD_THERMAL_MASS
 EXPORTED = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_particles", "mpm_get_particles",
             "mpm_set_surface", "mpm_get_surface", "mpm_resample", "mpm_p2g", "mpm_get_grid", "mpm_set_velocity",
             "mpm_energy_gradient", "mpm_apply_hessian", "mpm_heat_apply", "mpm_newton_step", "mpm_g2p", "mpm_step",
-            "mpm_sync", "mpm_counts"]
+            "mpm_sync", "mpm_counts", "mpm_profile_enable", "mpm_get_profile"]
 
 
 class GridDesc(ctypes.Structure):
@@ -68,6 +68,19 @@ class Stats(ctypes.Structure):
                     momentum=list(self.momentum))
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("apply_launches", ctypes.c_int64), ("apply_ms", ctypes.c_double),
+                ("heat_apply_launches", ctypes.c_int64), ("heat_apply_ms", ctypes.c_double),
+                ("phase_ms", ctypes.c_double * 5), ("newton_iters", ctypes.c_int64), ("cg_iters", ctypes.c_int64),
+                ("heat_iters", ctypes.c_int64)]
+
+    def as_dict(self):
+        return dict(kernel_launches=self.kernel_launches, apply_launches=self.apply_launches, apply_ms=self.apply_ms,
+                    heat_apply_launches=self.heat_apply_launches, heat_apply_ms=self.heat_apply_ms,
+                    phase_ms=dict(zip(("resample", "p2g", "heat", "newton", "g2p"), list(self.phase_ms))),
+                    newton_iters=self.newton_iters, cg_iters=self.cg_iters, heat_iters=self.heat_iters)
+
+
 _vp = ctypes.c_void_p
 _lib.mpm_create.argtypes = [ctypes.POINTER(SceneDesc), ctypes.c_int32, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
 _lib.mpm_destroy.argtypes = [_vp]
@@ -89,6 +102,8 @@ _lib.mpm_g2p.argtypes = [_vp]
 _lib.mpm_step.argtypes = [_vp, _vp]
 _lib.mpm_sync.argtypes = [_vp]
 _lib.mpm_counts.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
+_lib.mpm_profile_enable.argtypes = [_vp, ctypes.c_int32]
+_lib.mpm_get_profile.argtypes = [_vp, ctypes.POINTER(Profile)]
 for _name in EXPORTED:
     if _name != "mpm_last_error":
         getattr(_lib, _name).restype = ctypes.c_int
@@ -273,6 +288,14 @@ class Context:
         v = [ctypes.c_int64() for _ in range(4)]
         self._check(_lib.mpm_counts(self.h, *[ctypes.byref(x) for x in v]))
         return dict(particles=v[0].value, surface=v[1].value, blocks=v[2].value, work_blocks=v[3].value)
+
+    def profile_enable(self, on=True):
+        self._check(_lib.mpm_profile_enable(self.h, 1 if on else 0))
+
+    def profile(self):
+        p = Profile()
+        self._check(_lib.mpm_get_profile(self.h, ctypes.byref(p)))
+        return p.as_dict()
 
     # ---- grid access / operators ----
     def _nodes(self, k):

@@ -93,6 +93,7 @@ class Scene:
     kind: np.ndarray = None
     b: np.ndarray = None              # boundary heating rate per sample
     Tbar: np.ndarray = None           # ambient temperature per sample
+    meta: dict = dataclasses.field(default_factory=dict)   # generator bookkeeping (droplet centres, radii)
 
     @property
     def n_particles(self) -> int:
@@ -273,8 +274,8 @@ def film(nx=128, ny=128, nz=32, height_cells=6, seed=1002, ppc_axis=2, surf_per_
 
 
 def incline(n=256, n_drops=40, r_range=(9.3, 24.8), seed=1003, ppc_axis=2, surf_per_cell=2.0,
-            gamma_lg=1.0, gamma_sl=0.5, lambda_l=1000.0, mu_l=0.0, rho=1.0, dt=1e-3,
-            angle_deg=30.0, gap_cells=(0.5, 3.0)) -> Scene:
+            gamma_lg=1.0, gamma_sl=0.5, lambda_l=1e6, mu_l=0.0, rho=1000.0, dt=1e-3,
+            angle_deg=30.0, gap_cells=(0.5, 120.0)) -> Scene:
     """Droplets above a 30-degree inclined slip plane, gravity -9.8 in y.
 
     The plane passes through (0.5, 0.2, 0.5) with normal (-sin a, cos a, 0).
@@ -292,9 +293,11 @@ def incline(n=256, n_drops=40, r_range=(9.3, 24.8), seed=1003, ppc_axis=2, surf_
     centers, radii = [], []
     tries = 0
     margin = 4 * dx
+    r = rng.uniform(*r_range) * dx
     while len(centers) < n_drops and tries < 100000:
         tries += 1
-        r = rng.uniform(*r_range) * dx
+        if tries % 2000 == 0:  # a radius that does not fit is redrawn (rarely)
+            r = rng.uniform(*r_range) * dx
         gap = rng.uniform(*gap_cells) * dx
         x0 = rng.uniform(r + margin, 1.0 - r - margin)
         z0 = rng.uniform(r + margin, 1.0 - r - margin)
@@ -307,6 +310,7 @@ def incline(n=256, n_drops=40, r_range=(9.3, 24.8), seed=1003, ppc_axis=2, surf_
             continue
         centers.append(c)
         radii.append(r)
+        r = rng.uniform(*r_range) * dx
     xs, ss, dAs = [], [], []
     for c, r in zip(centers, radii):
         lo = np.floor((c - r) / dx).astype(int) - 1
@@ -326,7 +330,8 @@ def incline(n=256, n_drops=40, r_range=(9.3, 24.8), seed=1003, ppc_axis=2, surf_
                  gamma_law=GAMMA_CONST, gamma_lg=gamma_lg, gamma_sl=gamma_sl)
     walls = (WALL_STICKY,) * 6
     return Scene(name=f"incline{n}", n=(n, n, n), dx=dx, params=prm, walls=walls,
-                 plane_n=tuple(nrm), plane_d=d, plane_mode=WALL_SLIP, **P, **S)
+                 plane_n=tuple(nrm), plane_d=d, plane_mode=WALL_SLIP,
+                 meta=dict(centers=np.array(centers), radii=np.array(radii)), **P, **S)
 
 
 def wax(nx=256, ny=256, nz=128, cube_cells=96, seed=1004, ppc_axis=2, surf_per_cell=2,
@@ -419,3 +424,29 @@ def config(index: int, **kw):
     if index == 4:
         return batch(**kw)
     raise ValueError(index)
+
+
+def window(sc: Scene, center, size_cells: int, name=None) -> Scene:
+    """Sub-box of a scene: particles and samples within `size_cells` cells around
+    `center`, shifted into a grid of that size with the same dx and parameters
+    (a bounded sample of a large workload; droplets are independent within a step)."""
+    dx = sc.dx
+    c_cell = np.floor(np.asarray(center) / dx).astype(int)
+    lo = c_cell - size_cells // 2
+    lo = np.clip(lo, 0, np.asarray(sc.n) - size_cells)
+    shift = lo * dx
+    hi = shift + size_cells * dx
+    inside = np.all((sc.x >= shift + 2 * dx) & (sc.x < hi - 2 * dx), 1)
+    sin = np.all((sc.s >= shift + 2 * dx) & (sc.s < hi - 2 * dx), 1)
+    out = sc.copy()
+    out.name = name or f"{sc.name}_window{size_cells}"
+    out.n = (size_cells,) * 3
+    for f in ("x", "v", "A", "m", "V0", "J", "F", "T", "gradT", "phase"):
+        setattr(out, f, getattr(sc, f)[inside].copy())
+    out.x = out.x - shift
+    for f in ("s", "dA", "kind", "b", "Tbar"):
+        setattr(out, f, getattr(sc, f)[sin].copy())
+    out.s = out.s - shift
+    if sc.plane_mode:
+        out.plane_d = sc.plane_d - float(np.asarray(sc.plane_n) @ shift)
+    return out
