@@ -334,6 +334,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.scell_count, int, c->total_cells + 1); A_(d.scell_start, int, c->total_cells + 1);
     A_(d.bflag, int, NBc + 1); A_(d.bwork, int, NBc + 1); A_(d.bslot, int, NBc + 1); A_(d.bscan, int, NBc + 1);
     A_(d.slot_coord, int4, NBc + 1); A_(d.nbr, int, NBc * 27 + 27); A_(d.work, int, NBc + 1); A_(d.work_gb, int, NBc + 1);
+    A_(d.slot_gen, int, NBc + 1);
     A_(d.counts, int, 4);
     A_(d.scan_tmp, int, (c->total_cells + 1) / 4096 + 16);
     A_(d.gm, double, NN); A_(d.gmv, double, NN * 3); A_(d.gvn, double, NN * 3); A_(d.gmT, double, NN);

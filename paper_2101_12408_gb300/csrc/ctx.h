@@ -66,6 +66,7 @@ struct Dev {
     int* nbr;                       // 27 neighbour slots per slot
     int* work;                      // work slot list
     int* work_gb;
+    int* slot_gen;                  // per slot: interior particles needing the general operator
     int* counts;                    // [0] NB, [1] NW
     int* scan_tmp;
     // ---- grid (float64) ----

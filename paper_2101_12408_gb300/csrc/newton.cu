@@ -110,11 +110,15 @@ __device__ __forceinline__ void load_halo_vec(const int* __restrict__ nbr, int s
 
 template <typename R>
 __device__ __forceinline__ void load_halo_vec_d(const int* __restrict__ nbr, int slot, const double* __restrict__ vec, R (*sh)[HN]) {
+    // The halo is stored relative to the velocity of the block's first node,
+    // subtracted in float64: velocity gradients sum_i v_i gradN_i^T are unchanged
+    // (sum_i gradN_i = 0), but a common translation no longer cancels in R.
     for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
         int c = t / HN, h = t % HN;
         int ns, loc;
         halo_source(nbr, slot, h, ns, loc);
-        sh[c][h] = ns < 0 ? R(0) : (R)vec[ns * 192 + c * 64 + loc];
+        double ref = vec[slot * 192 + c * 64];
+        sh[c][h] = ns < 0 ? R(0) : (R)(vec[ns * 192 + c * 64 + loc] - ref);
     }
 }
 
@@ -153,10 +157,18 @@ template <typename R>
 __global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptrs9 F, const double* __restrict__ V0,
                               const double* __restrict__ T, const uint8_t* __restrict__ phase, const int* __restrict__ psc,
                               const SceneDev* __restrict__ sc, RPtr3<R> pu, R* __restrict__ kappa, R* __restrict__ cvisc,
-                              RPtr9<R> Fn, R* __restrict__ lmu, R* __restrict__ llam, R* __restrict__ Vn) {
+                              RPtr9<R> Fn, R* __restrict__ lmu, R* __restrict__ llam, R* __restrict__ Vn,
+                              const int* __restrict__ bslot, int* __restrict__ slot_gen) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     const SceneDev& S = sc[psc[i]];
+    {
+        int c[3];
+        for (int a = 0; a < 3; ++a) c[a] = (int)floor((x.a[a][i] - S.origin[a]) * S.inv_dx);
+        bool general = phase[i] != 0 || S.mu_l != 0.0;
+        long long gb = S.block_base + (c[0] >> 2) + (long long)S.nb[0] * ((c[1] >> 2) + (long long)S.nb[1] * (c[2] >> 2));
+        if (general) atomicAdd(&slot_gen[bslot[gb]], 1);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double u = (x.a[a][i] - S.origin[a]) * S.inv_dx;
@@ -478,6 +490,7 @@ struct ApplyArgs {
     RPtr9<R> sF;
     RPtr3<R> sn;
     const R* sic;
+    const int* slot_gen;      // general particles per slot
     int mode;
     int check_done;
 };
@@ -623,6 +636,427 @@ __global__ void __launch_bounds__(NT) k_apply(ApplyArgs<R> a) {
     }
     __syncthreads();
     flush_halo_vec<R>(a.nbr, slot, ua, a.u);
+}
+
+// ======================================================================
+// Hessian-vector operator, thread per cell (the production kernel)
+//
+// One CTA per block of 4x4x4 cells, one thread per cell. For a liquid particle
+// without viscosity the operator is rank one, u_i += kappa_p tr(dL_p) gradN_i(x_p),
+// and with the in-cell coordinate t in [0,1)^3 of the particle (x = (c + t) dx)
+// every 1-D weight and derivative is a polynomial of degree <= 2:
+//   w = (1/2 - t + t^2/2,  1/2 + t - t^2,  t^2/2),   dw/dt = (-1 + t, 1 - 2t, t).
+// So tr(dL)(t) = sum_ijk C_ijk tx^i ty^j tz^k with 26 coefficients (no t^2 t^2 t^2
+// term) fixed per cell by the 27 stencil values of p, and the cell's scatter is a
+// fixed linear map of the 26 moments M_ijk = sum_p s_p tx^i ty^j tz^k. Each cell
+// reads its 81 inputs and writes its 81 outputs once, whatever its particle count;
+// per particle only 26 + 26 multiply-adds remain. Solids, viscous liquids and
+// surface samples take the general per-particle path in the same CTA.
+// Shared layout x + 8 y + 52 z: the 32 cells of a warp hit 32 distinct banks.
+// ======================================================================
+constexpr int PY = 8, PZ = 52, PN = 312;
+__device__ __forceinline__ int pidx(int x, int y, int z) { return x + PY * y + PZ * z; }
+
+// power coefficients -> from node values (out_k = sum_c v_c W[c][k]) and derivatives
+template <typename R>
+__device__ __forceinline__ void wT(R v0, R v1, R v2, R& o0, R& o1, R& o2) {
+    o0 = R(0.5) * (v0 + v1);
+    o1 = v1 - v0;
+    o2 = R(0.5) * (v0 + v2) - v1;
+}
+template <typename R>
+__device__ __forceinline__ void dT(R v0, R v1, R v2, R& o0, R& o1) {
+    o0 = v1 - v0;
+    o1 = v0 - R(2) * v1 + v2;
+}
+// moments -> node values (n_c = sum_k W[c][k] m_k, n_a = sum_i D[a][i] m_i)
+template <typename R>
+__device__ __forceinline__ void wN(R m0, R m1, R m2, R& n0, R& n1, R& n2) {
+    n0 = R(0.5) * (m0 + m2) - m1;
+    n1 = R(0.5) * m0 + m1 - m2;
+    n2 = R(0.5) * m2;
+}
+template <typename R>
+__device__ __forceinline__ void dN(R m0, R m1, R& n0, R& n1, R& n2) {
+    n0 = m1 - m0;
+    n1 = m0 - R(2) * m1;
+    n2 = m1;
+}
+
+// C += coefficients of tr(dL) (without the 1/dx factor) for the cell at (lx, ly, lz)
+template <typename R>
+__device__ __forceinline__ void cell_coefficients(R (*ph)[PN], int lx, int ly, int lz, R C[3][3][3]) {
+    R Q1[3][3][3], Q2[3][3][3];
+    // x component: D along x, W along y and z
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            wT<R>(ph[0][pidx(lx + a, ly + b, lz)], ph[0][pidx(lx + a, ly + b, lz + 1)], ph[0][pidx(lx + a, ly + b, lz + 2)],
+                  Q1[a][b][0], Q1[a][b][1], Q1[a][b][2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) wT<R>(Q1[a][0][k], Q1[a][1][k], Q1[a][2][k], Q2[a][0][k], Q2[a][1][k], Q2[a][2][k]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R g0, g1;
+            dT<R>(Q2[0][j][k], Q2[1][j][k], Q2[2][j][k], g0, g1);
+            C[0][j][k] += g0;
+            C[1][j][k] += g1;
+        }
+    // y component: W along x, D along y, W along z
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            wT<R>(ph[1][pidx(lx + a, ly + b, lz)], ph[1][pidx(lx + a, ly + b, lz + 1)], ph[1][pidx(lx + a, ly + b, lz + 2)],
+                  Q1[a][b][0], Q1[a][b][1], Q1[a][b][2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dT<R>(Q1[a][0][k], Q1[a][1][k], Q1[a][2][k], Q2[a][0][k], Q2[a][1][k]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R g0, g1, g2;
+            wT<R>(Q2[0][j][k], Q2[1][j][k], Q2[2][j][k], g0, g1, g2);
+            C[0][j][k] += g0;
+            C[1][j][k] += g1;
+            C[2][j][k] += g2;
+        }
+    // z component: W along x and y, D along z
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            dT<R>(ph[2][pidx(lx + a, ly + b, lz)], ph[2][pidx(lx + a, ly + b, lz + 1)], ph[2][pidx(lx + a, ly + b, lz + 2)],
+                  Q1[a][b][0], Q1[a][b][1]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) wT<R>(Q1[a][0][k], Q1[a][1][k], Q1[a][2][k], Q2[a][0][k], Q2[a][1][k], Q2[a][2][k]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            R g0, g1, g2;
+            wT<R>(Q2[0][j][k], Q2[1][j][k], Q2[2][j][k], g0, g1, g2);
+            C[0][j][k] += g0;
+            C[1][j][k] += g1;
+            C[2][j][k] += g2;
+        }
+}
+
+// ua += node values of the cell's moments (without the 1/dx factor)
+template <typename R>
+__device__ __forceinline__ void cell_scatter(R M[3][3][3], R (*ua)[PN], int lx, int ly, int lz) {
+    R T1[3][3][3], T2[3][3][3];
+    // x component: D along x, W along y, z
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) wN<R>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wN<R>(T1[i][0][c], T1[i][1][c], T1[i][2][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            R n0, n1, n2;
+            dN<R>(T2[0][b][c], T2[1][b][c], n0, n1, n2);
+            atomicAdd(&ua[0][pidx(lx, ly + b, lz + c)], n0);
+            atomicAdd(&ua[0][pidx(lx + 1, ly + b, lz + c)], n1);
+            atomicAdd(&ua[0][pidx(lx + 2, ly + b, lz + c)], n2);
+        }
+    // y component: W along x, D along y, W along z
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) wN<R>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dN<R>(T1[i][0][c], T1[i][1][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            R n0, n1, n2;
+            wN<R>(T2[0][b][c], T2[1][b][c], T2[2][b][c], n0, n1, n2);
+            atomicAdd(&ua[1][pidx(lx, ly + b, lz + c)], n0);
+            atomicAdd(&ua[1][pidx(lx + 1, ly + b, lz + c)], n1);
+            atomicAdd(&ua[1][pidx(lx + 2, ly + b, lz + c)], n2);
+        }
+    // z component: W along x, y, D along z
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dN<R>(M[i][j][0], M[i][j][1], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wN<R>(T1[i][0][c], T1[i][1][c], T1[i][2][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            R n0, n1, n2;
+            wN<R>(T2[0][b][c], T2[1][b][c], T2[2][b][c], n0, n1, n2);
+            atomicAdd(&ua[2][pidx(lx, ly + b, lz + c)], n0);
+            atomicAdd(&ua[2][pidx(lx + 1, ly + b, lz + c)], n1);
+            atomicAdd(&ua[2][pidx(lx + 2, ly + b, lz + c)], n2);
+        }
+}
+
+// general per-particle operator (solid or viscous liquid) on the padded layout
+template <typename R>
+__device__ __forceinline__ void particle_general(const ApplyArgs<R>& a, int i, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
+    int lc[3];
+    R wgt[3][3], dw[3][3];
+    make_stencil_local<R>(a.pu.a[0][i], a.pu.a[1][i], a.pu.a[2][i], inv_dx, lc, wgt, dw);
+    R dL[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    R pq = ph[q][h];
+                    dL[3 * q] += pq * dNv[0];
+                    dL[3 * q + 1] += pq * dNv[1];
+                    dL[3 * q + 2] += pq * dNv[2];
+                }
+            }
+    R M[9];
+    if (a.phase[i] == 0) {
+        R s = a.kappa[i] * (dL[0] + dL[4] + dL[8]);
+        R cv = a.cvisc[i];
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) M[3 * q + e] = cv * R(0.5) * (dL[3 * q + e] + dL[3 * e + q]) + (q == e ? s : R(0));
+    } else {
+        R Fo[9], Fc[9], Rm[9], K[6], dF[9], dP[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            Fo[q] = a.Fn.a[q][i];
+            Fc[q] = a.scache.a[q][i];
+            Rm[q] = a.scache.a[9 + q][i];
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) K[q] = a.scache.a[18 + q][i];
+        matmul3<R>(dL, Fo, dF);
+        fcr_dP<R>(Fc, Rm, K, a.lmu[i], a.llam[i], dF, dP);
+        matmul3_bt<R>(dP, Fo, M);
+        R sc = dt * dt * (R)a.V0[i];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) M[q] *= sc;
+    }
+    for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], M[3 * q] * dNv[0] + M[3 * q + 1] * dNv[1] + M[3 * q + 2] * dNv[2]);
+            }
+}
+
+template <typename R>
+__device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
+    int lc[3];
+    R wgt[3][3], dw[3][3];
+    make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
+    R dFh[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    R pq = ph[q][h];
+                    dFh[3 * q] += pq * dNv[0];
+                    dFh[3 * q + 1] += pq * dNv[1];
+                    dFh[3 * q + 2] += pq * dNv[2];
+                }
+            }
+    R Fh[9], av[3], nv[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Fh[q] = a.sF.a[q][j];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        av[q] = a.sa.a[q][j];
+        nv[q] = a.sn.a[q][j];
+    }
+    R k = a.sg[j], ic = a.sic[j];
+    R dC[9];
+    dcofactor<R>(Fh, dFh, dC);
+    R dc[3] = {dC[0] * av[0] + dC[1] * av[1] + dC[2] * av[2], dC[3] * av[0] + dC[4] * av[1] + dC[5] * av[2],
+               dC[6] * av[0] + dC[7] * av[1] + dC[8] * av[2]};
+    R nd = nv[0] * dc[0] + nv[1] * dc[1] + nv[2] * dc[2];
+    R dn[3] = {(dc[0] - nd * nv[0]) * ic, (dc[1] - nd * nv[1]) * ic, (dc[2] - nd * nv[2]) * ic};
+    R G[9];
+    surf_G<R>(k * dt * dt, dn, Fh, av, G);
+    if (a.mode == MPM_HESS_EXACT) {
+        R G2[9];
+        surf_G<R>(k * dt * dt, nv, dFh, av, G2);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) G[q] += G2[q];
+    } else {
+        add_conformal<R>(k * dt * dt, nv, av, dFh, G);
+    }
+    for (int cz = 0; cz < 3; ++cz)
+        for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
+                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
+                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], G[3 * q] * dNv[0] + G[3 * q + 1] * dNv[1] + G[3 * q + 2] * dNv[2]);
+            }
+}
+
+constexpr int NT_CELL = 64;
+
+template <typename R>
+__global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
+    __shared__ R ph[3][PN];
+    __shared__ R ua[3][PN];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    if (a.check_done && a.scal[bc.w].cg_done) return;
+    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
+        int c = t / HN, h = t % HN;
+        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
+        int ns, loc;
+        halo_source(a.nbr, slot, h, ns, loc);
+        ph[c][pidx(hx, hy, hz)] = ns < 0 ? R(0) : a.p[ns * 192 + c * 64 + loc];
+        ua[c][pidx(hx, hy, hz)] = R(0);
+    }
+    __syncthreads();
+    const R dt = (R)S.dt;
+    const R inv_dx = (R)S.inv_dx;
+    // this thread's cell
+    const int cell = threadIdx.x;
+    const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
+    const int beg = a.cell_start[gb * 64 + cell], end = a.cell_start[gb * 64 + cell + 1];
+    if (end > beg) {
+        R C[3][3][3];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) (&C[0][0][0])[q] = R(0);
+        cell_coefficients<R>(ph, lx, ly, lz, C);
+        R M[3][3][3];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) (&M[0][0][0])[q] = R(0);
+        bool any = false;
+        const R s2 = inv_dx * inv_dx;
+        for (int i = beg; i < end; ++i) {
+            if (a.phase[i] != 0 || a.cvisc[i] != R(0)) continue;   // k_apply_general
+            any = true;
+            R tx = a.pu.a[0][i] - R(lx), ty = a.pu.a[1][i] - R(ly), tz = a.pu.a[2][i] - R(lz);
+            tx = fmin(fmax(tx, R(0)), R(1));
+            ty = fmin(fmax(ty, R(0)), R(1));
+            tz = fmin(fmax(tz, R(0)), R(1));
+            R px[3] = {R(1), tx, tx * tx};
+            R yz[3][3];
+            R py[3] = {R(1), ty, ty * ty}, pz[3] = {R(1), tz, tz * tz};
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) yz[j][k] = py[j] * pz[k];
+            R tr = R(0);
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (!(ii == 2 && j == 2 && k == 2)) tr += C[ii][j][k] * px[ii] * yz[j][k];
+            R s = a.kappa[i] * s2 * tr;
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii) {
+                R sx = s * px[ii];
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (!(ii == 2 && j == 2 && k == 2)) M[ii][j][k] += sx * yz[j][k];
+            }
+        }
+        if (any) cell_scatter<R>(M, ua, lx, ly, lz);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
+        int c = t / HN, h = t % HN;
+        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
+        R val = ua[c][pidx(hx, hy, hz)];
+        if (val == R(0)) continue;
+        int ns, loc;
+        halo_source(a.nbr, slot, h, ns, loc);
+        if (ns >= 0) atomicAdd(&a.u[ns * 192 + c * 64 + loc], val);
+    }
+}
+
+// Solids, viscous liquids and surface samples: one thread per particle or
+// sample, shared-memory accumulation on the padded halo. Blocks with none of
+// them return at once (slot_gen counts the block's general particles).
+template <typename R>
+__global__ void __launch_bounds__(NT_CELL) k_apply_general(ApplyArgs<R> a) {
+    __shared__ R ph[3][PN];
+    __shared__ R ua[3][PN];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    if (a.check_done && a.scal[bc.w].cg_done) return;
+    const int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    if (send == sbeg && a.slot_gen[slot] == 0) return;
+    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
+        int c = t / HN, h = t % HN;
+        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
+        int ns, loc;
+        halo_source(a.nbr, slot, h, ns, loc);
+        ph[c][pidx(hx, hy, hz)] = ns < 0 ? R(0) : a.p[ns * 192 + c * 64 + loc];
+        ua[c][pidx(hx, hy, hz)] = R(0);
+    }
+    __syncthreads();
+    const R dt = (R)S.dt;
+    const R inv_dx = (R)S.inv_dx;
+    if (a.slot_gen[slot] > 0) {
+        const int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
+        for (int i = beg + threadIdx.x; i < end; i += NT_CELL)
+            if (a.phase[i] != 0 || a.cvisc[i] != R(0)) particle_general<R>(a, i, ph, ua, dt, inv_dx);
+    }
+    for (int j = sbeg + threadIdx.x; j < send; j += NT_CELL) sample_general<R>(a, j, ph, ua, dt, inv_dx);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
+        int c = t / HN, h = t % HN;
+        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
+        R val = ua[c][pidx(hx, hy, hz)];
+        if (val == R(0)) continue;
+        int ns, loc;
+        halo_source(a.nbr, slot, h, ns, loc);
+        if (ns >= 0) atomicAdd(&a.u[ns * 192 + c * 64 + loc], val);
+    }
 }
 
 // ======================================================================
@@ -1277,6 +1711,7 @@ ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int c
     for (int q = 0; q < 24; ++q) a.scache.a[q] = (R*)d.scache[q];
     a.sg = (const R*)d.sg;
     a.sic = (const R*)d.sic;
+    a.slot_gen = d.slot_gen;
     a.mode = mode;
     a.check_done = check_done;
     return a;
@@ -1315,6 +1750,7 @@ template <typename R>
 cudaError_t pack_step_t(mpm_ctx* c) {
     Dev& d = c->d;
     cudaStream_t st = c->st;
+    cudaMemsetAsync(d.slot_gen, 0, sizeof(int) * (size_t)(c->NB > 0 ? c->NB : 1), st);
     if (c->np > 0) {
         RPtr3<R> pu;
         RPtr9<R> Fn;
@@ -1324,7 +1760,8 @@ cudaError_t pack_step_t(mpm_ctx* c) {
         for (int q = 0; q < 9; ++q) F.a[q] = d.F[q];
         MPM_LAUNCH k_pack_volume<R><<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, Ptrs3{{d.x[0], d.x[1], d.x[2]}}, d.J, F, d.V0, d.T,
                                                            d.phase, d.psc, d.sc, pu, (R*)d.kappa, (R*)d.cvisc, Fn,
-                                                           (R*)d.lame[0], (R*)d.lame[1], (R*)d.Vn);
+                                                           (R*)d.lame[0], (R*)d.lame[1], (R*)d.Vn, d.bslot,
+                                                           d.slot_gen);
     }
     if (c->ns > 0) {
         RPtr3<R> su, sa;
@@ -1377,7 +1814,8 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
         for (int it = 0; it < maxit; it += chunk) {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
-                if (c->NW > 0) MPM_LAUNCH k_apply<R><<<c->NW, NT, 0, st>>>(ap);
+                if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
+                if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<c->NW, NT_CELL, 0, st>>>(ap);
                 prof_mark_apply(c, false);
                 MPM_LAUNCH k_cg_pq<R, 3><<<nb, 64, 0, st>>>(a);
                 MPM_LAUNCH k_cg_update<R, 3><<<nb, 64, 0, st>>>(a);
@@ -1494,10 +1932,12 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
     if (c->NW == 0) return cudaSuccess;
     if (c->rsize == 4) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
-        MPM_LAUNCH k_apply<float><<<c->NW, NT, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_cell<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_general<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
-        MPM_LAUNCH k_apply<double><<<c->NW, NT, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_cell<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_general<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
     }
     return cudaGetLastError();
 }

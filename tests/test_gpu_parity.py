@@ -173,7 +173,9 @@ def test_step_grid_velocity_matches_oracle(name, prec):
     tol = 1e-9 if prec == mpm.PREC_FP64 else 1e-5
     assert relerr(vgpu, sim.vhat) < tol, stats
     if sc.params.thermal:
-        assert relerr(ctx.get_grid(0, mpm.FIELD_THAT), sim.That) < (1e-9 if prec == mpm.PREC_FP64 else 1e-5)
+        # float32 heat CG stops at |r| <= 1e-6 |rhs|; the temperature error is that
+        # times the heat operator's condition number (tens here), so 2e-4
+        assert relerr(ctx.get_grid(0, mpm.FIELD_THAT), sim.That) < (1e-9 if prec == mpm.PREC_FP64 else 2e-4)
     # G2P
     ctx.g2p()
     sim.g2p()
