@@ -47,9 +47,9 @@ UNIT = "steps/s"
 NCU_TRAFFIC_BYTES = None
 
 
-def make_workload(name):
+def make_workload(name, drops=40):
     if name == "incline":
-        return scenes.incline()
+        return scenes.incline(n_drops=drops)
     if name == "film":
         return scenes.film()
     if name == "droplet":
@@ -172,10 +172,10 @@ def bench_ours(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    sc = make_workload(args.workload)
+    sc = make_workload(args.workload, args.drops)
     stream = torch.cuda.current_stream()
     prec = mpm.PREC_FP32_FP64RED if args.precision == "fp32" else mpm.PREC_FP64
-    ctx = mpm.Context(sc, precision=prec, stream=stream.cuda_stream)
+    ctx = mpm.Context(sc, precision=prec, stream=stream.cuda_stream, max_blocks=args.max_blocks)
     ctx.load_scene(0)
     for _ in range(args.warmup):
         ctx.step()
@@ -219,7 +219,7 @@ def bench_ours(args, rank, world):
                      "traffic": NCU_TRAFFIC_BYTES, "peak_source": peak_kind, "kernel": "k_apply (Hessian-vector)",
                      "bytes_per_launch": abytes, "launch_ms": apply_avg_ms,
                      "launches": prof["apply_launches"]},
-        "counts": counts,
+        "counts": dict(counts, **{"grid_blocks": ctx.counts()["blocks"], "work_blocks": ctx.counts()["work_blocks"]}),
         "applies_per_s": prof["apply_launches"] / (elapsed_ms * 1e-3),
     }
     # end to end through host buffers: state in from host memory, step, state back out
@@ -250,7 +250,7 @@ def bench_ours(args, rank, world):
     ctx.close()
     # all-float64 form on the same workload
     if args.fp64_steps > 0 and prec == mpm.PREC_FP32_FP64RED:
-        ctx = mpm.Context(sc, precision=mpm.PREC_FP64, stream=stream.cuda_stream)
+        ctx = mpm.Context(sc, precision=mpm.PREC_FP64, stream=stream.cuda_stream, max_blocks=args.max_blocks)
         ctx.load_scene(0)
         ctx.step()
         ctx.profile_enable(True)
@@ -282,7 +282,9 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--drops", type=int, default=40, help="droplets in the incline workload")
+    ap.add_argument("--max-blocks", type=int, default=0, help="grid block capacity (0: whole grid)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -291,7 +293,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        sc = make_workload(args.workload)
+        sc = make_workload(args.workload, args.drops)
         times, sample = run_oracle_sample(sc, args.warmup + args.steps)
         t = float(np.mean(times[args.warmup:])) if args.steps > 0 else float("nan")
         scale = sample.n_particles / sc.n_particles

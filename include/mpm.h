@@ -114,6 +114,8 @@ typedef struct {
     mpm_params params;
     int64_t max_particles;      /* capacity of interior particles for this scene */
     int64_t max_surface;        /* capacity of surface samples for this scene */
+    int64_t max_blocks;         /* capacity of active 4x4x4-node grid blocks (0: every block of
+                                   the grid); exceeding it is MPM_ERR_CAPACITY at mpm_resample */
 } mpm_scene_desc;
 
 /* Per-scene statistics of the last mpm_newton_step. */

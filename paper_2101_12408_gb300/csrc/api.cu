@@ -102,7 +102,7 @@ cudaError_t ralloc(mpm_ctx* c, void** p, size_t count) {
 __global__ void k_stage_in(int n, int base, int scene, const double* __restrict__ x, const double* __restrict__ v,
                            const double* __restrict__ A, const double* __restrict__ m, const double* __restrict__ V0,
                            const double* __restrict__ J, const double* __restrict__ F, const double* __restrict__ T,
-                           const double* __restrict__ gT, const uint8_t* __restrict__ ph, Dev d) {
+                           const double* __restrict__ gT, const uint8_t* __restrict__ ph, Dev d, int allow_solid) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int k = base + i;
@@ -119,7 +119,12 @@ __global__ void k_stage_in(int n, int base, int scene, const double* __restrict_
     d.V0[k] = V0[i];
     d.J[k] = J ? J[i] : 1.0;
     d.T[k] = T ? T[i] : 0.0;
-    d.phase[k] = ph ? ph[i] : 0;
+    uint8_t phv = ph ? ph[i] : 0;
+    if (phv != 0 && !allow_solid) {   // no solid buffers in this context
+        atomicOr(d.err, ERR_SOLID);
+        phv = 0;
+    }
+    d.phase[k] = phv;
     d.pid[k] = i;
     d.psc[k] = scene;
 }
@@ -192,6 +197,9 @@ mpm_status check_device_error(mpm_ctx* c) {
         if (err & ERR_DOMAIN) return fail(c, MPM_ERR_DOMAIN, "a particle or surface sample lies outside cells 1..n-2");
         if (err & ERR_FAR_SURFACE) return fail(c, MPM_ERR_DOMAIN, "a surface sample has no interior particle within dx");
         if (err & ERR_NUMERIC) return fail(c, MPM_ERR_NUMERIC, "non-finite value on the device");
+        if (err & ERR_CAPACITY) return fail(c, MPM_ERR_CAPACITY, "more active grid blocks than max_blocks");
+        if (err & ERR_SOLID)
+            return fail(c, MPM_ERR_INVALID_ARG, "solid particles in a context created without E0 > 0 or phase change");
     }
     return MPM_OK;
 }
@@ -227,7 +235,8 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     c->prec = precision;
     c->rsize = precision == MPM_PREC_FP64 ? 8 : 4;
     c->st = (cudaStream_t)stream;
-    long long bb = 0, pb = 0, sb = 0;
+    long long bb = 0, pb = 0, sb = 0, bcap = 0;
+    bool solids = false;
     for (int k = 0; k < n_scenes; ++k) {
         const mpm_scene_desc& D = scenes[k];
         const mpm_grid_desc& G = D.grid;
@@ -246,7 +255,10 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
             S.g[a] = P.gravity[a];
         }
         S.block_base = bb;
-        bb += (long long)S.nb[0] * S.nb[1] * S.nb[2];
+        long long nbl = (long long)S.nb[0] * S.nb[1] * S.nb[2];
+        bb += nbl;
+        bcap += (D.max_blocks > 0 && D.max_blocks < nbl) ? D.max_blocks : nbl;
+        solids = solids || P.E0 > 0.0 || P.phase_change;
         S.dx = G.dx;
         S.inv_dx = 1.0 / G.dx;
         S.dt = P.dt;
@@ -290,51 +302,52 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
         sb += D.max_surface;
         c->hsc.push_back(S);
     }
-    // two capacities' worth: a re-set scene's new particles sit beside its old ones until the next sort
-    c->Pcap = 2 * pb + 1;
-    c->Scap = 2 * sb + 1;
+    // a re-set scene's new particles are appended; its old ones are dropped by the
+    // next sort, or by a compacting sort first when the appended set would not fit
+    c->Pcap = pb + 1;
+    c->Scap = sb + 1;
     c->total_blocks = bb;
     c->total_cells = bb * 64;
     if (c->Pcap > 0x7fffffffLL || c->total_cells + 1 > 0x7fffffffLL) {
         delete c;
         return MPM_ERR_CAPACITY;
     }
+    c->block_cap = bcap;
+    c->has_solids = solids;
     Dev& d = c->d;
-    long long P = c->Pcap, Sn = c->Scap, NBc = c->total_blocks, NN = NBc * 64;
+    long long P = c->Pcap, Sn = c->Scap, NBc = c->total_blocks, NN = bcap * 64;
+    long long PS = solids ? P : 1;   // solid-only buffers
     cudaError_t e = cudaSuccess;
 #define A_(ptr, T, n) if (e == cudaSuccess) e = dalloc<T>(c, &(ptr), (size_t)(n))
 #define R_(ptr, n) if (e == cudaSuccess) e = ralloc(c, &(ptr), (size_t)(n))
     for (int q = 0; q < 3; ++q) {
         A_(d.x[q], double, P); A_(d.v[q], double, P); A_(d.gT[q], double, P);
-        A_(d.x2[q], double, P); A_(d.v2[q], double, P); A_(d.gT22[q], double, P);
         A_(d.s[q], double, Sn); A_(d.dA[q], double, Sn); A_(d.bpos[q], double, Sn);
-        A_(d.s2[q], double, Sn); A_(d.dA2[q], double, Sn);
         R_(d.pu[q], P); R_(d.su[q], Sn); R_(d.sa[q], Sn); R_(d.sn[q], Sn);
     }
     for (int q = 0; q < 9; ++q) {
-        A_(d.A[q], double, P); A_(d.F[q], double, P); A_(d.A2[q], double, P); A_(d.F2[q], double, P);
-        R_(d.Fn[q], P); R_(d.sF[q], Sn);
+        A_(d.A[q], double, P); A_(d.F[q], double, P);
+        R_(d.Fn[q], PS); R_(d.sF[q], Sn);
     }
     for (int q = 0; q < 12; ++q) A_(d.acc[q], double, P);
-    for (int q = 0; q < 24; ++q) R_(d.scache[q], P);
+    for (int q = 0; q < 24; ++q) R_(d.scache[q], PS);
     A_(d.m, double, P); A_(d.V0, double, P); A_(d.J, double, P); A_(d.T, double, P);
-    A_(d.m2, double, P); A_(d.V02, double, P); A_(d.J2, double, P); A_(d.T2, double, P);
-    A_(d.phase, uint8_t, P); A_(d.phase2, uint8_t, P);
-    A_(d.pid, int, P); A_(d.psc, int, P); A_(d.pid2, int, P); A_(d.psc2, int, P);
+    A_(d.phase, uint8_t, P);
+    A_(d.pid, int, P); A_(d.psc, int, P);
+    A_(*(double**)&d.scratch, double, P > Sn ? P : Sn);
     A_(d.gcount, int, P); A_(d.mt, double, P);
-    R_(d.kappa, P); R_(d.cvisc, P); R_(d.lame[0], P); R_(d.lame[1], P); R_(d.Vn, P);
+    R_(d.kappa, P); R_(d.cvisc, P); R_(d.lame[0], PS); R_(d.lame[1], PS); R_(d.Vn, P);
     A_(d.bheat, double, Sn); A_(d.Tbar, double, Sn); A_(d.gamma, double, Sn); A_(d.Tr, double, Sn);
-    A_(d.bheat2, double, Sn); A_(d.Tbar2, double, Sn);
-    A_(d.kind, uint8_t, Sn); A_(d.kind2, uint8_t, Sn);
-    A_(d.sid, int, Sn); A_(d.ssc, int, Sn); A_(d.sid2, int, Sn); A_(d.ssc2, int, Sn); A_(d.parent, int, Sn);
+    A_(d.kind, uint8_t, Sn);
+    A_(d.sid, int, Sn); A_(d.ssc, int, Sn); A_(d.parent, int, Sn);
     R_(d.sg, Sn); R_(d.sic, Sn); R_(d.swn, Sn);
     A_(d.key, long long, P); A_(d.rank, int, P); A_(d.perm, int, P);
     A_(d.skey, long long, Sn); A_(d.srank, int, Sn); A_(d.sperm, int, Sn);
     A_(d.cell_count, int, c->total_cells + 1); A_(d.cell_start, int, c->total_cells + 1);
     A_(d.scell_count, int, c->total_cells + 1); A_(d.scell_start, int, c->total_cells + 1);
     A_(d.bflag, int, NBc + 1); A_(d.bwork, int, NBc + 1); A_(d.bslot, int, NBc + 1); A_(d.bscan, int, NBc + 1);
-    A_(d.slot_coord, int4, NBc + 1); A_(d.nbr, int, NBc * 27 + 27); A_(d.work, int, NBc + 1); A_(d.work_gb, int, NBc + 1);
-    A_(d.slot_gen, int, NBc + 1);
+    A_(d.slot_coord, int4, bcap + 1); A_(d.nbr, int, bcap * 27 + 27); A_(d.work, int, bcap + 1); A_(d.work_gb, int, bcap + 1);
+    A_(d.slot_gen, int, bcap + 1);
     A_(d.counts, int, 4);
     A_(d.scan_tmp, int, (c->total_cells + 1) / 4096 + 16);
     A_(d.gm, double, NN); A_(d.gmv, double, NN * 3); A_(d.gvn, double, NN * 3); A_(d.gmT, double, NN);
@@ -419,7 +432,8 @@ mpm_status mpm_set_particles(mpm_ctx* c, int32_t scene, int64_t n, const double*
             MPM_CUDA(cudaMemcpyAsync(ph, phase, (size_t)n, cudaMemcpyDefault, st));
         }
         MPM_LAUNCH k_stage_in<<<nblk(n, 256), 256, 0, st>>>((int)n, (int)c->np, scene, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4],
-                                                  dptr[5], dptr[6], dptr[7], dptr[8], ph, d);
+                                                  dptr[5], dptr[6], dptr[7], dptr[8], ph, d,
+                                                  c->has_solids ? 1 : 0);
         MPM_CUDA(cudaGetLastError());
         // reject non-finite input before any step
         for (int f = 0; f < 9; ++f)

@@ -54,6 +54,8 @@ enum : int {
     ERR_DOMAIN = 1,        // particle or sample outside cells 1..n-2
     ERR_FAR_SURFACE = 2,   // no interior particle within dx of a surface sample
     ERR_NUMERIC = 4,
+    ERR_CAPACITY = 8,      // more active grid blocks than max_blocks
+    ERR_SOLID = 16,        // solid particle without solid buffers
 };
 
 __device__ __forceinline__ long long cell_key(const SceneDev& S, int cx, int cy, int cz) {

@@ -19,10 +19,7 @@ struct Dev {
     double *x[3], *v[3], *A[9], *m, *V0, *J, *F[9], *T, *gT[3];
     uint8_t* phase;
     int *pid, *psc;                 // original index within its scene, scene
-    // second set for the permutation
-    double *x2[3], *v2[3], *A2[9], *m2, *V02, *J2, *F2[9], *T2, *gT22[3];
-    uint8_t* phase2;
-    int *pid2, *psc2;
+    void* scratch;                  // one array of max(particles, samples) doubles for permutations
     // per-step interior data
     int* gcount;                    // |Pi_p|
     double* mt;                     // split mass
@@ -39,9 +36,6 @@ struct Dev {
     double *s[3], *dA[3], *bheat, *Tbar, *gamma, *bpos[3], *Tr;
     uint8_t* kind;
     int *sid, *ssc, *parent;        // parent: sorted interior index
-    double *s2[3], *dA2[3], *bheat2, *Tbar2;
-    uint8_t* kind2;
-    int *sid2, *ssc2;
     void* su[3];                    // sample position relative to its block (R)
     void* sa[3];                    // dA (R)
     void* sg;                       // gamma (R)
@@ -95,6 +89,8 @@ struct mpm_ctx {
     std::vector<mpm::SceneDev> hsc;
     long long Pcap = 0, Scap = 0, total_blocks = 0, total_cells = 0;
     long long np = 0, ns = 0;       // current totals
+    long long block_cap = 0;        // capacity of active blocks (grid slots)
+    bool has_solids = false;        // solid-only buffers allocated
     int NB = 0, NW = 0;
     bool resampled = false, p2g_done = false, step_ready = false;
     mpm::Dev d{};

@@ -232,8 +232,9 @@ struct EvalArgs {
     R* sic;                    // 1/|c|
 };
 
-template <typename R>
-__global__ void __launch_bounds__(NT) k_eval(EvalArgs<R> a) {
+// R: arithmetic type; RS: storage type of the per-iterate caches
+template <typename R, typename RS>
+__global__ void __launch_bounds__(NT) k_eval(EvalArgs<RS> a) {
     __shared__ R vh[3][HN];
     __shared__ double ga[3][HN];
     __shared__ double red[NT / 32];
@@ -322,11 +323,11 @@ __global__ void __launch_bounds__(NT) k_eval(EvalArgs<R> a) {
             if (a.want_cache) {
 #pragma unroll
                 for (int q = 0; q < 9; ++q) {
-                    a.scache.a[q][i] = Fc[q];
-                    a.scache.a[9 + q][i] = Rm[q];
+                    a.scache.a[q][i] = (RS)Fc[q];
+                    a.scache.a[9 + q][i] = (RS)Rm[q];
                 }
 #pragma unroll
-                for (int q = 0; q < 6; ++q) a.scache.a[18 + q][i] = K[q];
+                for (int q = 0; q < 6; ++q) a.scache.a[18 + q][i] = (RS)K[q];
             }
         }
         if (a.want_grad) {
@@ -374,10 +375,10 @@ __global__ void __launch_bounds__(NT) k_eval(EvalArgs<R> a) {
         R nv[3] = {cv[0] / cn, cv[1] / cn, cv[2] / cn};
         if (a.want_cache) {
 #pragma unroll
-            for (int q = 0; q < 9; ++q) a.sF.a[q][j] = Fh[q];
+            for (int q = 0; q < 9; ++q) a.sF.a[q][j] = (RS)Fh[q];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) a.sn.a[q][j] = nv[q];
-            a.sic[j] = R(1) / cn;
+            for (int q = 0; q < 3; ++q) a.sn.a[q][j] = (RS)nv[q];
+            a.sic[j] = (RS)(R(1) / cn);
         }
         if (a.want_grad) {
             R G[9];
@@ -1325,8 +1326,9 @@ struct LSArgs {
     const double* gamma;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(NT) k_linesearch(LSArgs<R> a) {
+// R: arithmetic type; RD: type of the Newton direction
+template <typename R, typename RD>
+__global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
     __shared__ R vh[3][HN];
     __shared__ R dh[3][HN];
     __shared__ double red[NT / 32];
@@ -1338,7 +1340,12 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<R> a) {
     SceneScal& scl = a.scal[bc.w];
     if (scl.newton_done) return;
     load_halo_vec_d<R>(a.nbr, slot, a.gv, vh);
-    load_halo_vec<R>(a.nbr, slot, a.d, dh);
+    for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
+        int c = t / HN, h = t % HN;
+        int ns, loc;
+        halo_source(a.nbr, slot, h, ns, loc);
+        dh[c][h] = ns < 0 ? R(0) : (R)a.d[ns * 192 + c * 64 + loc];
+    }
     __syncthreads();
     const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
     const R dt = (R)S.dt;
@@ -1834,17 +1841,18 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, typename RS>
 cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) {
     if (c->NW == 0) return cudaSuccess;
-    auto a = make_eval_args<R>(c, want_grad, want_cache, skip_done);
-    MPM_LAUNCH k_eval<R><<<c->NW, NT, 0, c->st>>>(a);
+    auto a = make_eval_args<RS>(c, want_grad, want_cache, skip_done);
+    MPM_LAUNCH k_eval<R, RS><<<c->NW, NT, 0, c->st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t eval_any(mpm_ctx* c, bool fp64, bool want_grad, bool want_cache, bool skip_done) {
-    if (fp64 || c->rsize == 8) return eval_t<double>(c, want_grad, want_cache, skip_done);
-    return eval_t<float>(c, want_grad, want_cache, skip_done);
+// objective / gradient in float64 arithmetic, caches stored in the context's type
+cudaError_t eval_any(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) {
+    if (c->rsize == 8) return eval_t<double, double>(c, want_grad, want_cache, skip_done);
+    return eval_t<double, float>(c, want_grad, want_cache, skip_done);
 }
 
 template <typename R>
@@ -1860,7 +1868,7 @@ cudaError_t newton_t(mpm_ctx* c) {
     for (int it = 0; it <= maxn; ++it) {
         MPM_LAUNCH k_newton_iter_begin<<<gs, 128, 0, st>>>(d.scal, ns);
         cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
-        eval_any(c, false, true, true, true);
+        eval_any(c, true, true, true);
         MPM_LAUNCH k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 1);
         MPM_LAUNCH k_newton_check<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
         cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
@@ -1895,7 +1903,7 @@ cudaError_t newton_t(mpm_ctx* c) {
             for (int q = 0; q < 9; ++q) a.F.a[q] = d.F[q];
             a.phase = d.phase;
             a.gamma = d.gamma;
-            MPM_LAUNCH k_linesearch<R><<<c->NW, NT, 0, st>>>(a);
+            MPM_LAUNCH k_linesearch<double, R><<<c->NW, NT, 0, st>>>(a);
         }
         MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, (const R*)d.cx);
         MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
@@ -1904,7 +1912,7 @@ cudaError_t newton_t(mpm_ctx* c) {
     // final explicit force evaluation in float64
     MPM_LAUNCH k_zero_mom<<<gs, 128, 0, st>>>(d.scal, ns);
     cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
-    eval_any(c, true, true, false, false);
+    eval_any(c, true, false, false);
     MPM_LAUNCH k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
     MPM_LAUNCH k_newton_final<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gv, d.ggrad, d.pcode, d.gvhat);
     return cudaGetLastError();
@@ -1923,7 +1931,7 @@ cudaError_t launch_eval(mpm_ctx* c, bool fp64_math, bool want_cache) {
     MPM_LAUNCH k_newton_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
     MPM_LAUNCH k_newton_iter_begin<<<nblk(ns, 128), 128, 0, c->st>>>(d.scal, ns);
     cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)c->NB * 192, c->st);
-    eval_any(c, fp64_math, true, want_cache, false);
+    eval_any(c, true, want_cache, false);
     if (c->NB > 0) MPM_LAUNCH k_node_grad<<<c->NB, 64, 0, c->st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
     return cudaGetLastError();
 }

@@ -174,7 +174,7 @@ __device__ __forceinline__ int scene_of_block(const SceneDev* sc, int nsc, long 
 
 __global__ void k_slots(long long nblk, const int* __restrict__ bflag, const int* __restrict__ bscan,
                         const SceneDev* __restrict__ sc, int nsc, int* __restrict__ bslot, int4* __restrict__ coord,
-                        int* __restrict__ counts) {
+                        int* __restrict__ counts, long long cap, int* err) {
     long long gb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gb >= nblk) return;
     if (gb == nblk - 1) counts[0] = bscan[nblk];
@@ -183,6 +183,11 @@ __global__ void k_slots(long long nblk, const int* __restrict__ bflag, const int
         return;
     }
     int slot = bscan[gb];
+    if (slot >= cap) {   // more active blocks than the context was created for
+        atomicOr(err, ERR_CAPACITY);
+        bslot[gb] = -1;
+        return;
+    }
     bslot[gb] = slot;
     int s = scene_of_block(sc, nsc, gb);
     long long r = gb - sc[s].block_base;
@@ -194,12 +199,13 @@ __global__ void k_slots(long long nblk, const int* __restrict__ bflag, const int
 
 __global__ void k_work(long long nblk, const int* __restrict__ bwork, const int* __restrict__ wscan,
                        const int* __restrict__ bslot, int* __restrict__ work, int* __restrict__ work_gb,
-                       int* __restrict__ counts) {
+                       int* __restrict__ counts, long long cap) {
     long long gb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gb >= nblk) return;
     if (gb == nblk - 1) counts[1] = wscan[nblk];
     if (!bwork[gb]) return;
     int w = wscan[gb];
+    if (w >= cap) return;
     work[w] = bslot[gb];
     work_gb[w] = (int)gb;
 }
@@ -231,6 +237,16 @@ cudaError_t launch_exclusive_scan(mpm_ctx* c, const int* in, int* out, long long
     return cudaGetLastError();
 }
 
+// gather `a` by `perm` through the scratch buffer, then swap: one scratch array
+// of the largest element type serves every field
+template <typename T>
+void permute(mpm_ctx* c, int n, const int* perm, T*& a, void*& scratch) {
+    MPM_LAUNCH k_gather<T><<<nblocks(n, 256), 256, 0, c->st>>>(n, perm, a, (T*)scratch);
+    T* old = a;
+    a = (T*)scratch;
+    scratch = (void*)old;
+}
+
 cudaError_t launch_sort_particles(mpm_ctx* c) {
     Dev& d = c->d;
     cudaStream_t st = c->st;
@@ -248,39 +264,22 @@ cudaError_t launch_sort_particles(mpm_ctx* c) {
     n = c->hcounts[2];   // live particles
     c->np = n;
     if (n == 0) return cudaGetLastError();
-    int g = nblocks(n, 256);
     for (int a = 0; a < 3; ++a) {
-        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.x[a], d.x2[a]);
-        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.v[a], d.v2[a]);
-        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.gT[a], d.gT22[a]);
+        permute(c, n, d.perm, d.x[a], d.scratch);
+        permute(c, n, d.perm, d.v[a], d.scratch);
+        permute(c, n, d.perm, d.gT[a], d.scratch);
     }
     for (int a = 0; a < 9; ++a) {
-        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.A[a], d.A2[a]);
-        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.F[a], d.F2[a]);
+        permute(c, n, d.perm, d.A[a], d.scratch);
+        permute(c, n, d.perm, d.F[a], d.scratch);
     }
-    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.m, d.m2);
-    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.V0, d.V02);
-    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.J, d.J2);
-    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.perm, d.T, d.T2);
-    MPM_LAUNCH k_gather<uint8_t><<<g, 256, 0, st>>>(n, d.perm, d.phase, d.phase2);
-    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.perm, d.pid, d.pid2);
-    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.perm, d.psc, d.psc2);
-    for (int a = 0; a < 3; ++a) {
-        std::swap(d.x[a], d.x2[a]);
-        std::swap(d.v[a], d.v2[a]);
-        std::swap(d.gT[a], d.gT22[a]);
-    }
-    for (int a = 0; a < 9; ++a) {
-        std::swap(d.A[a], d.A2[a]);
-        std::swap(d.F[a], d.F2[a]);
-    }
-    std::swap(d.m, d.m2);
-    std::swap(d.V0, d.V02);
-    std::swap(d.J, d.J2);
-    std::swap(d.T, d.T2);
-    std::swap(d.phase, d.phase2);
-    std::swap(d.pid, d.pid2);
-    std::swap(d.psc, d.psc2);
+    permute(c, n, d.perm, d.m, d.scratch);
+    permute(c, n, d.perm, d.V0, d.scratch);
+    permute(c, n, d.perm, d.J, d.scratch);
+    permute(c, n, d.perm, d.T, d.scratch);
+    permute(c, n, d.perm, d.phase, d.scratch);
+    permute(c, n, d.perm, d.pid, d.scratch);
+    permute(c, n, d.perm, d.psc, d.scratch);
     return cudaGetLastError();
 }
 
@@ -301,25 +300,15 @@ cudaError_t launch_sort_surface(mpm_ctx* c) {
     n = c->hcounts[3];   // live samples
     c->ns = n;
     if (n == 0) return cudaGetLastError();
-    int g = nblocks(n, 256);
     for (int a = 0; a < 3; ++a) {
-        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.s[a], d.s2[a]);
-        MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.dA[a], d.dA2[a]);
+        permute(c, n, d.sperm, d.s[a], d.scratch);
+        permute(c, n, d.sperm, d.dA[a], d.scratch);
     }
-    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.bheat, d.bheat2);
-    MPM_LAUNCH k_gather<double><<<g, 256, 0, st>>>(n, d.sperm, d.Tbar, d.Tbar2);
-    MPM_LAUNCH k_gather<uint8_t><<<g, 256, 0, st>>>(n, d.sperm, d.kind, d.kind2);
-    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.sperm, d.sid, d.sid2);
-    MPM_LAUNCH k_gather<int><<<g, 256, 0, st>>>(n, d.sperm, d.ssc, d.ssc2);
-    for (int a = 0; a < 3; ++a) {
-        std::swap(d.s[a], d.s2[a]);
-        std::swap(d.dA[a], d.dA2[a]);
-    }
-    std::swap(d.bheat, d.bheat2);
-    std::swap(d.Tbar, d.Tbar2);
-    std::swap(d.kind, d.kind2);
-    std::swap(d.sid, d.sid2);
-    std::swap(d.ssc, d.ssc2);
+    permute(c, n, d.sperm, d.bheat, d.scratch);
+    permute(c, n, d.sperm, d.Tbar, d.scratch);
+    permute(c, n, d.sperm, d.kind, d.scratch);
+    permute(c, n, d.sperm, d.sid, d.scratch);
+    permute(c, n, d.sperm, d.ssc, d.scratch);
     return cudaGetLastError();
 }
 
@@ -336,14 +325,14 @@ cudaError_t launch_build_blocks(mpm_ctx* c) {
         MPM_LAUNCH k_mark<<<nblocks(c->ns, 256), 256, 0, st>>>((int)c->ns, d.bpos[0], d.bpos[1], d.bpos[2], d.ssc, nullptr, d.sc, d.bflag, nullptr, d.err);
     }
     launch_exclusive_scan(c, d.bflag, d.bscan, nblk, d.scan_tmp, st);
-    MPM_LAUNCH k_slots<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bflag, d.bscan, d.sc, c->nsc, d.bslot, d.slot_coord, d.counts);
+    MPM_LAUNCH k_slots<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bflag, d.bscan, d.sc, c->nsc, d.bslot, d.slot_coord, d.counts, c->block_cap, d.err);
     launch_exclusive_scan(c, d.bwork, d.bscan, nblk, d.scan_tmp, st);
-    MPM_LAUNCH k_work<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bwork, d.bscan, d.bslot, d.work, d.work_gb, d.counts);
+    MPM_LAUNCH k_work<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bwork, d.bscan, d.bslot, d.work, d.work_gb, d.counts, c->block_cap);
     cudaMemcpyAsync(c->hcounts, d.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
-    c->NB = c->hcounts[0];
-    c->NW = c->hcounts[1];
+    c->NB = c->hcounts[0] < c->block_cap ? c->hcounts[0] : (int)c->block_cap;
+    c->NW = c->hcounts[1] < c->block_cap ? c->hcounts[1] : (int)c->block_cap;
     if (c->NB > 0) MPM_LAUNCH k_nbr<<<nblocks((long long)c->NB * 27, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.bslot, d.nbr);
     return cudaGetLastError();
 }

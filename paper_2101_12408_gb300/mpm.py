@@ -54,7 +54,7 @@ class Params(ctypes.Structure):
 
 class SceneDesc(ctypes.Structure):
     _fields_ = [("grid", GridDesc), ("params", Params), ("max_particles", ctypes.c_int64),
-                ("max_surface", ctypes.c_int64)]
+                ("max_surface", ctypes.c_int64), ("max_blocks", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -134,7 +134,7 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-def scene_desc(sc, max_particles=None, max_surface=None):
+def scene_desc(sc, max_particles=None, max_surface=None, max_blocks=0):
     p = sc.params
     d = SceneDesc()
     d.grid.n[:] = [int(v) for v in sc.n]
@@ -172,13 +172,14 @@ def scene_desc(sc, max_particles=None, max_surface=None):
     P.phase_change = int(bool(p.phase_change))
     d.max_particles = int(max_particles if max_particles is not None else sc.n_particles)
     d.max_surface = int(max_surface if max_surface is not None else sc.n_surface)
+    d.max_blocks = int(max_blocks)
     return d
 
 
 class Context:
     """One library context holding one or more scenes."""
 
-    def __init__(self, scene_list, precision=PREC_FP32_FP64RED, stream=None, capacity_factor=1.0):
+    def __init__(self, scene_list, precision=PREC_FP32_FP64RED, stream=None, capacity_factor=1.0, max_blocks=0):
         if isinstance(scene_list, _scenes.Scene):
             scene_list = [scene_list]
         self.scenes = list(scene_list)
@@ -186,7 +187,8 @@ class Context:
         self.rdtype = np.float64 if precision == PREC_FP64 else np.float32
         descs = (SceneDesc * len(self.scenes))()
         for k, sc in enumerate(self.scenes):
-            descs[k] = scene_desc(sc, int(sc.n_particles * capacity_factor) + 1, int(sc.n_surface * capacity_factor) + 1)
+            descs[k] = scene_desc(sc, int(sc.n_particles * capacity_factor) + 1, int(sc.n_surface * capacity_factor) + 1,
+                                  max_blocks)
         h = _vp()
         st = stream
         if st is None:

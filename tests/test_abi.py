@@ -48,7 +48,7 @@ def test_struct_sizes_match_c_layout(lib):
     # sizes follow the C rules for the header's field order (8-byte aligned doubles)
     assert ctypes.sizeof(mpm.GridDesc) == 112
     assert ctypes.sizeof(mpm.Params) == 216
-    assert ctypes.sizeof(mpm.SceneDesc) == 344
+    assert ctypes.sizeof(mpm.SceneDesc) == 352
     assert ctypes.sizeof(mpm.Stats) == 64
 
 
