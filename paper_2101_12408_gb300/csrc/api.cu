@@ -334,7 +334,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.m, double, P); A_(d.V0, double, P); A_(d.J, double, P); A_(d.T, double, P);
     A_(d.phase, uint8_t, P);
     A_(d.pid, int, P); A_(d.psc, int, P);
-    A_(*(double**)&d.scratch, double, P > Sn ? P : Sn);
+    A_(d.scratch_p, double, P); A_(d.scratch_s, double, Sn);
     A_(d.gcount, int, P); A_(d.mt, double, P);
     R_(d.kappa, P); R_(d.cvisc, P); R_(d.lame[0], PS); R_(d.lame[1], PS); R_(d.Vn, P);
     A_(d.bheat, double, Sn); A_(d.Tbar, double, Sn); A_(d.gamma, double, Sn); A_(d.Tr, double, Sn);

@@ -19,7 +19,8 @@ struct Dev {
     double *x[3], *v[3], *A[9], *m, *V0, *J, *F[9], *T, *gT[3];
     uint8_t* phase;
     int *pid, *psc;                 // original index within its scene, scene
-    void* scratch;                  // one array of max(particles, samples) doubles for permutations
+    double* scratch_p;              // permutation scratch: particle capacity
+    double* scratch_s;              // permutation scratch: sample capacity
     // per-step interior data
     int* gcount;                    // |Pi_p|
     double* mt;                     // split mass

@@ -237,14 +237,20 @@ cudaError_t launch_exclusive_scan(mpm_ctx* c, const int* in, int* out, long long
     return cudaGetLastError();
 }
 
-// gather `a` by `perm` through the scratch buffer, then swap: one scratch array
-// of the largest element type serves every field
+// Reorder a float64 field by `perm`: gather into the scratch array of the same
+// capacity and swap the two (no copy back).
+void permute(mpm_ctx* c, int n, const int* perm, double*& a, double*& scratch) {
+    MPM_LAUNCH k_gather<double><<<nblocks(n, 256), 256, 0, c->st>>>(n, perm, a, scratch);
+    double* old = a;
+    a = scratch;
+    scratch = old;
+}
+
+// Smaller element types keep their own buffer: gather into scratch, copy back.
 template <typename T>
-void permute(mpm_ctx* c, int n, const int* perm, T*& a, void*& scratch) {
+void permute(mpm_ctx* c, int n, const int* perm, T* a, double* scratch) {
     MPM_LAUNCH k_gather<T><<<nblocks(n, 256), 256, 0, c->st>>>(n, perm, a, (T*)scratch);
-    T* old = a;
-    a = (T*)scratch;
-    scratch = (void*)old;
+    cudaMemcpyAsync(a, scratch, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, c->st);
 }
 
 cudaError_t launch_sort_particles(mpm_ctx* c) {
@@ -265,21 +271,21 @@ cudaError_t launch_sort_particles(mpm_ctx* c) {
     c->np = n;
     if (n == 0) return cudaGetLastError();
     for (int a = 0; a < 3; ++a) {
-        permute(c, n, d.perm, d.x[a], d.scratch);
-        permute(c, n, d.perm, d.v[a], d.scratch);
-        permute(c, n, d.perm, d.gT[a], d.scratch);
+        permute(c, n, d.perm, d.x[a], d.scratch_p);
+        permute(c, n, d.perm, d.v[a], d.scratch_p);
+        permute(c, n, d.perm, d.gT[a], d.scratch_p);
     }
     for (int a = 0; a < 9; ++a) {
-        permute(c, n, d.perm, d.A[a], d.scratch);
-        permute(c, n, d.perm, d.F[a], d.scratch);
+        permute(c, n, d.perm, d.A[a], d.scratch_p);
+        permute(c, n, d.perm, d.F[a], d.scratch_p);
     }
-    permute(c, n, d.perm, d.m, d.scratch);
-    permute(c, n, d.perm, d.V0, d.scratch);
-    permute(c, n, d.perm, d.J, d.scratch);
-    permute(c, n, d.perm, d.T, d.scratch);
-    permute(c, n, d.perm, d.phase, d.scratch);
-    permute(c, n, d.perm, d.pid, d.scratch);
-    permute(c, n, d.perm, d.psc, d.scratch);
+    permute(c, n, d.perm, d.m, d.scratch_p);
+    permute(c, n, d.perm, d.V0, d.scratch_p);
+    permute(c, n, d.perm, d.J, d.scratch_p);
+    permute(c, n, d.perm, d.T, d.scratch_p);
+    permute(c, n, d.perm, d.phase, d.scratch_p);
+    permute(c, n, d.perm, d.pid, d.scratch_p);
+    permute(c, n, d.perm, d.psc, d.scratch_p);
     return cudaGetLastError();
 }
 
@@ -301,14 +307,14 @@ cudaError_t launch_sort_surface(mpm_ctx* c) {
     c->ns = n;
     if (n == 0) return cudaGetLastError();
     for (int a = 0; a < 3; ++a) {
-        permute(c, n, d.sperm, d.s[a], d.scratch);
-        permute(c, n, d.sperm, d.dA[a], d.scratch);
+        permute(c, n, d.sperm, d.s[a], d.scratch_s);
+        permute(c, n, d.sperm, d.dA[a], d.scratch_s);
     }
-    permute(c, n, d.sperm, d.bheat, d.scratch);
-    permute(c, n, d.sperm, d.Tbar, d.scratch);
-    permute(c, n, d.sperm, d.kind, d.scratch);
-    permute(c, n, d.sperm, d.sid, d.scratch);
-    permute(c, n, d.sperm, d.ssc, d.scratch);
+    permute(c, n, d.sperm, d.bheat, d.scratch_s);
+    permute(c, n, d.sperm, d.Tbar, d.scratch_s);
+    permute(c, n, d.sperm, d.kind, d.scratch_s);
+    permute(c, n, d.sperm, d.sid, d.scratch_s);
+    permute(c, n, d.sperm, d.ssc, d.scratch_s);
     return cudaGetLastError();
 }
 
