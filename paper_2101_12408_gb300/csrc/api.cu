@@ -198,6 +198,7 @@ mpm_status check_device_error(mpm_ctx* c) {
         if (err & ERR_FAR_SURFACE) return fail(c, MPM_ERR_DOMAIN, "a surface sample has no interior particle within dx");
         if (err & ERR_NUMERIC) return fail(c, MPM_ERR_NUMERIC, "non-finite value on the device");
         if (err & ERR_CAPACITY) return fail(c, MPM_ERR_CAPACITY, "more active grid blocks than max_blocks");
+        if (err & ERR_TIMEOUT) return fail(c, MPM_ERR_TIMEOUT, "a bounded device wait ran out");
         if (err & ERR_SOLID)
             return fail(c, MPM_ERR_INVALID_ARG, "solid particles in a context created without E0 > 0 or phase change");
     }
@@ -336,7 +337,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.pid, int, P); A_(d.psc, int, P);
     A_(d.scratch_p, double, P); A_(d.scratch_s, double, Sn);
     A_(d.gcount, int, P); A_(d.mt, double, P);
-    R_(d.kappa, P); R_(d.cvisc, P); R_(d.lame[0], PS); R_(d.lame[1], PS); R_(d.Vn, P);
+    R_(d.opk, 4 * P); R_(d.kappa, P); R_(d.cvisc, P); R_(d.lame[0], PS); R_(d.lame[1], PS); R_(d.Vn, P);
     A_(d.bheat, double, Sn); A_(d.Tbar, double, Sn); A_(d.gamma, double, Sn); A_(d.Tr, double, Sn);
     A_(d.kind, uint8_t, Sn);
     A_(d.sid, int, Sn); A_(d.ssc, int, Sn); A_(d.parent, int, Sn);

@@ -56,6 +56,7 @@ enum : int {
     ERR_NUMERIC = 4,
     ERR_CAPACITY = 8,      // more active grid blocks than max_blocks
     ERR_SOLID = 16,        // solid particle without solid buffers
+    ERR_TIMEOUT = 32,      // a bounded device wait ran out
 };
 
 __device__ __forceinline__ long long cell_key(const SceneDev& S, int cx, int cy, int cz) {
@@ -184,6 +185,50 @@ __device__ __forceinline__ void matmul3_bt(const R* A, const R* B, R* C) {
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             C[3 * i + j] = A[3 * i] * B[3 * j] + A[3 * i + 1] * B[3 * j + 1] + A[3 * i + 2] * B[3 * j + 2];
+}
+
+// Four values of one type, 16- (float) or 32-byte (double) aligned: the packed
+// per-particle record of the Hessian operator.
+template <typename R>
+struct alignas(4 * sizeof(R)) R4 {
+    R x, y, z, w;
+};
+
+// ---- TMA bulk copy global -> shared with an mbarrier (sm_90+ PTX) ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// bytes: multiple of 16; dst and src 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on an mbarrier phase; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // warp + block sum of a double, then one atomicAdd per block

@@ -29,6 +29,7 @@ struct Dev {
     void* pu[3];                    // position relative to the block origin, in cells
     void* kappa;                    // dt^2 lambda (J^n)^2 V0 (liquid), 0 solid
     void* cvisc;                    // dt mu V^n (liquid), 0 solid
+    void* opk;                      // R4 per particle: block-relative position, kappa (< 0: general operator)
     void* Fn[9];                    // F^n (solid)
     void* lame[2];                  // mu, lambda (solid)
     void* scache[24];               // solid per-iterate: F (9), R (9), (tr S I - S)^-1 (6)

@@ -158,7 +158,7 @@ __global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptr
                               const double* __restrict__ T, const uint8_t* __restrict__ phase, const int* __restrict__ psc,
                               const SceneDev* __restrict__ sc, RPtr3<R> pu, R* __restrict__ kappa, R* __restrict__ cvisc,
                               RPtr9<R> Fn, R* __restrict__ lmu, R* __restrict__ llam, R* __restrict__ Vn,
-                              const int* __restrict__ bslot, int* __restrict__ slot_gen) {
+                              const int* __restrict__ bslot, int* __restrict__ slot_gen, R4<R>* __restrict__ opk) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     const SceneDev& S = sc[psc[i]];
@@ -184,6 +184,15 @@ __global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptr
     Vn[i] = (R)((liq ? Jn : detF) * v0);
     kappa[i] = liq ? (R)(dt * dt * S.lambda_l * Jn * Jn * v0) : R(0);
     cvisc[i] = liq ? (R)(dt * S.mu_l * Jn * v0) : R(0);
+    {
+        R4<R> rec;
+        rec.x = pu.a[0][i];
+        rec.y = pu.a[1][i];
+        rec.z = pu.a[2][i];
+        bool general = !liq || S.mu_l != 0.0;
+        rec.w = general ? R(-1) : (R)(dt * dt * S.lambda_l * Jn * Jn * v0);
+        opk[i] = rec;
+    }
     if (!liq) {
         for (int q = 0; q < 9; ++q) Fn.a[q][i] = (R)Fd[q];
         double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - T[i]) / (S.T_melt - S.T0));
@@ -226,6 +235,8 @@ struct EvalArgs {
     Ptrs3 s, dA;
     const double* gamma;
     int want_grad, want_cache, skip_done;
+    int skip_poly;             // non-viscous liquid particles are left to k_eval_cell
+    const int* slot_gen;
     RPtr24<R> scache;          // solid: F (9), R (9), Kinv (6)
     RPtr9<R> sF;               // surface F^
     RPtr3<R> sn;               // surface unit c
@@ -244,13 +255,17 @@ __global__ void __launch_bounds__(NT) k_eval(EvalArgs<RS> a) {
     int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
     if (a.skip_done && a.scal[bc.w].newton_done) return;
+    const bool poly = a.skip_poly && S.mu_l == 0.0;
+    if (poly && a.slot_gen[slot] == 0 && a.scell_start[gb * 64] == a.scell_start[gb * 64 + 64]) return;
     load_halo_vec_d<R>(a.nbr, slot, a.gv, vh);
     for (int t = threadIdx.x; t < 3 * HN; t += NT) (&ga[0][0])[t] = 0.0;
     __syncthreads();
     const R dt = (R)S.dt;
     double esum = 0.0;
     int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
+    if (poly && a.slot_gen[slot] == 0) end = beg;
     for (int i = beg + threadIdx.x; i < end; i += NT) {
+        if (poly && a.phase[i] == 0) continue;   // k_eval_cell
         double p[3] = {a.x.a[0][i], a.x.a[1][i], a.x.a[2][i]};
         int lc[3];
         R wgt[3][3], dw[3][3], f[3];
@@ -492,6 +507,8 @@ struct ApplyArgs {
     RPtr3<R> sn;
     const R* sic;
     const int* slot_gen;      // general particles per slot
+    const R4<R>* opk;         // packed record: position in the block (cells), kappa (< 0: general)
+    int* err;
     int mode;
     int check_done;
 };
@@ -933,87 +950,178 @@ __device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (
 }
 
 constexpr int NT_CELL = 64;
+constexpr int MAXP = 640;   // particle records staged per chunk
+
+// Halo rows along x: the four middle nodes of a row belong to one neighbour block
+// and are contiguous there (x fastest), so they move as one vector; the two end
+// nodes belong to the x-neighbours.
+template <typename R>
+__device__ __forceinline__ void halo_row(const int* __restrict__ nbr, int slot, int hy, int hz, int& nmid, int& nlo,
+                                         int& nhi, int& base) {
+    int oy = hy - 1, oz = hz - 1;
+    int by = oy < 0 ? -1 : (oy >= BS ? 1 : 0), bz = oz < 0 ? -1 : (oz >= BS ? 1 : 0);
+    const int* nb = nbr + slot * 27 + 3 * (by + 1) + 9 * (bz + 1);
+    nlo = nb[0];
+    nmid = nb[1];
+    nhi = nb[2];
+    base = BS * ((oy - BS * by) + BS * (oz - BS * bz));   // local index of x = 0 in the row
+}
+
+template <typename R>
+__device__ __forceinline__ void load_halo_rows(const int* __restrict__ nbr, int slot, const R* __restrict__ p,
+                                               R (*ph)[PN], R (*ua)[PN]) {
+    for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
+        int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<R>(nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
+        if (nmid >= 0) {
+            const R* src = p + nmid * 192 + c * 64 + base;
+            if constexpr (sizeof(R) == 4) {
+                float4 v = *reinterpret_cast<const float4*>(src);
+                m0 = v.x; m1 = v.y; m2 = v.z; m3 = v.w;
+            } else {
+                m0 = src[0]; m1 = src[1]; m2 = src[2]; m3 = src[3];
+            }
+        }
+        int h0 = pidx(0, hy, hz);
+        ph[c][h0] = nlo >= 0 ? p[nlo * 192 + c * 64 + base + 3] : R(0);
+        ph[c][h0 + 1] = m0;
+        ph[c][h0 + 2] = m1;
+        ph[c][h0 + 3] = m2;
+        ph[c][h0 + 4] = m3;
+        ph[c][h0 + 5] = nhi >= 0 ? p[nhi * 192 + c * 64 + base] : R(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ua[c][h0 + k] = R(0);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void flush_halo_rows(const int* __restrict__ nbr, int slot, R (*ua)[PN], R* __restrict__ u) {
+    for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
+        int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<R>(nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        int h0 = pidx(0, hy, hz);
+        R lo = ua[c][h0], hi = ua[c][h0 + 5];
+        R m0 = ua[c][h0 + 1], m1 = ua[c][h0 + 2], m2 = ua[c][h0 + 3], m3 = ua[c][h0 + 4];
+        if (nlo >= 0 && lo != R(0)) atomicAdd(&u[nlo * 192 + c * 64 + base + 3], lo);
+        if (nhi >= 0 && hi != R(0)) atomicAdd(&u[nhi * 192 + c * 64 + base], hi);
+        if (nmid >= 0 && (m0 != R(0) || m1 != R(0) || m2 != R(0) || m3 != R(0))) {
+            R* dst = u + nmid * 192 + c * 64 + base;
+            if constexpr (sizeof(R) == 4) {
+                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(m0, m1, m2, m3));
+            } else {
+                atomicAdd(dst, m0);
+                atomicAdd(dst + 1, m1);
+                atomicAdd(dst + 2, m2);
+                atomicAdd(dst + 3, m3);
+            }
+        }
+    }
+}
 
 template <typename R>
 __global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
     __shared__ R ua[3][PN];
+    __shared__ R4<R> sp[MAXP];
+    __shared__ __align__(8) uint64_t bar;
     int w = blockIdx.x;
     int slot = a.work[w];
     long long gb = a.work_gb[w];
     int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
     if (a.check_done && a.scal[bc.w].cg_done) return;
-    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
-        int c = t / HN, h = t % HN;
-        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
-        int ns, loc;
-        halo_source(a.nbr, slot, h, ns, loc);
-        ph[c][pidx(hx, hy, hz)] = ns < 0 ? R(0) : a.p[ns * 192 + c * 64 + loc];
-        ua[c][pidx(hx, hy, hz)] = R(0);
-    }
+    const int bbeg = a.cell_start[gb * 64], bend = a.cell_start[gb * 64 + 64];
+    const int nchunk = (bend - bbeg + MAXP - 1) / MAXP;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    const R dt = (R)S.dt;
+    // the block's particle records stream into shared memory (TMA bulk copy)
+    // while the threads stage the direction's halo
+    if (threadIdx.x == 0 && nchunk > 0) {
+        uint32_t cnt = (uint32_t)min(MAXP, bend - bbeg);
+        mbar_expect_tx(&bar, cnt * (uint32_t)sizeof(R4<R>));
+        bulk_g2s(sp, a.opk + bbeg, cnt * (uint32_t)sizeof(R4<R>), &bar);
+    }
+    load_halo_rows<R>(a.nbr, slot, a.p, ph, ua);
+    __syncthreads();
     const R inv_dx = (R)S.inv_dx;
-    // this thread's cell
+    const R s2 = inv_dx * inv_dx;
     const int cell = threadIdx.x;
     const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
-    const int beg = a.cell_start[gb * 64 + cell], end = a.cell_start[gb * 64 + cell + 1];
-    if (end > beg) {
-        R C[3][3][3];
+    const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
+    R C[3][3][3], M[3][3][3];
+    if (cend > cbeg) {
 #pragma unroll
-        for (int q = 0; q < 27; ++q) (&C[0][0][0])[q] = R(0);
+        for (int q = 0; q < 27; ++q) {
+            (&C[0][0][0])[q] = R(0);
+            (&M[0][0][0])[q] = R(0);
+        }
         cell_coefficients<R>(ph, lx, ly, lz, C);
-        R M[3][3][3];
-#pragma unroll
-        for (int q = 0; q < 27; ++q) (&M[0][0][0])[q] = R(0);
-        bool any = false;
-        const R s2 = inv_dx * inv_dx;
-        for (int i = beg; i < end; ++i) {
-            if (a.phase[i] != 0 || a.cvisc[i] != R(0)) continue;   // k_apply_general
+    }
+    bool any = false, timed_out = false;
+    uint32_t parity_left = 0;
+    for (int k = 0; k < nchunk; ++k) {
+        const int c0 = bbeg + k * MAXP;
+        const int cnt = min(MAXP, bend - c0);
+        // bounded wait; the CTA agrees on the outcome so that no thread is left at a barrier
+        bool ok = mbar_wait_bounded(&bar, (uint32_t)(k & 1), 1LL << 26);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            parity_left = (uint32_t)(k & 1);
+            break;
+        }
+        const int lo = max(cbeg, c0), hi = min(cend, c0 + cnt);
+        for (int i = lo; i < hi; ++i) {
+            R4<R> rec = sp[i - c0];
+            if (rec.w < R(0)) continue;   // general particle: k_apply_general
             any = true;
-            R tx = a.pu.a[0][i] - R(lx), ty = a.pu.a[1][i] - R(ly), tz = a.pu.a[2][i] - R(lz);
-            tx = fmin(fmax(tx, R(0)), R(1));
-            ty = fmin(fmax(ty, R(0)), R(1));
-            tz = fmin(fmax(tz, R(0)), R(1));
+            R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
+            R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
+            R tz = fmin(fmax(rec.z - R(lz), R(0)), R(1));
             R px[3] = {R(1), tx, tx * tx};
-            R yz[3][3];
             R py[3] = {R(1), ty, ty * ty}, pz[3] = {R(1), tz, tz * tz};
+            R yz[3][3];
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
-                for (int k = 0; k < 3; ++k) yz[j][k] = py[j] * pz[k];
+                for (int kk = 0; kk < 3; ++kk) yz[j][kk] = py[j] * pz[kk];
             R tr = R(0);
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        if (!(ii == 2 && j == 2 && k == 2)) tr += C[ii][j][k] * px[ii] * yz[j][k];
-            R s = a.kappa[i] * s2 * tr;
+                    for (int kk = 0; kk < 3; ++kk)
+                        if (!(ii == 2 && j == 2 && kk == 2)) tr += C[ii][j][kk] * px[ii] * yz[j][kk];
+            R s = rec.w * s2 * tr;
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii) {
                 R sx = s * px[ii];
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        if (!(ii == 2 && j == 2 && k == 2)) M[ii][j][k] += sx * yz[j][k];
+                    for (int kk = 0; kk < 3; ++kk)
+                        if (!(ii == 2 && j == 2 && kk == 2)) M[ii][j][kk] += sx * yz[j][kk];
             }
         }
-        if (any) cell_scatter<R>(M, ua, lx, ly, lz);
+        __syncthreads();   // every thread is done with this chunk
+        if (k + 1 < nchunk && threadIdx.x == 0) {
+            uint32_t cnt2 = (uint32_t)min(MAXP, bend - (c0 + MAXP));
+            mbar_expect_tx(&bar, cnt2 * (uint32_t)sizeof(R4<R>));
+            bulk_g2s(sp, a.opk + c0 + MAXP, cnt2 * (uint32_t)sizeof(R4<R>), &bar);
+        }
     }
+    if (timed_out) {
+        // record the failure; wait once more (bounded) for the copy in flight, then leave
+        if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
+        mbar_wait_bounded(&bar, parity_left, 1LL << 20);
+        return;
+    }
+    if (any) cell_scatter<R>(M, ua, lx, ly, lz);
     __syncthreads();
-    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
-        int c = t / HN, h = t % HN;
-        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
-        R val = ua[c][pidx(hx, hy, hz)];
-        if (val == R(0)) continue;
-        int ns, loc;
-        halo_source(a.nbr, slot, h, ns, loc);
-        if (ns >= 0) atomicAdd(&a.u[ns * 192 + c * 64 + loc], val);
-    }
+    flush_halo_rows<R>(a.nbr, slot, ua, a.u);
 }
 
 // Solids, viscous liquids and surface samples: one thread per particle or
@@ -1031,14 +1139,7 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_general(ApplyArgs<R> a) {
     if (a.check_done && a.scal[bc.w].cg_done) return;
     const int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
     if (send == sbeg && a.slot_gen[slot] == 0) return;
-    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
-        int c = t / HN, h = t % HN;
-        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
-        int ns, loc;
-        halo_source(a.nbr, slot, h, ns, loc);
-        ph[c][pidx(hx, hy, hz)] = ns < 0 ? R(0) : a.p[ns * 192 + c * 64 + loc];
-        ua[c][pidx(hx, hy, hz)] = R(0);
-    }
+    load_halo_rows<R>(a.nbr, slot, a.p, ph, ua);
     __syncthreads();
     const R dt = (R)S.dt;
     const R inv_dx = (R)S.inv_dx;
@@ -1049,15 +1150,174 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_general(ApplyArgs<R> a) {
     }
     for (int j = sbeg + threadIdx.x; j < send; j += NT_CELL) sample_general<R>(a, j, ph, ua, dt, inv_dx);
     __syncthreads();
-    for (int t = threadIdx.x; t < 3 * HN; t += NT_CELL) {
-        int c = t / HN, h = t % HN;
-        int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
-        R val = ua[c][pidx(hx, hy, hz)];
-        if (val == R(0)) continue;
-        int ns, loc;
-        halo_source(a.nbr, slot, h, ns, loc);
-        if (ns >= 0) atomicAdd(&a.u[ns * 192 + c * 64 + loc], val);
+    flush_halo_rows<R>(a.nbr, slot, ua, a.u);
+}
+
+// ======================================================================
+// float64 objective / gradient and line search of non-viscous liquid particles,
+// thread per cell, with the per-cell polynomial form of k_apply_cell:
+// tr L(t) = (1/dx) sum C_ijk t^ijk from the iterate's stencil values, and the
+// gradient dt lambda (J - 1) J^n V0 gradN_i scattered through 26 moments.
+// ======================================================================
+struct EvalCellArgs {
+    const int *work, *work_gb, *nbr, *cell_start;
+    const int4* coord;
+    const SceneDev* sc;
+    SceneScal* scal;
+    const double* gv;
+    double* grad;             // null: energy only
+    const double *x0, *x1, *x2, *J, *V0;
+    const uint8_t* phase;
+    int skip_done;
+};
+
+__device__ __forceinline__ void cell_t(const SceneDev& S, int4 bc, int lx, int ly, int lz, double x0, double x1,
+                                       double x2, double& tx, double& ty, double& tz) {
+    tx = fmin(fmax((x0 - S.origin[0]) * S.inv_dx - (double)(bc.x * BS + lx), 0.0), 1.0);
+    ty = fmin(fmax((x1 - S.origin[1]) * S.inv_dx - (double)(bc.y * BS + ly), 0.0), 1.0);
+    tz = fmin(fmax((x2 - S.origin[2]) * S.inv_dx - (double)(bc.z * BS + lz), 0.0), 1.0);
+}
+
+__device__ __forceinline__ double poly_eval(const double C[3][3][3], double tx, double ty, double tz) {
+    double px[3] = {1.0, tx, tx * tx}, py[3] = {1.0, ty, ty * ty}, pz[3] = {1.0, tz, tz * tz};
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (!(i == 2 && j == 2 && k == 2)) r += C[i][j][k] * px[i] * py[j] * pz[k];
+    return r;
+}
+
+__global__ void __launch_bounds__(NT_CELL) k_eval_cell(EvalCellArgs a) {
+    __shared__ double ph[3][PN];
+    __shared__ double ga[3][PN];
+    __shared__ double red[NT_CELL / 32];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    if (a.skip_done && a.scal[bc.w].newton_done) return;
+    if (S.mu_l != 0.0) return;   // viscous scene: k_eval takes every particle
+    load_halo_rows<double>(a.nbr, slot, a.gv, ph, ga);
+    __syncthreads();
+    const int cell = threadIdx.x;
+    const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
+    const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
+    const double dt = S.dt, lam = S.lambda_l, inv_dx = S.inv_dx;
+    double esum = 0.0;
+    if (cend > cbeg) {
+        double C[3][3][3], M[3][3][3];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            (&C[0][0][0])[q] = 0.0;
+            (&M[0][0][0])[q] = 0.0;
+        }
+        cell_coefficients<double>(ph, lx, ly, lz, C);
+        bool any = false;
+        for (int i = cbeg; i < cend; ++i) {
+            if (a.phase[i] != 0) continue;
+            any = true;
+            double tx, ty, tz;
+            cell_t(S, bc, lx, ly, lz, a.x0[i], a.x1[i], a.x2[i], tx, ty, tz);
+            double tr = inv_dx * poly_eval(C, tx, ty, tz);
+            double Jn = a.J[i], v0 = a.V0[i];
+            double jm1 = (Jn - 1.0) + dt * tr * Jn;
+            esum += 0.5 * lam * jm1 * jm1 * v0;
+            double sp = dt * lam * jm1 * Jn * v0 * inv_dx;
+            double px[3] = {1.0, tx, tx * tx}, py[3] = {1.0, ty, ty * ty}, pz[3] = {1.0, tz, tz * tz};
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (!(ii == 2 && j == 2 && k == 2)) M[ii][j][k] += sp * px[ii] * py[j] * pz[k];
+        }
+        if (any && a.grad) cell_scatter<double>(M, ga, lx, ly, lz);
     }
+    block_atomic_sum<NT_CELL>(esum, &a.scal[bc.w].phi_part, red);
+    if (a.grad) {
+        __syncthreads();
+        flush_halo_rows<double>(a.nbr, slot, ga, a.grad);
+    }
+}
+
+template <typename RD>
+struct LSCellArgs {
+    const int *work, *work_gb, *nbr, *cell_start;
+    const int4* coord;
+    const SceneDev* sc;
+    SceneScal* scal;
+    const double* gv;
+    const RD* d;
+    const double *x0, *x1, *x2, *J, *V0;
+    const uint8_t* phase;
+};
+
+// line search: liquid energy differences for alpha_k = 2^-k, float64
+template <typename RD>
+__global__ void __launch_bounds__(NT_CELL) k_ls_cell(LSCellArgs<RD> a) {
+    __shared__ double pv[3][PN];
+    __shared__ double pd[3][PN];
+    __shared__ double red[NT_CELL / 32];
+    int w = blockIdx.x;
+    int slot = a.work[w];
+    long long gb = a.work_gb[w];
+    int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    SceneScal& scl = a.scal[bc.w];
+    if (scl.newton_done) return;
+    if (S.mu_l != 0.0) return;
+    load_halo_rows<double>(a.nbr, slot, a.gv, pv, pd);   // pd zeroed, then filled below
+    __syncthreads();
+    for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
+        int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<double>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        int h0 = pidx(0, hy, hz);
+        pd[c][h0] = nlo >= 0 ? (double)a.d[nlo * 192 + c * 64 + base + 3] : 0.0;
+        for (int k = 0; k < 4; ++k) pd[c][h0 + 1 + k] = nmid >= 0 ? (double)a.d[nmid * 192 + c * 64 + base + k] : 0.0;
+        pd[c][h0 + 5] = nhi >= 0 ? (double)a.d[nhi * 192 + c * 64 + base] : 0.0;
+    }
+    __syncthreads();
+    const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
+    const int cell = threadIdx.x;
+    const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
+    const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
+    const double dt = S.dt, lam = S.lambda_l, inv_dx = S.inv_dx;
+    double de[MAX_LS];
+#pragma unroll
+    for (int k = 0; k < MAX_LS; ++k) de[k] = 0.0;
+    if (cend > cbeg) {
+        double Cv[3][3][3], Cd[3][3][3];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+            (&Cv[0][0][0])[q] = 0.0;
+            (&Cd[0][0][0])[q] = 0.0;
+        }
+        cell_coefficients<double>(pv, lx, ly, lz, Cv);
+        cell_coefficients<double>(pd, lx, ly, lz, Cd);
+        for (int i = cbeg; i < cend; ++i) {
+            if (a.phase[i] != 0) continue;
+            double tx, ty, tz;
+            cell_t(S, bc, lx, ly, lz, a.x0[i], a.x1[i], a.x2[i], tx, ty, tz);
+            double trL = inv_dx * poly_eval(Cv, tx, ty, tz);
+            double trD = inv_dx * poly_eval(Cd, tx, ty, tz);
+            double Jn = a.J[i], v0 = a.V0[i];
+            double jm1 = (Jn - 1.0) + dt * trL * Jn;
+            double alpha = 1.0;
+            for (int k = 0; k < nls; ++k) {
+                double dJ = alpha * dt * trD * Jn;
+                de[k] += 0.5 * lam * v0 * dJ * (2.0 * jm1 + dJ);
+                alpha *= 0.5;
+            }
+        }
+    }
+    for (int k = 0; k < nls; ++k) block_atomic_sum<NT_CELL>(de[k], &scl.dphi[k], red);
 }
 
 // ======================================================================
@@ -1085,128 +1345,171 @@ __device__ __forceinline__ void cg_proj(R* v, const CGArgs<R, NC>& a, int t, con
 template <typename R, int NC>
 __device__ __forceinline__ int vidx(int slot, int q, int l) { return NC == 3 ? slot * 192 + q * 64 + l : slot * 64 + l; }
 
-template <typename R, int NC>
-__device__ __forceinline__ void scal_add2(SceneScal* sc, double* f1, double v1, double* f2, double v2) {
+constexpr int CG_SLOTS = 8;             // grid slots per CTA
+constexpr int CG_NT = CG_SLOTS * 64;
+constexpr int OFF_RR = offsetof(SceneScal, rr) / 8, OFF_RZ = offsetof(SceneScal, rz) / 8,
+              OFF_RZN = offsetof(SceneScal, rz_new) / 8, OFF_PAP = offsetof(SceneScal, pAp) / 8,
+              OFF_BN = offsetof(SceneScal, bnorm) / 8;
+
+// Per-scene sums of two values over the CTA: warp sums, then one float64 atomic
+// per run of equal scenes (slots are ordered scene by scene). scene < 0: no slot.
+__device__ __forceinline__ void cta_scene_sum2(double v1, double v2, int scene, SceneScal* scal, int off1, int off2) {
+    __shared__ double s1[CG_NT / 32], s2[CG_NT / 32];
+    __shared__ int sid[CG_NT / 32];
     v1 = warp_sum(v1);
     v2 = warp_sum(v2);
+    int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
-        if (v1 != 0.0) atomicAdd(f1, v1);
-        if (f2 && v2 != 0.0) atomicAdd(f2, v2);
+        s1[w] = v1;
+        s2[w] = v2;
+        sid[w] = scene;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int cur = -1;
+        double a1 = 0.0, a2 = 0.0;
+        for (int k = 0; k <= CG_NT / 32; ++k) {
+            int sk = k < CG_NT / 32 ? sid[k] : -2;
+            if (sk != cur) {
+                if (cur >= 0) {
+                    double* base = reinterpret_cast<double*>(&scal[cur]);
+                    if (off1 >= 0 && a1 != 0.0) atomicAdd(base + off1, a1);
+                    if (off2 >= 0 && a2 != 0.0) atomicAdd(base + off2, a2);
+                }
+                cur = sk;
+                a1 = a2 = 0.0;
+            }
+            if (k < CG_NT / 32) {
+                a1 += s1[k];
+                a2 += s2[k];
+            }
+        }
     }
 }
 
 // r = P b, x = 0, z = P(inv r), p = z, u = 0; rz, bnorm (if requested)
 template <typename R, int NC>
-__global__ void k_cg_init(CGArgs<R, NC> a, int set_bnorm) {
-    int slot = blockIdx.x, l = threadIdx.x;
-    int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    SceneScal& sc = a.scal[bc.w];
-    if (sc.cg_done) return;
-    int t = slot * 64 + l;
-    R r[NC];
+__global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int set_bnorm) {
+    int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
+    int scene = -1;
     double bb = 0.0, rz = 0.0;
+    if (slot < nb) {
+        scene = a.coord[slot].w;
+        const SceneDev& S = a.sc[scene];
+        if (!a.scal[scene].cg_done) {
+            int t = slot * 64 + l;
+            R r[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) r[q] = (R)(a.rhs_sign * a.rhs_d[vidx<R, NC>(slot, q, l)]);
-    cg_proj<R, NC>(r, a, t, S);
-    R z[NC];
+            for (int q = 0; q < NC; ++q) r[q] = (R)(a.rhs_sign * a.rhs_d[vidx<R, NC>(slot, q, l)]);
+            cg_proj<R, NC>(r, a, t, S);
+            R z[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) z[q] = r[q] * a.inv[t];
-    cg_proj<R, NC>(z, a, t, S);
+            for (int q = 0; q < NC; ++q) z[q] = r[q] * a.inv[t];
+            cg_proj<R, NC>(z, a, t, S);
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-        int k = vidx<R, NC>(slot, q, l);
-        a.r[k] = r[q];
-        a.x[k] = R(0);
-        a.p[k] = z[q];
-        a.u[k] = R(0);
-        bb += (double)r[q] * (double)r[q];
-        rz += (double)r[q] * (double)z[q];
+            for (int q = 0; q < NC; ++q) {
+                int k = vidx<R, NC>(slot, q, l);
+                a.r[k] = r[q];
+                a.x[k] = R(0);
+                a.p[k] = z[q];
+                a.u[k] = R(0);
+                bb += (double)r[q] * (double)r[q];
+                rz += (double)r[q] * (double)z[q];
+            }
+        }
     }
-    scal_add2<R, NC>(&sc, &sc.rz, rz, set_bnorm ? &sc.bnorm : nullptr, bb);
+    cta_scene_sum2(rz, bb, scene, a.scal, OFF_RZ, set_bnorm ? OFF_BN : -1);
 }
 
 // q = P (D p + u) -> u ; pAp
 template <typename R, int NC>
-__global__ void k_cg_pq(CGArgs<R, NC> a) {
-    int slot = blockIdx.x, l = threadIdx.x;
-    int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    SceneScal& sc = a.scal[bc.w];
-    if (sc.cg_done) return;
-    int t = slot * 64 + l;
-    R q[NC], pv[NC];
-    double diag;
-    if (NC == 3) diag = a.gm[t];
-    else diag = a.inv[t] == R(0) ? 0.0 : 1.0 / (double)a.inv[t];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        int k = vidx<R, NC>(slot, c, l);
-        pv[c] = a.p[k];
-        q[c] = (R)diag * pv[c] + a.u[k];
-    }
-    cg_proj<R, NC>(q, a, t, S);
+__global__ void __launch_bounds__(CG_NT) k_cg_pq(CGArgs<R, NC> a, int nb) {
+    int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
+    int scene = -1;
     double pq = 0.0;
+    if (slot < nb) {
+        scene = a.coord[slot].w;
+        const SceneDev& S = a.sc[scene];
+        if (!a.scal[scene].cg_done) {
+            int t = slot * 64 + l;
+            R q[NC], pv[NC];
+            double diag;
+            if (NC == 3) diag = a.gm[t];
+            else diag = a.inv[t] == R(0) ? 0.0 : 1.0 / (double)a.inv[t];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        a.u[vidx<R, NC>(slot, c, l)] = q[c];
-        pq += (double)pv[c] * (double)q[c];
+            for (int c = 0; c < NC; ++c) {
+                int k = vidx<R, NC>(slot, c, l);
+                pv[c] = a.p[k];
+                q[c] = (R)diag * pv[c] + a.u[k];
+            }
+            cg_proj<R, NC>(q, a, t, S);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                a.u[vidx<R, NC>(slot, c, l)] = q[c];
+                pq += (double)pv[c] * (double)q[c];
+            }
+        }
     }
-    scal_add2<R, NC>(&sc, &sc.pAp, pq, nullptr, 0.0);
+    cta_scene_sum2(pq, 0.0, scene, a.scal, OFF_PAP, -1);
 }
 
 // x += alpha p, r -= alpha q, u = 0; rz_new, rr   (negative curvature: x = p on the first iteration)
 template <typename R, int NC>
-__global__ void k_cg_update(CGArgs<R, NC> a) {
-    int slot = blockIdx.x, l = threadIdx.x;
-    int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    SceneScal& sc = a.scal[bc.w];
-    if (sc.cg_done) return;
-    int t = slot * 64 + l;
-    double pAp = sc.pAp;
+__global__ void __launch_bounds__(CG_NT) k_cg_update(CGArgs<R, NC> a, int nb) {
+    int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
+    int scene = -1;
     double rz_new = 0.0, rr = 0.0;
-    if (!(pAp > 0.0)) {
-        if (sc.cg_it == 0) {
+    if (slot < nb) {
+        scene = a.coord[slot].w;
+        const SceneDev& S = a.sc[scene];
+        const SceneScal& sc = a.scal[scene];
+        if (!sc.cg_done) {
+            int t = slot * 64 + l;
+            double pAp = sc.pAp;
+            if (!(pAp > 0.0)) {
+                if (sc.cg_it == 0) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                int k = vidx<R, NC>(slot, c, l);
-                a.x[k] = a.p[k];
+                    for (int c = 0; c < NC; ++c) {
+                        int k = vidx<R, NC>(slot, c, l);
+                        a.x[k] = a.p[k];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c) a.u[vidx<R, NC>(slot, c, l)] = R(0);
+            } else {
+                R alpha = (R)(sc.rz / pAp);
+                R r[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    int k = vidx<R, NC>(slot, c, l);
+                    a.x[k] += alpha * a.p[k];
+                    r[c] = a.r[k] - alpha * a.u[k];
+                    a.r[k] = r[c];
+                    a.u[k] = R(0);
+                }
+                R z[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) z[c] = r[c] * a.inv[t];
+                cg_proj<R, NC>(z, a, t, S);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    rz_new += (double)r[c] * (double)z[c];
+                    rr += (double)r[c] * (double)r[c];
+                }
             }
         }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) a.u[vidx<R, NC>(slot, c, l)] = R(0);
-        return;
     }
-    R alpha = (R)(sc.rz / pAp);
-    R r[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        int k = vidx<R, NC>(slot, c, l);
-        a.x[k] += alpha * a.p[k];
-        r[c] = a.r[k] - alpha * a.u[k];
-        a.r[k] = r[c];
-        a.u[k] = R(0);
-    }
-    R z[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) z[c] = r[c] * a.inv[t];
-    cg_proj<R, NC>(z, a, t, S);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        rz_new += (double)r[c] * (double)z[c];
-        rr += (double)r[c] * (double)r[c];
-    }
-    scal_add2<R, NC>(&sc, &sc.rz_new, rz_new, &sc.rr, rr);
+    cta_scene_sum2(rz_new, rr, scene, a.scal, OFF_RZN, OFF_RR);
 }
 
 // p = z + beta p
 template <typename R, int NC>
-__global__ void k_cg_p(CGArgs<R, NC> a) {
-    int slot = blockIdx.x, l = threadIdx.x;
-    int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    SceneScal& sc = a.scal[bc.w];
+__global__ void __launch_bounds__(CG_NT) k_cg_p(CGArgs<R, NC> a, int nb) {
+    int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
+    if (slot >= nb) return;
+    int scene = a.coord[slot].w;
+    const SceneDev& S = a.sc[scene];
+    const SceneScal& sc = a.scal[scene];
     if (sc.cg_done) return;
     int t = slot * 64 + l;
     R beta = (R)sc.alpha;   // holds beta here (set by k_cg_check)
@@ -1324,6 +1627,8 @@ struct LSArgs {
     const uint8_t* phase;
     Ptrs3 s, dA;
     const double* gamma;
+    int skip_poly;             // non-viscous liquid particles are left to k_ls_cell
+    const int* slot_gen;
 };
 
 // R: arithmetic type; RD: type of the Newton direction
@@ -1339,6 +1644,8 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
     const SceneDev& S = a.sc[bc.w];
     SceneScal& scl = a.scal[bc.w];
     if (scl.newton_done) return;
+    const bool poly = a.skip_poly && S.mu_l == 0.0;
+    if (poly && a.slot_gen[slot] == 0 && a.scell_start[gb * 64] == a.scell_start[gb * 64 + 64]) return;
     load_halo_vec_d<R>(a.nbr, slot, a.gv, vh);
     for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
         int c = t / HN, h = t % HN;
@@ -1353,7 +1660,9 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
 #pragma unroll
     for (int k = 0; k < MAX_LS; ++k) de[k] = 0.0;
     int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
+    if (poly && a.slot_gen[slot] == 0) end = beg;
     for (int i = beg + threadIdx.x; i < end; i += NT) {
+        if (poly && a.phase[i] == 0) continue;   // k_ls_cell
         double p[3] = {a.x.a[0][i], a.x.a[1][i], a.x.a[2][i]};
         int lc[3];
         R wgt[3][3], dw[3][3], f[3];
@@ -1680,6 +1989,8 @@ EvalArgs<R> make_eval_args(mpm_ctx* c, bool want_grad, bool want_cache, bool ski
     a.want_grad = want_grad;
     a.want_cache = want_cache;
     a.skip_done = skip_done;
+    a.skip_poly = 1;
+    a.slot_gen = d.slot_gen;
     for (int q = 0; q < 24; ++q) a.scache.a[q] = (R*)d.scache[q];
     a.sic = (R*)d.sic;
     return a;
@@ -1719,6 +2030,8 @@ ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int c
     a.sg = (const R*)d.sg;
     a.sic = (const R*)d.sic;
     a.slot_gen = d.slot_gen;
+    a.opk = (const R4<R>*)d.opk;
+    a.err = d.err;
     a.mode = mode;
     a.check_done = check_done;
     return a;
@@ -1768,7 +2081,7 @@ cudaError_t pack_step_t(mpm_ctx* c) {
         MPM_LAUNCH k_pack_volume<R><<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, Ptrs3{{d.x[0], d.x[1], d.x[2]}}, d.J, F, d.V0, d.T,
                                                            d.phase, d.psc, d.sc, pu, (R*)d.kappa, (R*)d.cvisc, Fn,
                                                            (R*)d.lame[0], (R*)d.lame[1], (R*)d.Vn, d.bslot,
-                                                           d.slot_gen);
+                                                           d.slot_gen, (R4<R>*)d.opk);
     }
     if (c->ns > 0) {
         RPtr3<R> su, sa;
@@ -1795,16 +2108,16 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     const int chunk = 8;
     if (NC_is_heat) {
         auto a = make_cg_args<R, 1>(c);
-        MPM_LAUNCH k_cg_init<R, 1><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
+        MPM_LAUNCH k_cg_init<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init);
         for (int it = 0; it < maxit; it += chunk) {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
                 launch_heat_apply(c, d.hp, d.hu);
                 prof_mark_apply(c, false);
-                MPM_LAUNCH k_cg_pq<R, 1><<<nb, 64, 0, st>>>(a);
-                MPM_LAUNCH k_cg_update<R, 1><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_pq<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
+                MPM_LAUNCH k_cg_update<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
                 MPM_LAUNCH k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 1);
-                MPM_LAUNCH k_cg_p<R, 1><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_p<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
             }
             cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
@@ -1817,17 +2130,17 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     } else {
         auto a = make_cg_args<R, 3>(c);
         auto ap = make_apply_args<R>(c, d.cp, d.cu, MPM_HESS_PROJECTED, 1);
-        MPM_LAUNCH k_cg_init<R, 3><<<nb, 64, 0, st>>>(a, set_bnorm_in_init);
+        MPM_LAUNCH k_cg_init<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init);
         for (int it = 0; it < maxit; it += chunk) {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
                 if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
                 if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<c->NW, NT_CELL, 0, st>>>(ap);
                 prof_mark_apply(c, false);
-                MPM_LAUNCH k_cg_pq<R, 3><<<nb, 64, 0, st>>>(a);
-                MPM_LAUNCH k_cg_update<R, 3><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_pq<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
+                MPM_LAUNCH k_cg_update<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
                 MPM_LAUNCH k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 0);
-                MPM_LAUNCH k_cg_p<R, 3><<<nb, 64, 0, st>>>(a);
+                MPM_LAUNCH k_cg_p<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
             }
             cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
@@ -1846,6 +2159,25 @@ cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) 
     if (c->NW == 0) return cudaSuccess;
     auto a = make_eval_args<RS>(c, want_grad, want_cache, skip_done);
     MPM_LAUNCH k_eval<R, RS><<<c->NW, NT, 0, c->st>>>(a);
+    Dev& d = c->d;
+    EvalCellArgs e;
+    e.work = d.work;
+    e.work_gb = d.work_gb;
+    e.nbr = d.nbr;
+    e.cell_start = d.cell_start;
+    e.coord = d.slot_coord;
+    e.sc = d.sc;
+    e.scal = d.scal;
+    e.gv = d.gv;
+    e.grad = want_grad ? d.ggrad : nullptr;
+    e.x0 = d.x[0];
+    e.x1 = d.x[1];
+    e.x2 = d.x[2];
+    e.J = d.J;
+    e.V0 = d.V0;
+    e.phase = d.phase;
+    e.skip_done = skip_done;
+    MPM_LAUNCH k_eval_cell<<<c->NW, NT_CELL, 0, c->st>>>(e);
     return cudaGetLastError();
 }
 
@@ -1903,7 +2235,26 @@ cudaError_t newton_t(mpm_ctx* c) {
             for (int q = 0; q < 9; ++q) a.F.a[q] = d.F[q];
             a.phase = d.phase;
             a.gamma = d.gamma;
+            a.skip_poly = 1;
+            a.slot_gen = d.slot_gen;
             MPM_LAUNCH k_linesearch<double, R><<<c->NW, NT, 0, st>>>(a);
+            LSCellArgs<R> lc;
+            lc.work = d.work;
+            lc.work_gb = d.work_gb;
+            lc.nbr = d.nbr;
+            lc.cell_start = d.cell_start;
+            lc.coord = d.slot_coord;
+            lc.sc = d.sc;
+            lc.scal = d.scal;
+            lc.gv = d.gv;
+            lc.d = (const R*)d.cx;
+            lc.x0 = d.x[0];
+            lc.x1 = d.x[1];
+            lc.x2 = d.x[2];
+            lc.J = d.J;
+            lc.V0 = d.V0;
+            lc.phase = d.phase;
+            MPM_LAUNCH k_ls_cell<R><<<c->NW, NT_CELL, 0, st>>>(lc);
         }
         MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, (const R*)d.cx);
         MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
