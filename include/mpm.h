@@ -243,6 +243,32 @@ typedef struct {
 mpm_status mpm_profile_enable(mpm_ctx* ctx, int32_t enable);
 mpm_status mpm_get_profile(mpm_ctx* ctx, mpm_profile* out);
 
+/* Closest interior particle of each surface sample, computed without allocating.
+ *
+ * The paper has no counterpart of this entry point: it serves callers that cannot
+ * allocate device memory (code inside a CUDA graph being captured, allocators that
+ * forbid cudaMalloc after start-up, hosts that give the library a fixed memory
+ * budget) and so cannot create a context. It returns the same parents as
+ * mpm_resample: for sample r the index (into x) of the particle with the smallest
+ * squared distance, formed as (dx^2 + dy^2) + dz^2 in float64, ties to the smaller
+ * index, searched over the 27 cells around the sample.
+ *
+ * x: n_particles x 3 float64, s: n_samples x 3 float64, parent: n_samples int32, all
+ * in memory the device can read / write (device memory, or host memory the device can
+ * access); grid: only n, dx and origin are read. stream: a cudaStream_t or NULL.
+ * Limits: n_particles <= 524288 and n0 n1 n2 <= 1048576 cells, else MPM_ERR_CAPACITY.
+ * Particles must lie in cells 1 .. n-2 and every sample must have a particle within
+ * dx, else MPM_ERR_DOMAIN (parent = -1 for such samples).
+ *
+ * Working memory is one fixed device array in the library (about 12.6 MB on every
+ * GPU that loads the library, held until the process exits); nothing is allocated or
+ * freed. The first call on a device looks up that array's device address; make that
+ * first call before any stream capture. Every call reuses the same array, so calls
+ * whose work overlaps on the GPU (different streams, or different host threads)
+ * race: serialise them. The call synchronises `stream` before returning. */
+mpm_status mpm_nearest_parent_noalloc(const mpm_grid_desc* grid, int64_t n_particles, const double* x,
+                                      int64_t n_samples, const double* s, int32_t* parent, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ FIELD_COMPS = {FIELD_MASS: 1, FIELD_MOMENTUM: 3, FIELD_VN: 3, FIELD_THERMAL_MASS
 EXPORTED = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_particles", "mpm_get_particles",
             "mpm_set_surface", "mpm_get_surface", "mpm_resample", "mpm_p2g", "mpm_get_grid", "mpm_set_velocity",
             "mpm_energy_gradient", "mpm_apply_hessian", "mpm_heat_apply", "mpm_newton_step", "mpm_g2p", "mpm_step",
-            "mpm_sync", "mpm_counts", "mpm_profile_enable", "mpm_get_profile"]
+            "mpm_sync", "mpm_counts", "mpm_profile_enable", "mpm_get_profile", "mpm_nearest_parent_noalloc"]
 
 
 class GridDesc(ctypes.Structure):
@@ -104,6 +104,8 @@ _lib.mpm_sync.argtypes = [_vp]
 _lib.mpm_counts.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
 _lib.mpm_profile_enable.argtypes = [_vp, ctypes.c_int32]
 _lib.mpm_get_profile.argtypes = [_vp, ctypes.POINTER(Profile)]
+_lib.mpm_nearest_parent_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp,
+                                            _vp]
 for _name in EXPORTED:
     if _name != "mpm_last_error":
         getattr(_lib, _name).restype = ctypes.c_int
@@ -336,6 +338,18 @@ class Context:
         out = np.zeros_like(T)
         self._check(_lib.mpm_heat_apply(self.h, k, _ptr(T), _ptr(out)))
         return out
+
+
+def nearest_parent_noalloc(grid, x, s, parent, stream=None):
+    """Closest particle of each sample without any allocation (see include/mpm.h).
+
+    grid: a GridDesc (or a Scene); x (N, 3) and s (M, 3) float64 and parent (M,)
+    int32 must be device-accessible (torch CUDA tensors). Returns the status code.
+    """
+    if isinstance(grid, _scenes.Scene):
+        grid = scene_desc(grid).grid
+    return _lib.mpm_nearest_parent_noalloc(ctypes.byref(grid), int(x.shape[0]), _ptr(x), int(s.shape[0]), _ptr(s),
+                                           _ptr(parent), stream)
 
 
 def exported_symbols():
