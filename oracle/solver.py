@@ -11,7 +11,8 @@ earlier work. Readings used here:
   relative tolerance cg_rtol on the residual 2-norm; on non-positive curvature
   CG stops with the current iterate (or the preconditioned steepest descent
   direction if that happens on the first iteration);
-* Armijo backtracking on Phi (c = 1e-4, halving, at most max_ls trials);
+* Armijo backtracking on Phi (c = 1e-4, halving, at most max_ls trials); when no
+  trial decreases Phi the iterate is kept and Newton stops;
 * stop when |P r|_2 <= tol * max(|P r_0|_2, 1e-12);
 * the step ends with one explicit evaluation of the grid forces at the
   converged iterate, v = P (v - r(v)/m) = P (v^n + dt g + dt f(x + dt v)/m), so the
@@ -82,13 +83,21 @@ def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False):
             phi0 = state.energy(v)
             slope = float(np.sum(r * d))
             alpha = 1.0
+            accepted = False
             for _ in range(prm.max_ls):
                 if state.energy(v + alpha * d) <= phi0 + 1e-4 * alpha * slope:
+                    accepted = True
                     break
                 alpha *= 0.5
+            stats["newton"] = k + 1
+            if not accepted:
+                # no trial decreases Phi (round-off floor, or a CG direction that
+                # lost its meaning): keep the iterate and stop
+                stats["alpha"].append(0.0)
+                stats["stalled"] = True
+                break
             stats["alpha"].append(alpha)
             v = v + alpha * d
-            stats["newton"] = k + 1
     else:
         # explicit step (q = 0 in Eq. disc_force): forces at the unmoved nodes,
         # i.e. the objective's gradient at v = 0 gives -m v^n - dt m g - dt f(x)

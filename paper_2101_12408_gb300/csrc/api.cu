@@ -355,7 +355,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.gmTT, double, NN); A_(d.gTn, double, NN); A_(d.gv, double, NN * 3); A_(d.gvhat, double, NN * 3);
     A_(d.gThat, double, NN); A_(d.ggrad, double, NN * 3); A_(d.hrhs, double, NN);
     A_(d.pcode, uint8_t, NN);
-    R_(d.cx, NN * 3); R_(d.cr, NN * 3); R_(d.cp, NN * 3); R_(d.cu, NN * 3); R_(d.invm, NN);
+    R_(d.cx, NN * 3); R_(d.cr, NN * 3); R_(d.cp, NN * 3); R_(d.cu, NN * 3); R_(d.invm, NN); R_(d.pinv, NN * 3);
     R_(d.hx, NN); R_(d.hr, NN); R_(d.hp, NN); R_(d.hu, NN); R_(d.hinvd, NN); R_(d.hT, NN);
     size_t stg = staging_doubles(c);
     A_(*(double**)&d.dense_a, double, stg); A_(*(double**)&d.dense_b, double, stg);

@@ -70,6 +70,7 @@ struct Dev {
     uint8_t* pcode;
     // ---- solver vectors (R) ----
     void *cx, *cr, *cp, *cu, *invm;
+    void* pinv;                     // momentum CG preconditioner: 1 / diag(P H P) per component
     void *hx, *hr, *hp, *hu, *hinvd, *hT;   // heat CG (scalar fields)
     double* hrhs;
     // dense staging for the C ABI

@@ -950,6 +950,7 @@ __device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (
 }
 
 constexpr int NT_CELL = 64;
+constexpr int NT_GEN = 32;  // one warp: a block holds ~20-40 surface samples
 constexpr int MAXP = 640;   // particle records staged per chunk
 
 // Halo rows along x: the four middle nodes of a row belong to one neighbour block
@@ -1128,7 +1129,7 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
 // sample, shared-memory accumulation on the padded halo. Blocks with none of
 // them return at once (slot_gen counts the block's general particles).
 template <typename R>
-__global__ void __launch_bounds__(NT_CELL) k_apply_general(ApplyArgs<R> a) {
+__global__ void __launch_bounds__(NT_GEN) k_apply_general(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
     __shared__ R ua[3][PN];
     int w = blockIdx.x;
@@ -1145,10 +1146,10 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_general(ApplyArgs<R> a) {
     const R inv_dx = (R)S.inv_dx;
     if (a.slot_gen[slot] > 0) {
         const int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
-        for (int i = beg + threadIdx.x; i < end; i += NT_CELL)
+        for (int i = beg + threadIdx.x; i < end; i += blockDim.x)
             if (a.phase[i] != 0 || a.cvisc[i] != R(0)) particle_general<R>(a, i, ph, ua, dt, inv_dx);
     }
-    for (int j = sbeg + threadIdx.x; j < send; j += NT_CELL) sample_general<R>(a, j, ph, ua, dt, inv_dx);
+    for (int j = sbeg + threadIdx.x; j < send; j += blockDim.x) sample_general<R>(a, j, ph, ua, dt, inv_dx);
     __syncthreads();
     flush_halo_rows<R>(a.nbr, slot, ua, a.u);
 }
@@ -1321,6 +1322,28 @@ __global__ void __launch_bounds__(NT_CELL) k_ls_cell(LSCellArgs<RD> a) {
 }
 
 // ======================================================================
+// Jacobi preconditioner of the momentum CG: 1 / m_i on unknown components.
+// (Adding the liquid stiffness diagonal sum_p kappa_p (dN_i/dx_a)^2 was measured
+// to raise the CG count on the inclined droplets, 170 -> 202 per step: the
+// grad-div stiffness leaves divergence-free modes at the mass scale.)
+// ======================================================================
+// pinv = 1 / (m + pinv) on unknown components (pinv holds zero on entry), 0 elsewhere
+template <typename R>
+__global__ void k_pinv(int nb, const int4* __restrict__ coord, const SceneDev* __restrict__ sc,
+                       const double* __restrict__ gm, const uint8_t* __restrict__ pcode, R* __restrict__ pinv) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb * 64) return;
+    int slot = t >> 6, l = t & 63;
+    double m = gm[t];
+    uint8_t code = pcode[t];
+    for (int c = 0; c < 3; ++c) {
+        int k = slot * 192 + c * 64 + l;
+        double dg = m + (double)pinv[k];   // pinv holds the stiffness diagonal on entry
+        pinv[k] = (m > 0.0 && !(code & PC_FIXED)) ? (R)(1.0 / dg) : R(0);
+    }
+}
+
+// ======================================================================
 // CG vector kernels (one 64-thread CTA per slot; NC = 3 momentum, 1 heat)
 // ======================================================================
 template <typename R, int NC>
@@ -1334,7 +1357,15 @@ struct CGArgs {
     R *x, *r, *p, *u;
     const double* rhs_d;      // for init: b = sign * rhs (double)
     double rhs_sign;
+    const R* pinv3;           // NC == 3: inverse diagonal of the projected Hessian, per component
 };
+
+// preconditioner entry of node t, component c
+template <typename R, int NC>
+__device__ __forceinline__ R cg_prec(const CGArgs<R, NC>& a, int slot, int c, int l, int t) {
+    if (NC == 3) return a.pinv3[slot * 192 + c * 64 + l];
+    return a.inv[t];
+}
 
 template <typename R, int NC>
 __device__ __forceinline__ void cg_proj(R* v, const CGArgs<R, NC>& a, int t, const SceneDev& S) {
@@ -1404,8 +1435,9 @@ __global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int 
             cg_proj<R, NC>(r, a, t, S);
             R z[NC];
 #pragma unroll
-            for (int q = 0; q < NC; ++q) z[q] = r[q] * a.inv[t];
+            for (int q = 0; q < NC; ++q) z[q] = r[q] * cg_prec<R, NC>(a, slot, q, l, t);
             cg_proj<R, NC>(z, a, t, S);
+            R bbl = R(0), rzl = R(0);   // the node's products in R; sums across nodes in float64
 #pragma unroll
             for (int q = 0; q < NC; ++q) {
                 int k = vidx<R, NC>(slot, q, l);
@@ -1413,9 +1445,11 @@ __global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int 
                 a.x[k] = R(0);
                 a.p[k] = z[q];
                 a.u[k] = R(0);
-                bb += (double)r[q] * (double)r[q];
-                rz += (double)r[q] * (double)z[q];
+                bbl += r[q] * r[q];
+                rzl += r[q] * z[q];
             }
+            bb = (double)bbl;
+            rz = (double)rzl;
         }
     }
     cta_scene_sum2(rz, bb, scene, a.scal, OFF_RZ, set_bnorm ? OFF_BN : -1);
@@ -1443,11 +1477,13 @@ __global__ void __launch_bounds__(CG_NT) k_cg_pq(CGArgs<R, NC> a, int nb) {
                 q[c] = (R)diag * pv[c] + a.u[k];
             }
             cg_proj<R, NC>(q, a, t, S);
+            R pql = R(0);
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 a.u[vidx<R, NC>(slot, c, l)] = q[c];
-                pq += (double)pv[c] * (double)q[c];
+                pql += pv[c] * q[c];
             }
+            pq = (double)pql;
         }
     }
     cta_scene_sum2(pq, 0.0, scene, a.scal, OFF_PAP, -1);
@@ -1489,13 +1525,16 @@ __global__ void __launch_bounds__(CG_NT) k_cg_update(CGArgs<R, NC> a, int nb) {
                 }
                 R z[NC];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) z[c] = r[c] * a.inv[t];
+                for (int c = 0; c < NC; ++c) z[c] = r[c] * cg_prec<R, NC>(a, slot, c, l, t);
                 cg_proj<R, NC>(z, a, t, S);
+                R rzl = R(0), rrl = R(0);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    rz_new += (double)r[c] * (double)z[c];
-                    rr += (double)r[c] * (double)r[c];
+                    rzl += r[c] * z[c];
+                    rrl += r[c] * r[c];
                 }
+                rz_new = (double)rzl;
+                rr = (double)rrl;
             }
         }
     }
@@ -1515,7 +1554,7 @@ __global__ void __launch_bounds__(CG_NT) k_cg_p(CGArgs<R, NC> a, int nb) {
     R beta = (R)sc.alpha;   // holds beta here (set by k_cg_check)
     R z[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) z[c] = a.r[vidx<R, NC>(slot, c, l)] * a.inv[t];
+    for (int c = 0; c < NC; ++c) z[c] = a.r[vidx<R, NC>(slot, c, l)] * cg_prec<R, NC>(a, slot, c, l, t);
     cg_proj<R, NC>(z, a, t, S);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -1836,10 +1875,17 @@ __global__ void k_ls_pick(SceneScal* scal, const SceneDev* sc, int nsc) {
         }
         alpha *= 0.5;
     }
-    c.alpha = alpha;   // 2^-nls when no trial passed
     c.ls_pick = pick;
     c.cg_total += c.cg_it;
     c.newton_it += 1;
+    if (pick == nls) {
+        // no trial decreases Phi: keep the iterate and stop (above tolerance)
+        c.alpha = 0.0;
+        c.newton_done = 1;
+        c.status = MPM_ERR_NOT_CONVERGED;
+    } else {
+        c.alpha = alpha;
+    }
 }
 
 template <typename R>
@@ -1878,6 +1924,13 @@ __global__ void k_newton_final(const int4* __restrict__ coord, const SceneDev* _
         double mv = warp_sum(m * v[q]);
         if ((l & 31) == 0 && mv != 0.0) atomicAdd(&scal[bc.w].mom[q], mv);
     }
+}
+
+__global__ void k_zero_grad_active(int nb, const int4* __restrict__ coord, const SceneScal* __restrict__ scal,
+                                   double* __restrict__ grad) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nb * 192) return;
+    if (!scal[coord[t / 192].w].newton_done) grad[t] = 0.0;
 }
 
 __global__ void k_zero_mom(SceneScal* scal, int nsc) {
@@ -2048,6 +2101,7 @@ CGArgs<R, NC> make_cg_args(mpm_ctx* c) {
     a.gm = d.gm;
     if (NC == 3) {
         a.inv = (const R*)d.invm;
+        a.pinv3 = (const R*)d.pinv;
         a.x = (R*)d.cx;
         a.r = (R*)d.cr;
         a.p = (R*)d.cp;
@@ -2056,6 +2110,7 @@ CGArgs<R, NC> make_cg_args(mpm_ctx* c) {
         a.rhs_sign = -1.0;
     } else {
         a.inv = (const R*)d.hinvd;
+        a.pinv3 = nullptr;
         a.x = (R*)d.hx;
         a.r = (R*)d.hr;
         a.p = (R*)d.hp;
@@ -2082,6 +2137,11 @@ cudaError_t pack_step_t(mpm_ctx* c) {
                                                            d.phase, d.psc, d.sc, pu, (R*)d.kappa, (R*)d.cvisc, Fn,
                                                            (R*)d.lame[0], (R*)d.lame[1], (R*)d.Vn, d.bslot,
                                                            d.slot_gen, (R4<R>*)d.opk);
+    }
+    if (c->NW > 0) {
+        cudaMemsetAsync(d.pinv, 0, sizeof(R) * (size_t)c->NB * 192, st);
+        MPM_LAUNCH k_pinv<R><<<nblk((long long)c->NB * 64, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.pcode,
+                                                                             (R*)d.pinv);
     }
     if (c->ns > 0) {
         RPtr3<R> su, sa;
@@ -2135,7 +2195,7 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
                 if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
-                if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<c->NW, NT_CELL, 0, st>>>(ap);
+                if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<c->NW, NT_GEN, 0, st>>>(ap);
                 prof_mark_apply(c, false);
                 MPM_LAUNCH k_cg_pq<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
                 MPM_LAUNCH k_cg_update<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
@@ -2199,7 +2259,9 @@ cudaError_t newton_t(mpm_ctx* c) {
     for (auto& S : c->hsc) maxn = maxn > S.max_newton ? maxn : S.max_newton;
     for (int it = 0; it <= maxn; ++it) {
         MPM_LAUNCH k_newton_iter_begin<<<gs, 128, 0, st>>>(d.scal, ns);
-        cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
+        // zero the gradient of scenes still iterating; converged scenes keep the
+        // gradient at their final iterate for the closing force evaluation
+        MPM_LAUNCH k_zero_grad_active<<<nblk((long long)nb * 192, 256), 256, 0, st>>>(nb, d.slot_coord, d.scal, d.ggrad);
         eval_any(c, true, true, true);
         MPM_LAUNCH k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 1);
         MPM_LAUNCH k_newton_check<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
@@ -2260,11 +2322,9 @@ cudaError_t newton_t(mpm_ctx* c) {
         MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
         MPM_LAUNCH k_newton_update<R><<<nb, 64, 0, st>>>(d.slot_coord, d.scal, (const R*)d.cx, d.gv);
     }
-    // final explicit force evaluation in float64
+    // final explicit force evaluation: the loop ends right after evaluating the
+    // float64 gradient at the final iterate of every scene, so it is in ggrad
     MPM_LAUNCH k_zero_mom<<<gs, 128, 0, st>>>(d.scal, ns);
-    cudaMemsetAsync(d.ggrad, 0, sizeof(double) * (size_t)nb * 192, st);
-    eval_any(c, true, false, false);
-    MPM_LAUNCH k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 0);
     MPM_LAUNCH k_newton_final<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gv, d.ggrad, d.pcode, d.gvhat);
     return cudaGetLastError();
 }
@@ -2292,11 +2352,11 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
     if (c->rsize == 4) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
-        MPM_LAUNCH k_apply_general<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_general<float><<<c->NW, NT_GEN, 0, c->st>>>(a);
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
-        MPM_LAUNCH k_apply_general<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_general<double><<<c->NW, NT_GEN, 0, c->st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -231,3 +231,92 @@ def test_nonfinite_input_rejected():
     with pytest.raises(mpm.MPMError) as ei:
         ctx.load_scene(0)
     assert ei.value.status == mpm.MPM_ERR_NUMERIC
+
+
+# ----------------------------------------------------------------------------
+# the other workloads at parity-test sizes, and batched scenes
+# ----------------------------------------------------------------------------
+
+def _small_film():
+    return scenes.film(nx=24, ny=24, nz=12, height_cells=4, seed=41)
+
+
+def _small_wax():
+    sc = scenes.wax(nx=24, ny=24, nz=20, cube_cells=10, seed=42, b_heat=5000.0)
+    return sc
+
+
+def _small_incline():
+    sc = scenes.incline(n=48, n_drops=2, r_range=(3.0, 5.0), seed=43, gap_cells=(0.0, 0.5))
+    return sc
+
+
+WORKLOADS = {"film": _small_film, "wax": _small_wax, "incline": _small_incline}
+
+
+def _tight(sc):
+    # float64 forms on both sides converge well below the comparison tolerance; the
+    # Newton floor of these stiff scenes (lambda up to 1e6) is near 1e-11 relative
+    sc.params.newton_tol = 1e-9
+    sc.params.cg_rtol = 1e-6
+    sc.params.heat_rtol = 1e-12
+    sc.params.max_cg = 1000
+    return sc
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_workload_step_matches_oracle(name, prec):
+    sc = WORKLOADS[name]()
+    if prec == mpm.PREC_FP64:
+        _tight(sc)
+    ctx = mpm.Context(sc, precision=prec)
+    ctx.load_scene(0)
+    sim = oracle.OracleSim(sc)
+    tol = 1e-8 if prec == mpm.PREC_FP64 else 1e-5
+    for step in range(2):
+        ctx.resample()
+        ctx.p2g()
+        stats = ctx.newton_step()
+        sim.resample()
+        sim.p2g()
+        sim.grid_update()
+        np.testing.assert_array_equal(ctx.get_surface(0)["parent"], sim.parent)
+        assert relerr(ctx.get_grid(0, mpm.FIELD_VHAT), sim.vhat) < tol, (step, stats)
+        if sc.params.thermal:
+            assert relerr(ctx.get_grid(0, mpm.FIELD_THAT), sim.That) < (1e-9 if prec == mpm.PREC_FP64 else 2e-4)
+        ctx.g2p()
+        sim.g2p()
+    p = ctx.get_particles(0)
+    assert relerr(p["v"], sim.sc.v) < tol
+    np.testing.assert_array_equal(p["phase"], sim.sc.phase)
+
+
+def test_wax_melts_on_the_heated_face():
+    sc = _small_wax()
+    ctx = mpm.Context(sc, precision=mpm.PREC_FP32_FP64RED)
+    ctx.load_scene(0)
+    for _ in range(3):
+        ctx.step()
+    p = ctx.get_particles(0)
+    hot = sc.x[:, 0] < sc.x[:, 0].min() + 1.5 * sc.dx
+    assert p["T"][hot].mean() > p["T"][~hot].mean()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_scenes_match_the_oracle_scene_by_scene(prec):
+    group = scenes.batch(n_scenes=4, n_range=(16, 24), count_range=(800.0, 4000.0), seed=2000)
+    if prec == mpm.PREC_FP64:
+        for sc in group:
+            _tight(sc)
+    ctx = mpm.Context(group, precision=prec)
+    for k in range(len(group)):
+        ctx.load_scene(k)
+    stats = ctx.step()
+    tol = 1e-8 if prec == mpm.PREC_FP64 else 1e-5
+    for k, sc in enumerate(group):
+        sim = oracle.OracleSim(sc)
+        sim.step()
+        p = ctx.get_particles(k)
+        assert relerr(p["v"], sim.sc.v) < tol, (k, sc.name, stats[k])
+        assert relerr(p["x"], sim.sc.x) < 1e-9
