@@ -122,17 +122,17 @@ class ClockSampler:
 
 
 def algorithmic_bytes(ctx, sc, rsize):
-    """Bytes one Hessian-operator launch must move: per liquid particle its
-    position and two coefficients, per solid particle position, F^n, Lame pair
-    and the iterate's F, R, (tr S I - S)^-1, per surface sample position, dA,
-    F^, n, 1/|c|, gamma, per active node the direction read and the product
-    written (3 components each)."""
+    """Bytes one Hessian-operator launch must move (the packed record of a liquid
+    particle: position in its block and kappa, 4 values; a solid particle:
+    position, F^n, Lame pair and the iterate's F, R, (tr S I - S)^-1; a surface
+    sample: position, dA, F^, n, 1/|c|, gamma; an active node: the direction read
+    and the product written, 3 components each)."""
     p = ctx.get_particles(0)
     nsol = int(np.sum(p["phase"] == 1))
     nliq = ctx.np[0] - nsol
     m = ctx.get_grid(0, 0)
     g_active = int(np.sum(m > 0))
-    b = rsize * (nliq * 5 + nsol * (3 + 9 + 2 + 24) + ctx.ns[0] * 20 + g_active * 6)
+    b = rsize * (nliq * 4 + nsol * (3 + 9 + 2 + 24) + ctx.ns[0] * 20 + g_active * 6)
     return b, dict(liquid=nliq, solid=nsol, surface=ctx.ns[0], active_nodes=g_active)
 
 
