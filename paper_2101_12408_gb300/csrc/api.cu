@@ -337,7 +337,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.pid, int, P); A_(d.psc, int, P);
     A_(d.scratch_p, double, P); A_(d.scratch_s, double, Sn);
     A_(d.gcount, int, P); A_(d.mt, double, P);
-    R_(d.opk, 4 * P); R_(d.kappa, P); R_(d.cvisc, P); R_(d.lame[0], PS); R_(d.lame[1], PS); R_(d.Vn, P);
+    R_(d.kappa, P); R_(d.cvisc, P); R_(d.lame[0], PS); R_(d.lame[1], PS); R_(d.Vn, P);
     A_(d.bheat, double, Sn); A_(d.Tbar, double, Sn); A_(d.gamma, double, Sn); A_(d.Tr, double, Sn);
     A_(d.kind, uint8_t, Sn);
     A_(d.sid, int, Sn); A_(d.ssc, int, Sn); A_(d.parent, int, Sn);
@@ -346,26 +346,26 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.skey, long long, Sn); A_(d.srank, int, Sn); A_(d.sperm, int, Sn);
     A_(d.cell_count, int, c->total_cells + 1); A_(d.cell_start, int, c->total_cells + 1);
     A_(d.scell_count, int, c->total_cells + 1); A_(d.scell_start, int, c->total_cells + 1);
-    A_(d.bflag, int, NBc + 1); A_(d.bwork, int, NBc + 1); A_(d.bslot, int, NBc + 1); A_(d.bscan, int, NBc + 1);
+    A_(d.bflag, int, NBc + 1); A_(d.bwork, int, NBc + 1); A_(d.bslot, int, NBc + 1); A_(d.bscan, int, NBc + 1); A_(d.bw, int, NBc + 1);
     A_(d.slot_coord, int4, bcap + 1); A_(d.nbr, int, bcap * 27 + 27); A_(d.work, int, bcap + 1); A_(d.work_gb, int, bcap + 1);
-    A_(d.slot_gen, int, bcap + 1);
+    A_(d.slot_gen, int, bcap + 1); A_(d.wrows, int, bcap + 1); A_(d.wroff, int, bcap + 2);
     A_(d.counts, int, 4);
     A_(d.scan_tmp, int, (c->total_cells + 1) / 4096 + 16);
     A_(d.gm, double, NN); A_(d.gmv, double, NN * 3); A_(d.gvn, double, NN * 3); A_(d.gmT, double, NN);
     A_(d.gmTT, double, NN); A_(d.gTn, double, NN); A_(d.gv, double, NN * 3); A_(d.gvhat, double, NN * 3);
-    A_(d.gThat, double, NN); A_(d.ggrad, double, NN * 3); A_(d.hrhs, double, NN);
+    A_(d.gThat, double, NN); A_(d.ggrad, double, NN * 3); A_(d.ggrad_l, double, NN * 3); A_(d.hrhs, double, NN);
     A_(d.pcode, uint8_t, NN);
     R_(d.cx, NN * 3); R_(d.cr, NN * 3); R_(d.cp, NN * 3); R_(d.cu, NN * 3); R_(d.invm, NN); R_(d.pinv, NN * 3);
     R_(d.hx, NN); R_(d.hr, NN); R_(d.hp, NN); R_(d.hu, NN); R_(d.hinvd, NN); R_(d.hT, NN);
     size_t stg = staging_doubles(c);
     A_(*(double**)&d.dense_a, double, stg); A_(*(double**)&d.dense_b, double, stg);
-    A_(d.sc, SceneDev, n_scenes); A_(d.scal, SceneScal, n_scenes); A_(d.err, int, 1);
+    A_(d.sc, SceneDev, n_scenes); A_(d.scal, SceneScal, n_scenes); A_(d.err, int, 1); A_(d.cg_bar, unsigned, 2);
 #undef A_
 #undef R_
     for (int k = 0; k < 34 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     if (e == cudaSuccess) e = cudaMallocHost(&c->hscal, sizeof(SceneScal) * n_scenes);
     if (e == cudaSuccess) e = cudaMallocHost(&c->herr, sizeof(int));
-    if (e == cudaSuccess) e = cudaMallocHost(&c->hcounts, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->hcounts, sizeof(int) * 8);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d.sc, c->hsc.data(), sizeof(SceneDev) * n_scenes, cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.scal, 0, sizeof(SceneScal) * n_scenes, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.err, 0, sizeof(int), c->st);
@@ -382,6 +382,7 @@ mpm_status mpm_destroy(mpm_ctx* c) {
     if (!c) return MPM_ERR_INVALID_ARG;
     if (c->st) cudaStreamSynchronize(c->st); else cudaDeviceSynchronize();
     for (void* p : c->allocs) cudaFree(p);
+    if (c->d.opk) cudaFree(c->d.opk);
     for (int k = 0; k < 34; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->hscal) cudaFreeHost(c->hscal);

@@ -44,6 +44,7 @@ struct SceneScal {
     double rr, rz, rz_new, pAp, bnorm, r0, rnorm, slope;
     double phi_kin, phi_part;
     double dphi[MAX_LS];
+    double dkd;        // d . K_liquid d of the current Newton direction
     double alpha;
     double mom[3];
     int cg_it, cg_total, newton_it, cg_done, newton_done, ls_pick, status, heat_it;

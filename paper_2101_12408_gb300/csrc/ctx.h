@@ -29,7 +29,11 @@ struct Dev {
     void* pu[3];                    // position relative to the block origin, in cells
     void* kappa;                    // dt^2 lambda (J^n)^2 V0 (liquid), 0 solid
     void* cvisc;                    // dt mu V^n (liquid), 0 solid
-    void* opk;                      // R4 per particle: block-relative position, kappa (< 0: general operator)
+    void* opk;                      // R4 records (block-relative position, kappa; kappa < 0: general
+                                    // operator), rank-major per work block: the k-th particle of cell c
+                                    // of work block w sits at (wroff[w] + k) * 64 + c
+    int* wrows;                     // per work block: record rows (most particles in one of its cells)
+    int* wroff;                     // exclusive scan of wrows (+ total)
     void* Fn[9];                    // F^n (solid)
     void* lame[2];                  // mu, lambda (solid)
     void* scache[24];               // solid per-iterate: F (9), R (9), (tr S I - S)^-1 (6)
@@ -62,11 +66,13 @@ struct Dev {
     int* nbr;                       // 27 neighbour slots per slot
     int* work;                      // work slot list
     int* work_gb;
+    int* bw;                        // per global block: its work index (where it holds particles)
     int* slot_gen;                  // per slot: interior particles needing the general operator
     int* counts;                    // [0] NB, [1] NW
     int* scan_tmp;
     // ---- grid (float64) ----
     double *gm, *gmv, *gvn, *gmT, *gmTT, *gTn, *gv, *gvhat, *gThat, *ggrad;
+    double* ggrad_l;                // liquid (cell-kernel) part of ggrad, for the line search
     uint8_t* pcode;
     // ---- solver vectors (R) ----
     void *cx, *cr, *cp, *cu, *invm;
@@ -80,6 +86,7 @@ struct Dev {
     SceneDev* sc;
     SceneScal* scal;
     int* err;
+    unsigned* cg_bar;               // grid barrier of the cooperative CG kernel (2 words)
 };
 
 }  // namespace mpm
@@ -93,6 +100,7 @@ struct mpm_ctx {
     long long Pcap = 0, Scap = 0, total_blocks = 0, total_cells = 0;
     long long np = 0, ns = 0;       // current totals
     long long block_cap = 0;        // capacity of active blocks (grid slots)
+    long long opk_cap = 0;          // capacity of d.opk in records (grown by the per-step pack)
     bool has_solids = false;        // solid-only buffers allocated
     int NB = 0, NW = 0;
     bool resampled = false, p2g_done = false, step_ready = false;

@@ -158,16 +158,27 @@ __global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptr
                               const double* __restrict__ T, const uint8_t* __restrict__ phase, const int* __restrict__ psc,
                               const SceneDev* __restrict__ sc, RPtr3<R> pu, R* __restrict__ kappa, R* __restrict__ cvisc,
                               RPtr9<R> Fn, R* __restrict__ lmu, R* __restrict__ llam, R* __restrict__ Vn,
-                              const int* __restrict__ bslot, int* __restrict__ slot_gen, R4<R>* __restrict__ opk) {
+                              const int* __restrict__ bslot, int* __restrict__ slot_gen,
+                              const int* __restrict__ cell_start, int nw, const int* __restrict__ bw,
+                              const int* __restrict__ wrows, const int* __restrict__ wroff, long long opk_cap,
+                              R4<R>* __restrict__ opk) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
     const SceneDev& S = sc[psc[i]];
+    long long rec_at = -1;   // rank-major record slot of this particle
     {
         int c[3];
         for (int a = 0; a < 3; ++a) c[a] = (int)floor((x.a[a][i] - S.origin[a]) * S.inv_dx);
         bool general = phase[i] != 0 || S.mu_l != 0.0;
         long long gb = S.block_base + (c[0] >> 2) + (long long)S.nb[0] * ((c[1] >> 2) + (long long)S.nb[1] * (c[2] >> 2));
         if (general) atomicAdd(&slot_gen[bslot[gb]], 1);
+        int lc = (c[0] & 3) + 4 * (c[1] & 3) + 16 * (c[2] & 3);
+        int w = bw[gb];
+        int k = i - cell_start[gb * 64 + lc];
+        if (w >= 0 && w < nw && k >= 0 && k < wrows[w]) {
+            long long at = ((long long)wroff[w] + k) * 64 + lc;
+            if (at < opk_cap) rec_at = at;
+        }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -191,7 +202,7 @@ __global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptr
         rec.z = pu.a[2][i];
         bool general = !liq || S.mu_l != 0.0;
         rec.w = general ? R(-1) : (R)(dt * dt * S.lambda_l * Jn * Jn * v0);
-        opk[i] = rec;
+        if (rec_at >= 0) opk[rec_at] = rec;
     }
     if (!liq) {
         for (int q = 0; q < 9; ++q) Fn.a[q][i] = (R)Fd[q];
@@ -507,7 +518,8 @@ struct ApplyArgs {
     RPtr3<R> sn;
     const R* sic;
     const int* slot_gen;      // general particles per slot
-    const R4<R>* opk;         // packed record: position in the block (cells), kappa (< 0: general)
+    const R4<R>* opk;         // rank-major records: position in the block (cells), kappa (< 0: general)
+    const int *wrows, *wroff; // per work block: record rows and their offset
     int* err;
     int mode;
     int check_done;
@@ -832,28 +844,63 @@ __device__ __forceinline__ void cell_scatter(R M[3][3][3], R (*ua)[PN], int lx, 
         }
 }
 
+// Separable stencil gather / scatter on the padded halo (one axis at a time):
+// G_qe = sum_abc p_q(abc) dN_abc/dx_e, and u_q(abc) += sum_e M_qe dN_abc/dx_e.
+template <typename R>
+__device__ __forceinline__ void gather_grad_sep(R (*ph)[PN], const int* lc, const R (*w)[3], const R (*dw)[3], R* G) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        R gx = R(0), gy = R(0), gz = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R u0 = R(0), u1 = R(0), u2 = R(0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R* row = &ph[q][pidx(lc[0] + a, lc[1] + b, lc[2])];
+                R p0 = row[0], p1 = row[PZ], p2 = row[2 * PZ];
+                R s0 = w[2][0] * p0 + w[2][1] * p1 + w[2][2] * p2;
+                R s1 = dw[2][0] * p0 + dw[2][1] * p1 + dw[2][2] * p2;
+                u0 += w[1][b] * s0;
+                u1 += dw[1][b] * s0;
+                u2 += w[1][b] * s1;
+            }
+            gx += dw[0][a] * u0;
+            gy += w[0][a] * u1;
+            gz += w[0][a] * u2;
+        }
+        G[3 * q] = gx;
+        G[3 * q + 1] = gy;
+        G[3 * q + 2] = gz;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void scatter_sep(R (*ua)[PN], const int* lc, const R (*w)[3], const R (*dw)[3], const R* M) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R A0 = M[3 * q] * dw[0][a], A1 = M[3 * q + 1] * w[0][a], A2 = M[3 * q + 2] * w[0][a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                R B0 = A0 * w[1][b] + A1 * dw[1][b];
+                R B1 = A2 * w[1][b];
+                R* row = &ua[q][pidx(lc[0] + a, lc[1] + b, lc[2])];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(row + c * PZ, B0 * w[2][c] + B1 * dw[2][c]);
+            }
+        }
+    }
+}
+
 // general per-particle operator (solid or viscous liquid) on the padded layout
 template <typename R>
 __device__ __forceinline__ void particle_general(const ApplyArgs<R>& a, int i, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
     int lc[3];
     R wgt[3][3], dw[3][3];
     make_stencil_local<R>(a.pu.a[0][i], a.pu.a[1][i], a.pu.a[2][i], inv_dx, lc, wgt, dw);
-    R dL[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int cz = 0; cz < 3; ++cz)
-        for (int cy = 0; cy < 3; ++cy)
-#pragma unroll
-            for (int cx = 0; cx < 3; ++cx) {
-                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    R pq = ph[q][h];
-                    dL[3 * q] += pq * dNv[0];
-                    dL[3 * q + 1] += pq * dNv[1];
-                    dL[3 * q + 2] += pq * dNv[2];
-                }
-            }
+    R dL[9];
+    gather_grad_sep<R>(ph, lc, wgt, dw, dL);
     R M[9];
     if (a.phase[i] == 0) {
         R s = a.kappa[i] * (dL[0] + dL[4] + dL[8]);
@@ -879,16 +926,7 @@ __device__ __forceinline__ void particle_general(const ApplyArgs<R>& a, int i, R
 #pragma unroll
         for (int q = 0; q < 9; ++q) M[q] *= sc;
     }
-    for (int cz = 0; cz < 3; ++cz)
-        for (int cy = 0; cy < 3; ++cy)
-#pragma unroll
-            for (int cx = 0; cx < 3; ++cx) {
-                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], M[3 * q] * dNv[0] + M[3 * q + 1] * dNv[1] + M[3 * q + 2] * dNv[2]);
-            }
+    scatter_sep<R>(ua, lc, wgt, dw, M);
 }
 
 template <typename R>
@@ -896,22 +934,8 @@ __device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (
     int lc[3];
     R wgt[3][3], dw[3][3];
     make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
-    R dFh[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int cz = 0; cz < 3; ++cz)
-        for (int cy = 0; cy < 3; ++cy)
-#pragma unroll
-            for (int cx = 0; cx < 3; ++cx) {
-                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    R pq = ph[q][h];
-                    dFh[3 * q] += pq * dNv[0];
-                    dFh[3 * q + 1] += pq * dNv[1];
-                    dFh[3 * q + 2] += pq * dNv[2];
-                }
-            }
+    R dFh[9];
+    gather_grad_sep<R>(ph, lc, wgt, dw, dFh);
     R Fh[9], av[3], nv[3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Fh[q] = a.sF.a[q][j];
@@ -937,21 +961,13 @@ __device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (
     } else {
         add_conformal<R>(k * dt * dt, nv, av, dFh, G);
     }
-    for (int cz = 0; cz < 3; ++cz)
-        for (int cy = 0; cy < 3; ++cy)
-#pragma unroll
-            for (int cx = 0; cx < 3; ++cx) {
-                int h = pidx(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                R dNv[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                            wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], G[3 * q] * dNv[0] + G[3 * q + 1] * dNv[1] + G[3 * q + 2] * dNv[2]);
-            }
+    scatter_sep<R>(ua, lc, wgt, dw, G);
 }
 
 constexpr int NT_CELL = 64;
 constexpr int NT_GEN = 32;  // one warp: a block holds ~20-40 surface samples
-constexpr int MAXP = 640;   // particle records staged per chunk
+constexpr int KROWS = 10;   // record rows staged per chunk
+constexpr int MAXP = KROWS * 64;
 
 // Halo rows along x: the four middle nodes of a row belong to one neighbour block
 // and are contiguous there (x fastest), so they move as one vector; the two end
@@ -1023,7 +1039,7 @@ __device__ __forceinline__ void flush_halo_rows(const int* __restrict__ nbr, int
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
+__global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
     __shared__ R ua[3][PN];
     __shared__ R4<R> sp[MAXP];
@@ -1034,16 +1050,19 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
     int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
     if (a.check_done && a.scal[bc.w].cg_done) return;
-    const int bbeg = a.cell_start[gb * 64], bend = a.cell_start[gb * 64 + 64];
-    const int nchunk = (bend - bbeg + MAXP - 1) / MAXP;
+    // rank-major records: row r holds the r-th particle of each of the 64 cells,
+    // so a warp reads 32 consecutive records (no bank conflicts)
+    const int rows = a.wrows[w];
+    const R4<R>* recs = a.opk + (long long)a.wroff[w] * 64;
+    const int nchunk = (rows + KROWS - 1) / KROWS;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    // the block's particle records stream into shared memory (TMA bulk copy)
-    // while the threads stage the direction's halo
+    // the block's records stream into shared memory (TMA bulk copy) while the
+    // threads stage the direction's halo
     if (threadIdx.x == 0 && nchunk > 0) {
-        uint32_t cnt = (uint32_t)min(MAXP, bend - bbeg);
+        uint32_t cnt = (uint32_t)min(KROWS, rows) * 64u;
         mbar_expect_tx(&bar, cnt * (uint32_t)sizeof(R4<R>));
-        bulk_g2s(sp, a.opk + bbeg, cnt * (uint32_t)sizeof(R4<R>), &bar);
+        bulk_g2s(sp, recs, cnt * (uint32_t)sizeof(R4<R>), &bar);
     }
     load_halo_rows<R>(a.nbr, slot, a.p, ph, ua);
     __syncthreads();
@@ -1063,9 +1082,9 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
     }
     bool any = false, timed_out = false;
     uint32_t parity_left = 0;
+    const int ncell = cend - cbeg;
     for (int k = 0; k < nchunk; ++k) {
-        const int c0 = bbeg + k * MAXP;
-        const int cnt = min(MAXP, bend - c0);
+        const int r0 = k * KROWS;
         // bounded wait; the CTA agrees on the outcome so that no thread is left at a barrier
         bool ok = mbar_wait_bounded(&bar, (uint32_t)(k & 1), 1LL << 26);
         if (__syncthreads_or(!ok)) {
@@ -1073,45 +1092,44 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
             parity_left = (uint32_t)(k & 1);
             break;
         }
-        const int lo = max(cbeg, c0), hi = min(cend, c0 + cnt);
-        for (int i = lo; i < hi; ++i) {
-            R4<R> rec = sp[i - c0];
+        const int rhi = min(ncell, r0 + KROWS);
+        for (int r = r0; r < rhi; ++r) {
+            R4<R> rec = sp[(r - r0) * 64 + cell];
             if (rec.w < R(0)) continue;   // general particle: k_apply_general
             any = true;
             R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
             R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
             R tz = fmin(fmax(rec.z - R(lz), R(0)), R(1));
-            R px[3] = {R(1), tx, tx * tx};
             R py[3] = {R(1), ty, ty * ty}, pz[3] = {R(1), tz, tz * tz};
             R yz[3][3];
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
                 for (int kk = 0; kk < 3; ++kk) yz[j][kk] = py[j] * pz[kk];
-            R tr = R(0);
+            R srow[3] = {R(0), R(0), R(0)};
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int kk = 0; kk < 3; ++kk)
-                        if (!(ii == 2 && j == 2 && kk == 2)) tr += C[ii][j][kk] * px[ii] * yz[j][kk];
-            R s = rec.w * s2 * tr;
+                        if (!(ii == 2 && j == 2 && kk == 2)) srow[ii] += C[ii][j][kk] * yz[j][kk];
+            const R tr = srow[0] + tx * (srow[1] + tx * srow[2]);
+            const R s = rec.w * s2 * tr;
+            const R sx[3] = {s, s * tx, s * tx * tx};
 #pragma unroll
-            for (int ii = 0; ii < 3; ++ii) {
-                R sx = s * px[ii];
+            for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int kk = 0; kk < 3; ++kk)
-                        if (!(ii == 2 && j == 2 && kk == 2)) M[ii][j][kk] += sx * yz[j][kk];
-            }
+                        if (!(ii == 2 && j == 2 && kk == 2)) M[ii][j][kk] += sx[ii] * yz[j][kk];
         }
         __syncthreads();   // every thread is done with this chunk
         if (k + 1 < nchunk && threadIdx.x == 0) {
-            uint32_t cnt2 = (uint32_t)min(MAXP, bend - (c0 + MAXP));
+            uint32_t cnt2 = (uint32_t)min(KROWS, rows - (r0 + KROWS)) * 64u;
             mbar_expect_tx(&bar, cnt2 * (uint32_t)sizeof(R4<R>));
-            bulk_g2s(sp, a.opk + c0 + MAXP, cnt2 * (uint32_t)sizeof(R4<R>), &bar);
+            bulk_g2s(sp, recs + (long long)(r0 + KROWS) * 64, cnt2 * (uint32_t)sizeof(R4<R>), &bar);
         }
     }
     if (timed_out) {
@@ -1129,7 +1147,7 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
 // sample, shared-memory accumulation on the padded halo. Blocks with none of
 // them return at once (slot_gen counts the block's general particles).
 template <typename R>
-__global__ void __launch_bounds__(NT_GEN) k_apply_general(ApplyArgs<R> a) {
+__global__ void __launch_bounds__(NT_GEN, 16) k_apply_general(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
     __shared__ R ua[3][PN];
     int w = blockIdx.x;
@@ -1167,6 +1185,7 @@ struct EvalCellArgs {
     SceneScal* scal;
     const double* gv;
     double* grad;             // null: energy only
+    double* grad_l;           // null, or a second target for the same (liquid) gradient
     const double *x0, *x1, *x2, *J, *V0;
     const uint8_t* phase;
     int skip_done;
@@ -1177,19 +1196,6 @@ __device__ __forceinline__ void cell_t(const SceneDev& S, int4 bc, int lx, int l
     tx = fmin(fmax((x0 - S.origin[0]) * S.inv_dx - (double)(bc.x * BS + lx), 0.0), 1.0);
     ty = fmin(fmax((x1 - S.origin[1]) * S.inv_dx - (double)(bc.y * BS + ly), 0.0), 1.0);
     tz = fmin(fmax((x2 - S.origin[2]) * S.inv_dx - (double)(bc.z * BS + lz), 0.0), 1.0);
-}
-
-__device__ __forceinline__ double poly_eval(const double C[3][3][3], double tx, double ty, double tz) {
-    double px[3] = {1.0, tx, tx * tx}, py[3] = {1.0, ty, ty * ty}, pz[3] = {1.0, tz, tz * tz};
-    double r = 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                if (!(i == 2 && j == 2 && k == 2)) r += C[i][j][k] * px[i] * py[j] * pz[k];
-    return r;
 }
 
 __global__ void __launch_bounds__(NT_CELL) k_eval_cell(EvalCellArgs a) {
@@ -1224,19 +1230,35 @@ __global__ void __launch_bounds__(NT_CELL) k_eval_cell(EvalCellArgs a) {
             any = true;
             double tx, ty, tz;
             cell_t(S, bc, lx, ly, lz, a.x0[i], a.x1[i], a.x2[i], tx, ty, tz);
-            double tr = inv_dx * poly_eval(C, tx, ty, tz);
-            double Jn = a.J[i], v0 = a.V0[i];
-            double jm1 = (Jn - 1.0) + dt * tr * Jn;
-            esum += 0.5 * lam * jm1 * jm1 * v0;
-            double sp = dt * lam * jm1 * Jn * v0 * inv_dx;
-            double px[3] = {1.0, tx, tx * tx}, py[3] = {1.0, ty, ty * ty}, pz[3] = {1.0, tz, tz * tz};
+            // monomials factored as t_x^i (t_y^j t_z^k): the y-z products serve the
+            // evaluation and the moments
+            const double py[3] = {1.0, ty, ty * ty}, pz[3] = {1.0, tz, tz * tz};
+            double yz[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) yz[j][k] = py[j] * pz[k];
+            double srow[3] = {0.0, 0.0, 0.0};
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int k = 0; k < 3; ++k)
-                        if (!(ii == 2 && j == 2 && k == 2)) M[ii][j][k] += sp * px[ii] * py[j] * pz[k];
+                        if (!(ii == 2 && j == 2 && k == 2)) srow[ii] += C[ii][j][k] * yz[j][k];
+            double tr = inv_dx * (srow[0] + tx * (srow[1] + tx * srow[2]));
+            double Jn = a.J[i], v0 = a.V0[i];
+            double jm1 = (Jn - 1.0) + dt * tr * Jn;
+            esum += 0.5 * lam * jm1 * jm1 * v0;
+            double sp = dt * lam * jm1 * Jn * v0 * inv_dx;
+            const double sx[3] = {sp, sp * tx, sp * tx * tx};
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (!(ii == 2 && j == 2 && k == 2)) M[ii][j][k] += sx[ii] * yz[j][k];
         }
         if (any && a.grad) cell_scatter<double>(M, ga, lx, ly, lz);
     }
@@ -1244,81 +1266,61 @@ __global__ void __launch_bounds__(NT_CELL) k_eval_cell(EvalCellArgs a) {
     if (a.grad) {
         __syncthreads();
         flush_halo_rows<double>(a.nbr, slot, ga, a.grad);
+        if (a.grad_l) flush_halo_rows<double>(a.nbr, slot, ga, a.grad_l);
     }
 }
 
-template <typename RD>
-struct LSCellArgs {
-    const int *work, *work_gb, *nbr, *cell_start;
-    const int4* coord;
-    const SceneDev* sc;
-    SceneScal* scal;
-    const double* gv;
-    const RD* d;
-    const double *x0, *x1, *x2, *J, *V0;
-    const uint8_t* phase;
-};
-
-// line search: liquid energy differences for alpha_k = 2^-k, float64
-template <typename RD>
-__global__ void __launch_bounds__(NT_CELL) k_ls_cell(LSCellArgs<RD> a) {
-    __shared__ double pv[3][PN];
-    __shared__ double pd[3][PN];
+// Line search, liquid part. The liquid energy is exactly quadratic along a
+// Newton direction d (J is affine in v), so its change over a step alpha is
+// alpha g_l . d + alpha^2/2 d.K_l d, with g_l the float64 liquid gradient at the
+// iterate (k_eval_cell keeps a copy) and d.K_l d = sum_p kappa_p (tr L_d)_p^2,
+// a sum of non-negative terms formed here in the operator type.
+template <typename R>
+__global__ void __launch_bounds__(NT_CELL) k_curv_cell(ApplyArgs<R> a) {
+    __shared__ R ph[3][PN];
+    __shared__ R ua[3][PN];
     __shared__ double red[NT_CELL / 32];
     int w = blockIdx.x;
     int slot = a.work[w];
     long long gb = a.work_gb[w];
     int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
-    SceneScal& scl = a.scal[bc.w];
-    if (scl.newton_done) return;
-    if (S.mu_l != 0.0) return;
-    load_halo_rows<double>(a.nbr, slot, a.gv, pv, pd);   // pd zeroed, then filled below
+    if (a.scal[bc.w].newton_done) return;
+    const int rows = a.wrows[w];
+    if (rows == 0) return;
+    load_halo_rows<R>(a.nbr, slot, a.p, ph, ua);
     __syncthreads();
-    for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
-        int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
-        int nmid, nlo, nhi, base;
-        halo_row<double>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
-        int h0 = pidx(0, hy, hz);
-        pd[c][h0] = nlo >= 0 ? (double)a.d[nlo * 192 + c * 64 + base + 3] : 0.0;
-        for (int k = 0; k < 4; ++k) pd[c][h0 + 1 + k] = nmid >= 0 ? (double)a.d[nmid * 192 + c * 64 + base + k] : 0.0;
-        pd[c][h0 + 5] = nhi >= 0 ? (double)a.d[nhi * 192 + c * 64 + base] : 0.0;
-    }
-    __syncthreads();
-    const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
+    const R inv_dx = (R)S.inv_dx;
     const int cell = threadIdx.x;
     const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
-    const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
-    const double dt = S.dt, lam = S.lambda_l, inv_dx = S.inv_dx;
-    double de[MAX_LS];
+    const int n = a.cell_start[gb * 64 + cell + 1] - a.cell_start[gb * 64 + cell];
+    const R4<R>* recs = a.opk + (long long)a.wroff[w] * 64 + cell;
+    R acc = R(0);
+    if (n > 0) {
+        R C[3][3][3];
 #pragma unroll
-    for (int k = 0; k < MAX_LS; ++k) de[k] = 0.0;
-    if (cend > cbeg) {
-        double Cv[3][3][3], Cd[3][3][3];
+        for (int q = 0; q < 27; ++q) (&C[0][0][0])[q] = R(0);
+        cell_coefficients<R>(ph, lx, ly, lz, C);
+        for (int r = 0; r < n; ++r) {
+            R4<R> rec = recs[(long long)r * 64];
+            if (rec.w < R(0)) continue;
+            R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
+            R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
+            R tz = fmin(fmax(rec.z - R(lz), R(0)), R(1));
+            R py[3] = {R(1), ty, ty * ty}, pz[3] = {R(1), tz, tz * tz};
+            R srow[3] = {R(0), R(0), R(0)};
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            (&Cv[0][0][0])[q] = 0.0;
-            (&Cd[0][0][0])[q] = 0.0;
-        }
-        cell_coefficients<double>(pv, lx, ly, lz, Cv);
-        cell_coefficients<double>(pd, lx, ly, lz, Cd);
-        for (int i = cbeg; i < cend; ++i) {
-            if (a.phase[i] != 0) continue;
-            double tx, ty, tz;
-            cell_t(S, bc, lx, ly, lz, a.x0[i], a.x1[i], a.x2[i], tx, ty, tz);
-            double trL = inv_dx * poly_eval(Cv, tx, ty, tz);
-            double trD = inv_dx * poly_eval(Cd, tx, ty, tz);
-            double Jn = a.J[i], v0 = a.V0[i];
-            double jm1 = (Jn - 1.0) + dt * trL * Jn;
-            double alpha = 1.0;
-            for (int k = 0; k < nls; ++k) {
-                double dJ = alpha * dt * trD * Jn;
-                de[k] += 0.5 * lam * v0 * dJ * (2.0 * jm1 + dJ);
-                alpha *= 0.5;
-            }
+            for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk)
+                        if (!(ii == 2 && j == 2 && kk == 2)) srow[ii] += C[ii][j][kk] * (py[j] * pz[kk]);
+            const R tr = inv_dx * (srow[0] + tx * (srow[1] + tx * srow[2]));
+            acc += rec.w * tr * tr;
         }
     }
-    for (int k = 0; k < nls; ++k) block_atomic_sum<NT_CELL>(de[k], &scl.dphi[k], red);
+    block_atomic_sum<NT_CELL>((double)acc, const_cast<double*>(&a.scal[bc.w].dkd), red);
 }
 
 // ======================================================================
@@ -1455,29 +1457,112 @@ __global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int 
     cta_scene_sum2(rz, bb, scene, a.scal, OFF_RZ, set_bnorm ? OFF_BN : -1);
 }
 
-// q = P (D p + u) -> u ; pAp
+// ---- one CG iteration's vector work as a single cooperative launch ----
+// Per-thread partial sums (float64) of the nodes it visits; warps stay
+// scene-uniform (a warp covers 32 nodes of one slot and all lanes visit the
+// same slots), so a change of scene flushes the warp's sum with one atomic.
+// The last scene's sums go through the CTA reduction (cta_scene_sum2).
+struct SceneAcc {
+    double v1 = 0.0, v2 = 0.0;
+    int cur = -1;
+    __device__ void add(int scene, double x1, double x2, SceneScal* scal, int off1, int off2) {
+        if (scene != cur) {
+            flush(scal, off1, off2);
+            cur = scene;
+        }
+        v1 += x1;
+        v2 += x2;
+    }
+    __device__ void flush(SceneScal* scal, int off1, int off2) {
+        double a1 = warp_sum(v1), a2 = warp_sum(v2);
+        if (cur >= 0 && (threadIdx.x & 31) == 0) {
+            double* base = reinterpret_cast<double*>(&scal[cur]);
+            if (off1 >= 0 && a1 != 0.0) atomicAdd(base + off1, a1);
+            if (off2 >= 0 && a2 != 0.0) atomicAdd(base + off2, a2);
+        }
+        v1 = v2 = 0.0;
+    }
+};
+
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is
+// the generation. The wait is bounded; on timeout ERR_TIMEOUT is set and every
+// thread of the CTA gets false.
+__device__ bool grid_barrier(unsigned* bar, int* err) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > (1LL << 24)) {
+                    ok = 0;
+                    atomicOr(err, ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// per-scene CG control: count, test, beta (held in alpha)
+__device__ __forceinline__ void cg_check_scene(SceneScal& c, const SceneDev& S, int heat) {
+    if (c.cg_done) return;
+    c.cg_it += 1;
+    double rtol = heat ? S.heat_rtol : S.cg_rtol;
+    bool done = !(c.pAp > 0.0) || c.rr <= rtol * rtol * c.bnorm || c.cg_it >= S.max_cg;
+    if (done) {
+        c.cg_done = 1;
+    } else {
+        c.alpha = c.rz_new / c.rz;
+        c.rz = c.rz_new;
+    }
+    c.rz_new = 0.0;
+    c.rr = 0.0;
+    c.pAp = 0.0;
+}
+
+// After the operator apply u = K p:
+//   A: q = P (D p + u) -> u, pAp
+//   B: x += alpha p, r -= alpha q, u = 0, z = P(inv r); rz_new, rr
+//      (non-positive curvature: x = p on the first iteration, then stop)
+//   C: per-scene control
+//   D: p = z + beta p
 template <typename R, int NC>
-__global__ void __launch_bounds__(CG_NT) k_cg_pq(CGArgs<R, NC> a, int nb) {
-    int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
-    int scene = -1;
-    double pq = 0.0;
-    if (slot < nb) {
-        scene = a.coord[slot].w;
+__global__ void __launch_bounds__(CG_NT) k_cg_iter(CGArgs<R, NC> a, int nb, int nsc, int heat, unsigned* bar, int* err) {
+    const int nchunks = (nb + CG_SLOTS - 1) / CG_SLOTS;
+    const int l = threadIdx.x & 63;
+    SceneAcc acc;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
+        if (slot >= nb) continue;
+        const int scene = a.coord[slot].w;
         const SceneDev& S = a.sc[scene];
+        double pq = 0.0;
         if (!a.scal[scene].cg_done) {
-            int t = slot * 64 + l;
+            const int t = slot * 64 + l;
             R q[NC], pv[NC];
             double diag;
             if (NC == 3) diag = a.gm[t];
             else diag = a.inv[t] == R(0) ? 0.0 : 1.0 / (double)a.inv[t];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                int k = vidx<R, NC>(slot, c, l);
+                const int k = vidx<R, NC>(slot, c, l);
                 pv[c] = a.p[k];
                 q[c] = (R)diag * pv[c] + a.u[k];
             }
             cg_proj<R, NC>(q, a, t, S);
-            R pql = R(0);
+            R pql = R(0);   // the node's products in R; sums across nodes in float64
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 a.u[vidx<R, NC>(slot, c, l)] = q[c];
@@ -1485,45 +1570,43 @@ __global__ void __launch_bounds__(CG_NT) k_cg_pq(CGArgs<R, NC> a, int nb) {
             }
             pq = (double)pql;
         }
+        acc.add(scene, pq, 0.0, a.scal, OFF_PAP, -1);
     }
-    cta_scene_sum2(pq, 0.0, scene, a.scal, OFF_PAP, -1);
-}
-
-// x += alpha p, r -= alpha q, u = 0; rz_new, rr   (negative curvature: x = p on the first iteration)
-template <typename R, int NC>
-__global__ void __launch_bounds__(CG_NT) k_cg_update(CGArgs<R, NC> a, int nb) {
-    int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
-    int scene = -1;
-    double rz_new = 0.0, rr = 0.0;
-    if (slot < nb) {
-        scene = a.coord[slot].w;
+    cta_scene_sum2(acc.v1, acc.v2, acc.cur, a.scal, OFF_PAP, -1);
+    if (!grid_barrier(bar, err)) return;
+    acc.v1 = acc.v2 = 0.0;
+    acc.cur = -1;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
+        if (slot >= nb) continue;
+        const int scene = a.coord[slot].w;
         const SceneDev& S = a.sc[scene];
         const SceneScal& sc = a.scal[scene];
+        double rz_new = 0.0, rr = 0.0;
         if (!sc.cg_done) {
-            int t = slot * 64 + l;
-            double pAp = sc.pAp;
+            const int t = slot * 64 + l;
+            const double pAp = sc.pAp;
             if (!(pAp > 0.0)) {
                 if (sc.cg_it == 0) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
-                        int k = vidx<R, NC>(slot, c, l);
+                        const int k = vidx<R, NC>(slot, c, l);
                         a.x[k] = a.p[k];
                     }
                 }
 #pragma unroll
                 for (int c = 0; c < NC; ++c) a.u[vidx<R, NC>(slot, c, l)] = R(0);
             } else {
-                R alpha = (R)(sc.rz / pAp);
-                R r[NC];
+                const R alpha = (R)(sc.rz / pAp);
+                R r[NC], z[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    int k = vidx<R, NC>(slot, c, l);
+                    const int k = vidx<R, NC>(slot, c, l);
                     a.x[k] += alpha * a.p[k];
                     r[c] = a.r[k] - alpha * a.u[k];
                     a.r[k] = r[c];
                     a.u[k] = R(0);
                 }
-                R z[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) z[c] = r[c] * cg_prec<R, NC>(a, slot, c, l, t);
                 cg_proj<R, NC>(z, a, t, S);
@@ -1537,51 +1620,32 @@ __global__ void __launch_bounds__(CG_NT) k_cg_update(CGArgs<R, NC> a, int nb) {
                 rr = (double)rrl;
             }
         }
+        acc.add(scene, rz_new, rr, a.scal, OFF_RZN, OFF_RR);
     }
-    cta_scene_sum2(rz_new, rr, scene, a.scal, OFF_RZN, OFF_RR);
-}
-
-// p = z + beta p
-template <typename R, int NC>
-__global__ void __launch_bounds__(CG_NT) k_cg_p(CGArgs<R, NC> a, int nb) {
-    int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
-    if (slot >= nb) return;
-    int scene = a.coord[slot].w;
-    const SceneDev& S = a.sc[scene];
-    const SceneScal& sc = a.scal[scene];
-    if (sc.cg_done) return;
-    int t = slot * 64 + l;
-    R beta = (R)sc.alpha;   // holds beta here (set by k_cg_check)
-    R z[NC];
+    cta_scene_sum2(acc.v1, acc.v2, acc.cur, a.scal, OFF_RZN, OFF_RR);
+    if (!grid_barrier(bar, err)) return;
+    if (blockIdx.x == 0)
+        for (int s = threadIdx.x; s < nsc; s += blockDim.x) cg_check_scene(a.scal[s], a.sc[s], heat);
+    if (!grid_barrier(bar, err)) return;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
+        if (slot >= nb) continue;
+        const int scene = a.coord[slot].w;
+        const SceneDev& S = a.sc[scene];
+        const SceneScal& sc = a.scal[scene];
+        if (sc.cg_done) continue;
+        const int t = slot * 64 + l;
+        const R beta = (R)sc.alpha;
+        R z[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) z[c] = a.r[vidx<R, NC>(slot, c, l)] * cg_prec<R, NC>(a, slot, c, l, t);
-    cg_proj<R, NC>(z, a, t, S);
+        for (int c = 0; c < NC; ++c) z[c] = a.r[vidx<R, NC>(slot, c, l)] * cg_prec<R, NC>(a, slot, c, l, t);
+        cg_proj<R, NC>(z, a, t, S);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        int k = vidx<R, NC>(slot, c, l);
-        a.p[k] = z[c] + beta * a.p[k];
+        for (int c = 0; c < NC; ++c) {
+            const int k = vidx<R, NC>(slot, c, l);
+            a.p[k] = z[c] + beta * a.p[k];
+        }
     }
-}
-
-// per-scene CG control: count, test, beta
-__global__ void k_cg_check(SceneScal* scal, const SceneDev* sc, int nsc, int heat) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsc) return;
-    SceneScal& c = scal[s];
-    if (c.cg_done) return;
-    c.cg_it += 1;
-    double rtol = heat ? sc[s].heat_rtol : sc[s].cg_rtol;
-    int maxit = sc[s].max_cg;
-    bool done = !(c.pAp > 0.0) || c.rr <= rtol * rtol * c.bnorm || c.cg_it >= maxit;
-    if (done) {
-        c.cg_done = 1;
-    } else {
-        c.alpha = c.rz_new / c.rz;
-        c.rz = c.rz_new;
-    }
-    c.rz_new = 0.0;
-    c.rr = 0.0;
-    c.pAp = 0.0;
 }
 
 __global__ void k_cg_begin(SceneScal* scal, int nsc, int from_newton) {
@@ -1617,6 +1681,7 @@ __global__ void k_newton_iter_begin(SceneScal* scal, int nsc) {
     c.phi_kin = 0.0;
     c.phi_part = 0.0;
     c.slope = 0.0;
+    c.dkd = 0.0;
     for (int k = 0; k < MAX_LS; ++k) c.dphi[k] = 0.0;
 }
 
@@ -1825,11 +1890,12 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
     for (int k = 0; k < nls; ++k) block_atomic_sum<NT>(de[k], &scl.dphi[k], red);
 }
 
-// node part of the line search: kinetic + gravity differences, slope = grad . d
+// node part of the line search: kinetic + gravity differences, the liquid
+// energy's linear term alpha g_l . d, and slope = grad . d
 template <typename R>
 __global__ void k_ls_nodes(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, SceneScal* __restrict__ scal,
                            const double* __restrict__ gm, const double* __restrict__ gvn, const double* __restrict__ gv,
-                           const double* __restrict__ grad, const R* __restrict__ d) {
+                           const double* __restrict__ grad, const double* __restrict__ grad_l, const R* __restrict__ d) {
     int slot = blockIdx.x, l = threadIdx.x;
     int4 bc = coord[slot];
     const SceneDev& S = sc[bc.w];
@@ -1837,11 +1903,12 @@ __global__ void k_ls_nodes(const int4* __restrict__ coord, const SceneDev* __res
     if (c.newton_done) return;
     int t = slot * 64 + l;
     double m = gm[t];
-    double dv = 0.0, dd = 0.0, gd = 0.0, sl = 0.0;
-    if (m > 0.0) {
-        for (int q = 0; q < 3; ++q) {
-            int k = slot * 192 + q * 64 + l;
-            double dq = (double)d[k];
+    double dv = 0.0, dd = 0.0, gd = 0.0, sl = 0.0, ld = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        int k = slot * 192 + q * 64 + l;
+        double dq = (double)d[k];
+        ld += grad_l[k] * dq;   // liquid forces also reach massless halo nodes: d is 0 there
+        if (m > 0.0) {
             dv += dq * (gv[k] - gvn[k]);
             dd += dq * dq;
             gd += S.g[q] * dq;
@@ -1851,7 +1918,7 @@ __global__ void k_ls_nodes(const int4* __restrict__ coord, const SceneDev* __res
     const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
     double alpha = 1.0;
     for (int k = 0; k < nls; ++k) {
-        double e = 0.5 * m * (2.0 * alpha * dv + alpha * alpha * dd) - S.dt * alpha * m * gd;
+        double e = 0.5 * m * (2.0 * alpha * dv + alpha * alpha * dd) - S.dt * alpha * m * gd + alpha * ld;
         e = warp_sum(e);
         if ((l & 31) == 0 && e != 0.0) atomicAdd(&c.dphi[k], e);
         alpha *= 0.5;
@@ -1869,7 +1936,7 @@ __global__ void k_ls_pick(SceneScal* scal, const SceneDev* sc, int nsc) {
     double alpha = 1.0;
     int pick = nls;
     for (int k = 0; k < nls; ++k) {
-        if (c.dphi[k] <= 1e-4 * alpha * c.slope) {
+        if (c.dphi[k] + 0.5 * alpha * alpha * c.dkd <= 1e-4 * alpha * c.slope) {
             pick = k;
             break;
         }
@@ -1927,10 +1994,13 @@ __global__ void k_newton_final(const int4* __restrict__ coord, const SceneDev* _
 }
 
 __global__ void k_zero_grad_active(int nb, const int4* __restrict__ coord, const SceneScal* __restrict__ scal,
-                                   double* __restrict__ grad) {
+                                   double* __restrict__ grad, double* __restrict__ grad_l) {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nb * 192) return;
-    if (!scal[coord[t / 192].w].newton_done) grad[t] = 0.0;
+    if (!scal[coord[t / 192].w].newton_done) {
+        grad[t] = 0.0;
+        grad_l[t] = 0.0;
+    }
 }
 
 __global__ void k_zero_mom(SceneScal* scal, int nsc) {
@@ -2084,6 +2154,8 @@ ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int c
     a.sic = (const R*)d.sic;
     a.slot_gen = d.slot_gen;
     a.opk = (const R4<R>*)d.opk;
+    a.wrows = d.wrows;
+    a.wroff = d.wroff;
     a.err = d.err;
     a.mode = mode;
     a.check_done = check_done;
@@ -2121,11 +2193,49 @@ CGArgs<R, NC> make_cg_args(mpm_ctx* c) {
     return a;
 }
 
+// rows of a work block's rank-major records: the most particles in one of its cells
+__global__ void k_rows(const int* __restrict__ work_gb, const int* __restrict__ cell_start, int* __restrict__ rows) {
+    const long long base = (long long)work_gb[blockIdx.x] * 64;
+    const int l = threadIdx.x;
+    int m = max(cell_start[base + l + 1] - cell_start[base + l], cell_start[base + l + 33] - cell_start[base + l + 32]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (l == 0) rows[blockIdx.x] = m;
+}
+
+// Sizes the rank-major operator records for the current sort and grows the
+// buffer when it is too small (one host synchronisation per step).
+template <typename R>
+cudaError_t size_records(mpm_ctx* c) {
+    Dev& d = c->d;
+    cudaStream_t st = c->st;
+    MPM_LAUNCH k_rows<<<c->NW, 32, 0, st>>>(d.work_gb, d.cell_start, d.wrows);
+    launch_exclusive_scan(c, d.wrows, d.wroff, c->NW, d.scan_tmp, st);
+    cudaMemcpyAsync(c->hcounts + 4, d.wroff + c->NW, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    long long need = (long long)c->hcounts[4] * 64;
+    if (need > c->opk_cap) {
+        if (d.opk) cudaFree(d.opk);
+        d.opk = nullptr;
+        c->opk_cap = 0;
+        long long cap = need + need / 8 + 4096;
+        e = cudaMalloc(&d.opk, (size_t)cap * sizeof(R4<R>));
+        if (e != cudaSuccess) return e;
+        c->opk_cap = cap;
+    }
+    return cudaSuccess;
+}
+
 template <typename R>
 cudaError_t pack_step_t(mpm_ctx* c) {
     Dev& d = c->d;
     cudaStream_t st = c->st;
     cudaMemsetAsync(d.slot_gen, 0, sizeof(int) * (size_t)(c->NB > 0 ? c->NB : 1), st);
+    if (c->np > 0 && c->NW > 0) {
+        cudaError_t e = size_records<R>(c);
+        if (e != cudaSuccess) return e;
+    }
     if (c->np > 0) {
         RPtr3<R> pu;
         RPtr9<R> Fn;
@@ -2136,7 +2246,8 @@ cudaError_t pack_step_t(mpm_ctx* c) {
         MPM_LAUNCH k_pack_volume<R><<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, Ptrs3{{d.x[0], d.x[1], d.x[2]}}, d.J, F, d.V0, d.T,
                                                            d.phase, d.psc, d.sc, pu, (R*)d.kappa, (R*)d.cvisc, Fn,
                                                            (R*)d.lame[0], (R*)d.lame[1], (R*)d.Vn, d.bslot,
-                                                           d.slot_gen, (R4<R>*)d.opk);
+                                                           d.slot_gen, d.cell_start, c->NW, d.bw, d.wrows, d.wroff,
+                                                           c->opk_cap, (R4<R>*)d.opk);
     }
     if (c->NW > 0) {
         cudaMemsetAsync(d.pinv, 0, sizeof(R) * (size_t)c->NB * 192, st);
@@ -2156,6 +2267,33 @@ cudaError_t pack_step_t(mpm_ctx* c) {
     return cudaGetLastError();
 }
 
+// one CG iteration's vector work: a cooperative launch of k_cg_iter over the
+// CTAs that fit on the device at once (grid-stride over the slots)
+template <typename R, int NC>
+cudaError_t launch_cg_iter(mpm_ctx* c, CGArgs<R, NC>& a, int heat) {
+    static int per_sm[2][2] = {{-1, -1}, {-1, -1}};
+    static int n_sm = 0;
+    int& occ = per_sm[sizeof(R) == 4 ? 0 : 1][NC == 3 ? 0 : 1];
+    if (occ < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_iter<R, NC>, CG_NT, 0);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+    }
+    int nb = c->NB, ns = c->nsc;
+    int chunks = nblk(nb, CG_SLOTS);
+    int grid = occ * n_sm;
+    if (grid > chunks) grid = chunks;
+    if (grid < 1) grid = 1;
+    unsigned* bar = c->d.cg_bar;
+    int* err = c->d.err;
+    void* args[] = {(void*)&a, (void*)&nb, (void*)&ns, (void*)&heat, (void*)&bar, (void*)&err};
+    c->launches++;
+    return cudaLaunchCooperativeKernel((const void*)k_cg_iter<R, NC>, dim3(grid), dim3(CG_NT), args, 0, c->st);
+}
+
 template <typename R>
 cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     // runs CG to completion on every scene that is not done; returns after the host saw all done
@@ -2166,6 +2304,8 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     int maxit = 0;
     for (auto& S : c->hsc) maxit = maxit > S.max_cg ? maxit : S.max_cg;
     const int chunk = 8;
+    cudaError_t e0 = cudaMemsetAsync(d.cg_bar, 0, 2 * sizeof(unsigned), st);
+    if (e0 != cudaSuccess) return e0;
     if (NC_is_heat) {
         auto a = make_cg_args<R, 1>(c);
         MPM_LAUNCH k_cg_init<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init);
@@ -2174,10 +2314,8 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
                 prof_mark_apply(c, true);
                 launch_heat_apply(c, d.hp, d.hu);
                 prof_mark_apply(c, false);
-                MPM_LAUNCH k_cg_pq<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
-                MPM_LAUNCH k_cg_update<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
-                MPM_LAUNCH k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 1);
-                MPM_LAUNCH k_cg_p<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
+                e0 = launch_cg_iter<R, 1>(c, a, 1);
+                if (e0 != cudaSuccess) return e0;
             }
             cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
@@ -2197,10 +2335,8 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
                 if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
                 if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<c->NW, NT_GEN, 0, st>>>(ap);
                 prof_mark_apply(c, false);
-                MPM_LAUNCH k_cg_pq<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
-                MPM_LAUNCH k_cg_update<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
-                MPM_LAUNCH k_cg_check<<<nblk(ns, 128), 128, 0, st>>>(d.scal, d.sc, ns, 0);
-                MPM_LAUNCH k_cg_p<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb);
+                e0 = launch_cg_iter<R, 3>(c, a, 0);
+                if (e0 != cudaSuccess) return e0;
             }
             cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
@@ -2230,6 +2366,7 @@ cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) 
     e.scal = d.scal;
     e.gv = d.gv;
     e.grad = want_grad ? d.ggrad : nullptr;
+    e.grad_l = want_grad && skip_done ? d.ggrad_l : nullptr;   // Newton iterations only
     e.x0 = d.x[0];
     e.x1 = d.x[1];
     e.x2 = d.x[2];
@@ -2261,7 +2398,7 @@ cudaError_t newton_t(mpm_ctx* c) {
         MPM_LAUNCH k_newton_iter_begin<<<gs, 128, 0, st>>>(d.scal, ns);
         // zero the gradient of scenes still iterating; converged scenes keep the
         // gradient at their final iterate for the closing force evaluation
-        MPM_LAUNCH k_zero_grad_active<<<nblk((long long)nb * 192, 256), 256, 0, st>>>(nb, d.slot_coord, d.scal, d.ggrad);
+        MPM_LAUNCH k_zero_grad_active<<<nblk((long long)nb * 192, 256), 256, 0, st>>>(nb, d.slot_coord, d.scal, d.ggrad, d.ggrad_l);
         eval_any(c, true, true, true);
         MPM_LAUNCH k_node_grad<<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.pcode, d.ggrad, 1);
         MPM_LAUNCH k_newton_check<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
@@ -2300,25 +2437,10 @@ cudaError_t newton_t(mpm_ctx* c) {
             a.skip_poly = 1;
             a.slot_gen = d.slot_gen;
             MPM_LAUNCH k_linesearch<double, R><<<c->NW, NT, 0, st>>>(a);
-            LSCellArgs<R> lc;
-            lc.work = d.work;
-            lc.work_gb = d.work_gb;
-            lc.nbr = d.nbr;
-            lc.cell_start = d.cell_start;
-            lc.coord = d.slot_coord;
-            lc.sc = d.sc;
-            lc.scal = d.scal;
-            lc.gv = d.gv;
-            lc.d = (const R*)d.cx;
-            lc.x0 = d.x[0];
-            lc.x1 = d.x[1];
-            lc.x2 = d.x[2];
-            lc.J = d.J;
-            lc.V0 = d.V0;
-            lc.phase = d.phase;
-            MPM_LAUNCH k_ls_cell<R><<<c->NW, NT_CELL, 0, st>>>(lc);
+            auto cv = make_apply_args<R>(c, d.cx, nullptr, MPM_HESS_PROJECTED, 0);
+            MPM_LAUNCH k_curv_cell<R><<<c->NW, NT_CELL, 0, st>>>(cv);
         }
-        MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, (const R*)d.cx);
+        MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, d.ggrad_l, (const R*)d.cx);
         MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
         MPM_LAUNCH k_newton_update<R><<<nb, 64, 0, st>>>(d.slot_coord, d.scal, (const R*)d.cx, d.gv);
     }

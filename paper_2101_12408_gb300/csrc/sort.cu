@@ -199,13 +199,14 @@ __global__ void k_slots(long long nblk, const int* __restrict__ bflag, const int
 
 __global__ void k_work(long long nblk, const int* __restrict__ bwork, const int* __restrict__ wscan,
                        const int* __restrict__ bslot, int* __restrict__ work, int* __restrict__ work_gb,
-                       int* __restrict__ counts, long long cap) {
+                       int* __restrict__ bw, int* __restrict__ counts, long long cap) {
     long long gb = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gb >= nblk) return;
     if (gb == nblk - 1) counts[1] = wscan[nblk];
     if (!bwork[gb]) return;
     int w = wscan[gb];
     if (w >= cap) return;
+    bw[gb] = w;
     work[w] = bslot[gb];
     work_gb[w] = (int)gb;
 }
@@ -333,7 +334,7 @@ cudaError_t launch_build_blocks(mpm_ctx* c) {
     launch_exclusive_scan(c, d.bflag, d.bscan, nblk, d.scan_tmp, st);
     MPM_LAUNCH k_slots<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bflag, d.bscan, d.sc, c->nsc, d.bslot, d.slot_coord, d.counts, c->block_cap, d.err);
     launch_exclusive_scan(c, d.bwork, d.bscan, nblk, d.scan_tmp, st);
-    MPM_LAUNCH k_work<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bwork, d.bscan, d.bslot, d.work, d.work_gb, d.counts, c->block_cap);
+    MPM_LAUNCH k_work<<<nblocks(nblk, 256), 256, 0, st>>>(nblk, d.bwork, d.bscan, d.bslot, d.work, d.work_gb, d.bw, d.counts, c->block_cap);
     cudaMemcpyAsync(c->hcounts, d.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;

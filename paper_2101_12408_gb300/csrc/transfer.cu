@@ -122,29 +122,45 @@ __global__ void __launch_bounds__(NT) k_p2g_volume(P2GArgs a) {
         make_stencil<double>(u, S.inv_dx, st);
         double f[3];
         for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
-        double mt = a.mt[i], mp = a.m[i];
-        double vp[3] = {a.v.a[0][i], a.v.a[1][i], a.v.a[2][i]};
-        double Ap[9];
-        for (int q = 0; q < 9; ++q) Ap[q] = a.A.a[q][i];
-        double Tp = S.thermal ? a.T[i] : 0.0;
-        double gTp[3] = {0, 0, 0};
-        if (S.thermal)
-            for (int q = 0; q < 3; ++q) gTp[q] = a.gT.a[q][i];
-        int lx = st.c[0] - ob[0], ly = st.c[1] - ob[1], lz = st.c[2] - ob[2];
+        const double mt = a.mt[i], dx = S.dx;
+        // node (cx, cy, cz) receives mt N (v + A (x_i - x_p)) with x_i - x_p = (c - f) dx,
+        // i.e. N (B + E c): B = mt (v - dx A f), E = mt dx A
+        double B[3], E[9];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            double Aq[3] = {a.A.a[3 * q][i], a.A.a[3 * q + 1][i], a.A.a[3 * q + 2][i]};
+            B[q] = mt * (a.v.a[q][i] - dx * (Aq[0] * f[0] + Aq[1] * f[1] + Aq[2] * f[2]));
+#pragma unroll
+            for (int e = 0; e < 3; ++e) E[3 * q + e] = mt * dx * Aq[e];
+        }
+        double TB = 0.0, TE[3] = {0, 0, 0}, mp = 0.0;
+        if (S.thermal) {
+            mp = a.m[i];
+            double g[3] = {a.gT.a[0][i], a.gT.a[1][i], a.gT.a[2][i]};
+            TB = mp * (a.T[i] - dx * (g[0] * f[0] + g[1] * f[1] + g[2] * f[2]));
+            for (int e = 0; e < 3; ++e) TE[e] = mp * dx * g[e];
+        }
+        double wyz[3][3];
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+            for (int cz = 0; cz < 3; ++cz) wyz[cy][cz] = st.w[1][cy] * st.w[2][cz];
+        const int lx = st.c[0] - ob[0], ly = st.c[1] - ob[1], lz = st.c[2] - ob[2];
+#pragma unroll
         for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
             for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
                 for (int cx = 0; cx < 3; ++cx) {
-                    double N = st.w[0][cx] * st.w[1][cy] * st.w[2][cz];
-                    double r[3] = {(cx - f[0]) * S.dx, (cy - f[1]) * S.dx, (cz - f[2]) * S.dx};
-                    int h = halo_index(lx + cx, ly + cy, lz + cz);
-                    double wm = mt * N;
-                    atomicAdd(&acc[0][h], wm);
+                    const double N = st.w[0][cx] * wyz[cy][cz];
+                    const int h = halo_index(lx + cx, ly + cy, lz + cz);
+                    atomicAdd(&acc[0][h], mt * N);
+#pragma unroll
                     for (int q = 0; q < 3; ++q)
-                        atomicAdd(&acc[1 + q][h], wm * (vp[q] + Ap[3 * q] * r[0] + Ap[3 * q + 1] * r[1] + Ap[3 * q + 2] * r[2]));
+                        atomicAdd(&acc[1 + q][h], N * (B[q] + E[3 * q] * cx + E[3 * q + 1] * cy + E[3 * q + 2] * cz));
                     if (S.thermal) {
-                        double wT = mp * N;
-                        atomicAdd(&acc[4][h], wT);
-                        atomicAdd(&acc[5][h], wT * (Tp + r[0] * gTp[0] + r[1] * gTp[1] + r[2] * gTp[2]));
+                        atomicAdd(&acc[4][h], mp * N);
+                        atomicAdd(&acc[5][h], N * (TB + TE[0] * cx + TE[1] * cy + TE[2] * cz));
                     }
                 }
     }
@@ -300,7 +316,114 @@ struct G2PArgs {
     double *J, *T;
     W9 F;
     W3 gT;
+    const float *vhi, *vlo;   // float-float copy of gvhat (k_g2p_volume_mixed)
 };
+
+// hi = fl32(v), lo = fl32(v - hi): v to about 48 bits in two float32 arrays
+__global__ void k_split_ff(long long n, const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double x = v[t];
+    float h = (float)x;
+    hi[t] = h;
+    lo[t] = (float)(x - (double)h);
+}
+
+// G2P of the float32 operator form. The particle velocity keeps float64
+// weights and node values, so sum_p m_p v_p = sum_i m_i v_i still holds to
+// float64 round-off; the affine moment, the velocity gradient and the
+// temperature gradient are formed in float32 from the node values minus the
+// stencil's centre node (exact in exact arithmetic: the B-spline weights have
+// zero first moment and their gradients sum to zero). Differences come from the
+// float-float copy, so float32 rounds the variation over the stencil, not the
+// velocity itself.
+__global__ void __launch_bounds__(128) k_g2p_volume_mixed(G2PArgs a) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.np) return;
+    const SceneDev& S = a.sc[a.psc[i]];
+    double u[3];
+    for (int q = 0; q < 3; ++q) u[q] = (a.x.a[q][i] - S.origin[q]) * S.inv_dx;
+    Stencil<double> st;
+    make_stencil<double>(u, S.inv_dx, st);
+    float wf[3][3], dwf[3][3], ff[3];
+    const float inv_dxf = (float)S.inv_dx, dxf = (float)S.dx;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        ff[q] = (float)(u[q] - 0.5 - (double)(st.c[q] - 1));
+        bspline<float>(ff[q], wf[q], dwf[q]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dwf[q][k] *= inv_dxf;
+    }
+    const int ic = node_slot_index(S, a.bslot, st.c[0], st.c[1], st.c[2]);
+    float rhi[3] = {0.f, 0.f, 0.f}, rlo[3] = {0.f, 0.f, 0.f};
+    double Tc = 0.0;
+    if (ic >= 0) {
+        const int k0 = (ic >> 6) * 192 + (ic & 63);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            rhi[q] = a.vhi[k0 + q * 64];
+            rlo[q] = a.vlo[k0 + q * 64];
+        }
+        if (S.thermal) Tc = a.gThat[ic];
+    }
+    double wyz[3][3];
+#pragma unroll
+    for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+        for (int cz = 0; cz < 3; ++cz) wyz[cy][cz] = st.w[1][cy] * st.w[2][cz];
+    double pv[3] = {0, 0, 0}, T = 0.0;
+    float tv[9] = {0}, L[9] = {0}, gT[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int cz = 0; cz < 3; ++cz)
+#pragma unroll
+        for (int cy = 0; cy < 3; ++cy)
+#pragma unroll
+            for (int cx = 0; cx < 3; ++cx) {
+                int idx = node_slot_index(S, a.bslot, st.c[0] - 1 + cx, st.c[1] - 1 + cy, st.c[2] - 1 + cz);
+                if (idx < 0) continue;
+                const int k0 = (idx >> 6) * 192 + (idx & 63);
+                const double N = st.w[0][cx] * wyz[cy][cz];
+                const float Nf = wf[0][cx] * wf[1][cy] * wf[2][cz];
+                const float dN[3] = {dwf[0][cx] * wf[1][cy] * wf[2][cz], wf[0][cx] * dwf[1][cy] * wf[2][cz],
+                                     wf[0][cx] * wf[1][cy] * dwf[2][cz]};
+                const float r[3] = {((float)cx - ff[0]) * dxf, ((float)cy - ff[1]) * dxf, ((float)cz - ff[2]) * dxf};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    pv[q] += N * a.gvhat[k0 + q * 64];
+                    const float dq = (a.vhi[k0 + q * 64] - rhi[q]) + (a.vlo[k0 + q * 64] - rlo[q]);
+                    const float Nd = Nf * dq;
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        tv[3 * q + e] += Nd * r[e];
+                        L[3 * q + e] += dq * dN[e];
+                    }
+                }
+                if (S.thermal) {
+                    double Th = a.gThat[idx];
+                    T += N * Th;
+                    float dT = (float)(Th - Tc);
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) gT[e] += dT * dN[e];
+                }
+            }
+    double mt = a.mt[i];
+    for (int q = 0; q < 3; ++q) a.acc.a[q][i] = mt * pv[q];
+    for (int q = 0; q < 9; ++q) a.acc.a[3 + q][i] = mt * (double)tv[q];
+    double dt = S.dt;
+    if (a.phase[i] == 0) {
+        a.J[i] = (1.0 + dt * (double)(L[0] + L[4] + L[8])) * a.J[i];
+    } else {
+        double Fo[9], M[9], Fnew[9];
+        for (int q = 0; q < 9; ++q) Fo[q] = a.F.a[q][i];
+        for (int q = 0; q < 9; ++q) M[q] = dt * (double)L[q] + ((q % 4 == 0) ? 1.0 : 0.0);
+        matmul3<double>(M, Fo, Fnew);
+        for (int q = 0; q < 9; ++q) a.F.a[q][i] = Fnew[q];
+    }
+    if (S.thermal) {
+        a.T[i] = T;
+        for (int e = 0; e < 3; ++e) a.gT.a[e][i] = (double)gT[e];
+    }
+}
 
 __global__ void k_g2p_volume(G2PArgs a) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -537,7 +660,17 @@ cudaError_t launch_g2p(mpm_ctx* c) {
         a.T = d.T;
         for (int q = 0; q < 9; ++q) a.F.a[q] = d.F[q];
         for (int q = 0; q < 3; ++q) a.gT.a[q] = d.gT[q];
-        MPM_LAUNCH k_g2p_volume<<<nblk(c->np, 128), 128, 0, st>>>(a);
+        if (c->rsize == 4 && c->NB > 0) {
+            // the momentum CG vectors are free after the solve: hold the float-float copy
+            long long n3 = (long long)c->NB * 192;
+            a.vhi = (const float*)d.cr;
+            a.vlo = (const float*)d.cp;
+            MPM_LAUNCH k_split_ff<<<nblk(n3, 256), 256, 0, st>>>(n3, d.gvhat, (float*)d.cr, (float*)d.cp);
+            MPM_LAUNCH k_g2p_volume_mixed<<<nblk(c->np, 128), 128, 0, st>>>(a);
+        } else {
+            a.vhi = a.vlo = nullptr;
+            MPM_LAUNCH k_g2p_volume<<<nblk(c->np, 128), 128, 0, st>>>(a);
+        }
     }
     W12 acc;
     for (int q = 0; q < 12; ++q) acc.a[q] = d.acc[q];
