@@ -19,8 +19,10 @@ Reported (one JSON line on rank 0):
   e2e          the same steps/s through the C ABI with host buffers: particle and
                surface state copied in from host memory and back out every step
   fp64_form    the all-float64 GPU form on the same workload (fewer steps)
-  cpu_baseline the FP64 numpy oracle on one droplet of the workload (a bounded
-               sample), scaled per particle to the full workload
+  cpu_baseline the FP64 numpy oracle on a bounded sample of the workload (a
+               16^3-cell window at the lower surface of its smallest droplet,
+               same dx, parameters and plane), scaled per particle to the full
+               workload; one host thread (BLAS pools pinned to 1)
   --impl reference: the oracle alone, timed on the host, same metric.
 Multi-GPU (torchrun): replicas only -- every rank advances its own copy of the
 workload; value is the sum over ranks (weak scaling, no collective on the path).
@@ -33,7 +35,11 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# the oracle baseline runs on one host thread: pin the BLAS pools before numpy loads
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -42,9 +48,12 @@ from paper_2101_12408_gb300 import scenes  # noqa: E402
 
 METRIC = "implicit steps/sec (float32 operator + float64 reductions)"
 UNIT = "steps/s"
-# ncu traffic of one Hessian-operator launch (dram read + write bytes) from the
-# capture summarised in profiles/apply_hessian_incline.md; None until captured
-NCU_TRAFFIC_BYTES = None
+# ncu DRAM traffic (read + write bytes) of one Hessian-operator apply at the
+# full workload, from the 20-droplet capture in
+# profiles/apply_cg_kernels_incline20_fp32.md scaled by the units each kernel
+# processes: k_apply_cell (149.2 MB) x 8272476 / 5128948 particles plus
+# k_apply_general (58.3 MB) x 317603 / 185006 samples
+NCU_TRAFFIC_BYTES = 340817654
 
 
 def make_workload(name, drops=40):
@@ -122,22 +131,23 @@ class ClockSampler:
 
 
 def algorithmic_bytes(ctx, sc, rsize):
-    """Bytes one Hessian-operator launch must move (the packed record of a liquid
-    particle: position in its block and kappa, 4 values; a solid particle:
-    position, F^n, Lame pair and the iterate's F, R, (tr S I - S)^-1; a surface
-    sample: position, dA, F^, n, 1/|c|, gamma; an active node: the direction read
-    and the product written, 3 components each)."""
+    """Bytes one Hessian-operator launch (projected form, as CG applies it) must
+    move: the packed record of a liquid particle (position in its block and
+    kappa, 4 values); a solid particle (position, F^n, Lame pair and the
+    iterate's F, R, (tr S I - S)^-1); a surface sample (position in its block and
+    the iterate's symmetric 9x9 Hessian map, 3 + 45 values); an active node (the
+    direction read and the product written, 3 components each)."""
     p = ctx.get_particles(0)
     nsol = int(np.sum(p["phase"] == 1))
     nliq = ctx.np[0] - nsol
     m = ctx.get_grid(0, 0)
     g_active = int(np.sum(m > 0))
-    b = rsize * (nliq * 4 + nsol * (3 + 9 + 2 + 24) + ctx.ns[0] * 20 + g_active * 6)
+    b = rsize * (nliq * 4 + nsol * (3 + 9 + 2 + 24) + ctx.ns[0] * (3 + 45) + g_active * 6)
     return b, dict(liquid=nliq, solid=nsol, surface=ctx.ns[0], active_nodes=g_active)
 
 
 def run_oracle_sample(sc, steps):
-    """FP64 oracle on one droplet of the workload; returns seconds per step and the sample size."""
+    """FP64 oracle on the workload's window sample; returns seconds per step and the sample."""
     import oracle
     # the smallest droplet: its particles and samples in a window of the same grid
     from scipy.spatial import cKDTree  # noqa: F401  (scipy present on both machines)
@@ -303,9 +313,10 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "particles": sc.n_particles},
                 "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"one droplet ({sample.n_particles} particles, {sample.n_surface} samples, "
-                                           f"{sample.n[0]}^3 window) of the workload per step, scaled by particle "
-                                           f"count {scale:.5f}"},
+                                 "sample": f"{sample.n[0]}^3-cell window at the lower surface of the smallest "
+                                           f"droplet ({sample.n_particles} of {sc.n_particles} particles, "
+                                           f"{sample.n_surface} samples) per step, seconds per step scaled by "
+                                           f"particle count ({scale:.5f})"},
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -322,8 +333,9 @@ def main():
         t = float(np.mean(times))
         scale = sample.n_particles / sc.n_particles
         cpu = {"value": scale / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one droplet of the workload ({sample.n_particles} of {sc.n_particles} particles, "
-                         f"{sample.n[0]}^3 window, {args.cpu_steps} step), seconds per step scaled by particle count"}
+               "sample": f"{sample.n[0]}^3-cell window at the lower surface of the smallest droplet "
+                         f"({sample.n_particles} of {sc.n_particles} particles, {sample.n_surface} samples, "
+                         f"{args.cpu_steps} steps), seconds per step scaled by particle count"}
     prof = res["prof"]
     line = {
         "metric": METRIC, "value": res["steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -288,6 +288,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
             return MPM_ERR_INVALID_ARG;
         }
         for (int a = 0; a < 3; ++a) S.plane_n[a] = G.plane_mode ? G.plane_n[a] / nn : 0.0;
+        for (int a = 0; a < 3; ++a) S.plane_nf[a] = (float)S.plane_n[a];
         S.plane_d = G.plane_mode ? G.plane_d / nn : 0.0;
         S.newton_tol = P.newton_tol;
         S.cg_rtol = P.cg_rtol;
@@ -342,6 +343,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.kind, uint8_t, Sn);
     A_(d.sid, int, Sn); A_(d.ssc, int, Sn); A_(d.parent, int, Sn);
     R_(d.sg, Sn); R_(d.sic, Sn); R_(d.swn, Sn);
+    for (int q = 0; q < 45; ++q) R_(d.sK[q], Sn);
     A_(d.key, long long, P); A_(d.rank, int, P); A_(d.perm, int, P);
     A_(d.skey, long long, Sn); A_(d.srank, int, Sn); A_(d.sperm, int, Sn);
     A_(d.cell_count, int, c->total_cells + 1); A_(d.cell_start, int, c->total_cells + 1);
@@ -349,13 +351,14 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.bflag, int, NBc + 1); A_(d.bwork, int, NBc + 1); A_(d.bslot, int, NBc + 1); A_(d.bscan, int, NBc + 1); A_(d.bw, int, NBc + 1);
     A_(d.slot_coord, int4, bcap + 1); A_(d.nbr, int, bcap * 27 + 27); A_(d.work, int, bcap + 1); A_(d.work_gb, int, bcap + 1);
     A_(d.slot_gen, int, bcap + 1); A_(d.wrows, int, bcap + 1); A_(d.wroff, int, bcap + 2);
+    A_(d.gen_flag, int, bcap + 1); A_(d.gen_pos, int, bcap + 2); A_(d.gen_list, int, bcap + 1);
     A_(d.counts, int, 4);
     A_(d.scan_tmp, int, (c->total_cells + 1) / 4096 + 16);
     A_(d.gm, double, NN); A_(d.gmv, double, NN * 3); A_(d.gvn, double, NN * 3); A_(d.gmT, double, NN);
     A_(d.gmTT, double, NN); A_(d.gTn, double, NN); A_(d.gv, double, NN * 3); A_(d.gvhat, double, NN * 3);
     A_(d.gThat, double, NN); A_(d.ggrad, double, NN * 3); A_(d.ggrad_l, double, NN * 3); A_(d.hrhs, double, NN);
     A_(d.pcode, uint8_t, NN);
-    R_(d.cx, NN * 3); R_(d.cr, NN * 3); R_(d.cp, NN * 3); R_(d.cu, NN * 3); R_(d.invm, NN); R_(d.pinv, NN * 3);
+    R_(d.cx, NN * 3); R_(d.cr, NN * 3); R_(d.cp, NN * 3); R_(d.cu, NN * 3); R_(d.invm, NN); R_(d.pinv, NN * 3); R_(d.mR, NN);
     R_(d.hx, NN); R_(d.hr, NN); R_(d.hp, NN); R_(d.hu, NN); R_(d.hinvd, NN); R_(d.hT, NN);
     size_t stg = staging_doubles(c);
     A_(*(double**)&d.dense_a, double, stg); A_(*(double**)&d.dense_b, double, stg);

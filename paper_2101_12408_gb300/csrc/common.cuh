@@ -33,6 +33,7 @@ struct SceneDev {
     double gamma_p[4], gamma_lg, gamma_sl;
     int walls[6];
     double plane_n[3], plane_d;
+    float plane_nf[3], pad_f_;      // plane normal in float32 (the float32 projections)
     double newton_tol, cg_rtol, heat_rtol;
     int max_newton, max_cg, max_ls, pad_;
     long long p_begin, p_end;    // interior particles (set order == storage offset)

@@ -34,6 +34,7 @@ struct Dev {
                                     // of work block w sits at (wroff[w] + k) * 64 + c
     int* wrows;                     // per work block: record rows (most particles in one of its cells)
     int* wroff;                     // exclusive scan of wrows (+ total)
+    int *gen_flag, *gen_pos, *gen_list;   // work blocks with samples or general particles: flag, scan, list
     void* Fn[9];                    // F^n (solid)
     void* lame[2];                  // mu, lambda (solid)
     void* scache[24];               // solid per-iterate: F (9), R (9), (tr S I - S)^-1 (6)
@@ -49,6 +50,7 @@ struct Dev {
     void* sn[3];                    // unit c (R)
     void* sic;                      // 1/|c| (R)
     void* swn;                      // Robin normaliser 1/sum_j N_j [m^T_j > 0] (R)
+    void* sK[45];                   // per-iterate symmetric 9x9 projected-Hessian map of a sample (R)
     // ---- sort / blocks ----
     long long* key;                 // interior cell keys
     int* rank;
@@ -77,6 +79,7 @@ struct Dev {
     // ---- solver vectors (R) ----
     void *cx, *cr, *cp, *cu, *invm;
     void* pinv;                     // momentum CG preconditioner: 1 / diag(P H P) per component
+    void* mR;                       // node mass in R (the CG's mass term)
     void *hx, *hr, *hp, *hu, *hinvd, *hT;   // heat CG (scalar fields)
     double* hrhs;
     // dense staging for the C ABI
@@ -102,6 +105,7 @@ struct mpm_ctx {
     long long block_cap = 0;        // capacity of active blocks (grid slots)
     long long opk_cap = 0;          // capacity of d.opk in records (grown by the per-step pack)
     bool has_solids = false;        // solid-only buffers allocated
+    bool sK_valid = false;          // d.sK holds the maps of the cached iterate
     int NB = 0, NW = 0;
     bool resampled = false, p2g_done = false, step_ready = false;
     mpm::Dev d{};

@@ -31,6 +31,10 @@ struct Ptrs9 { const double* a[9]; };
 template <typename R> struct RPtr3 { R* a[3]; };
 template <typename R> struct RPtr9 { R* a[9]; };
 template <typename R> struct RPtr24 { R* a[24]; };
+template <typename R> struct RPtr45 { R* a[45]; };
+
+// packed index of the symmetric 9x9 entry (m, l), m <= l
+__host__ __device__ constexpr int sym9(int m, int l) { return m * 9 - m * (m - 1) / 2 + (l - m); }
 
 template <typename R>
 __device__ __forceinline__ void cross_mat(const R* a, R* M) {
@@ -247,6 +251,7 @@ struct EvalArgs {
     const double* gamma;
     int want_grad, want_cache, skip_done;
     int skip_poly;             // non-viscous liquid particles are left to k_eval_cell
+    int skip_samples;          // surface samples are left to k_eval_surf
     const int* slot_gen;
     RPtr24<R> scache;          // solid: F (9), R (9), Kinv (6)
     RPtr9<R> sF;               // surface F^
@@ -267,7 +272,8 @@ __global__ void __launch_bounds__(NT) k_eval(EvalArgs<RS> a) {
     const SceneDev& S = a.sc[bc.w];
     if (a.skip_done && a.scal[bc.w].newton_done) return;
     const bool poly = a.skip_poly && S.mu_l == 0.0;
-    if (poly && a.slot_gen[slot] == 0 && a.scell_start[gb * 64] == a.scell_start[gb * 64 + 64]) return;
+    const bool no_samples = a.skip_samples || a.scell_start[gb * 64] == a.scell_start[gb * 64 + 64];
+    if (poly && a.slot_gen[slot] == 0 && no_samples) return;
     load_halo_vec_d<R>(a.nbr, slot, a.gv, vh);
     for (int t = threadIdx.x; t < 3 * HN; t += NT) (&ga[0][0])[t] = 0.0;
     __syncthreads();
@@ -370,6 +376,7 @@ __global__ void __launch_bounds__(NT) k_eval(EvalArgs<RS> a) {
         }
     }
     int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    if (a.skip_samples) send = sbeg;
     for (int j = sbeg + threadIdx.x; j < send; j += NT) {
         double p[3] = {a.s.a[0][j], a.s.a[1][j], a.s.a[2][j]};
         int lc[3];
@@ -453,7 +460,16 @@ __device__ __forceinline__ void project3r(R* v, uint8_t code, const SceneDev& S)
     if (code & PC_SLIPY) v[1] = R(0);
     if (code & PC_SLIPZ) v[2] = R(0);
     if (code & PC_PLANE) {
-        R n0 = (R)S.plane_n[0], n1 = (R)S.plane_n[1], n2 = (R)S.plane_n[2];
+        R n0, n1, n2;
+        if constexpr (sizeof(R) == 4) {
+            n0 = S.plane_nf[0];
+            n1 = S.plane_nf[1];
+            n2 = S.plane_nf[2];
+        } else {
+            n0 = (R)S.plane_n[0];
+            n1 = (R)S.plane_n[1];
+            n2 = (R)S.plane_n[2];
+        }
         R d = v[0] * n0 + v[1] * n1 + v[2] * n2;
         v[0] -= d * n0;
         v[1] -= d * n1;
@@ -517,9 +533,12 @@ struct ApplyArgs {
     RPtr9<R> sF;
     RPtr3<R> sn;
     const R* sic;
+    RPtr45<R> sK;             // surface: symmetric 9x9 map dF^ -> G of the projected Hessian (per iterate)
+    int use_sK;
     const int* slot_gen;      // general particles per slot
     const R4<R>* opk;         // rank-major records: position in the block (cells), kappa (< 0: general)
     const int *wrows, *wroff; // per work block: record rows and their offset
+    const int *gen_list, *gen_count;   // work blocks with samples or general particles
     int* err;
     int mode;
     int check_done;
@@ -936,6 +955,20 @@ __device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (
     make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
     R dFh[9];
     gather_grad_sep<R>(ph, lc, wgt, dw, dFh);
+    if (a.use_sK && a.mode == MPM_HESS_PROJECTED) {
+        // the sample's projected Hessian is a fixed symmetric map of dF^ for the iterate
+        R G[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+        for (int m = 0; m < 9; ++m)
+#pragma unroll
+            for (int l = m; l < 9; ++l) {
+                const R kml = a.sK.a[sym9(m, l)][j];
+                G[m] += kml * dFh[l];
+                if (l != m) G[l] += kml * dFh[m];
+            }
+        scatter_sep<R>(ua, lc, wgt, dw, G);
+        return;
+    }
     R Fh[9], av[3], nv[3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Fh[q] = a.sF.a[q][j];
@@ -1039,7 +1072,7 @@ __device__ __forceinline__ void flush_halo_rows(const int* __restrict__ nbr, int
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell(ApplyArgs<R> a) {
+__global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
     __shared__ R ua[3][PN];
     __shared__ R4<R> sp[MAXP];
@@ -1100,30 +1133,31 @@ __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell
             R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
             R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
             R tz = fmin(fmax(rec.z - R(lz), R(0)), R(1));
+            R px[3] = {R(1), tx, tx * tx};
             R py[3] = {R(1), ty, ty * ty}, pz[3] = {R(1), tz, tz * tz};
             R yz[3][3];
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
                 for (int kk = 0; kk < 3; ++kk) yz[j][kk] = py[j] * pz[kk];
-            R srow[3] = {R(0), R(0), R(0)};
+            R tr = R(0);
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int kk = 0; kk < 3; ++kk)
-                        if (!(ii == 2 && j == 2 && kk == 2)) srow[ii] += C[ii][j][kk] * yz[j][kk];
-            const R tr = srow[0] + tx * (srow[1] + tx * srow[2]);
-            const R s = rec.w * s2 * tr;
-            const R sx[3] = {s, s * tx, s * tx * tx};
+                        if (!(ii == 2 && j == 2 && kk == 2)) tr += C[ii][j][kk] * px[ii] * yz[j][kk];
+            R s = rec.w * s2 * tr;
 #pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
+            for (int ii = 0; ii < 3; ++ii) {
+                R sx = s * px[ii];
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
 #pragma unroll
                     for (int kk = 0; kk < 3; ++kk)
-                        if (!(ii == 2 && j == 2 && kk == 2)) M[ii][j][kk] += sx[ii] * yz[j][kk];
+                        if (!(ii == 2 && j == 2 && kk == 2)) M[ii][j][kk] += sx * yz[j][kk];
+            }
         }
         __syncthreads();   // every thread is done with this chunk
         if (k + 1 < nchunk && threadIdx.x == 0) {
@@ -1143,33 +1177,179 @@ __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell
     flush_halo_rows<R>(a.nbr, slot, ua, a.u);
 }
 
-// Solids, viscous liquids and surface samples: one thread per particle or
-// sample, shared-memory accumulation on the padded halo. Blocks with none of
-// them return at once (slot_gen counts the block's general particles).
+// Per-iterate symmetric 9x9 map of each surface sample's projected Hessian
+// (Gauss-Newton part plus the conformal part of the cofactor curvature), from
+// the same cached F^, n, 1/|c| the operator uses: column l is the map applied
+// to the l-th unit dF^. The operator then costs 45 loads and 81 multiply-adds
+// per sample instead of re-deriving frames and cofactor derivatives.
 template <typename R>
-__global__ void __launch_bounds__(NT_GEN, 16) k_apply_general(ApplyArgs<R> a) {
-    __shared__ R ph[3][PN];
-    __shared__ R ua[3][PN];
-    int w = blockIdx.x;
-    int slot = a.work[w];
-    long long gb = a.work_gb[w];
-    int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    if (a.check_done && a.scal[bc.w].cg_done) return;
-    const int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
-    if (send == sbeg && a.slot_gen[slot] == 0) return;
-    load_halo_rows<R>(a.nbr, slot, a.p, ph, ua);
-    __syncthreads();
+__global__ void k_surf_hess(int ns, const int* __restrict__ ssc, const SceneDev* __restrict__ sc, RPtr9<R> sF,
+                            RPtr3<R> sa, RPtr3<R> sn, const R* __restrict__ sic, const R* __restrict__ sg, RPtr45<R> K) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ns) return;
+    const SceneDev& S = sc[ssc[j]];
     const R dt = (R)S.dt;
-    const R inv_dx = (R)S.inv_dx;
-    if (a.slot_gen[slot] > 0) {
+    R Fh[9], av[3], nv[3];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Fh[q] = sF.a[q][j];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        av[q] = sa.a[q][j];
+        nv[q] = sn.a[q][j];
+    }
+    const R k = sg[j] * dt * dt, ic = sic[j];
+    for (int l = 0; l < 9; ++l) {
+        R X[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        X[l] = R(1);
+        R dC[9];
+        dcofactor<R>(Fh, X, dC);
+        R dc[3] = {dC[0] * av[0] + dC[1] * av[1] + dC[2] * av[2], dC[3] * av[0] + dC[4] * av[1] + dC[5] * av[2],
+                   dC[6] * av[0] + dC[7] * av[1] + dC[8] * av[2]};
+        R nd = nv[0] * dc[0] + nv[1] * dc[1] + nv[2] * dc[2];
+        R dn[3] = {(dc[0] - nd * nv[0]) * ic, (dc[1] - nd * nv[1]) * ic, (dc[2] - nd * nv[2]) * ic};
+        R G[9];
+        surf_G<R>(k, dn, Fh, av, G);
+        add_conformal<R>(k, nv, av, X, G);
+        for (int m = 0; m <= l; ++m) K.a[sym9(m, l)][j] = G[m];
+    }
+}
+
+// Solids, viscous liquids and surface samples: one thread per particle or
+// sample, shared-memory accumulation on the padded halo. A CTA is one warp and
+// takes GEN_B blocks of the compact list of blocks that hold any of them
+// (a block holds ~10-40 samples: one block per warp left most lanes idle);
+// the warp's lanes run over the concatenated samples of its blocks.
+constexpr int GEN_B = 2;
+template <typename R>
+__global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_general(ApplyArgs<R> a) {
+    __shared__ R ph[GEN_B][3][PN];
+    __shared__ R ua[GEN_B][3][PN];
+    const int g0 = blockIdx.x * GEN_B;
+    const int ng = *a.gen_count;
+    if (g0 >= ng) return;
+    int slot[GEN_B], sbeg[GEN_B], nsm[GEN_B], scene[GEN_B];
+    bool act[GEN_B];
+    int total = 0;
+#pragma unroll
+    for (int b = 0; b < GEN_B; ++b) {
+        act[b] = false;
+        slot[b] = -1;
+        sbeg[b] = nsm[b] = 0;
+        scene[b] = 0;
+        if (g0 + b < ng) {
+            const int w = a.gen_list[g0 + b];
+            slot[b] = a.work[w];
+            const long long gb = a.work_gb[w];
+            scene[b] = a.coord[slot[b]].w;
+            act[b] = !(a.check_done && a.scal[scene[b]].cg_done);
+            if (act[b]) {
+                sbeg[b] = a.scell_start[gb * 64];
+                nsm[b] = a.scell_start[gb * 64 + 64] - sbeg[b];
+                total += nsm[b];
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < GEN_B; ++b)
+        if (act[b]) load_halo_rows<R>(a.nbr, slot[b], a.p, ph[b], ua[b]);
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < GEN_B; ++b) {
+        if (!act[b] || a.slot_gen[slot[b]] == 0) continue;
+        const SceneDev& S = a.sc[scene[b]];
+        const int4 bc = a.coord[slot[b]];
+        const long long gb = S.block_base + bc.x + (long long)S.nb[0] * (bc.y + (long long)S.nb[1] * bc.z);
         const int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
         for (int i = beg + threadIdx.x; i < end; i += blockDim.x)
-            if (a.phase[i] != 0 || a.cvisc[i] != R(0)) particle_general<R>(a, i, ph, ua, dt, inv_dx);
+            if (a.phase[i] != 0 || a.cvisc[i] != R(0))
+                particle_general<R>(a, i, ph[b], ua[b], (R)S.dt, (R)S.inv_dx);
     }
-    for (int j = sbeg + threadIdx.x; j < send; j += blockDim.x) sample_general<R>(a, j, ph, ua, dt, inv_dx);
+    static_assert(GEN_B == 2, "the sample loop below selects between two blocks");
+    for (int k = threadIdx.x; k < total; k += blockDim.x) {
+        const bool second = k >= nsm[0];
+        const int j = second ? sbeg[1] + (k - nsm[0]) : sbeg[0] + k;
+        const SceneDev& S = a.sc[second ? scene[1] : scene[0]];
+        sample_general<R>(a, j, second ? ph[1] : ph[0], second ? ua[1] : ua[0], (R)S.dt, (R)S.inv_dx);
+    }
     __syncthreads();
-    flush_halo_rows<R>(a.nbr, slot, ua, a.u);
+#pragma unroll
+    for (int b = 0; b < GEN_B; ++b)
+        if (act[b]) flush_halo_rows<R>(a.nbr, slot[b], ua[b], a.u);
+}
+
+// Compact list of the work blocks that hold surface samples or general particles.
+__global__ void k_gen_flags(int nw, const int* __restrict__ work, const int* __restrict__ work_gb,
+                            const int* __restrict__ scell_start, const int* __restrict__ slot_gen, int* __restrict__ flag) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    long long gb = work_gb[w];
+    flag[w] = (scell_start[gb * 64 + 64] > scell_start[gb * 64] || slot_gen[work[w]] > 0) ? 1 : 0;
+}
+
+__global__ void k_gen_list(int nw, const int* __restrict__ flag, const int* __restrict__ pos, int* __restrict__ list) {
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw || !flag[w]) return;
+    list[pos[w]] = w;
+}
+
+// Surface samples of the float64 objective / gradient and of the line search:
+// one warp per block holding samples, padded float64 halos, separable
+// gather and scatter (k_eval and k_linesearch leave the samples to these).
+template <typename RS>
+__global__ void __launch_bounds__(32) k_eval_surf(EvalArgs<RS> a) {
+    __shared__ double ph[3][PN];
+    __shared__ double ga[3][PN];
+    const int w = blockIdx.x;
+    const int slot = a.work[w];
+    const long long gb = a.work_gb[w];
+    const int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    if (a.skip_done && a.scal[bc.w].newton_done) return;
+    const int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    if (send == sbeg) return;
+    load_halo_rows<double>(a.nbr, slot, a.gv, ph, ga);
+    __syncthreads();
+    const double dt = S.dt;
+    double esum = 0.0;
+    for (int j = sbeg + threadIdx.x; j < send; j += 32) {
+        const double p[3] = {a.s.a[0][j], a.s.a[1][j], a.s.a[2][j]};
+        int lc[3];
+        double wgt[3][3], dw[3][3], f[3];
+        stencil_in_block<double>(p, S, bc, lc, wgt, dw, f);
+        double L[9];
+        gather_grad_sep<double>(ph, lc, wgt, dw, L);
+        double Fh[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Fh[q] = dt * L[q] + ((q % 4 == 0) ? 1.0 : 0.0);
+        const double av[3] = {a.dA.a[0][j], a.dA.a[1][j], a.dA.a[2][j]};
+        double C[9];
+        cofactor<double>(Fh, C);
+        const double cv[3] = {C[0] * av[0] + C[1] * av[1] + C[2] * av[2], C[3] * av[0] + C[4] * av[1] + C[5] * av[2],
+                              C[6] * av[0] + C[7] * av[1] + C[8] * av[2]};
+        const double cn = sqrt(cv[0] * cv[0] + cv[1] * cv[1] + cv[2] * cv[2]);
+        const double k = a.gamma[j];
+        esum += k * cn;
+        const double ic = 1.0 / cn;
+        const double nv[3] = {cv[0] * ic, cv[1] * ic, cv[2] * ic};
+        if (a.want_cache) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) a.sF.a[q][j] = (RS)Fh[q];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) a.sn.a[q][j] = (RS)nv[q];
+            a.sic[j] = (RS)ic;
+        }
+        if (a.want_grad) {
+            double G[9];
+            surf_G<double>(k * dt, nv, Fh, av, G);
+            scatter_sep<double>(ga, lc, wgt, dw, G);
+        }
+    }
+    esum = warp_sum(esum);
+    if (threadIdx.x == 0 && esum != 0.0) atomicAdd(&a.scal[bc.w].phi_part, esum);
+    if (a.want_grad) {
+        __syncthreads();
+        flush_halo_rows<double>(a.nbr, slot, ga, a.grad);
+    }
 }
 
 // ======================================================================
@@ -1332,11 +1512,13 @@ __global__ void __launch_bounds__(NT_CELL) k_curv_cell(ApplyArgs<R> a) {
 // pinv = 1 / (m + pinv) on unknown components (pinv holds zero on entry), 0 elsewhere
 template <typename R>
 __global__ void k_pinv(int nb, const int4* __restrict__ coord, const SceneDev* __restrict__ sc,
-                       const double* __restrict__ gm, const uint8_t* __restrict__ pcode, R* __restrict__ pinv) {
+                       const double* __restrict__ gm, const uint8_t* __restrict__ pcode, R* __restrict__ pinv,
+                       R* __restrict__ mR) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nb * 64) return;
     int slot = t >> 6, l = t & 63;
     double m = gm[t];
+    mR[t] = (R)m;
     uint8_t code = pcode[t];
     for (int c = 0; c < 3; ++c) {
         int k = slot * 192 + c * 64 + l;
@@ -1356,6 +1538,7 @@ struct CGArgs {
     const uint8_t* pcode;     // NC == 3
     const R* inv;             // inverse diagonal (0 = not an unknown)
     const double* gm;         // NC == 3: mass diagonal
+    const R* mR;              // NC == 3: mass diagonal in R
     R *x, *r, *p, *u;
     const double* rhs_d;      // for init: b = sign * rhs (double)
     double rhs_sign;
@@ -1386,11 +1569,15 @@ constexpr int OFF_RR = offsetof(SceneScal, rr) / 8, OFF_RZ = offsetof(SceneScal,
 
 // Per-scene sums of two values over the CTA: warp sums, then one float64 atomic
 // per run of equal scenes (slots are ordered scene by scene). scene < 0: no slot.
+__device__ __forceinline__ void cta_scene_sum2_warp(double v1, double v2, int scene, SceneScal* scal, int off1, int off2);
 __device__ __forceinline__ void cta_scene_sum2(double v1, double v2, int scene, SceneScal* scal, int off1, int off2) {
+    cta_scene_sum2_warp(warp_sum(v1), warp_sum(v2), scene, scal, off1, off2);
+}
+
+// same, from warp totals held by lane 0 of each warp
+__device__ __forceinline__ void cta_scene_sum2_warp(double v1, double v2, int scene, SceneScal* scal, int off1, int off2) {
     __shared__ double s1[CG_NT / 32], s2[CG_NT / 32];
     __shared__ int sid[CG_NT / 32];
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
     int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
         s1[w] = v1;
@@ -1458,29 +1645,69 @@ __global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int 
 }
 
 // ---- one CG iteration's vector work as a single cooperative launch ----
-// Per-thread partial sums (float64) of the nodes it visits; warps stay
-// scene-uniform (a warp covers 32 nodes of one slot and all lanes visit the
-// same slots), so a change of scene flushes the warp's sum with one atomic.
-// The last scene's sums go through the CTA reduction (cta_scene_sum2).
+// Each thread sums the per-node products (formed in R) of the nodes it visits:
+// compensated (Kahan) in float32, plain in float64, and hands the sum on in
+// float64. Warps stay scene-uniform (a warp covers 32 nodes of one slot and all
+// lanes visit the same slots), so a change of scene flushes the warp's sums
+// with one atomic; the last scene's sums go through the CTA reduction
+// (cta_scene_sum2).
+template <typename R>
+struct KSum {
+    R s = R(0), c = R(0);   // value s - c
+    __device__ void add(R x) {
+        if constexpr (sizeof(R) == 4) {
+            R y = x - c;
+            R t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    // sum over the warp (valid in lane 0), float32 pairs combined with an
+    // error-free two-sum, so the float64 pipe only sees lane 0's conversion
+    __device__ double warp_total() const {
+        if constexpr (sizeof(R) == 4) {
+            R hs = s, hc = c;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                R os = __shfl_down_sync(0xffffffffu, hs, o), oc = __shfl_down_sync(0xffffffffu, hc, o);
+                R t = hs + os;
+                R bb = t - hs;
+                R err = (hs - (t - bb)) + (os - bb);   // hs + os = t + err exactly
+                hs = t;
+                hc = hc + oc - err;
+            }
+            return (threadIdx.x & 31) == 0 ? (double)hs - (double)hc : 0.0;
+        } else {
+            return warp_sum((double)s);
+        }
+    }
+    __device__ void clear() { s = c = R(0); }
+};
+
+template <typename R>
 struct SceneAcc {
-    double v1 = 0.0, v2 = 0.0;
+    KSum<R> a1, a2;
     int cur = -1;
-    __device__ void add(int scene, double x1, double x2, SceneScal* scal, int off1, int off2) {
+    __device__ void add(int scene, R x1, R x2, SceneScal* scal, int off1, int off2) {
         if (scene != cur) {
             flush(scal, off1, off2);
             cur = scene;
         }
-        v1 += x1;
-        v2 += x2;
+        a1.add(x1);
+        a2.add(x2);
     }
     __device__ void flush(SceneScal* scal, int off1, int off2) {
-        double a1 = warp_sum(v1), a2 = warp_sum(v2);
-        if (cur >= 0 && (threadIdx.x & 31) == 0) {
+        if (cur < 0) return;   // warp-uniform
+        double v1 = a1.warp_total(), v2 = a2.warp_total();
+        if ((threadIdx.x & 31) == 0) {
             double* base = reinterpret_cast<double*>(&scal[cur]);
-            if (off1 >= 0 && a1 != 0.0) atomicAdd(base + off1, a1);
-            if (off2 >= 0 && a2 != 0.0) atomicAdd(base + off2, a2);
+            if (off1 >= 0 && v1 != 0.0) atomicAdd(base + off1, v1);
+            if (off2 >= 0 && v2 != 0.0) atomicAdd(base + off2, v2);
         }
-        v1 = v2 = 0.0;
+        a1.clear();
+        a2.clear();
     }
 };
 
@@ -1539,54 +1766,61 @@ __device__ __forceinline__ void cg_check_scene(SceneScal& c, const SceneDev& S, 
 //   C: per-scene control
 //   D: p = z + beta p
 template <typename R, int NC>
-__global__ void __launch_bounds__(CG_NT) k_cg_iter(CGArgs<R, NC> a, int nb, int nsc, int heat, unsigned* bar, int* err) {
+__global__ void __launch_bounds__(CG_NT, 3) k_cg_iter(CGArgs<R, NC> a, int nb, int nsc, int heat, unsigned* bar, int* err) {
     const int nchunks = (nb + CG_SLOTS - 1) / CG_SLOTS;
     const int l = threadIdx.x & 63;
-    SceneAcc acc;
+    SceneAcc<R> acc;
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
         if (slot >= nb) continue;
         const int scene = a.coord[slot].w;
         const SceneDev& S = a.sc[scene];
-        double pq = 0.0;
+        R pql = R(0);   // the node's products in R
         if (!a.scal[scene].cg_done) {
             const int t = slot * 64 + l;
             R q[NC], pv[NC];
-            double diag;
-            if (NC == 3) diag = a.gm[t];
-            else diag = a.inv[t] == R(0) ? 0.0 : 1.0 / (double)a.inv[t];
+            R diag;
+            if (NC == 3) diag = a.mR[t];
+            else diag = a.inv[t] == R(0) ? R(0) : R(1) / a.inv[t];
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const int k = vidx<R, NC>(slot, c, l);
                 pv[c] = a.p[k];
-                q[c] = (R)diag * pv[c] + a.u[k];
+                q[c] = diag * pv[c] + a.u[k];
             }
             cg_proj<R, NC>(q, a, t, S);
-            R pql = R(0);   // the node's products in R; sums across nodes in float64
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 a.u[vidx<R, NC>(slot, c, l)] = q[c];
                 pql += pv[c] * q[c];
             }
-            pq = (double)pql;
         }
-        acc.add(scene, pq, 0.0, a.scal, OFF_PAP, -1);
+        acc.add(scene, pql, R(0), a.scal, OFF_PAP, -1);
     }
-    cta_scene_sum2(acc.v1, acc.v2, acc.cur, a.scal, OFF_PAP, -1);
+    cta_scene_sum2_warp(acc.a1.warp_total(), acc.a2.warp_total(), acc.cur, a.scal, OFF_PAP, -1);
     if (!grid_barrier(bar, err)) return;
-    acc.v1 = acc.v2 = 0.0;
+    acc.a1.clear();
+    acc.a2.clear();
     acc.cur = -1;
+    int ascene = -1;
+    R alpha = R(0);
+    bool curv_ok = true;
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
         if (slot >= nb) continue;
         const int scene = a.coord[slot].w;
         const SceneDev& S = a.sc[scene];
         const SceneScal& sc = a.scal[scene];
-        double rz_new = 0.0, rr = 0.0;
+        R rzl = R(0), rrl = R(0);
         if (!sc.cg_done) {
             const int t = slot * 64 + l;
-            const double pAp = sc.pAp;
-            if (!(pAp > 0.0)) {
+            if (scene != ascene) {   // once per scene change, not per node
+                const double pAp = sc.pAp;
+                curv_ok = pAp > 0.0;
+                alpha = curv_ok ? (R)sc.rz / (R)pAp : R(0);   // the step is applied in R
+                ascene = scene;
+            }
+            if (!curv_ok) {
                 if (sc.cg_it == 0) {
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
@@ -1597,7 +1831,6 @@ __global__ void __launch_bounds__(CG_NT) k_cg_iter(CGArgs<R, NC> a, int nb, int 
 #pragma unroll
                 for (int c = 0; c < NC; ++c) a.u[vidx<R, NC>(slot, c, l)] = R(0);
             } else {
-                const R alpha = (R)(sc.rz / pAp);
                 R r[NC], z[NC];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
@@ -1610,23 +1843,22 @@ __global__ void __launch_bounds__(CG_NT) k_cg_iter(CGArgs<R, NC> a, int nb, int 
 #pragma unroll
                 for (int c = 0; c < NC; ++c) z[c] = r[c] * cg_prec<R, NC>(a, slot, c, l, t);
                 cg_proj<R, NC>(z, a, t, S);
-                R rzl = R(0), rrl = R(0);
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     rzl += r[c] * z[c];
                     rrl += r[c] * r[c];
                 }
-                rz_new = (double)rzl;
-                rr = (double)rrl;
             }
         }
-        acc.add(scene, rz_new, rr, a.scal, OFF_RZN, OFF_RR);
+        acc.add(scene, rzl, rrl, a.scal, OFF_RZN, OFF_RR);
     }
-    cta_scene_sum2(acc.v1, acc.v2, acc.cur, a.scal, OFF_RZN, OFF_RR);
+    cta_scene_sum2_warp(acc.a1.warp_total(), acc.a2.warp_total(), acc.cur, a.scal, OFF_RZN, OFF_RR);
     if (!grid_barrier(bar, err)) return;
     if (blockIdx.x == 0)
         for (int s = threadIdx.x; s < nsc; s += blockDim.x) cg_check_scene(a.scal[s], a.sc[s], heat);
     if (!grid_barrier(bar, err)) return;
+    int bscene = -1;
+    R beta = R(0);
     for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
         const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
         if (slot >= nb) continue;
@@ -1634,8 +1866,11 @@ __global__ void __launch_bounds__(CG_NT) k_cg_iter(CGArgs<R, NC> a, int nb, int 
         const SceneDev& S = a.sc[scene];
         const SceneScal& sc = a.scal[scene];
         if (sc.cg_done) continue;
+        if (scene != bscene) {
+            beta = (R)sc.alpha;   // holds beta here (set by the control phase)
+            bscene = scene;
+        }
         const int t = slot * 64 + l;
-        const R beta = (R)sc.alpha;
         R z[NC];
 #pragma unroll
         for (int c = 0; c < NC; ++c) z[c] = a.r[vidx<R, NC>(slot, c, l)] * cg_prec<R, NC>(a, slot, c, l, t);
@@ -1731,7 +1966,8 @@ struct LSArgs {
     const uint8_t* phase;
     Ptrs3 s, dA;
     const double* gamma;
-    int skip_poly;             // non-viscous liquid particles are left to k_ls_cell
+    int skip_poly;             // non-viscous liquid particles take the closed form (k_curv_cell)
+    int skip_samples;          // surface samples are left to k_ls_surf
     const int* slot_gen;
 };
 
@@ -1749,7 +1985,8 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
     SceneScal& scl = a.scal[bc.w];
     if (scl.newton_done) return;
     const bool poly = a.skip_poly && S.mu_l == 0.0;
-    if (poly && a.slot_gen[slot] == 0 && a.scell_start[gb * 64] == a.scell_start[gb * 64 + 64]) return;
+    const bool no_samples = a.skip_samples || a.scell_start[gb * 64] == a.scell_start[gb * 64 + 64];
+    if (poly && a.slot_gen[slot] == 0 && no_samples) return;
     load_halo_vec_d<R>(a.nbr, slot, a.gv, vh);
     for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
         int c = t / HN, h = t % HN;
@@ -1839,6 +2076,7 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
         }
     }
     int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    if (a.skip_samples) send = sbeg;
     for (int j = sbeg + threadIdx.x; j < send; j += NT) {
         double p[3] = {a.s.a[0][j], a.s.a[1][j], a.s.a[2][j]};
         int lc[3];
@@ -1888,6 +2126,90 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
         }
     }
     for (int k = 0; k < nls; ++k) block_atomic_sum<NT>(de[k], &scl.dphi[k], red);
+}
+
+template <typename RD>
+__global__ void __launch_bounds__(32) k_ls_surf(LSArgs<RD> a) {
+    __shared__ double pv[3][PN];
+    __shared__ double pd[3][PN];
+    const int w = blockIdx.x;
+    const int slot = a.work[w];
+    const long long gb = a.work_gb[w];
+    const int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    SceneScal& scl = a.scal[bc.w];
+    if (scl.newton_done) return;
+    const int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    if (send == sbeg) return;
+    load_halo_rows<double>(a.nbr, slot, a.gv, pv, pd);   // pd zeroed, then filled below
+    __syncthreads();
+    for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
+        int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<double>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        int h0 = pidx(0, hy, hz);
+        pd[c][h0] = nlo >= 0 ? (double)a.d[nlo * 192 + c * 64 + base + 3] : 0.0;
+        for (int k = 0; k < 4; ++k) pd[c][h0 + 1 + k] = nmid >= 0 ? (double)a.d[nmid * 192 + c * 64 + base + k] : 0.0;
+        pd[c][h0 + 5] = nhi >= 0 ? (double)a.d[nhi * 192 + c * 64 + base] : 0.0;
+    }
+    __syncthreads();
+    const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
+    const double dt = S.dt;
+    double de[MAX_LS];
+#pragma unroll
+    for (int k = 0; k < MAX_LS; ++k) de[k] = 0.0;
+    for (int j = sbeg + threadIdx.x; j < send; j += 32) {
+        const double p[3] = {a.s.a[0][j], a.s.a[1][j], a.s.a[2][j]};
+        int lc[3];
+        double wgt[3][3], dw[3][3], f[3];
+        stencil_in_block<double>(p, S, bc, lc, wgt, dw, f);
+        double Lv[9], Ld[9];
+        gather_grad_sep<double>(pv, lc, wgt, dw, Lv);
+        gather_grad_sep<double>(pd, lc, wgt, dw, Ld);
+        double Fh[9], Dh[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            Fh[q] = dt * Lv[q] + ((q % 4 == 0) ? 1.0 : 0.0);
+            Dh[q] = dt * Ld[q];
+        }
+        const double av[3] = {a.dA.a[0][j], a.dA.a[1][j], a.dA.a[2][j]};
+        double C[9], dC[9], CD[9];
+        cofactor<double>(Fh, C);
+        dcofactor<double>(Fh, Dh, dC);
+        cofactor<double>(Dh, CD);
+        double c0[3], c1[3], c2[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            c0[q] = C[3 * q] * av[0] + C[3 * q + 1] * av[1] + C[3 * q + 2] * av[2];
+            c1[q] = dC[3 * q] * av[0] + dC[3 * q + 1] * av[1] + dC[3 * q + 2] * av[2];
+            c2[q] = CD[3 * q] * av[0] + CD[3 * q + 1] * av[1] + CD[3 * q + 2] * av[2];
+        }
+        // |c0 + alpha c1 + alpha^2 c2| - |c0| without cancellation
+        const double n0 = sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
+        const double k = a.gamma[j];
+        double alpha = 1.0;
+#pragma unroll
+        for (int kk = 0; kk < MAX_LS; ++kk) {
+            if (kk < nls) {
+                double dc[3], cn[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    dc[q] = alpha * c1[q] + alpha * alpha * c2[q];
+                    cn[q] = c0[q] + dc[q];
+                }
+                const double n1 = sqrt(cn[0] * cn[0] + cn[1] * cn[1] + cn[2] * cn[2]);
+                const double num = 2.0 * (c0[0] * dc[0] + c0[1] * dc[1] + c0[2] * dc[2]) + dc[0] * dc[0] +
+                                   dc[1] * dc[1] + dc[2] * dc[2];
+                de[kk] += k * num / (n1 + n0);
+            }
+            alpha *= 0.5;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MAX_LS; ++k) {
+        const double v = warp_sum(de[k]);
+        if (k < nls && threadIdx.x == 0 && v != 0.0) atomicAdd(&scl.dphi[k], v);
+    }
 }
 
 // node part of the line search: kinetic + gravity differences, the liquid
@@ -2113,6 +2435,7 @@ EvalArgs<R> make_eval_args(mpm_ctx* c, bool want_grad, bool want_cache, bool ski
     a.want_cache = want_cache;
     a.skip_done = skip_done;
     a.skip_poly = 1;
+    a.skip_samples = 1;
     a.slot_gen = d.slot_gen;
     for (int q = 0; q < 24; ++q) a.scache.a[q] = (R*)d.scache[q];
     a.sic = (R*)d.sic;
@@ -2153,9 +2476,13 @@ ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int c
     a.sg = (const R*)d.sg;
     a.sic = (const R*)d.sic;
     a.slot_gen = d.slot_gen;
+    for (int q = 0; q < 45; ++q) a.sK.a[q] = (R*)d.sK[q];
+    a.use_sK = c->sK_valid ? 1 : 0;
     a.opk = (const R4<R>*)d.opk;
     a.wrows = d.wrows;
     a.wroff = d.wroff;
+    a.gen_list = d.gen_list;
+    a.gen_count = d.gen_pos + c->NW;
     a.err = d.err;
     a.mode = mode;
     a.check_done = check_done;
@@ -2171,6 +2498,7 @@ CGArgs<R, NC> make_cg_args(mpm_ctx* c) {
     a.scal = d.scal;
     a.pcode = d.pcode;
     a.gm = d.gm;
+    a.mR = (const R*)d.mR;
     if (NC == 3) {
         a.inv = (const R*)d.invm;
         a.pinv3 = (const R*)d.pinv;
@@ -2252,7 +2580,7 @@ cudaError_t pack_step_t(mpm_ctx* c) {
     if (c->NW > 0) {
         cudaMemsetAsync(d.pinv, 0, sizeof(R) * (size_t)c->NB * 192, st);
         MPM_LAUNCH k_pinv<R><<<nblk((long long)c->NB * 64, 256), 256, 0, st>>>(c->NB, d.slot_coord, d.sc, d.gm, d.pcode,
-                                                                             (R*)d.pinv);
+                                                                             (R*)d.pinv, (R*)d.mR);
     }
     if (c->ns > 0) {
         RPtr3<R> su, sa;
@@ -2263,6 +2591,12 @@ cudaError_t pack_step_t(mpm_ctx* c) {
         MPM_LAUNCH k_pack_surface<R><<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, Ptrs3{{d.s[0], d.s[1], d.s[2]}},
                                                             Ptrs3{{d.dA[0], d.dA[1], d.dA[2]}}, d.gamma, d.ssc, d.sc, su,
                                                             sa, (R*)d.sg);
+    }
+    if (c->NW > 0) {
+        MPM_LAUNCH k_gen_flags<<<nblk(c->NW, 256), 256, 0, st>>>(c->NW, d.work, d.work_gb, d.scell_start, d.slot_gen,
+                                                               d.gen_flag);
+        launch_exclusive_scan(c, d.gen_flag, d.gen_pos, c->NW, d.scan_tmp, st);
+        MPM_LAUNCH k_gen_list<<<nblk(c->NW, 256), 256, 0, st>>>(c->NW, d.gen_flag, d.gen_pos, d.gen_list);
     }
     return cudaGetLastError();
 }
@@ -2333,7 +2667,7 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
                 if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
-                if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<c->NW, NT_GEN, 0, st>>>(ap);
+                if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<nblk(c->NW, GEN_B), NT_GEN, 0, st>>>(ap);
                 prof_mark_apply(c, false);
                 e0 = launch_cg_iter<R, 3>(c, a, 0);
                 if (e0 != cudaSuccess) return e0;
@@ -2355,6 +2689,24 @@ cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) 
     if (c->NW == 0) return cudaSuccess;
     auto a = make_eval_args<RS>(c, want_grad, want_cache, skip_done);
     MPM_LAUNCH k_eval<R, RS><<<c->NW, NT, 0, c->st>>>(a);
+    if (c->ns > 0) {
+        MPM_LAUNCH k_eval_surf<RS><<<c->NW, 32, 0, c->st>>>(a);
+        if (want_cache) {
+            Dev& dd = c->d;
+            RPtr9<RS> sF;
+            RPtr3<RS> sa, sn;
+            RPtr45<RS> K;
+            for (int q = 0; q < 9; ++q) sF.a[q] = (RS*)dd.sF[q];
+            for (int q = 0; q < 3; ++q) {
+                sa.a[q] = (RS*)dd.sa[q];
+                sn.a[q] = (RS*)dd.sn[q];
+            }
+            for (int q = 0; q < 45; ++q) K.a[q] = (RS*)dd.sK[q];
+            MPM_LAUNCH k_surf_hess<RS><<<nblk(c->ns, 128), 128, 0, c->st>>>((int)c->ns, dd.ssc, dd.sc, sF, sa, sn,
+                                                                        (const RS*)dd.sic, (const RS*)dd.sg, K);
+            c->sK_valid = true;
+        }
+    }
     Dev& d = c->d;
     EvalCellArgs e;
     e.work = d.work;
@@ -2435,8 +2787,10 @@ cudaError_t newton_t(mpm_ctx* c) {
             a.phase = d.phase;
             a.gamma = d.gamma;
             a.skip_poly = 1;
+            a.skip_samples = 1;
             a.slot_gen = d.slot_gen;
             MPM_LAUNCH k_linesearch<double, R><<<c->NW, NT, 0, st>>>(a);
+            if (c->ns > 0) MPM_LAUNCH k_ls_surf<R><<<c->NW, 32, 0, st>>>(a);
             auto cv = make_apply_args<R>(c, d.cx, nullptr, MPM_HESS_PROJECTED, 0);
             MPM_LAUNCH k_curv_cell<R><<<c->NW, NT_CELL, 0, st>>>(cv);
         }
@@ -2474,11 +2828,11 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
     if (c->rsize == 4) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
-        MPM_LAUNCH k_apply_general<float><<<c->NW, NT_GEN, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_general<float><<<nblk(c->NW, GEN_B), NT_GEN, 0, c->st>>>(a);
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
-        MPM_LAUNCH k_apply_general<double><<<c->NW, NT_GEN, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_general<double><<<nblk(c->NW, GEN_B), NT_GEN, 0, c->st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -104,25 +104,31 @@ struct P2GArgs {
     double *gm, *gmv, *gmT, *gmTT;
 };
 
-__global__ void __launch_bounds__(NT) k_p2g_volume(P2GArgs a) {
+// One CTA per work block, one thread per cell: a thread walks its cell's
+// particles, so the 32 lanes of a warp write 32 distinct halo nodes for each
+// stencil offset (sorted particles of one cell would otherwise hit the same
+// nodes from many lanes at once).
+__global__ void __launch_bounds__(64) k_p2g_volume(P2GArgs a) {
     __shared__ double acc[6][HN];
-    int w = blockIdx.x;
-    int slot = a.work[w];
-    long long gb = a.work_gb[w];
-    int4 bc = a.coord[slot];
+    const int w = blockIdx.x;
+    const int slot = a.work[w];
+    const long long gb = a.work_gb[w];
+    const int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
-    for (int t = threadIdx.x; t < 6 * HN; t += NT) (&acc[0][0])[t] = 0.0;
+    for (int t = threadIdx.x; t < 6 * HN; t += blockDim.x) (&acc[0][0])[t] = 0.0;
     __syncthreads();
-    int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
-    int ob[3] = {bc.x * BS, bc.y * BS, bc.z * BS};
-    for (int i = beg + threadIdx.x; i < end; i += NT) {
+    const int cell = threadIdx.x;
+    const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
+    const int ob[3] = {bc.x * BS, bc.y * BS, bc.z * BS};
+    const double dx = S.dx;
+    for (int i = cbeg; i < cend; ++i) {
         double u[3];
         for (int q = 0; q < 3; ++q) u[q] = (a.x.a[q][i] - S.origin[q]) * S.inv_dx;
         Stencil<double> st;
         make_stencil<double>(u, S.inv_dx, st);
         double f[3];
         for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
-        const double mt = a.mt[i], dx = S.dx;
+        const double mt = a.mt[i];
         // node (cx, cy, cz) receives mt N (v + A (x_i - x_p)) with x_i - x_p = (c - f) dx,
         // i.e. N (B + E c): B = mt (v - dx A f), E = mt dx A
         double B[3], E[9];
@@ -165,7 +171,7 @@ __global__ void __launch_bounds__(NT) k_p2g_volume(P2GArgs a) {
                 }
     }
     __syncthreads();
-    for (int h = threadIdx.x; h < HN; h += NT) {
+    for (int h = threadIdx.x; h < HN; h += blockDim.x) {
         if (acc[0][h] == 0.0 && acc[4][h] == 0.0) continue;
         int ns, loc;
         halo_source(a.nbr, slot, h, ns, loc);
@@ -612,7 +618,7 @@ cudaError_t launch_p2g(mpm_ctx* c) {
         a.gmv = d.gmv;
         a.gmT = d.gmT;
         a.gmTT = d.gmTT;
-        MPM_LAUNCH k_p2g_volume<<<c->NW, NT, 0, st>>>(a);
+        MPM_LAUNCH k_p2g_volume<<<c->NW, 64, 0, st>>>(a);
     }
     if (c->ns > 0) {
         P9 A;
