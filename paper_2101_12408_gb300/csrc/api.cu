@@ -343,7 +343,8 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.kind, uint8_t, Sn);
     A_(d.sid, int, Sn); A_(d.ssc, int, Sn); A_(d.parent, int, Sn);
     R_(d.sg, Sn); R_(d.sic, Sn); R_(d.swn, Sn);
-    for (int q = 0; q < 45; ++q) R_(d.sK[q], Sn);
+    R_(d.sK[0], 45 * Sn);   // one allocation: the 45 entries of a sample's map are Sn apart
+    for (int q = 1; q < 45; ++q) d.sK[q] = (char*)d.sK[0] + (size_t)q * Sn * c->rsize;
     A_(d.key, long long, P); A_(d.rank, int, P); A_(d.perm, int, P);
     A_(d.skey, long long, Sn); A_(d.srank, int, Sn); A_(d.sperm, int, Sn);
     A_(d.cell_count, int, c->total_cells + 1); A_(d.cell_start, int, c->total_cells + 1);
@@ -352,6 +353,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.slot_coord, int4, bcap + 1); A_(d.nbr, int, bcap * 27 + 27); A_(d.work, int, bcap + 1); A_(d.work_gb, int, bcap + 1);
     A_(d.slot_gen, int, bcap + 1); A_(d.wrows, int, bcap + 1); A_(d.wroff, int, bcap + 2);
     A_(d.gen_flag, int, bcap + 1); A_(d.gen_pos, int, bcap + 2); A_(d.gen_list, int, bcap + 1);
+    A_(d.gen_flag_g, int, bcap + 1); A_(d.gen_pos_g, int, bcap + 2); A_(d.gen_list_g, int, bcap + 1);
     A_(d.counts, int, 4);
     A_(d.scan_tmp, int, (c->total_cells + 1) / 4096 + 16);
     A_(d.gm, double, NN); A_(d.gmv, double, NN * 3); A_(d.gvn, double, NN * 3); A_(d.gmT, double, NN);

@@ -35,6 +35,7 @@ struct Dev {
     int* wrows;                     // per work block: record rows (most particles in one of its cells)
     int* wroff;                     // exclusive scan of wrows (+ total)
     int *gen_flag, *gen_pos, *gen_list;   // work blocks with samples or general particles: flag, scan, list
+    int *gen_flag_g, *gen_pos_g, *gen_list_g;   // the same for general particles only
     void* Fn[9];                    // F^n (solid)
     void* lame[2];                  // mu, lambda (solid)
     void* scache[24];               // solid per-iterate: F (9), R (9), (tr S I - S)^-1 (6)

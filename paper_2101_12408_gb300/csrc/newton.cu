@@ -534,7 +534,9 @@ struct ApplyArgs {
     RPtr3<R> sn;
     const R* sic;
     RPtr45<R> sK;             // surface: symmetric 9x9 map dF^ -> G of the projected Hessian (per iterate)
-    int use_sK;
+    const R* sK0;             // the same 45 arrays, contiguous: entry e of sample j at sK0[e * sKs + j]
+    long long sKs;
+    int samples_in_cell;      // projected mode with current maps: k_apply_cell applies the samples
     const int* slot_gen;      // general particles per slot
     const R4<R>* opk;         // rank-major records: position in the block (cells), kappa (< 0: general)
     const int *wrows, *wroff; // per work block: record rows and their offset
@@ -893,6 +895,48 @@ __device__ __forceinline__ void gather_grad_sep(R (*ph)[PN], const int* lc, cons
     }
 }
 
+// one component q of the two above: row q of the gradient, and the scatter of row q
+template <typename R>
+__device__ __forceinline__ void gather_grad_row(const R* ph, const int* lc, const R (*w)[3], const R (*dw)[3], R* g) {
+    R gx = R(0), gy = R(0), gz = R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R u0 = R(0), u1 = R(0), u2 = R(0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const R* row = &ph[pidx(lc[0] + a, lc[1] + b, lc[2])];
+            R p0 = row[0], p1 = row[PZ], p2 = row[2 * PZ];
+            R s0 = w[2][0] * p0 + w[2][1] * p1 + w[2][2] * p2;
+            R s1 = dw[2][0] * p0 + dw[2][1] * p1 + dw[2][2] * p2;
+            u0 += w[1][b] * s0;
+            u1 += dw[1][b] * s0;
+            u2 += w[1][b] * s1;
+        }
+        gx += dw[0][a] * u0;
+        gy += w[0][a] * u1;
+        gz += w[0][a] * u2;
+    }
+    g[0] = gx;
+    g[1] = gy;
+    g[2] = gz;
+}
+
+template <typename R>
+__device__ __forceinline__ void scatter_row(R* ua, const int* lc, const R (*w)[3], const R (*dw)[3], const R* m) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R A0 = m[0] * dw[0][a], A1 = m[1] * w[0][a], A2 = m[2] * w[0][a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            R B0 = A0 * w[1][b] + A1 * dw[1][b];
+            R B1 = A2 * w[1][b];
+            R* row = &ua[pidx(lc[0] + a, lc[1] + b, lc[2])];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(row + c * PZ, B0 * w[2][c] + B1 * dw[2][c]);
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ void scatter_sep(R (*ua)[PN], const int* lc, const R (*w)[3], const R (*dw)[3], const R* M) {
 #pragma unroll
@@ -955,20 +999,6 @@ __device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (
     make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
     R dFh[9];
     gather_grad_sep<R>(ph, lc, wgt, dw, dFh);
-    if (a.use_sK && a.mode == MPM_HESS_PROJECTED) {
-        // the sample's projected Hessian is a fixed symmetric map of dF^ for the iterate
-        R G[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
-#pragma unroll
-        for (int m = 0; m < 9; ++m)
-#pragma unroll
-            for (int l = m; l < 9; ++l) {
-                const R kml = a.sK.a[sym9(m, l)][j];
-                G[m] += kml * dFh[l];
-                if (l != m) G[l] += kml * dFh[m];
-            }
-        scatter_sep<R>(ua, lc, wgt, dw, G);
-        return;
-    }
     R Fh[9], av[3], nv[3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Fh[q] = a.sF.a[q][j];
@@ -1072,7 +1102,7 @@ __device__ __forceinline__ void flush_halo_rows(const int* __restrict__ nbr, int
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
+__global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
     __shared__ R ua[3][PN];
     __shared__ R4<R> sp[MAXP];
@@ -1173,6 +1203,46 @@ __global__ void __launch_bounds__(NT_CELL) k_apply_cell(ApplyArgs<R> a) {
         return;
     }
     if (any) cell_scatter<R>(M, ua, lx, ly, lz);
+    if (a.samples_in_cell) {
+        // The block's surface samples share the halo already staged for its
+        // particles. Three lanes per sample, one per component: lane q gathers row q
+        // of dF^, the rows are exchanged within the lane triple, lane q forms row q of
+        // G = K dF^ and scatters it (10 samples per warp, lanes 30 and 31 idle).
+        const int sbeg = a.scell_start[gb * 64], nsm = a.scell_start[gb * 64 + 64] - sbeg;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int si = lane / 3, q = lane - 3 * (lane / 3);
+        for (int base = 0; base < nsm; base += 10 * (NT_CELL / 32)) {
+            const int k = base + wid * 10 + si;
+            const bool act = lane < 30 && k < nsm;
+            const int j = sbeg + (act ? k : 0);
+            int lc[3];
+            R wgt[3][3], dw[3][3];
+            make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
+            R g[3] = {R(0), R(0), R(0)};
+            if (act) gather_grad_row<R>(ph[q], lc, wgt, dw, g);
+            R dF[9];
+            const int l0 = 3 * si < 30 ? 3 * si : 0;
+#pragma unroll
+            for (int qq = 0; qq < 3; ++qq)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) dF[3 * qq + e] = __shfl_sync(0xffffffffu, g[e], l0 + qq);
+            if (act) {
+                R m3[3];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    const int row = 3 * q + e;
+                    R acc = R(0);
+#pragma unroll
+                    for (int l = 0; l < 9; ++l) {
+                        const int lo = row < l ? row : l, hi = row < l ? l : row;
+                        acc += a.sK0[(long long)sym9(lo, hi) * a.sKs + j] * dF[l];
+                    }
+                    m3[e] = acc;
+                }
+                scatter_row<R>(ua[q], lc, wgt, dw, m3);
+            }
+        }
+    }
     __syncthreads();
     flush_halo_rows<R>(a.nbr, slot, ua, a.u);
 }
@@ -1242,7 +1312,7 @@ __global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_gener
             const long long gb = a.work_gb[w];
             scene[b] = a.coord[slot[b]].w;
             act[b] = !(a.check_done && a.scal[scene[b]].cg_done);
-            if (act[b]) {
+            if (act[b] && !a.samples_in_cell) {
                 sbeg[b] = a.scell_start[gb * 64];
                 nsm[b] = a.scell_start[gb * 64 + 64] - sbeg[b];
                 total += nsm[b];
@@ -1279,11 +1349,14 @@ __global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_gener
 
 // Compact list of the work blocks that hold surface samples or general particles.
 __global__ void k_gen_flags(int nw, const int* __restrict__ work, const int* __restrict__ work_gb,
-                            const int* __restrict__ scell_start, const int* __restrict__ slot_gen, int* __restrict__ flag) {
+                            const int* __restrict__ scell_start, const int* __restrict__ slot_gen, int* __restrict__ flag,
+                            int* __restrict__ flag_g) {
     int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nw) return;
     long long gb = work_gb[w];
-    flag[w] = (scell_start[gb * 64 + 64] > scell_start[gb * 64] || slot_gen[work[w]] > 0) ? 1 : 0;
+    const bool gen = slot_gen[work[w]] > 0;
+    flag[w] = (scell_start[gb * 64 + 64] > scell_start[gb * 64] || gen) ? 1 : 0;
+    flag_g[w] = gen ? 1 : 0;
 }
 
 __global__ void k_gen_list(int nw, const int* __restrict__ flag, const int* __restrict__ pos, int* __restrict__ list) {
@@ -2477,12 +2550,19 @@ ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int c
     a.sic = (const R*)d.sic;
     a.slot_gen = d.slot_gen;
     for (int q = 0; q < 45; ++q) a.sK.a[q] = (R*)d.sK[q];
-    a.use_sK = c->sK_valid ? 1 : 0;
+    a.sK0 = (const R*)d.sK[0];
+    a.sKs = c->Scap;
+    a.samples_in_cell = (c->sK_valid && mode == MPM_HESS_PROJECTED) ? 1 : 0;
     a.opk = (const R4<R>*)d.opk;
     a.wrows = d.wrows;
     a.wroff = d.wroff;
-    a.gen_list = d.gen_list;
-    a.gen_count = d.gen_pos + c->NW;
+    if (a.samples_in_cell) {
+        a.gen_list = d.gen_list_g;
+        a.gen_count = d.gen_pos_g + c->NW;
+    } else {
+        a.gen_list = d.gen_list;
+        a.gen_count = d.gen_pos + c->NW;
+    }
     a.err = d.err;
     a.mode = mode;
     a.check_done = check_done;
@@ -2594,9 +2674,11 @@ cudaError_t pack_step_t(mpm_ctx* c) {
     }
     if (c->NW > 0) {
         MPM_LAUNCH k_gen_flags<<<nblk(c->NW, 256), 256, 0, st>>>(c->NW, d.work, d.work_gb, d.scell_start, d.slot_gen,
-                                                               d.gen_flag);
+                                                               d.gen_flag, d.gen_flag_g);
         launch_exclusive_scan(c, d.gen_flag, d.gen_pos, c->NW, d.scan_tmp, st);
         MPM_LAUNCH k_gen_list<<<nblk(c->NW, 256), 256, 0, st>>>(c->NW, d.gen_flag, d.gen_pos, d.gen_list);
+        launch_exclusive_scan(c, d.gen_flag_g, d.gen_pos_g, c->NW, d.scan_tmp, st);
+        MPM_LAUNCH k_gen_list<<<nblk(c->NW, 256), 256, 0, st>>>(c->NW, d.gen_flag_g, d.gen_pos_g, d.gen_list_g);
     }
     return cudaGetLastError();
 }
