@@ -176,6 +176,21 @@ def sample_scene(sc, size=SAMPLE_CELLS):
     return scenes.window(sc, c, size, name=f"{sc.name}_window{size}")
 
 
+def job_rate(units, elapsed_ms, device=None):
+    """Whole-job throughput of replicas: the units all ranks processed divided by
+    the slowest rank's time. Returns (units / s, the slowest time in ms). Without an
+    initialised process group it is the local rate."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return units / (elapsed_ms * 1e-3), elapsed_ms
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    tdist.all_reduce(u, op=tdist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) * 1e-3), float(t.item())
+
+
 def bench_ours(args, rank, world):
     import torch
     from paper_2101_12408_gb300 import mpm
@@ -210,17 +225,14 @@ def bench_ours(args, rank, world):
     clk = clocks.stop()
     prof = ctx.profile()
     ctx.profile_enable(False)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    steps_per_s, elapsed_ms = job_rate(args.steps, elapsed_ms, dev)
     rsize = 4 if prec == mpm.PREC_FP32_FP64RED else 8
     abytes, counts = algorithmic_bytes(ctx, sc, rsize)
     apply_avg_ms = prof["apply_ms"] / max(prof["apply_launches"], 1)
     peak, peak_kind = measured_peak()
     achieved = abytes / (apply_avg_ms * 1e-3) / 1e9
     out = {
-        "steps_per_s": world * args.steps / (elapsed_ms * 1e-3),
+        "steps_per_s": steps_per_s,
         "ms_per_step": elapsed_ms / args.steps,
         "prof": prof,
         "stats": stats,
@@ -251,11 +263,11 @@ def bench_ours(args, rank, world):
                 setattr(cur, f, p[f])
             cur.s, cur.dA, cur.kind = srf["s"], srf["dA"], srf["kind"]
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        e2e_rate, _ = job_rate(args.e2e_steps, (time.perf_counter() - t0) * 1e3, dev)
         n, ns = ctx.np[0], ctx.ns[0]
         h2d = n * (3 + 3 + 9 + 1 + 1 + 1 + 9 + 1 + 3) * 8 + n + ns * (3 + 3 + 1 + 1) * 8 + ns
         d2h = n * (3 + 3 + 9 + 1 + 9 + 1 + 3) * 8 + n + ns * (3 + 3 + 1 + 3) * 8 + ns + ns * 4
-        out["e2e"] = {"value": world * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        out["e2e"] = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
     ctx.close()
     # all-float64 form on the same workload
@@ -353,6 +365,8 @@ def main():
         "hessian_applies_per_s": res["applies_per_s"],
         "fp64_form": res.get("fp64_form"),
         "phases_ms_per_step": {k: v / args.steps for k, v in prof["phase_ms"].items()},
+        "cg_launch": {"ctas_per_sm": prof["cg_ctas_per_sm"], "iters_per_check": prof["cg_chunk"],
+                      "cuda_graphs": bool(prof["cg_graphs"]), "graph_error": prof["cg_graph_error"]},
         "newton_iters": [s["newton_iters"] for s in res["stats"]],
         "cg_iters": [s["cg_iters"] for s in res["stats"]],
         "residual_rel": [s["residual"] / max(s["residual0"], 1e-300) for s in res["stats"]],

@@ -237,6 +237,13 @@ typedef struct {
     double heat_apply_ms;
     double phase_ms[5];           /* resample, p2g, heat solve, Newton solve, g2p */
     int64_t newton_iters, cg_iters, heat_iters;
+    /* CG launch configuration in use. The first six momentum solves of a context
+     * each try one (CTAs per SM of the CG vector kernel x CG iterations between
+     * host checks) and later solves keep the fastest per iteration. */
+    int32_t cg_ctas_per_sm;       /* 0 before the first solve */
+    int32_t cg_chunk;
+    int32_t cg_graphs;            /* 1: CG chunks run as CUDA graphs */
+    int32_t cg_graph_error;       /* cudaError_t of a refused capture, else 0 */
 } mpm_profile;
 
 /* enable != 0 resets the counters and starts accumulating; 0 stops. */

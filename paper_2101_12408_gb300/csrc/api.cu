@@ -368,6 +368,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
 #undef A_
 #undef R_
     for (int k = 0; k < 34 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->tune_ev[k]);
     if (e == cudaSuccess) e = cudaMallocHost(&c->hscal, sizeof(SceneScal) * n_scenes);
     if (e == cudaSuccess) e = cudaMallocHost(&c->herr, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->hcounts, sizeof(int) * 8);
@@ -390,6 +391,8 @@ mpm_status mpm_destroy(mpm_ctx* c) {
     if (c->d.opk) cudaFree(c->d.opk);
     for (int k = 0; k < 34; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    for (int k = 0; k < 2; ++k)
+        if (c->tune_ev[k]) cudaEventDestroy(c->tune_ev[k]);
     if (c->hscal) cudaFreeHost(c->hscal);
     if (c->herr) cudaFreeHost(c->herr);
     if (c->hcounts) cudaFreeHost(c->hcounts);
@@ -799,6 +802,10 @@ mpm_status mpm_get_profile(mpm_ctx* c, mpm_profile* out) {
     if (!c || !out) return MPM_ERR_INVALID_ARG;
     *out = c->pr;
     out->kernel_launches = c->pr.kernel_launches + c->launches;
+    out->cg_ctas_per_sm = c->cg_ctas_per_sm;
+    out->cg_chunk = c->cg_chunk;
+    out->cg_graphs = c->use_graphs ? 1 : 0;
+    out->cg_graph_error = c->graph_error;
     return MPM_OK;
 }
 

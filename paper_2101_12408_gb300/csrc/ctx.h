@@ -107,6 +107,14 @@ struct mpm_ctx {
     long long opk_cap = 0;          // capacity of d.opk in records (grown by the per-step pack)
     bool has_solids = false;        // solid-only buffers allocated
     bool sK_valid = false;          // d.sK holds the maps of the cached iterate
+    bool use_graphs = true;         // CG chunks as CUDA graphs (cleared if capture is refused)
+    int graph_error = 0;            // the refusal's error code
+    // CG launch configuration and its autotuner state
+    int cg_ctas_per_sm = 0;         // 0: as many as fit
+    int cg_chunk = 8;               // CG iterations per host check
+    int tune_next = 0, tune_best = -1;
+    double tune_best_ms = 0.0;
+    cudaEvent_t tune_ev[2] = {};
     int NB = 0, NW = 0;
     bool resampled = false, p2g_done = false, step_ready = false;
     mpm::Dev d{};

@@ -2685,8 +2685,9 @@ cudaError_t pack_step_t(mpm_ctx* c) {
 
 // one CG iteration's vector work: a cooperative launch of k_cg_iter over the
 // CTAs that fit on the device at once (grid-stride over the slots)
+// CTAs of k_cg_iter that fit on the device at once (queried once per type)
 template <typename R, int NC>
-cudaError_t launch_cg_iter(mpm_ctx* c, CGArgs<R, NC>& a, int heat) {
+cudaError_t cg_iter_capacity(int& grid, int per_sm_cap = 0) {
     static int per_sm[2][2] = {{-1, -1}, {-1, -1}};
     static int n_sm = 0;
     int& occ = per_sm[sizeof(R) == 4 ? 0 : 1][NC == 3 ? 0 : 1];
@@ -2698,16 +2699,36 @@ cudaError_t launch_cg_iter(mpm_ctx* c, CGArgs<R, NC>& a, int heat) {
         if (e != cudaSuccess) return e;
         if (occ < 1) return cudaErrorInvalidConfiguration;
     }
+    grid = (per_sm_cap > 0 && per_sm_cap < occ ? per_sm_cap : occ) * n_sm;
+    return cudaSuccess;
+}
+
+template <typename R, int NC>
+cudaError_t launch_cg_iter(mpm_ctx* c, CGArgs<R, NC>& a, int heat) {
+    int grid = 0;
+    cudaError_t e = cg_iter_capacity<R, NC>(grid, c->cg_ctas_per_sm);
+    if (e != cudaSuccess) return e;
     int nb = c->NB, ns = c->nsc;
     int chunks = nblk(nb, CG_SLOTS);
-    int grid = occ * n_sm;
     if (grid > chunks) grid = chunks;
     if (grid < 1) grid = 1;
     unsigned* bar = c->d.cg_bar;
     int* err = c->d.err;
     void* args[] = {(void*)&a, (void*)&nb, (void*)&ns, (void*)&heat, (void*)&bar, (void*)&err};
+    // a cooperative launch (all CTAs co-resident), expressed as a launch attribute
+    // so that it can also be captured into a CUDA graph
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(CG_NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c->st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     c->launches++;
-    return cudaLaunchCooperativeKernel((const void*)k_cg_iter<R, NC>, dim3(grid), dim3(CG_NT), args, 0, c->st);
+    return cudaLaunchKernelExC(&cfg, (const void*)k_cg_iter<R, NC>, args);
 }
 
 template <typename R>
@@ -2719,7 +2740,20 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     Dev& d = c->d;
     int maxit = 0;
     for (auto& S : c->hsc) maxit = maxit > S.max_cg ? maxit : S.max_cg;
-    const int chunk = 8;
+    // Autotuner: the first momentum solves of a context each try one launch
+    // configuration of the CG loop (CTAs per SM of the vector kernel, iterations per
+    // host check); later solves use the one with the least device time per
+    // iteration.
+    static const int kTune[][2] = {{3, 8}, {2, 8}, {1, 8}, {3, 16}, {2, 16}, {1, 16}};
+    constexpr int nTune = (int)(sizeof(kTune) / sizeof(kTune[0]));
+    const bool tuning = !NC_is_heat && c->tune_next < nTune;
+    if (!NC_is_heat) {
+        const int k = tuning ? c->tune_next : c->tune_best;
+        c->cg_ctas_per_sm = kTune[k][0];
+        c->cg_chunk = kTune[k][1];
+    }
+    const int chunk = NC_is_heat ? 8 : c->cg_chunk;
+    if (tuning) cudaEventRecord(c->tune_ev[0], st);
     cudaError_t e0 = cudaMemsetAsync(d.cg_bar, 0, 2 * sizeof(unsigned), st);
     if (e0 != cudaSuccess) return e0;
     if (NC_is_heat) {
@@ -2745,22 +2779,93 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
         auto a = make_cg_args<R, 3>(c);
         auto ap = make_apply_args<R>(c, d.cp, d.cu, MPM_HESS_PROJECTED, 1);
         MPM_LAUNCH k_cg_init<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init);
-        for (int it = 0; it < maxit; it += chunk) {
+        // one chunk of CG iterations: operator apply, then the cooperative vector kernel
+        auto enqueue_chunk = [&]() -> cudaError_t {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
                 if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
                 if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<nblk(c->NW, GEN_B), NT_GEN, 0, st>>>(ap);
                 prof_mark_apply(c, false);
-                e0 = launch_cg_iter<R, 3>(c, a, 0);
+                cudaError_t e = launch_cg_iter<R, 3>(c, a, 0);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        };
+        // The chunk is captured once per solve as a CUDA graph (the operands and
+        // grid sizes are fixed for the solve) and replayed until every scene's CG
+        // is done; the host reads the per-scene flags between chunks. Without graph
+        // support (capture refused) the chunk is launched directly.
+        cudaGraphExec_t gexec = nullptr;
+        long long per_chunk = 0;
+        int nev_chunk = 0;
+        if (c->use_graphs) {
+            int grid = 0;
+            e0 = cg_iter_capacity<R, 3>(grid);   // occupancy query outside the capture
+            if (e0 != cudaSuccess) return e0;
+            const long long l0 = c->launches;
+            const int nev0 = c->nev;
+            cudaGraph_t graph = nullptr;
+            cudaError_t ec = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (ec == cudaSuccess) {
+                cudaError_t eq = enqueue_chunk();
+                ec = cudaStreamEndCapture(st, &graph);
+                if (eq != cudaSuccess) ec = eq;
+            }
+            if (ec == cudaSuccess) ec = cudaGraphInstantiate(&gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) {
+                cudaGetLastError();
+                c->graph_error = (int)ec;
+                if (gexec) cudaGraphExecDestroy(gexec);
+                gexec = nullptr;
+                c->use_graphs = false;
+                c->nev = nev0;
+            } else {
+                per_chunk = c->launches - l0;
+                nev_chunk = c->nev - nev0;
+                c->launches = l0;
+            }
+        }
+        for (int it = 0; it < maxit; it += chunk) {
+            if (gexec) {
+                cudaError_t e = cudaGraphLaunch(gexec, st);
+                if (e != cudaSuccess) {
+                    cudaGraphExecDestroy(gexec);
+                    return e;
+                }
+                c->launches += per_chunk;
+                if (c->prof) c->nev = nev_chunk;   // the graph recorded the chunk's event pairs
+            } else {
+                e0 = enqueue_chunk();
                 if (e0 != cudaSuccess) return e0;
             }
             cudaMemcpyAsync(c->hscal, d.scal, sizeof(SceneScal) * ns, cudaMemcpyDeviceToHost, st);
             cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return e;
+            if (e != cudaSuccess) {
+                if (gexec) cudaGraphExecDestroy(gexec);
+                return e;
+            }
             prof_collect_applies(c, NC_is_heat != 0);
             bool all = true;
             for (int s = 0; s < ns; ++s) all = all && c->hscal[s].cg_done;
             if (all) break;
+        }
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (tuning) {
+            cudaEventRecord(c->tune_ev[1], st);
+            float ms = 0.f;
+            int its = 0;
+            for (int s = 0; s < ns; ++s) its = its > c->hscal[s].cg_it ? its : c->hscal[s].cg_it;
+            if (cudaEventSynchronize(c->tune_ev[1]) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]) == cudaSuccess && its > 0) {
+                const double per_it = ms / its;
+                if (c->tune_best < 0 || per_it < c->tune_best_ms) {
+                    c->tune_best = c->tune_next;
+                    c->tune_best_ms = per_it;
+                }
+            }
+            c->tune_next++;
+            if (c->tune_next == nTune && c->tune_best < 0) c->tune_best = 0;
         }
     }
     return cudaGetLastError();
