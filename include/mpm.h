@@ -26,7 +26,7 @@
  *     stays inside the grid); violations are reported as MPM_ERR_DOMAIN.
  *   - Errors: every entry point returns an mpm_status; mpm_last_error() gives a
  *     one-line reason. Device-side failures (a particle leaving the grid, a surface
- *     sample with no particle within dx, a non-finite value) are recorded in a
+ *     sample with no particle within 2 dx, a non-finite value) are recorded in a
  *     device status word and reported by the next call that synchronises.
  *   - Thread safety: one context per host thread; calls on a context are ordered
  *     on its stream.
@@ -164,6 +164,30 @@ mpm_status mpm_set_surface(mpm_ctx* ctx, int32_t scene, int64_t n, const double*
  * mpm_set_particles order) and the balance position b_r. NULL pointers skipped. */
 mpm_status mpm_get_surface(mpm_ctx* ctx, int32_t scene, int64_t n, double* s, double* dA,
                            uint8_t* kind, double* gamma, int32_t* parent, double* bpos);
+
+/* Surface samples generated from the particles (section "Surface Particle
+ * Sampling"), replacing every scene's samples; call it before mpm_resample.
+ *
+ * The level set is the union of spheres of radius 0.867 dx around the interior
+ * particles, sampled on the grid nodes (cell centres) as
+ * phi = min(distance to the nearest particle, 1.5 dx) - 0.867 dx. Its zero
+ * isocontour is triangulated by marching tetrahedra: each cube of 8 nodes is cut
+ * into the 6 tetrahedra around its 000-111 diagonal, inside is phi < 0, edge
+ * points by linear interpolation, triangles facing outward. Each triangle draws
+ * a Poisson count with mean density * area (density = per_cell_area / dx^2,
+ * capped at 31) and places that many points uniformly (Osada's construction);
+ * every sample carries dA = unit normal / density, so sum |dA| estimates the
+ * area without bias. Random numbers come from SplitMix64 seeded with
+ * seed ^ (scene * 0x9E3779B97F4A7C15), counter ((6 q + e) 2 + t) 64 + j for
+ * triangle t of tetrahedron e of the cube with block-major corner key q, draw j.
+ * Kind: solid-liquid where the plane's signed distance is below dx; heating
+ * rate b = 0 and ambient temperature T0 on every sample.
+ *
+ * counts: host array of n_scenes entries receiving each scene's sample count
+ * (may be NULL). A scene whose count exceeds its max_surface: MPM_ERR_CAPACITY,
+ * samples unchanged. Samples come out in the deterministic enumeration order
+ * (cube key, tetrahedron, triangle, draw), which is their set order. */
+mpm_status mpm_generate_surface(mpm_ctx* ctx, uint64_t seed, double per_cell_area, int64_t* counts);
 
 /* (1) Resample: sort by cell, closest interior particle p(r) of each sample
  * (smallest squared distance, ties to the smaller particle index), balance

@@ -35,6 +35,7 @@ from .heat import HeatSystem
 from .resample import split
 from .solver import newton_solve, heat_solve
 from .spline import Stencil
+from .surface import generate
 from .transfer import p2g, g2p, grid_velocity
 
 
@@ -68,6 +69,16 @@ class OracleSim:
         sc = self.sc
         self.P = projector(sc.n, sc.dx, sc.walls, sc.plane_n, sc.plane_d, sc.plane_mode)
         self.G = int(np.prod(sc.n))
+
+    # (0) surface samples generated on the particles' union-of-spheres surface
+    def generate_surface(self, seed, per_cell_area=2.0):
+        sc = self.sc
+        plane = (sc.plane_n, sc.plane_d) if sc.plane_mode else None
+        s, dA, kind, _ = generate(sc.x, sc.n, sc.dx, seed, per_cell_area, plane)
+        sc.s, sc.dA, sc.kind = s, dA, kind
+        sc.b = np.zeros(s.shape[0])
+        sc.Tbar = np.full(s.shape[0], self.prm.T0)
+        return s.shape[0]
 
     # (1) resample
     def resample(self):

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpm_gb300.so")
-SOURCES = ["api.cu", "sort.cu", "transfer.cu", "newton.cu", "heat.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "sort.cu", "transfer.cu", "newton.cu", "heat.cu", "surfgen.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

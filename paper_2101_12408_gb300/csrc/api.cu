@@ -195,7 +195,7 @@ mpm_status check_device_error(mpm_ctx* c) {
         cudaMemsetAsync(c->d.err, 0, sizeof(int), c->st);
         cudaStreamSynchronize(c->st);
         if (err & ERR_DOMAIN) return fail(c, MPM_ERR_DOMAIN, "a particle or surface sample lies outside cells 1..n-2");
-        if (err & ERR_FAR_SURFACE) return fail(c, MPM_ERR_DOMAIN, "a surface sample has no interior particle within dx");
+        if (err & ERR_FAR_SURFACE) return fail(c, MPM_ERR_DOMAIN, "a surface sample has no interior particle within 2 dx");
         if (err & ERR_NUMERIC) return fail(c, MPM_ERR_NUMERIC, "non-finite value on the device");
         if (err & ERR_CAPACITY) return fail(c, MPM_ERR_CAPACITY, "more active grid blocks than max_blocks");
         if (err & ERR_TIMEOUT) return fail(c, MPM_ERR_TIMEOUT, "a bounded device wait ran out");
@@ -365,6 +365,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     size_t stg = staging_doubles(c);
     A_(*(double**)&d.dense_a, double, stg); A_(*(double**)&d.dense_b, double, stg);
     A_(d.sc, SceneDev, n_scenes); A_(d.scal, SceneScal, n_scenes); A_(d.err, int, 1); A_(d.cg_bar, unsigned, 2);
+    A_(d.scene_cnt, unsigned long long, n_scenes); A_(d.scene_first, long long, n_scenes);
 #undef A_
 #undef R_
     for (int k = 0; k < 34 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
@@ -389,6 +390,7 @@ mpm_status mpm_destroy(mpm_ctx* c) {
     if (c->st) cudaStreamSynchronize(c->st); else cudaDeviceSynchronize();
     for (void* p : c->allocs) cudaFree(p);
     if (c->d.opk) cudaFree(c->d.opk);
+    if (c->tri_buf) cudaFree(c->tri_buf);
     for (int k = 0; k < 34; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     for (int k = 0; k < 2; ++k)
@@ -570,6 +572,27 @@ mpm_status mpm_get_surface(mpm_ctx* c, int32_t scene, int64_t n, double* s, doub
         MPM_CUDA(cudaStreamSynchronize(st));
     }
     return check_device_error(c);
+}
+
+mpm_status mpm_generate_surface(mpm_ctx* c, uint64_t seed, double per_cell_area, int64_t* counts) {
+    if (!c) return MPM_ERR_INVALID_ARG;
+    if (!(per_cell_area > 0.0) || !std::isfinite(per_cell_area))
+        return fail(c, MPM_ERR_INVALID_ARG, "mpm_generate_surface: per_cell_area must be positive");
+    if (c->hscene_cnt.size() != (size_t)c->nsc) {
+        c->hscene_cnt.assign(c->nsc, 0ull);
+        c->hscene_first.assign(c->nsc, 0ll);
+    }
+    std::vector<long long> cnt(c->nsc, 0);
+    int cap_err = 0;
+    PhaseTimer timer(c, 0);
+    MPM_CUDA(launch_generate_surface(c, (unsigned long long)seed, per_cell_area, cnt.data(), &cap_err));
+    MPM_CUDA(cudaStreamSynchronize(c->st));
+    mpm_status s = check_device_error(c);
+    if (s != MPM_OK) return s;
+    if (cap_err) return fail(c, MPM_ERR_CAPACITY, "mpm_generate_surface: more samples than max_surface");
+    if (counts)
+        for (int k = 0; k < c->nsc; ++k) counts[k] = cnt[k];
+    return MPM_OK;
 }
 
 mpm_status mpm_resample(mpm_ctx* c) {

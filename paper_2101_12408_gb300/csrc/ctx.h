@@ -91,6 +91,8 @@ struct Dev {
     SceneScal* scal;
     int* err;
     unsigned* cg_bar;               // grid barrier of the cooperative CG kernel (2 words)
+    unsigned long long* scene_cnt;  // per scene: generated surface samples
+    long long* scene_first;         // per scene: first generated sample
 };
 
 }  // namespace mpm
@@ -115,6 +117,11 @@ struct mpm_ctx {
     int tune_next = 0, tune_best = -1;
     double tune_best_ms = 0.0;
     cudaEvent_t tune_ev[2] = {};
+    // surface generation: triangle records (grown on demand), per-scene counts
+    void* tri_buf = nullptr;
+    size_t tri_bytes = 0;
+    std::vector<unsigned long long> hscene_cnt;
+    std::vector<long long> hscene_first;
     int NB = 0, NW = 0;
     bool resampled = false, p2g_done = false, step_ready = false;
     mpm::Dev d{};
@@ -156,6 +163,13 @@ cudaError_t launch_dense_to_grid(mpm_ctx* c, int scene, const void* dense, void*
 cudaError_t launch_grid_to_dense(mpm_ctx* c, int scene, const void* grid, void* dense, int comps, int rsize_in, int rsize_out);
 cudaError_t launch_project_vec(mpm_ctx* c, void* vec, int rsize);
 cudaError_t launch_mass_term(mpm_ctx* c, const void* p, void* u);
+
+// ---- surfgen.cu ----
+// Replaces every scene's surface samples with ones generated on the particles'
+// union-of-spheres surface; counts[s] receives scene s's count. A count above a
+// scene's max_surface sets *capacity_error and leaves the samples unchanged.
+cudaError_t launch_generate_surface(mpm_ctx* c, unsigned long long seed, double per_cell_area, long long* counts,
+                                    int* capacity_error);
 
 // ---- heat.cu ----
 cudaError_t run_heat(mpm_ctx* c);

@@ -48,25 +48,34 @@ __global__ void k_nearest(int ns, P3 s, const int* __restrict__ ssc, P3 x, const
     }
     double best = 1e300;
     int bi = -1, bid = 0x7fffffff;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dxx = -1; dxx <= 1; ++dxx) {
-                long long k = cell_key(S, c[0] + dxx, c[1] + dy, c[2] + dz);
-                int e = cell_start[k + 1];
-                for (int i = cell_start[k]; i < e; ++i) {
-                    double d0 = __dsub_rn(q[0], x.a[0][i]);
-                    double d1 = __dsub_rn(q[1], x.a[1][i]);
-                    double d2 = __dsub_rn(q[2], x.a[2][i]);
-                    double dist = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-                    int id = pid[i];
-                    if (dist < best || (dist == best && id < bid)) {
-                        best = dist;
-                        bi = i;
-                        bid = id;
+    // the 27 cells around the sample hold every particle within dx; when the
+    // nearest is farther (samples generated on the union-of-spheres surface reach
+    // ~1.1 dx), the 125 cells around it hold every particle within 2 dx
+    for (int reach = 1; reach <= 2; ++reach) {
+        if (reach == 2 && best <= S.dx * S.dx) break;
+        for (int dz = -reach; dz <= reach; ++dz)
+            for (int dy = -reach; dy <= reach; ++dy)
+                for (int dxx = -reach; dxx <= reach; ++dxx) {
+                    if (reach == 2 && dz > -2 && dz < 2 && dy > -2 && dy < 2 && dxx > -2 && dxx < 2) continue;
+                    const int cx = c[0] + dxx, cy = c[1] + dy, cz = c[2] + dz;
+                    if (cx < 0 || cy < 0 || cz < 0 || cx >= S.n[0] || cy >= S.n[1] || cz >= S.n[2]) continue;
+                    long long k = cell_key(S, cx, cy, cz);
+                    int e = cell_start[k + 1];
+                    for (int i = cell_start[k]; i < e; ++i) {
+                        double d0 = __dsub_rn(q[0], x.a[0][i]);
+                        double d1 = __dsub_rn(q[1], x.a[1][i]);
+                        double d2 = __dsub_rn(q[2], x.a[2][i]);
+                        double dist = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+                        int id = pid[i];
+                        if (dist < best || (dist == best && id < bid)) {
+                            best = dist;
+                            bi = i;
+                            bid = id;
+                        }
                     }
                 }
-            }
-    if (bi < 0 || best > S.dx * S.dx) {
+    }
+    if (bi < 0 || best > 4.0 * S.dx * S.dx) {
         atomicOr(err, ERR_FAR_SURFACE);
         parent[j] = -1;
         for (int a = 0; a < 3; ++a) bpos.a[a][j] = q[a];

@@ -32,7 +32,8 @@ FIELD_COMPS = {FIELD_MASS: 1, FIELD_MOMENTUM: 3, FIELD_VN: 3, FIELD_THERMAL_MASS
 EXPORTED = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_particles", "mpm_get_particles",
             "mpm_set_surface", "mpm_get_surface", "mpm_resample", "mpm_p2g", "mpm_get_grid", "mpm_set_velocity",
             "mpm_energy_gradient", "mpm_apply_hessian", "mpm_heat_apply", "mpm_newton_step", "mpm_g2p", "mpm_step",
-            "mpm_sync", "mpm_counts", "mpm_profile_enable", "mpm_get_profile", "mpm_nearest_parent_noalloc"]
+            "mpm_sync", "mpm_counts", "mpm_profile_enable", "mpm_get_profile", "mpm_nearest_parent_noalloc",
+            "mpm_generate_surface"]
 
 
 class GridDesc(ctypes.Structure):
@@ -94,6 +95,7 @@ _lib.mpm_get_particles.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64] + [_vp] 
 _lib.mpm_set_surface.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64] + [_vp] * 5
 _lib.mpm_get_surface.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64] + [_vp] * 6
 _lib.mpm_resample.argtypes = [_vp]
+_lib.mpm_generate_surface.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _vp]
 _lib.mpm_p2g.argtypes = [_vp]
 _lib.mpm_get_grid.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp]
 _lib.mpm_set_velocity.argtypes = [_vp, ctypes.c_int32, _vp]
@@ -184,7 +186,10 @@ def scene_desc(sc, max_particles=None, max_surface=None, max_blocks=0):
 class Context:
     """One library context holding one or more scenes."""
 
-    def __init__(self, scene_list, precision=PREC_FP32_FP64RED, stream=None, capacity_factor=1.0, max_blocks=0):
+    def __init__(self, scene_list, precision=PREC_FP32_FP64RED, stream=None, capacity_factor=1.0, max_blocks=0,
+                 surface_capacity_factor=None):
+        # generated surfaces (generate_surface) need room beyond the initial samples
+        sfac = capacity_factor if surface_capacity_factor is None else surface_capacity_factor
         if isinstance(scene_list, _scenes.Scene):
             scene_list = [scene_list]
         self.scenes = list(scene_list)
@@ -192,7 +197,7 @@ class Context:
         self.rdtype = np.float64 if precision == PREC_FP64 else np.float32
         descs = (SceneDesc * len(self.scenes))()
         for k, sc in enumerate(self.scenes):
-            descs[k] = scene_desc(sc, int(sc.n_particles * capacity_factor) + 1, int(sc.n_surface * capacity_factor) + 1,
+            descs[k] = scene_desc(sc, int(sc.n_particles * capacity_factor) + 1, int(sc.n_surface * sfac) + 1,
                                   max_blocks)
         h = _vp()
         st = stream
@@ -265,6 +270,15 @@ class Context:
         return out
 
     # ---- phases ----
+    def generate_surface(self, seed, per_cell_area=2.0):
+        """Replaces every scene's surface samples with ones generated on the
+        particles' union-of-spheres surface; returns the per-scene counts."""
+        cnt = np.zeros(len(self.scenes), np.int64)
+        self._check(_lib.mpm_generate_surface(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF, float(per_cell_area), _ptr(cnt)))
+        for k in range(len(self.scenes)):
+            self.ns[k] = int(cnt[k])
+        return cnt
+
     def resample(self):
         self._check(_lib.mpm_resample(self.h))
 
