@@ -50,10 +50,10 @@ METRIC = "implicit steps/sec (float32 operator + float64 reductions)"
 UNIT = "steps/s"
 # ncu DRAM traffic (read + write bytes) of one Hessian-operator apply at the
 # full workload, from the 20-droplet capture in
-# profiles/apply_cg_kernels_incline20_fp32.md scaled by the units each kernel
-# processes: k_apply_cell (149.2 MB) x 8272476 / 5128948 particles plus
-# k_apply_general (58.3 MB) x 317603 / 185006 samples
-NCU_TRAFFIC_BYTES = 340817654
+# profiles/apply_cg_kernels_incline20_fp32.md scaled by the units processed:
+# k_apply_cell (188.6 MB, particles and samples) x 8272476 / 5128948 particles
+# plus k_apply_general (0.07 MB) x 317603 / 185006 samples
+NCU_TRAFFIC_BYTES = 304312853
 
 
 def make_workload(name, drops=40):
@@ -200,7 +200,8 @@ def bench_ours(args, rank, world):
     sc = make_workload(args.workload, args.drops)
     stream = torch.cuda.current_stream()
     prec = mpm.PREC_FP32_FP64RED if args.precision == "fp32" else mpm.PREC_FP64
-    ctx = mpm.Context(sc, precision=prec, stream=stream.cuda_stream, max_blocks=args.max_blocks)
+    ctx = mpm.Context(sc, precision=prec, stream=stream.cuda_stream, max_blocks=args.max_blocks,
+                      surface_capacity_factor=2.0)
     ctx.load_scene(0)
     for _ in range(args.warmup):
         ctx.step()
@@ -269,6 +270,19 @@ def bench_ours(args, rank, world):
         d2h = n * (3 + 3 + 9 + 1 + 9 + 1 + 3) * 8 + n + ns * (3 + 3 + 1 + 3) * 8 + ns + ns * 4
         out["e2e"] = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
+    # surface regeneration (mpm_generate_surface), timed once on the final state,
+    # outside the timed steps (the timed steps carry their samples)
+    if args.surface_gen:
+        ctx.generate_surface(1)   # warm-up (grows the triangle buffer)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        cnt = ctx.generate_surface(2)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        out["surface_generation"] = {"ms": g0.elapsed_time(g1), "samples": int(cnt[0]),
+                                     "carried_samples": int(sc.n_surface)}
     ctx.close()
     # all-float64 form on the same workload
     if args.fp64_steps > 0 and prec == mpm.PREC_FP32_FP64RED:
@@ -305,6 +319,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--surface-gen", type=int, default=1, help="time one surface regeneration (0: skip)")
     ap.add_argument("--drops", type=int, default=40, help="droplets in the incline workload")
     ap.add_argument("--max-blocks", type=int, default=0, help="grid block capacity (0: whole grid)")
     args = ap.parse_args()
@@ -365,6 +380,7 @@ def main():
         "hessian_applies_per_s": res["applies_per_s"],
         "fp64_form": res.get("fp64_form"),
         "phases_ms_per_step": {k: v / args.steps for k, v in prof["phase_ms"].items()},
+        "surface_generation": res.get("surface_generation"),
         "cg_launch": {"ctas_per_sm": prof["cg_ctas_per_sm"], "iters_per_check": prof["cg_chunk"],
                       "cuda_graphs": bool(prof["cg_graphs"]), "graph_error": prof["cg_graph_error"]},
         "newton_iters": [s["newton_iters"] for s in res["stats"]],
