@@ -245,10 +245,19 @@ __global__ void k_cube_emit(long long ncube, const int* __restrict__ list, CubeC
     for (int e = 0; e < 6; ++e) {
         double T[18];
         const int nt = tet_tris(*S, q, e, cphi, T);
-        for (int tt = 0; tt < nt; ++tt, ++o) {
-            for (int a = 0; a < 9; ++a) tv[o * 9 + a] = T[9 * tt + a];
-            tkey[o] = (6 * key + e) * 2 + tt;
+        if (nt > 0) {   // constant indices keep T out of local memory
+#pragma unroll
+            for (int a = 0; a < 9; ++a) tv[o * 9 + a] = T[a];
+            tkey[o] = (6 * key + e) * 2;
             tscene[o] = scene;
+            ++o;
+        }
+        if (nt > 1) {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) tv[o * 9 + a] = T[9 + a];
+            tkey[o] = (6 * key + e) * 2 + 1;
+            tscene[o] = scene;
+            ++o;
         }
     }
 }
