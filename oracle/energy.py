@@ -24,7 +24,9 @@ Hessian-vector products (the linearisation the paper defers to earlier work):
   kinetic   m_i dv_i
   liquid    dt^2 lambda (J^n)^2 V^0 gradN_i (sum_j gradN_j . dv_j)     (rank one, PSD)
   viscous   dt mu V^n sym(dL) gradN_i                                  (PSD)
-  solid     dt^2 V^0 dP(F; dL F^n) F^nT gradN_i                         (exact)
+  solid     dt^2 V^0 dP(F; dL F^n) F^nT gradN_i                         EXACT
+            the same with dP = H+ : dF, H+ the particle's 9x9 Hessian
+            d^2 psi / dF^2 with its negative eigenvalues set to zero         PROJECTED
   surface   dt^2 dG gradN_i(s_r) with, for c = cof(F^) a, n = c/|c|, C = dc/dF^,
             dc = C : dF, dn = (I - n n^T) dc / |c|,
             dG_gd = k (dn_a C_agd + n_a dC_agd)         EXACT
@@ -38,6 +40,11 @@ Hessian-vector products (the linearisation the paper defers to earlier work):
   projected Hessian keeps the Gauss-Newton term and the positive (conformal)
   part Q+, so it stays PSD and keeps the surface's stiffness against in-plane
   dilation (dropping the whole curvature term loses it and stalls Newton).
+  For solids the paper's "definiteness fix" is read as the usual per-particle
+  projection: eigen-decompose the particle's symmetric 9x9 Hessian of psi(F)
+  (formed here by applying the exact dP to the nine unit directions) and clamp
+  its negative eigenvalues to zero. Where psi is convex at F (e.g. near rest)
+  PROJECTED equals EXACT.
 """
 import numpy as np
 
@@ -164,6 +171,20 @@ class NewtonState:
             out += scatter(G, self.ss.node, dt * np.einsum("rgd,rqd->rqg", Gs, self.ss.dN))
         return out
 
+    @staticmethod
+    def solid_hessian_psd(F, mu, lam):
+        """Per particle: d^2 psi / dF^2 as a 9x9 matrix (row-major dF), with its
+        negative eigenvalues set to zero."""
+        n = F.shape[0]
+        H = np.zeros((n, 9, 9))
+        for l in range(9):
+            E = np.zeros((n, 9))
+            E[:, l] = 1.0
+            H[:, :, l] = fcr_dP(F, E.reshape(n, 3, 3), mu, lam).reshape(n, 9)
+        H = 0.5 * (H + np.swapaxes(H, 1, 2))
+        w, Q = np.linalg.eigh(H)
+        return np.einsum("pak,pk,pbk->pab", Q, np.maximum(w, 0.0), Q)
+
     def hessvec(self, v, dv, mode=HESS_PROJECTED):
         """(d^2 Phi / dv^2) dv on every node (G, 3)."""
         dt = self.dt
@@ -181,7 +202,11 @@ class NewtonState:
         if np.any(sol):
             dF = np.einsum("pab,pbc->pac", dL[sol], self.Fn[sol])
             dP = np.zeros((st.count, 3, 3))
-            dP[sol] = fcr_dP(F[sol], dF, self.mu_h[sol], self.lam_h[sol])
+            if mode == HESS_EXACT:
+                dP[sol] = fcr_dP(F[sol], dF, self.mu_h[sol], self.lam_h[sol])
+            else:
+                Hp = self.solid_hessian_psd(F[sol], self.mu_h[sol], self.lam_h[sol])
+                dP[sol] = np.einsum("pab,pb->pa", Hp, dF.reshape(-1, 9)).reshape(-1, 3, 3)
             M = M + (dt * dt * self.V0)[:, None, None] * np.einsum("pab,pcb->pac", dP, self.Fn)
         out += scatter(G, st.node, np.einsum("pab,pqb->pqa", M, st.dN))
         if self.ss.count:

@@ -432,3 +432,93 @@ def test_implicit_step_conserves_linear_momentum():
     sim.step()
     s = sim.sc
     np.testing.assert_allclose(np.sum(s.m[:, None] * s.v, 0), m0, atol=1e-10 * np.abs(m0).max())
+
+
+def _analytic_fcr_hessian(F, mu, lam):
+    """The 9x9 Hessian of the fixed-corotated energy from the analytic eigensystem of
+    isotropic energies: with the signed SVD F = U diag(s) V^T, each pair (x, y)
+    (third index z) has eigenvalue (psi_x - psi_y) / (s_x - s_y) on U sym(e_x e_y) V^T
+    and (psi_x + psi_y) / (s_x + s_y) on U skew(e_x e_y) V^T, and the scaling modes
+    U diag(q) V^T carry the eigen-pairs of d^2 psi / ds^2."""
+    U, s, Vt = np.linalg.svd(F)
+    s = s.copy()
+    if np.linalg.det(U) < 0:
+        U[:, 2] *= -1
+        s[2] *= -1
+    if np.linalg.det(Vt) < 0:
+        Vt[2, :] *= -1
+        s[2] *= -1
+    J = s.prod()
+    modes = []
+    Hs = np.zeros((3, 3))
+    for i in range(3):
+        for j in range(3):
+            pi = np.prod([s[a] for a in range(3) if a != i])
+            pj = np.prod([s[a] for a in range(3) if a != j])
+            Hs[i, j] = (2 * mu if i == j else 0.0) + lam * pi * pj + (lam * (J - 1) * s[3 - i - j] if i != j else 0.0)
+    w, q = np.linalg.eigh(Hs)
+    for t in range(3):
+        modes.append((w[t], U @ np.diag(q[:, t]) @ Vt))
+    for x, y in ((0, 1), (0, 2), (1, 2)):
+        z = 3 - x - y
+        L = np.zeros((3, 3))
+        L[x, y] = L[y, x] = 1 / math.sqrt(2)
+        T = np.zeros((3, 3))
+        T[x, y], T[y, x] = 1 / math.sqrt(2), -1 / math.sqrt(2)
+        modes.append((2 * mu - lam * (J - 1) * s[z], U @ L @ Vt))
+        modes.append((2 * mu - 4 * mu / (s[x] + s[y]) + lam * (J - 1) * s[z], U @ T @ Vt))
+    return sum(lv * np.outer(Q.ravel(), Q.ravel()) for lv, Q in modes), modes
+
+
+def test_solid_hessian_matches_analytic_eigensystem_and_projection_is_psd():
+    from oracle.energy import NewtonState
+    rng = np.random.default_rng(11)
+    F = np.eye(3) + 0.45 * rng.standard_normal((6, 3, 3))
+    F[0] = np.eye(3)
+    F[1] = np.diag([0.5, 0.8, 1.4])                       # compressed: indefinite twist modes
+    F[2] = np.diag([1.0, 1.0, -0.3])                      # inverted
+    mu = np.full(6, 2.0)
+    lam = np.full(6, 5.0)
+    Hp = NewtonState.solid_hessian_psd(F, mu, lam)
+    for p in range(6):
+        H = np.zeros((9, 9))
+        for l in range(9):
+            E = np.zeros((1, 3, 3))
+            E.reshape(9)[l] = 1.0
+            H[:, l] = oracle.constitutive.fcr_dP(F[p:p + 1], E, mu[p:p + 1], lam[p:p + 1]).reshape(9)
+        Ha, modes = _analytic_fcr_hessian(F[p], 2.0, 5.0)
+        # the exact dP, applied to the nine unit directions, is the analytic Hessian
+        np.testing.assert_allclose(H, Ha, atol=1e-12 * np.abs(Ha).max())
+        # the projection clamps exactly the negative analytic eigenvalues
+        Hplus = sum(max(lv, 0.0) * np.outer(Q.ravel(), Q.ravel()) for lv, Q in modes)
+        np.testing.assert_allclose(Hp[p], Hplus, atol=1e-12 * np.abs(Ha).max())
+        assert np.linalg.eigvalsh(Hp[p]).min() >= -1e-12 * np.abs(Ha).max()
+    # at rest psi is convex: projected = exact
+    assert min(lv for lv, _ in _analytic_fcr_hessian(F[0], 2.0, 5.0)[1]) >= -1e-14
+    # the compressed state has negative (twist) eigenvalues, which the projection removes
+    assert min(lv for lv, _ in _analytic_fcr_hessian(F[1], 2.0, 5.0)[1]) < 0.0
+
+
+def test_projected_operator_psd_with_deformed_solids():
+    sc = _mixed_scene()
+    rng = np.random.default_rng(7)
+    sol = sc.phase == scenes.PHASE_SOLID
+    sc.F[sol] = np.diag([0.55, 0.8, 1.3]) + 0.1 * rng.standard_normal((sol.sum(), 3, 3))
+    sc.params.E0 = 3000.0
+    sc.params.gamma_lg = 0.0
+    sim, st = _state(sc)
+    v = st.vn * st.active[:, None]
+    idx = np.flatnonzero(st.active)
+    ncol = idx.size * 3
+    ev = {}
+    for mode in (HESS_EXACT, HESS_PROJECTED):
+        H = np.zeros((ncol, ncol))
+        for c in range(ncol):
+            e = np.zeros((st.G, 3))
+            e[idx[c // 3], c % 3] = 1.0
+            H[:, c] = st.hessvec(v, e, mode)[idx].ravel()
+        np.testing.assert_allclose(H, H.T, atol=1e-10 * np.abs(H).max())
+        ev[mode] = np.linalg.eigvalsh(0.5 * (H + H.T))
+    mmin = st.m[idx].min()
+    assert ev[HESS_EXACT].min() < mmin                     # the exact operator is indefinite here
+    assert ev[HESS_PROJECTED].min() >= mmin - 1e-10 * np.abs(ev[HESS_PROJECTED]).max()
