@@ -133,8 +133,8 @@ class ClockSampler:
 def algorithmic_bytes(ctx, sc, rsize):
     """Bytes one Hessian-operator launch (projected form, as CG applies it) must
     move: the packed record of a liquid particle (position in its block and
-    kappa, 4 values); a solid particle (position, F^n, Lame pair and the
-    iterate's F, R, (tr S I - S)^-1); a surface sample (position in its block and
+    kappa, 4 values); a solid particle (position in its block and the iterate's
+    symmetric 9x9 projected-Hessian map, 3 + 45 values); a surface sample (position in its block and
     the iterate's symmetric 9x9 Hessian map, 3 + 45 values); an active node (the
     direction read and the product written, 3 components each)."""
     p = ctx.get_particles(0)
@@ -142,7 +142,7 @@ def algorithmic_bytes(ctx, sc, rsize):
     nliq = ctx.np[0] - nsol
     m = ctx.get_grid(0, 0)
     g_active = int(np.sum(m > 0))
-    b = rsize * (nliq * 4 + nsol * (3 + 9 + 2 + 24) + ctx.ns[0] * (3 + 45) + g_active * 6)
+    b = rsize * (nliq * 4 + nsol * (3 + 45) + ctx.ns[0] * (3 + 45) + g_active * 6)
     return b, dict(liquid=nliq, solid=nsol, surface=ctx.ns[0], active_nodes=g_active)
 
 

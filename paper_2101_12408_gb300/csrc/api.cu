@@ -333,6 +333,8 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     }
     for (int q = 0; q < 12; ++q) A_(d.acc[q], double, P);
     for (int q = 0; q < 24; ++q) R_(d.scache[q], PS);
+    R_(d.pK[0], 45 * PS);   // one allocation, the 45 entries PS apart
+    for (int q = 1; q < 45; ++q) d.pK[q] = (char*)d.pK[0] + (size_t)q * PS * c->rsize;
     A_(d.m, double, P); A_(d.V0, double, P); A_(d.J, double, P); A_(d.T, double, P);
     A_(d.phase, uint8_t, P);
     A_(d.pid, int, P); A_(d.psc, int, P);

@@ -52,6 +52,7 @@ struct Dev {
     void* sic;                      // 1/|c| (R)
     void* swn;                      // Robin normaliser 1/sum_j N_j [m^T_j > 0] (R)
     void* sK[45];                   // per-iterate symmetric 9x9 projected-Hessian map of a sample (R)
+    void* pK[45];                   // the same for a solid particle (R, solid buffers only)
     // ---- sort / blocks ----
     long long* key;                 // interior cell keys
     int* rank;
@@ -109,6 +110,7 @@ struct mpm_ctx {
     long long opk_cap = 0;          // capacity of d.opk in records (grown by the per-step pack)
     bool has_solids = false;        // solid-only buffers allocated
     bool sK_valid = false;          // d.sK holds the maps of the cached iterate
+    bool pK_valid = false;          // d.pK holds the solids' maps of the cached iterate
     bool use_graphs = true;         // CG chunks as CUDA graphs (cleared if capture is refused)
     int graph_error = 0;            // the refusal's error code
     // CG launch configuration and its autotuner state

@@ -534,6 +534,8 @@ struct ApplyArgs {
     RPtr3<R> sn;
     const R* sic;
     RPtr45<R> sK;             // surface: symmetric 9x9 map dF^ -> G of the projected Hessian (per iterate)
+    RPtr45<R> pK;             // solid: symmetric 9x9 map dL -> M of the projected Hessian (per iterate)
+    int use_pK;
     const R* sK0;             // the same 45 arrays, contiguous: entry e of sample j at sK0[e * sKs + j]
     long long sKs;
     int samples_in_cell;      // projected mode with current maps: k_apply_cell applies the samples
@@ -972,6 +974,18 @@ __device__ __forceinline__ void particle_general(const ApplyArgs<R>& a, int i, R
         for (int q = 0; q < 3; ++q)
 #pragma unroll
             for (int e = 0; e < 3; ++e) M[3 * q + e] = cv * R(0.5) * (dL[3 * q + e] + dL[3 * e + q]) + (q == e ? s : R(0));
+    } else if (a.use_pK) {
+        // projected: the particle's per-iterate 9x9 map
+#pragma unroll
+        for (int m = 0; m < 9; ++m) M[m] = R(0);
+#pragma unroll
+        for (int m = 0; m < 9; ++m)
+#pragma unroll
+            for (int l = m; l < 9; ++l) {
+                const R kml = a.pK.a[sym9(m, l)][i];
+                M[m] += kml * dL[l];
+                if (l != m) M[l] += kml * dL[m];
+            }
     } else {
         R Fo[9], Fc[9], Rm[9], K[6], dF[9], dP[9];
 #pragma unroll
@@ -1245,6 +1259,104 @@ __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell
     }
     __syncthreads();
     flush_halo_rows<R>(a.nbr, slot, ua, a.u);
+}
+
+// Per-iterate projected Hessian of each solid particle (the reading of the
+// paper's "definiteness fix" for solids): the 9x9 Hessian of psi(F) from the
+// analytic eigensystem of isotropic energies, with the signed SVD
+// F = U diag(s) V^T and psi_k = d psi / d s_k:
+//   pair (x, y), third index z: (psi_x - psi_y)/(s_x - s_y) = 2 mu - lambda (J-1) s_z
+//     on U sym(e_x e_y) V^T, and (psi_x + psi_y)/(s_x + s_y)
+//     = 2 mu - 4 mu / (s_x + s_y) + lambda (J-1) s_z on U skew(e_x e_y) V^T;
+//   scaling modes U diag(q) V^T with (eigenvalue, q) of d^2 psi / ds^2;
+// negative eigenvalues dropped. Composed with dF = dL F^n and M = dt^2 V0 dP F^nT
+// it is the symmetric map dL -> M = dt^2 V0 sum_k lambda_k+ <W_k, dL> W_k with
+// W_k = Q_k F^nT, stored as 45 values.
+template <typename R>
+__global__ void k_solid_hess(int np, const uint8_t* __restrict__ phase, const int* __restrict__ psc,
+                             const SceneDev* __restrict__ sc, RPtr24<R> scache, RPtr9<R> Fn, const R* __restrict__ lmu,
+                             const R* __restrict__ llam, const double* __restrict__ V0, RPtr45<R> K) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np || phase[i] == 0) return;
+    const SceneDev& S = sc[psc[i]];
+    R F[9], Fo[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        F[q] = scache.a[q][i];
+        Fo[q] = Fn.a[q][i];
+    }
+    const R mu = lmu[i], lam = llam[i];
+    const R scale = (R)(S.dt * S.dt * V0[i]);
+    R u[3][3], V[9], s[3];
+    svd3<R>(F, u, V, s);
+    const R J = s[0] * s[1] * s[2];
+    const R p[3] = {s[1] * s[2], s[0] * s[2], s[0] * s[1]};
+    // d^2 psi / ds^2 and its eigen-pairs
+    R A[9], Q[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            A[3 * a + b] = lam * p[a] * p[b] + (a == b ? R(2) * mu : lam * (J - R(1)) * s[3 - a - b]);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        R off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        R dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+        const R eps = sizeof(R) == 4 ? R(1e-7) : R(1e-16);   // converged to the type's precision
+        if (off <= eps * eps * dia) break;
+        jacobi_rot(A, Q, 0, 1);
+        jacobi_rot(A, Q, 0, 2);
+        jacobi_rot(A, Q, 1, 2);
+    }
+    R Kp[45];
+#pragma unroll
+    for (int k = 0; k < 45; ++k) Kp[k] = R(0);
+    const R h = R(0.70710678118654752440);
+    for (int mode = 0; mode < 9; ++mode) {
+        R lv, D[9];   // mode matrix in the SVD frame: Q_mode = U D V^T
+#pragma unroll
+        for (int k = 0; k < 9; ++k) D[k] = R(0);
+        if (mode < 3) {
+            lv = A[4 * mode];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) D[4 * c] = Q[3 * c + mode];
+        } else {
+            const int pr = (mode - 3) >> 1, x = pr == 2 ? 1 : 0, y = pr == 0 ? 1 : 2, z = 3 - x - y;
+            const bool twist = (mode - 3) & 1;
+            if (!twist) {
+                lv = R(2) * mu - lam * (J - R(1)) * s[z];
+                D[3 * x + y] = h;
+                D[3 * y + x] = h;
+            } else {
+                R den = s[x] + s[y];
+                den = fabs(den) > R(1e-12) ? den : copysign(R(1e-12), den);
+                lv = R(2) * mu - R(4) * mu / den + lam * (J - R(1)) * s[z];
+                D[3 * x + y] = h;
+                D[3 * y + x] = -h;
+            }
+        }
+        if (!(lv > R(0))) continue;
+        R Qm[9], W[9];
+        // Qm = U D V^T, U_ac = u[c][a]
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                R acc = R(0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) acc += u[c][a] * D[3 * c + d] * V[3 * b + d];
+                Qm[3 * a + b] = acc;
+            }
+        matmul3_bt<R>(Qm, Fo, W);   // W = Qm F^nT
+        const R lw = scale * lv;
+#pragma unroll
+        for (int m = 0; m < 9; ++m)
+#pragma unroll
+            for (int l = m; l < 9; ++l) Kp[sym9(m, l)] += lw * W[m] * W[l];
+    }
+#pragma unroll
+    for (int k = 0; k < 45; ++k) K.a[k][i] = Kp[k];
 }
 
 // Per-iterate symmetric 9x9 map of each surface sample's projected Hessian
@@ -2551,6 +2663,8 @@ ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int c
     a.slot_gen = d.slot_gen;
     for (int q = 0; q < 45; ++q) a.sK.a[q] = (R*)d.sK[q];
     a.sK0 = (const R*)d.sK[0];
+    for (int q = 0; q < 45; ++q) a.pK.a[q] = (R*)d.pK[q];
+    a.use_pK = (c->pK_valid && mode == MPM_HESS_PROJECTED) ? 1 : 0;
     a.sKs = c->Scap;
     a.samples_in_cell = (c->sK_valid && mode == MPM_HESS_PROJECTED) ? 1 : 0;
     a.opk = (const R4<R>*)d.opk;
@@ -2893,6 +3007,19 @@ cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) 
                                                                         (const RS*)dd.sic, (const RS*)dd.sg, K);
             c->sK_valid = true;
         }
+    }
+    if (want_cache && c->has_solids && c->np > 0) {
+        Dev& dd = c->d;
+        RPtr24<RS> scache;
+        RPtr9<RS> Fn;
+        RPtr45<RS> K;
+        for (int q = 0; q < 24; ++q) scache.a[q] = (RS*)dd.scache[q];
+        for (int q = 0; q < 9; ++q) Fn.a[q] = (RS*)dd.Fn[q];
+        for (int q = 0; q < 45; ++q) K.a[q] = (RS*)dd.pK[q];
+        MPM_LAUNCH k_solid_hess<RS><<<nblk(c->np, 128), 128, 0, c->st>>>((int)c->np, dd.phase, dd.psc, dd.sc, scache, Fn,
+                                                                        (const RS*)dd.lame[0], (const RS*)dd.lame[1],
+                                                                        dd.V0, K);
+        c->pK_valid = true;
     }
     Dev& d = c->d;
     EvalCellArgs e;

@@ -56,10 +56,14 @@ __device__ __forceinline__ void swap_cols(R* V, R* lam, int a, int b) {
     }
 }
 
-// F -> rotation Rm, (tr S I - S)^-1 as symmetric 6 (xx yy zz xy xz yz), signed singular values
+// Signed SVD F = U diag(sig) V^T with U, V rotations (u[k] is U's column k,
+// V row-major), singular values descending in magnitude, the last one carrying
+// the sign of det F.
 template <typename R>
-__device__ void polar3(const R* F, R* Rm, R* Kinv, R* sig) {
-    R A[9], V[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+__device__ void svd3(const R* F, R (*u)[3], R* V, R* sig) {
+    R A[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) V[k] = (k % 4 == 0) ? R(1) : R(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -82,7 +86,6 @@ __device__ void polar3(const R* F, R* Rm, R* Kinv, R* sig) {
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int i = 0; i < 3; ++i) Fv[k][i] = F[3 * i] * V[k] + F[3 * i + 1] * V[3 + k] + F[3 * i + 2] * V[6 + k];
-    R u[3][3];
     R n1 = sqrt(Fv[0][0] * Fv[0][0] + Fv[0][1] * Fv[0][1] + Fv[0][2] * Fv[0][2]);
     if (n1 > R(1e-30)) {
         for (int i = 0; i < 3; ++i) u[0][i] = Fv[0][i] / n1;
@@ -109,6 +112,13 @@ __device__ void polar3(const R* F, R* Rm, R* Kinv, R* sig) {
     u[2][2] = u[0][0] * u[1][1] - u[0][1] * u[1][0];
 #pragma unroll
     for (int k = 0; k < 3; ++k) sig[k] = u[k][0] * Fv[k][0] + u[k][1] * Fv[k][1] + u[k][2] * Fv[k][2];
+}
+
+// F -> rotation Rm, (tr S I - S)^-1 as symmetric 6 (xx yy zz xy xz yz), signed singular values
+template <typename R>
+__device__ void polar3(const R* F, R* Rm, R* Kinv, R* sig) {
+    R u[3][3], V[9];
+    svd3<R>(F, u, V, sig);
     // R = U V^T : R_ij = sum_k u[k][i] V[j][k]
 #pragma unroll
     for (int i = 0; i < 3; ++i)

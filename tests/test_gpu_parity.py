@@ -55,10 +55,23 @@ def _mixed_scene(seed=9):
     return sc
 
 
+def _deformed_solids():
+    """The mixed scene with strongly compressed and sheared solids: their exact
+    Hessian is indefinite, so the projected operator clamps eigenvalues."""
+    sc = _mixed_scene()
+    rng = np.random.default_rng(7)
+    sol = sc.phase == scenes.PHASE_SOLID
+    sc.F[sol] = np.diag([0.55, 0.8, 1.3]) + 0.1 * rng.standard_normal((sol.sum(), 3, 3))
+    sc.params.E0 = 3000.0
+    return sc
+
+
 SCENES = {
     "droplet": lambda: scenes.config(0),
     "mixed": _mixed_scene,
 }
+# the operator tests also take the deformed solids
+OP_SCENES = dict(SCENES, deformed=_deformed_solids)
 
 
 def _setup(sc, prec):
@@ -122,9 +135,9 @@ def test_energy_gradient_matches_oracle(name, prec):
 
 @pytest.mark.parametrize("mode", [HESS_PROJECTED, HESS_EXACT])
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("name", list(SCENES))
+@pytest.mark.parametrize("name", list(OP_SCENES))
 def test_apply_hessian_matches_oracle(name, prec, mode):
-    sc = SCENES[name]()
+    sc = OP_SCENES[name]()
     ctx, sim = _setup(sc, prec)
     st, v = _iterate(sim)
     ctx.set_velocity(0, v)
