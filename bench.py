@@ -21,7 +21,8 @@ Reported (one JSON line on rank 0):
   fp64_form    the all-float64 GPU form on the same workload (fewer steps)
   cpu_baseline the FP64 numpy oracle on a bounded sample of the workload (a
                16^3-cell window at the lower surface of its smallest droplet,
-               same dx, parameters and plane), scaled per particle to the full
+               or around the centroid of a scene without droplets; same dx,
+               parameters and plane), scaled per particle to the full
                workload; one host thread (BLAS pools pinned to 1)
   --impl reference: the oracle alone, timed on the host, same metric.
 Multi-GPU (torchrun): replicas only -- every rank advances its own copy of the
@@ -149,7 +150,6 @@ def algorithmic_bytes(ctx, sc, rsize):
 def run_oracle_sample(sc, steps):
     """FP64 oracle on the workload's window sample; returns seconds per step and the sample."""
     import oracle
-    # the smallest droplet: its particles and samples in a window of the same grid
     from scipy.spatial import cKDTree  # noqa: F401  (scipy present on both machines)
     sample = sample_scene(sc)
     sim = oracle.OracleSim(sample)
@@ -164,10 +164,18 @@ def run_oracle_sample(sc, steps):
 SAMPLE_CELLS = 16
 
 
+def sample_where(sc):
+    """Where `sample_scene` puts its window, in words."""
+    if "radii" in sc.meta:
+        return "at the lower surface of the smallest droplet"
+    return "around the particles' centroid"
+
+
 def sample_scene(sc, size=SAMPLE_CELLS):
     """A bounded piece of the workload for the CPU oracle: the particles and
     surface samples in a `size`^3-cell window (same dx, parameters and plane)
-    around the lower surface of the smallest droplet."""
+    around the lower surface of the smallest droplet, or around the particles'
+    centroid in a scene without droplets."""
     if "radii" in sc.meta:
         k = int(np.argmin(sc.meta["radii"]))
         c = sc.meta["centers"][k] - np.array([0.0, sc.meta["radii"][k] - 3 * sc.dx, 0.0])
@@ -340,8 +348,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "particles": sc.n_particles},
                 "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"{sample.n[0]}^3-cell window at the lower surface of the smallest "
-                                           f"droplet ({sample.n_particles} of {sc.n_particles} particles, "
+                                 "sample": f"{sample.n[0]}^3-cell window {sample_where(sc)} "
+                                           f"({sample.n_particles} of {sc.n_particles} particles, "
                                            f"{sample.n_surface} samples) per step, seconds per step scaled by "
                                            f"particle count ({scale:.5f})"},
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -360,7 +368,7 @@ def main():
         t = float(np.mean(times))
         scale = sample.n_particles / sc.n_particles
         cpu = {"value": scale / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{sample.n[0]}^3-cell window at the lower surface of the smallest droplet "
+               "sample": f"{sample.n[0]}^3-cell window {sample_where(sc)} "
                          f"({sample.n_particles} of {sc.n_particles} particles, {sample.n_surface} samples, "
                          f"{args.cpu_steps} steps), seconds per step scaled by particle count"}
     prof = res["prof"]

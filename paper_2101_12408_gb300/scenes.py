@@ -234,14 +234,34 @@ def droplet(n=32, r_cells=8.0, seed=1001, ppc_axis=2, surf_per_cell=2.0,
 
 
 def film(nx=128, ny=128, nz=32, height_cells=6, seed=1002, ppc_axis=2, surf_per_cell=2,
-         T0=0.0, dT=1.0, sigma_cells=10.0, h=5.0, K=0.1, cp=1.0, lambda_l=100.0,
-         mu_l=1e-3, rho=1.0, dt=5e-4, gravity=(0.0, 0.0, -9.8)) -> Scene:
+         T0=0.0, dT=1.0, sigma_cells=10.0, h=5.0, K=0.1, cp=1e-3, lambda_l=1e6,
+         mu_l=1e-3, rho=1000.0, dt=5e-4, gravity=(0.0, 0.0, -9.8)) -> Scene:
     """Marangoni thin film: a liquid layer `height_cells` thick over a sticky floor.
 
-    Slip side walls; surface samples (2 per top-face cell, jittered) on the top
-    face only; linear gamma(T) = 1 - 0.5 (T - T0) clamped at 0; Gaussian hot
-    spot T = T0 + dT exp(-rho^2 / (2 sigma^2)) with rho in cells from the centre;
+    Slip side walls; surface samples on the top face only; linear
+    gamma(T) = 1 - 0.5 (T - T0) clamped at 0; Gaussian hot spot
+    T = T0 + dT exp(-rho^2 / (2 sigma^2)) with rho in cells from the centre;
     Robin convection h with ambient T0 on the top face.
+
+    Water in SI units (rho = 1000, bulk modulus 1e6, viscosity 1e-3), as for the
+    inclined droplets. The heat problem per unit volume is rho c_p = 1 with
+    conductivity K = 0.1 and h = 5. With rho = 1 the Marangoni stress
+    accelerates the top node row at ~800 m/s^2 at dx = 1/128. The surface flow
+    then reaches metres per second within 15 steps and converges at the walls,
+    where the carried samples outrun their particles.
+
+    The top sheet is a regular lattice of `surf_per_cell` (1, 2 or 4) samples
+    per face cell that is point-symmetric about every node centre, and it runs
+    over cells 1..n-2 in x and y, i.e. onto the slip node layers. A flat sheet
+    of constant gamma then exerts no tangential force on any free node: the
+    interior dipoles cancel by the symmetry, and the edge's pull
+    (gamma N_i(x_edge) per unit length) lands on the wall nodes, whose normal
+    velocity is zeroed. Only gamma's variation (the Marangoni stress) drives the
+    surface. A sheet that ends at the liquid's edge (x = 2 dx) instead pulls the
+    first free node row inward with gamma/2 per unit length, an acceleration of
+    order gamma / (rho dx^2) at the light top nodes that grows 16-fold from
+    dx = 1/32 to 1/128; jittered samples add forces of the same order at every
+    top node.
     """
     rng = np.random.default_rng(seed)
     dx = 1.0 / nx
@@ -257,12 +277,12 @@ def film(nx=128, ny=128, nz=32, height_cells=6, seed=1002, ppc_axis=2, surf_per_
         return T0 + dT * np.exp(-rr / (2.0 * sigma_cells ** 2))
 
     P = _particles(x, rho, dx, ppc, rng, T=temp(x))
-    # top-face samples: surf_per_cell per cell, jittered inside the face cell
-    fx, fy = np.meshgrid(np.arange(lo[0], hi[0]), np.arange(lo[1], hi[1]), indexing="ij")
-    fx = np.repeat(fx.ravel(), surf_per_cell)
-    fy = np.repeat(fy.ravel(), surf_per_cell)
-    sxy = np.stack([fx, fy], -1) + rng.uniform(0.0, 1.0, size=(fx.size, 2))
-    s = np.concatenate([sxy * dx, np.full((fx.size, 1), z1 * dx)], -1)
+    # top-face samples: a regular lattice over face cells 1..n-2 (onto the wall layers)
+    offs = {1: [(0.5, 0.5)], 2: [(0.25, 0.25), (0.75, 0.75)],
+            4: [(0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75)]}[surf_per_cell]
+    fx, fy = np.meshgrid(np.arange(1, nx - 1), np.arange(1, ny - 1), indexing="ij")
+    sxy = (np.stack([fx.ravel(), fy.ravel()], -1)[:, None, :] + np.asarray(offs)[None]).reshape(-1, 2)
+    s = np.concatenate([sxy * dx, np.full((sxy.shape[0], 1), z1 * dx)], -1)
     dA = np.zeros_like(s)
     dA[:, 2] = dx * dx / surf_per_cell
     S = _surface(s, dA, b=np.zeros(s.shape[0]), Tbar=np.full(s.shape[0], T0))

@@ -23,6 +23,26 @@ def relerr(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
+def _check_heat(ctx, sim, prec):
+    """End-of-step temperature against the oracle's (solved to 1e-13).
+
+    The float64 form is solved tightly and compared node by node. The float32
+    form's heat CG stops at |r| <= 1e-6 |rhs|. The error that stop leaves is
+    small in the thermal-mass-weighted norm but gathers at nodes with little
+    thermal mass. On the small film, the oracle's own float64 solve stopped at
+    1e-6 differs from its tight solve by 1.5e-6 weighted and by 4.0e-4 node by
+    node, at a node with 0.27% of the largest thermal mass.
+    """
+    T = ctx.get_grid(0, mpm.FIELD_THAT)
+    if prec == mpm.PREC_FP64:
+        assert relerr(T, sim.That) < 1e-9
+        return
+    mT = sim.grid["mT"]
+    weighted = np.sqrt(np.sum(mT * (T - sim.That) ** 2) / np.sum(mT * sim.That ** 2))
+    assert weighted < 1e-5
+    assert relerr(T, sim.That) < 2e-3
+
+
 TOL = {mpm.PREC_FP64: 1e-9, mpm.PREC_FP32_FP64RED: 2e-5}
 PRECS = [mpm.PREC_FP64, mpm.PREC_FP32_FP64RED]
 
@@ -186,9 +206,7 @@ def test_step_grid_velocity_matches_oracle(name, prec):
     tol = 1e-9 if prec == mpm.PREC_FP64 else 1e-5
     assert relerr(vgpu, sim.vhat) < tol, stats
     if sc.params.thermal:
-        # float32 heat CG stops at |r| <= 1e-6 |rhs|; the temperature error is that
-        # times the heat operator's condition number (tens here), so 2e-4
-        assert relerr(ctx.get_grid(0, mpm.FIELD_THAT), sim.That) < (1e-9 if prec == mpm.PREC_FP64 else 2e-4)
+        _check_heat(ctx, sim, prec)
     # G2P
     ctx.g2p()
     sim.g2p()
@@ -299,7 +317,7 @@ def test_workload_step_matches_oracle(name, prec):
         np.testing.assert_array_equal(ctx.get_surface(0)["parent"], sim.parent)
         assert relerr(ctx.get_grid(0, mpm.FIELD_VHAT), sim.vhat) < tol, (step, stats)
         if sc.params.thermal:
-            assert relerr(ctx.get_grid(0, mpm.FIELD_THAT), sim.That) < (1e-9 if prec == mpm.PREC_FP64 else 2e-4)
+            _check_heat(ctx, sim, prec)
         ctx.g2p()
         sim.g2p()
     # The grid velocity is compared above at tol. Particle velocities come from it
