@@ -107,6 +107,15 @@ typedef struct {
     double heat_rtol;           /* heat CG tolerance relative to |rhs| */
     int32_t max_newton, max_cg, max_ls;
     int32_t phase_change;       /* 1: melt / freeze at T_melt after G2P */
+    double friction;            /* Coulomb coefficient mu_f >= 0 at the nodes of a slip plane, applied
+                                   to the end-of-step grid velocity (section "Examples", inclined
+                                   ramps): with v~ = v - r/m and v_n = v~ . n < 0 the tangential part t
+                                   becomes max(0, 1 - mu_f |v_n| / |t|) t; 0 is the frictionless slip */
+    int32_t massless_surface;   /* 1: the massless-sample variant the paper compares against (section
+                                   "Surface Particle Sampling"): samples carry no mass, no balance
+                                   particles, and the parents keep their whole mass. Forces that land
+                                   on nodes without mass are lost, so momentum is not conserved */
+    int32_t pad_;
 } mpm_params;
 
 typedef struct {

@@ -19,8 +19,8 @@ import numpy as np
 from .spline import node_positions
 
 
-def projector(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
-    """Per-node projection matrices (G, 3, 3)."""
+def _node_classes(n, dx, walls, plane_n, plane_d, plane_mode):
+    """Fully fixed nodes (G,), slip axes (G, 3) and nodes below the plane (G,)."""
     n = tuple(int(v) for v in n)
     G = n[0] * n[1] * n[2]
     k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
@@ -45,6 +45,13 @@ def projector(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
             sticky |= on_plane
     nslip = slip_axis.sum(1)
     full = sticky | (on_plane & (nslip > 0)) | (nslip == 3)
+    return full, slip_axis, on_plane
+
+
+def projector(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
+    """Per-node projection matrices (G, 3, 3)."""
+    full, slip_axis, on_plane = _node_classes(n, dx, walls, plane_n, plane_d, plane_mode)
+    G = full.shape[0]
     P = np.broadcast_to(np.eye(3), (G, 3, 3)).copy()
     for a in range(3):
         P[slip_axis[:, a], a, :] = 0.0
@@ -60,3 +67,31 @@ def projector(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
 
 def apply_projector(P, v):
     return np.einsum("gab,gb->ga", P, v)
+
+
+def slip_plane_nodes(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
+    """Nodes whose projection is the slip plane's, I - n n^T (G,) bool."""
+    full, _, on_plane = _node_classes(n, dx, walls, plane_n, plane_d, plane_mode)
+    return on_plane & ~full if plane_mode == 1 else np.zeros_like(full)
+
+
+def coulomb_plane(v, nodes, plane_n, mu):
+    """Coulomb friction of the slip plane on end-of-step node velocities (G, 3).
+
+    At a plane node whose velocity presses into the plane, v_n = v . n < 0, the
+    plane's normal impulse m |v_n| bounds the tangential impulse by mu m |v_n|:
+    the tangential part t = v - v_n n keeps its direction and loses mu |v_n| of
+    its length, or stops when |t| <= mu |v_n|. The normal part is left for the
+    projection. Other nodes are returned unchanged.
+    """
+    nn = np.asarray(plane_n, float)
+    nn = nn / np.linalg.norm(nn)
+    out = v.copy()
+    vn = v @ nn
+    sel = nodes & (vn < 0.0)
+    t = v[sel] - vn[sel, None] * nn
+    tl = np.linalg.norm(t, axis=1)
+    lim = -mu * vn[sel]
+    s = np.where(tl > lim, 1.0 - lim / np.where(tl > 0, tl, 1.0), 0.0)
+    out[sel] = s[:, None] * t + vn[sel, None] * nn
+    return out

@@ -23,7 +23,7 @@ heat operator, initial guess T^n.
 """
 import numpy as np
 
-from .boundary import apply_projector
+from .boundary import apply_projector, coulomb_plane
 from .energy import HESS_PROJECTED
 
 
@@ -56,8 +56,12 @@ def pcg(apply, b, precond, rtol, maxit, neg_curv_exit=True):
     return x, it
 
 
-def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False):
-    """Returns the end-of-step grid velocity and a stats dict."""
+def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False, friction=None):
+    """Returns the end-of-step grid velocity and a stats dict.
+
+    friction: None, or (plane nodes (G,) bool, plane normal, mu) for the slip
+    plane's Coulomb friction on the end-of-step velocity before the projection.
+    """
     m = state.m
     act = state.active
     inv_m = np.where(act, 1.0 / np.where(act, m, 1.0), 0.0)
@@ -104,7 +108,11 @@ def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False):
         v = np.zeros_like(state.vn)
     # explicit force evaluation at the final iterate
     r = state.gradient(v)
-    v = proj(v - r * inv_m[:, None])
+    v = v - r * inv_m[:, None]
+    if friction is not None:
+        nodes, nrm, mu = friction
+        v = coulomb_plane(v, nodes & act, nrm, mu)
+    v = proj(v)
     return v, stats
 
 

@@ -24,11 +24,19 @@ Readings:
   dA <- cof(I + dt sum_i v_i gradN_i(s)^T) dA (the updated-Lagrangian area map
   of Eq. pestul);
 * particles move with their new velocity, x <- x + dt v_p; liquids update
-  J <- (1 + dt tr grad v) J, solids F <- (I + dt grad v) F.
+  J <- (1 + dt tr grad v) J, solids F <- (I + dt grad v) F;
+* Coulomb friction of a slip plane (section "Examples", liquid drops on ramps
+  with friction coefficient 0.2; no formula is given): applied at the plane's
+  nodes to the end-of-step velocity of the final force evaluation, before the
+  projection (see boundary.coulomb_plane);
+* the massless-sample variant the paper compares against (section "Surface
+  Particle Sampling"): samples carry no mass and have no balance particles, so
+  P2G and G2P see the interior particles alone with their whole mass, while the
+  surface energy still acts through the samples.
 """
 import numpy as np
 
-from .boundary import projector
+from .boundary import projector, slip_plane_nodes
 from .constitutive import cof
 from .energy import NewtonState, HESS_PROJECTED
 from .heat import HeatSystem
@@ -69,6 +77,12 @@ class OracleSim:
         sc = self.sc
         self.P = projector(sc.n, sc.dx, sc.walls, sc.plane_n, sc.plane_d, sc.plane_mode)
         self.G = int(np.prod(sc.n))
+        self.friction = None
+        if self.prm.friction > 0.0 and sc.plane_mode == 1:
+            nodes = slip_plane_nodes(sc.n, sc.dx, sc.walls, sc.plane_n, sc.plane_d, sc.plane_mode)
+            self.friction = (nodes, sc.plane_n, self.prm.friction)
+        # the massless-sample variant: samples carry no mass, no balance particles
+        self.massless = bool(self.prm.massless_surface)
 
     # (0) surface samples generated on the particles' union-of-spheres surface
     def generate_surface(self, seed, per_cell_area=2.0):
@@ -87,12 +101,15 @@ class OracleSim:
             phi = sc.s @ np.asarray(sc.plane_n) - sc.plane_d
             sc.kind = np.where(phi < sc.dx, 1, 0).astype(np.uint8)
         self.parent, self.count, self.mt, self.bpos = split(sc.x, sc.m, sc.s)
+        if self.massless:
+            self.mt = sc.m.copy()
 
     # (2) P2G
     def p2g(self):
         sc = self.sc
         thermal = self.prm.thermal
-        out = p2g(sc.n, sc.dx, sc.x, sc.v, sc.A, self.mt, sc.s, self.bpos, self.parent,
+        group = (None, None, None) if self.massless else (sc.s, self.bpos, self.parent)
+        out = p2g(sc.n, sc.dx, sc.x, sc.v, sc.A, self.mt, *group,
                   m=sc.m, T=sc.T if thermal else None, gradT=sc.gradT if thermal else None)
         self.grid = out
         self.vn = grid_velocity(out["m"], out["mv"])
@@ -133,12 +150,14 @@ class OracleSim:
             # solved to 1e-13 relative to |rhs| (near round-off), tighter than any GPU tolerance
             self.That, self.heat_its = heat_solve(self.heat_system(), 1e-13, 20000)
         self.state = self.newton_state()
-        self.vhat, self.stats = newton_solve(self.state, self.P, prm, self.hess_mode, self.explicit)
+        self.vhat, self.stats = newton_solve(self.state, self.P, prm, self.hess_mode, self.explicit,
+                                             friction=self.friction)
 
     # (4) G2P
     def g2p(self):
         sc, prm = self.sc, self.prm
-        out = g2p(sc.n, sc.dx, self.vhat, sc.x, sc.m, self.mt, sc.s, self.bpos, self.parent, self.That)
+        group = (None, None, None) if self.massless else (sc.s, self.bpos, self.parent)
+        out = g2p(sc.n, sc.dx, self.vhat, sc.x, sc.m, self.mt, *group, self.That)
         dt = prm.dt
         Lg = out["grad_v"]
         liq = sc.phase == 0

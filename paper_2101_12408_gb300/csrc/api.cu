@@ -243,7 +243,8 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
         const mpm_grid_desc& G = D.grid;
         const mpm_params& P = D.params;
         if (G.n[0] < 4 || G.n[1] < 4 || G.n[2] < 4 || !(G.dx > 0) || D.max_particles < 0 || D.max_surface < 0 ||
-            !(P.dt > 0) || P.max_ls < 1 || P.max_ls > MAX_LS || P.max_newton < 0 || P.max_cg < 1) {
+            !(P.dt > 0) || P.max_ls < 1 || P.max_ls > MAX_LS || P.max_newton < 0 || P.max_cg < 1 ||
+            !(P.friction >= 0.0) || !std::isfinite(P.friction) || (P.massless_surface != 0 && P.massless_surface != 1)) {
             delete c;
             return MPM_ERR_INVALID_ARG;
         }
@@ -296,6 +297,8 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
         S.max_newton = P.max_newton;
         S.max_cg = P.max_cg;
         S.max_ls = P.max_ls;
+        S.massless = P.massless_surface;
+        S.friction = G.plane_mode == MPM_WALL_SLIP ? P.friction : 0.0;
         S.p_begin = pb;
         S.p_end = pb + D.max_particles;
         S.s_begin = sb;

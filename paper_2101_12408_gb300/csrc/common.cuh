@@ -35,7 +35,8 @@ struct SceneDev {
     double plane_n[3], plane_d;
     float plane_nf[3], pad_f_;      // plane normal in float32 (the float32 projections)
     double newton_tol, cg_rtol, heat_rtol;
-    int max_newton, max_cg, max_ls, pad_;
+    int max_newton, max_cg, max_ls, massless;
+    double friction;             // Coulomb coefficient at slip-plane nodes
     long long p_begin, p_end;    // interior particles (set order == storage offset)
     long long s_begin, s_end;    // surface samples
 };

@@ -2476,7 +2476,24 @@ __global__ void k_newton_update(const int4* __restrict__ coord, const SceneScal*
     }
 }
 
-// final explicit force evaluation: vhat = P (v - grad / m); momentum sums
+// Coulomb friction of the slip plane on the end-of-step velocity v~ of one node:
+// when v~ presses into the plane (v_n = v~ . n < 0) the plane's normal impulse
+// m |v_n| bounds the tangential one by mu_f m |v_n|, so the tangential part t
+// shrinks by mu_f |v_n| or stops (|t| <= mu_f |v_n|). The normal part is left
+// for the slip projection.
+__device__ __forceinline__ void coulomb_plane(double* v, const SceneDev& S) {
+    const double* n = S.plane_n;
+    double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+    if (!(vn < 0.0)) return;
+    double t[3] = {v[0] - vn * n[0], v[1] - vn * n[1], v[2] - vn * n[2]};
+    double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    double lim = -S.friction * vn;
+    double s = tn > lim ? 1.0 - lim / tn : 0.0;
+    for (int q = 0; q < 3; ++q) v[q] = s * t[q] + vn * n[q];
+}
+
+// final explicit force evaluation: vhat = P (v - grad / m), with the plane's
+// Coulomb friction before the projection; momentum sums
 __global__ void k_newton_final(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, SceneScal* __restrict__ scal,
                                const double* __restrict__ gm, const double* __restrict__ gv, const double* __restrict__ grad,
                                const uint8_t* __restrict__ pcode, double* __restrict__ gvhat) {
@@ -2491,7 +2508,9 @@ __global__ void k_newton_final(const int4* __restrict__ coord, const SceneDev* _
             int k = slot * 192 + q * 64 + l;
             v[q] = gv[k] - grad[k] / m;
         }
-        project3(v, pcode[t], S);
+        const uint8_t code = pcode[t];
+        if ((code & PC_PLANE) && !(code & PC_FIXED) && S.friction > 0.0) coulomb_plane(v, S);
+        project3(v, code, S);
     }
     for (int q = 0; q < 3; ++q) {
         gvhat[slot * 192 + q * 64 + l] = v[q];

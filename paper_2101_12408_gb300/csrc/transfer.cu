@@ -91,10 +91,12 @@ __global__ void k_nearest(int ns, P3 s, const int* __restrict__ ssc, P3 x, const
     }
 }
 
-__global__ void k_split(int np, const double* __restrict__ m, const int* __restrict__ gcount, double* __restrict__ mt) {
+__global__ void k_split(int np, const double* __restrict__ m, const int* __restrict__ gcount, const int* __restrict__ psc,
+                        const SceneDev* __restrict__ sc, double* __restrict__ mt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np) return;
-    mt[i] = m[i] / (2.0 * gcount[i] + 1.0);
+    // the massless-sample variant keeps the parent's whole mass
+    mt[i] = sc[psc[i]].massless ? m[i] : m[i] / (2.0 * gcount[i] + 1.0);
 }
 
 // ---------------------------------------------------------------- P2G
@@ -202,6 +204,7 @@ __global__ void k_p2g_surface(int ns, P3 s, P3 bpos, const int* __restrict__ ssc
     int p = parent[j];
     if (p < 0) return;
     const SceneDev& S = sc[ssc[j]];
+    if (S.massless) return;   // massless samples and no balance particles
     double mp = mt[p];
     double vp[3] = {v.a[0][p], v.a[1][p], v.a[2][p]};
     double Ap[9];
@@ -540,7 +543,7 @@ __global__ void k_g2p_surface(int ns, W3 s, W3 dA, P3 bpos, const int* __restric
                         }
                     }
                 }
-        if (p >= 0) {
+        if (p >= 0 && !S.massless) {
             for (int q = 0; q < 3; ++q) atomicAdd(&acc.a[q][p], mp * pv[q]);
             for (int q = 0; q < 9; ++q) atomicAdd(&acc.a[3 + q][p], mp * tv[q]);
         }
@@ -596,7 +599,7 @@ cudaError_t launch_nearest_parent(mpm_ctx* c) {
                                                     P3{{d.x[0], d.x[1], d.x[2]}}, d.pid, d.cell_start, d.sc, d.parent,
                                                     W3{{d.bpos[0], d.bpos[1], d.bpos[2]}}, d.gcount, d.kind, d.err);
     }
-    if (c->np > 0) MPM_LAUNCH k_split<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, d.m, d.gcount, d.mt);
+    if (c->np > 0) MPM_LAUNCH k_split<<<nblk(c->np, 256), 256, 0, st>>>((int)c->np, d.m, d.gcount, d.psc, d.sc, d.mt);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,8 @@ class Params(ctypes.Structure):
                 ("gamma_law", ctypes.c_int32), ("thermal", ctypes.c_int32), ("gamma_p", ctypes.c_double * 4),
                 ("gamma_lg", ctypes.c_double), ("gamma_sl", ctypes.c_double), ("newton_tol", ctypes.c_double),
                 ("cg_rtol", ctypes.c_double), ("heat_rtol", ctypes.c_double), ("max_newton", ctypes.c_int32),
-                ("max_cg", ctypes.c_int32), ("max_ls", ctypes.c_int32), ("phase_change", ctypes.c_int32)]
+                ("max_cg", ctypes.c_int32), ("max_ls", ctypes.c_int32), ("phase_change", ctypes.c_int32),
+                ("friction", ctypes.c_double), ("massless_surface", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class SceneDesc(ctypes.Structure):
@@ -177,6 +178,8 @@ def scene_desc(sc, max_particles=None, max_surface=None, max_blocks=0):
     P.max_cg = p.max_cg
     P.max_ls = p.max_ls
     P.phase_change = int(bool(p.phase_change))
+    P.friction = float(getattr(p, "friction", 0.0))
+    P.massless_surface = int(bool(getattr(p, "massless_surface", False)))
     d.max_particles = int(max_particles if max_particles is not None else sc.n_particles)
     d.max_surface = int(max_surface if max_surface is not None else sc.n_surface)
     d.max_blocks = int(max_blocks)

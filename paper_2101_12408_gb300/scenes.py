@@ -64,6 +64,8 @@ class Params:
     max_ls: int = 12
     thermal: bool = False            # run the heat solve and gamma(T)
     phase_change: bool = False
+    friction: float = 0.0            # Coulomb coefficient at nodes of a slip plane (0: frictionless)
+    massless_surface: bool = False   # samples carry no mass and have no balance particles
 
 
 @dataclasses.dataclass

@@ -47,9 +47,30 @@ def test_struct_sizes_match_c_layout(lib):
     from paper_2101_12408_gb300 import mpm
     # sizes follow the C rules for the header's field order (8-byte aligned doubles)
     assert ctypes.sizeof(mpm.GridDesc) == 112
-    assert ctypes.sizeof(mpm.Params) == 216
-    assert ctypes.sizeof(mpm.SceneDesc) == 352
+    assert ctypes.sizeof(mpm.Params) == 232
+    assert ctypes.sizeof(mpm.SceneDesc) == 368
     assert ctypes.sizeof(mpm.Stats) == 64
+
+
+def test_struct_layout_matches_the_header_compiled(tmp_path):
+    """Sizes and the offsets of the last fields, from the header compiled by the host C compiler."""
+    import shutil
+    import subprocess
+    from paper_2101_12408_gb300 import mpm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "mpm.h"\n'
+        'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(mpm_params), sizeof(mpm_scene_desc),'
+        ' offsetof(mpm_params, phase_change), offsetof(mpm_params, friction),'
+        ' offsetof(mpm_params, massless_surface)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(mpm.Params), ctypes.sizeof(mpm.SceneDesc), mpm.Params.phase_change.offset,
+                   mpm.Params.friction.offset, mpm.Params.massless_surface.offset]
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):

@@ -282,7 +282,23 @@ def _small_incline():
     return sc
 
 
-WORKLOADS = {"film": _small_film, "wax": _small_wax, "incline": _small_incline}
+def _small_incline_friction():
+    # Coulomb friction 0.2 on the plane (the paper's ramps); the drops start on it
+    sc = _small_incline()
+    sc.params.friction = 0.2
+    return sc
+
+
+def _massless_droplet():
+    # the massless-sample variant, on a moving droplet under gravity
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=44, v0=(0.3, -0.1, 0.2), spin=1.0, lambda_l=50.0,
+                        gravity=(0.0, -9.8, 0.0))
+    sc.params.massless_surface = True
+    return sc
+
+
+WORKLOADS = {"film": _small_film, "wax": _small_wax, "incline": _small_incline,
+             "incline_friction": _small_incline_friction, "massless": _massless_droplet}
 
 
 def _tight(sc):
