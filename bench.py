@@ -17,7 +17,8 @@ Reported (one JSON line on rank 0):
   roofline     the Hessian-vector kernel: algorithmic bytes per launch / its mean
                CUDA-event duration inside the timed steps, against measured HBM
   e2e          the same steps/s through the C ABI with host buffers: particle and
-               surface state copied in from host memory and back out every step
+               surface state copied in from pinned host memory and back out into
+               it every step
   fp64_form    the all-float64 GPU form on the same workload (fewer steps)
   cpu_baseline the FP64 numpy oracle on a bounded sample of the workload (a
                16^3-cell window at the lower surface of its smallest droplet,
@@ -255,22 +256,34 @@ def bench_ours(args, rank, world):
     }
     # end to end through host buffers: state in from host memory, step, state back out
     if args.e2e_steps > 0:
+        tdt = {np.dtype(np.float64): torch.float64, np.dtype(np.uint8): torch.uint8, np.dtype(np.int32): torch.int32}
+
+        def pinned(a):
+            # a page-locked host copy: the step's inputs and outputs live in pinned memory
+            buf = torch.empty(a.shape, dtype=tdt[a.dtype], pin_memory=True).numpy()
+            buf[...] = a
+            return buf
+
         cur = sc.copy()
         p = ctx.get_particles(0)
         srf = ctx.get_surface(0)
-        for f in ("x", "v", "A", "J", "F", "T", "gradT", "phase"):
-            setattr(cur, f, p[f])
-        cur.s, cur.dA, cur.kind = srf["s"], srf["dA"], srf["kind"]
+        pf = ("x", "v", "A", "J", "F", "T", "gradT", "phase")
+        for f in pf:
+            setattr(cur, f, pinned(p[f]))
+        for f in ("m", "V0", "b", "Tbar"):
+            setattr(cur, f, pinned(np.ascontiguousarray(getattr(sc, f))))
+        cur.s, cur.dA, cur.kind = pinned(srf["s"]), pinned(srf["dA"]), pinned(srf["kind"])
+        # each step's outputs land in the arrays the next step loads
+        pout = {f: getattr(cur, f) for f in pf}
+        sout = dict(s=cur.s, dA=cur.dA, kind=cur.kind, gamma=pinned(srf["gamma"]), parent=pinned(srf["parent"]),
+                    b=pinned(srf["b"]))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             ctx.load_scene(0, cur)
             ctx.step()
-            p = ctx.get_particles(0)
-            srf = ctx.get_surface(0)
-            for f in ("x", "v", "A", "J", "F", "T", "gradT", "phase"):
-                setattr(cur, f, p[f])
-            cur.s, cur.dA, cur.kind = srf["s"], srf["dA"], srf["kind"]
+            ctx.get_particles(0, out=pout)
+            ctx.get_surface(0, out=sout)
         torch.cuda.synchronize()
         e2e_rate, _ = job_rate(args.e2e_steps, (time.perf_counter() - t0) * 1e3, dev)
         n, ns = ctx.np[0], ctx.ns[0]

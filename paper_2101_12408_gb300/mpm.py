@@ -256,18 +256,31 @@ class Context:
                            phase=sc.phase)
         self.set_surface(k, sc.s, sc.dA, kind=sc.kind, b=sc.b, Tbar=sc.Tbar)
 
-    def get_particles(self, k):
+    @staticmethod
+    def _outputs(spec, out):
+        """Fresh arrays, or the caller's (e.g. in pinned host memory), checked."""
+        if out is None:
+            return {f: np.zeros(shape, dt) for f, (shape, dt) in spec.items()}
+        for f, (shape, dt) in spec.items():
+            a = out[f]
+            if a.shape != shape or a.dtype != dt or not a.flags["C_CONTIGUOUS"] or not a.flags["WRITEABLE"]:
+                raise ValueError(f"output {f}: need a writeable C-contiguous {np.dtype(dt).name} array {shape}")
+        return out
+
+    def get_particles(self, k, out=None):
         n = self.np[k]
-        out = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), A=np.zeros((n, 3, 3)), J=np.zeros(n), F=np.zeros((n, 3, 3)),
-                   T=np.zeros(n), gradT=np.zeros((n, 3)), phase=np.zeros(n, np.uint8))
+        f8 = np.float64
+        out = self._outputs(dict(x=((n, 3), f8), v=((n, 3), f8), A=((n, 3, 3), f8), J=((n,), f8), F=((n, 3, 3), f8),
+                                 T=((n,), f8), gradT=((n, 3), f8), phase=((n,), np.uint8)), out)
         self._check(_lib.mpm_get_particles(self.h, k, n, *[_ptr(out[f]) for f in
                                                          ("x", "v", "A", "J", "F", "T", "gradT", "phase")]))
         return out
 
-    def get_surface(self, k):
+    def get_surface(self, k, out=None):
         n = self.ns[k]
-        out = dict(s=np.zeros((n, 3)), dA=np.zeros((n, 3)), kind=np.zeros(n, np.uint8), gamma=np.zeros(n),
-                   parent=np.zeros(n, np.int32), b=np.zeros((n, 3)))
+        f8 = np.float64
+        out = self._outputs(dict(s=((n, 3), f8), dA=((n, 3), f8), kind=((n,), np.uint8), gamma=((n,), f8),
+                                 parent=((n,), np.int32), b=((n, 3), f8)), out)
         self._check(_lib.mpm_get_surface(self.h, k, n, *[_ptr(out[f]) for f in
                                                        ("s", "dA", "kind", "gamma", "parent", "b")]))
         return out
