@@ -7,6 +7,9 @@ follow exactly. With the massless-sample variant (the earlier method the paper
 compares against), surface forces that land on nodes without mass are dropped,
 and momentum drifts.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -14,11 +17,15 @@ from paper_2101_12408_gb300 import mpm, scenes
 
 pytestmark = pytest.mark.gpu
 
+with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.json")) as _f:
+    PAPER = json.load(_f)
+
 
 def oscillating_droplet(massless, n=32, r_cells=8.0, rate=2.0):
     """Zero gravity, bulk modulus and surface coefficient of the paper's ellipse
     example, a volume-preserving stretch v = rate (x - c, -(y - c), 0)."""
-    sc = scenes.droplet(n=n, r_cells=r_cells, seed=61, lambda_l=4166.67, gamma=0.1, dt=1e-3)
+    sc = scenes.droplet(n=n, r_cells=r_cells, seed=61, lambda_l=PAPER["ellipse_bulk_modulus"]["value"],
+                        gamma=PAPER["ellipse_surface_coefficient"]["value"], dt=1e-3)
     c = np.full(3, 0.5)
     sc.v = np.stack([rate * (sc.x[:, 0] - c[0]), -rate * (sc.x[:, 1] - c[1]), np.zeros(sc.n_particles)], -1)
     sc.A = np.broadcast_to(np.diag([rate, -rate, 0.0]), sc.A.shape).copy()

@@ -5,6 +5,9 @@ float32-operator form 1e-5 relative for the step's grid velocity (the target
 of the workload) and 2e-5 for single operator applications, relative to the
 largest entry of the oracle's result. Index work (closest parent) is bit-exact.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -283,9 +286,11 @@ def _small_incline():
 
 
 def _small_incline_friction():
-    # Coulomb friction 0.2 on the plane (the paper's ramps); the drops start on it
+    # Coulomb friction on the plane with the paper's ramp coefficient; the drops start on it
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.json")) as f:
+        mu = json.load(f)["ramp_friction"]["value"]
     sc = _small_incline()
-    sc.params.friction = 0.2
+    sc.params.friction = mu
     return sc
 
 
