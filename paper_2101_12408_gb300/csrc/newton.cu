@@ -1441,10 +1441,15 @@ __global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_gener
         const SceneDev& S = a.sc[scene[b]];
         const int4 bc = a.coord[slot[b]];
         const long long gb = S.block_base + bc.x + (long long)S.nb[0] * (bc.y + (long long)S.nb[1] * bc.z);
-        const int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
-        for (int i = beg + threadIdx.x; i < end; i += blockDim.x)
-            if (a.phase[i] != 0 || a.cvisc[i] != R(0))
-                particle_general<R>(a, i, ph[b], ua[b], (R)S.dt, (R)S.inv_dx);
+        // lanes take cells, not consecutive particles: particles of one cell share
+        // their 27 nodes, so a warp over consecutive particles would serialise its
+        // shared atomics; 32 distinct cells hit 32 distinct nodes per offset
+        for (int c = threadIdx.x; c < 64; c += blockDim.x) {
+            const int cb = a.cell_start[gb * 64 + c], ce = a.cell_start[gb * 64 + c + 1];
+            for (int i = cb; i < ce; ++i)
+                if (a.phase[i] != 0 || a.cvisc[i] != R(0))
+                    particle_general<R>(a, i, ph[b], ua[b], (R)S.dt, (R)S.inv_dx);
+        }
     }
     static_assert(GEN_B == 2, "the sample loop below selects between two blocks");
     for (int k = threadIdx.x; k < total; k += blockDim.x) {
