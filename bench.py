@@ -54,7 +54,10 @@ UNIT = "steps/s"
 # full workload, from the 20-droplet capture in
 # profiles/apply_cg_kernels_incline20_fp32.md scaled by the units processed:
 # k_apply_cell (188.6 MB, particles and samples) x 8272476 / 5128948 particles
-# plus k_apply_general (0.07 MB) x 317603 / 185006 samples
+# plus k_apply_general (0.07 MB) x 317603 / 185006 samples. k_apply_cell's code
+# is unchanged since that capture. k_apply_general has changed since (its
+# particle loop and the projected solid maps), but this workload gives it no
+# particles: its share is the scan of an empty list.
 NCU_TRAFFIC_BYTES = 304312853
 
 

@@ -628,3 +628,45 @@ def test_massless_samples_lose_momentum_only_through_massless_nodes():
     # massless variant: the nodes touched only by the outer samples carry forces but no mass
     assert out[True][0] > 1e-4
     assert np.any((out[True][1] == 0) & (out[False][1] > 0))
+
+
+# ----------------------------------------------------------------------------
+# Dirichlet conditions (section "Conservation of Mass and Momentum", Eq. vbc:
+# v . n = 0 on slip boundaries, v = 0 on sticky ones) as a per-node projection
+# ----------------------------------------------------------------------------
+
+def test_projector_is_the_orthogonal_projection_onto_admissible_velocities():
+    from oracle.boundary import projector, slip_plane_nodes
+    n = (9, 8, 10)
+    dx = 1.0 / 10
+    walls = (scenes.WALL_SLIP, scenes.WALL_STICKY, scenes.WALL_SLIP, scenes.WALL_NONE,
+             scenes.WALL_NONE, scenes.WALL_SLIP)
+    nrm = np.array([0.3, 0.9, 0.2])
+    nrm /= np.linalg.norm(nrm)
+    d = float(nrm @ np.array([0.45, 0.25, 0.5]))
+    P = projector(n, dx, walls, tuple(nrm), d, scenes.WALL_SLIP)
+    # symmetric and idempotent at every node
+    np.testing.assert_allclose(P, np.swapaxes(P, 1, 2), atol=1e-15)
+    np.testing.assert_allclose(np.einsum("gab,gbc->gac", P, P), P, atol=1e-14)
+    g = np.stack(np.unravel_index(np.arange(P.shape[0]), n, order="F"), -1)
+    xi = oracle.node_positions(n, dx)
+    below = xi @ nrm - d < 0
+    slip_x = g[:, 0] <= 1
+    sticky = g[:, 0] >= n[0] - 2
+    slip_y = g[:, 1] <= 1
+    slip_z = g[:, 2] >= n[2] - 2
+    e = np.eye(3)
+    for k in range(P.shape[0]):
+        walls_here = [a for a, on in enumerate((slip_x[k], slip_y[k], slip_z[k])) if on]
+        if sticky[k] or (below[k] and walls_here) or len(walls_here) == 3:
+            expect = np.zeros((3, 3))
+        elif below[k]:
+            expect = e - np.outer(nrm, nrm)
+        else:
+            expect = e.copy()
+            for a in walls_here:
+                expect[a, a] = 0.0
+        np.testing.assert_allclose(P[k], expect, atol=1e-15)
+    # the friction nodes are exactly the nodes projected by the plane alone
+    plane_only = np.array([np.allclose(P[k], e - np.outer(nrm, nrm)) for k in range(P.shape[0])])
+    np.testing.assert_array_equal(slip_plane_nodes(n, dx, walls, tuple(nrm), d, scenes.WALL_SLIP), plane_only)
