@@ -80,3 +80,16 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.mpm_create(None, 0, 1, None, ctypes.byref(out)) == mpm.MPM_ERR_INVALID_ARG
     assert lib.mpm_resample(None) == mpm.MPM_ERR_INVALID_ARG
     assert lib.mpm_destroy(None) == mpm.MPM_ERR_INVALID_ARG
+
+
+def test_invalid_friction_and_massless_flag_rejected_without_gpu(lib):
+    """mpm_create checks every scene's parameters before any CUDA call."""
+    from paper_2101_12408_gb300 import mpm, scenes
+    sc = scenes.droplet(n=8, r_cells=2.0, seed=1)
+    for field, bad in (("friction", -0.1), ("friction", float("nan")), ("friction", float("inf")),
+                       ("massless_surface", 2), ("massless_surface", -1)):
+        d = mpm.scene_desc(sc)
+        setattr(d.params, field, bad)
+        out = ctypes.c_void_p()
+        assert lib.mpm_create(ctypes.byref(d), 1, 1, None, ctypes.byref(out)) == mpm.MPM_ERR_INVALID_ARG, field
+        assert not out.value
