@@ -37,3 +37,16 @@ def test_film_flat_sheet_exerts_no_tangential_force_on_free_nodes():
             # the two edges' pull, gamma/2 per unit length on each wall layer
             assert np.max(np.abs(f[wall, ax])) > 0.1 * scale
         assert np.isclose(np.sum(np.abs(sc.dA[:, 2])), (sc.n[0] - 2) * (sc.n[1] - 2) * sc.dx ** 2)
+
+
+def test_film_steps_converge_and_stay_slow():
+    """The film at its default (SI water) parameters: Newton converges within a
+    few iterations each step and the flow stays far below a cell per step."""
+    sc = scenes.film(nx=24, ny=24, nz=12, height_cells=4, seed=41)
+    sim = oracle.OracleSim(sc)
+    for _ in range(3):
+        sim.step()
+        assert 0 < sim.stats["newton"] <= 5 and not sim.stats.get("stalled", False)
+        assert sim.stats["residual"][-1] <= sc.params.newton_tol * sim.stats["residual"][0]
+    vmax = np.abs(sim.sc.v).max()
+    assert vmax * sc.params.dt < 0.01 * sc.dx
