@@ -17,7 +17,10 @@ earlier work. Readings used here:
 * the step ends with one explicit evaluation of the grid forces at the
   converged iterate, v = P (v - r(v)/m) = P (v^n + dt g + dt f(x + dt v)/m), so the
   total grid momentum changes by exactly dt sum_i (f_i + m_i g) (the internal
-  forces sum to zero) instead of by the leftover Newton residual.
+  forces sum to zero) instead of by the leftover Newton residual;
+* with a slip plane and a friction coefficient, Coulomb friction acts on that
+  end-of-step velocity at the plane's nodes before the projection (the paper
+  gives only the coefficient, section "Examples"; see boundary.coulomb_plane).
 Heat: CG with the same preconditioner form (diagonal c_p m^T/dt) on the SPD
 heat operator, initial guess T^n.
 """
