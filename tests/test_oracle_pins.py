@@ -367,6 +367,75 @@ def _thermal_scene():
     return sc
 
 
+def test_temperature_transfers_are_exact_for_affine_fields():
+    """Temperature P2G with the gradient term and G2P of T and grad T (section
+    "Transfer: P2G" and the G2P of section "Discretization") reproduce an affine
+    field T = a + g.x exactly: the B-spline weights sum to one and have zero
+    first moment about the particle."""
+    sc = scenes.droplet(n=12, r_cells=3.0, seed=22, thermal=True)
+    a, g = 0.4, np.array([1.5, -0.7, 0.3])
+    sc.T = a + sc.x @ g
+    sc.gradT = np.broadcast_to(g, sc.gradT.shape).copy()
+    out = oracle.p2g(sc.n, sc.dx, sc.x, sc.v, sc.A, sc.m, m=sc.m, T=sc.T, gradT=sc.gradT)
+    xi = oracle.node_positions(sc.n, sc.dx)
+    act = out["mT"] > 0
+    np.testing.assert_allclose(out["mTT"][act] / out["mT"][act], a + xi[act] @ g, atol=1e-13)
+    That = a + xi @ g
+    back = oracle.g2p(sc.n, sc.dx, np.zeros((xi.shape[0], 3)), sc.x, sc.m, sc.m, That=That)
+    np.testing.assert_allclose(back["T"], sc.T, atol=1e-13)
+    np.testing.assert_allclose(back["gradT"], sc.gradT, atol=1e-11)
+
+
+def test_gamma_reads_the_affine_grid_temperature_at_the_samples():
+    """gamma(T) of each sample from the renormalised interpolation of the grid
+    temperature T^n (reading R9): exact for an affine field wherever all of the
+    sample's stencil nodes carry thermal mass, then the linear law."""
+    sc = scenes.droplet(n=12, r_cells=4.0, seed=23, thermal=True)
+    a, g = 0.2, np.array([0.5, 1.0, -0.8])
+    sc.T = a + sc.x @ g
+    sc.gradT = np.broadcast_to(g, sc.gradT.shape).copy()
+    rng = np.random.default_rng(9)
+    c = np.full(3, 0.5)
+    d = rng.standard_normal((40, 3))
+    sc.s = c + d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(0.0, 1.5, (40, 1)) * sc.dx
+    sc.dA = np.tile([0.0, 0.0, sc.dx ** 2], (40, 1))
+    sc.kind = np.zeros(40, np.uint8)
+    sc.b = np.zeros(40)
+    sc.Tbar = np.zeros(40)
+    sc.params.gamma_law = scenes.GAMMA_LINEAR
+    sc.params.gamma_p = (1.0, -0.3, 0.2, 1.1)
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    st = oracle.Stencil(sc.s, sc.dx, sc.n)
+    full = np.all(sim.grid["mT"][st.node] > 0, axis=1)
+    assert full.sum() >= 30
+    Ts = a + sc.s @ g
+    np.testing.assert_allclose(sim.Tr[full], Ts[full], atol=1e-12)
+    np.testing.assert_allclose(sim.gamma[full], np.clip(1.0 - 0.3 * (Ts[full] - sc.params.T0), 0.2, 1.1), atol=1e-12)
+
+
+def test_uniform_heat_source_raises_temperature_by_dt_H_over_rho_cp():
+    """The source term sum_p N_i(x_p) H V^n_p of section "Temperature Update"
+    (reading R4) with no conduction and no boundary flux: every node with
+    thermal mass warms by dt H / (rho c_p)."""
+    sc = scenes.droplet(n=12, r_cells=3.0, seed=24, thermal=True, rho=2.0)
+    sc.T[:] = 0.3
+    sc.gradT[:] = 0.0
+    sc.params.K = 0.0
+    sc.params.h = 0.0
+    sc.b[:] = 0.0
+    sc.params.H = 5.0
+    sc.params.cp = 0.8
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    hs = sim.heat_system()
+    T, _ = oracle.heat_solve(hs, 1e-14, 5000)
+    rise = sc.params.dt * sc.params.H / (2.0 * sc.params.cp)
+    np.testing.assert_allclose(T[hs.unknown], 0.3 + rise, rtol=1e-12)
+
+
 def test_heat_operator_symmetric_spd_and_balance():
     sc = _thermal_scene()
     sim = oracle.OracleSim(sc)
