@@ -436,6 +436,39 @@ def test_uniform_heat_source_raises_temperature_by_dt_H_over_rho_cp():
     np.testing.assert_allclose(T[hs.unknown], 0.3 + rise, rtol=1e-12)
 
 
+def test_affine_grid_motion_moves_particles_and_carries_samples_exactly():
+    """Under an affine grid velocity a + B x the end of a step is a closed form:
+    particles move to x + dt (a + B x), liquids scale J by 1 + dt tr B and solids
+    map F to (I + dt B) F (reading R11); carried samples move the same way and
+    their area vectors follow Nanson's formula det(F) F^-T dA with F = I + dt B
+    (the updated-Lagrangian area map of Eq. pestul, reading R16)."""
+    sc = _mixed_scene()
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    rng = np.random.default_rng(17)
+    a = rng.standard_normal(3)
+    B = rng.standard_normal((3, 3))
+    xi = oracle.node_positions(sc.n, sc.dx)
+    sim.vhat = a + xi @ B.T
+    sim.That = None
+    x0, s0, dA0, J0, F0 = sc.x.copy(), sc.s.copy(), sc.dA.copy(), sc.J.copy(), sc.F.copy()
+    sim.prm.phase_change = False
+    sim.g2p()
+    out = sim.sc
+    dt = sc.params.dt
+    Fm = np.eye(3) + dt * B
+    free = sim.count == 0
+    np.testing.assert_allclose(out.x[free], x0[free] + dt * (a + x0[free] @ B.T), atol=1e-13)
+    liq = free & (sc.phase == 0)
+    sol = free & (sc.phase == 1)
+    np.testing.assert_allclose(out.J[liq], (1 + dt * np.trace(B)) * J0[liq], rtol=1e-12)
+    np.testing.assert_allclose(out.F[sol], np.einsum("ab,pbc->pac", Fm, F0[sol]), atol=1e-12)
+    np.testing.assert_allclose(out.s, s0 + dt * (a + s0 @ B.T), atol=1e-13)
+    nanson = np.linalg.det(Fm) * np.linalg.inv(Fm).T
+    np.testing.assert_allclose(out.dA, dA0 @ nanson.T, atol=1e-14 * np.abs(dA0).max() + 1e-15)
+
+
 def test_heat_operator_symmetric_spd_and_balance():
     sc = _thermal_scene()
     sim = oracle.OracleSim(sc)
