@@ -772,3 +772,64 @@ def test_projector_is_the_orthogonal_projection_onto_admissible_velocities():
     # the friction nodes are exactly the nodes projected by the plane alone
     plane_only = np.array([np.allclose(P[k], e - np.outer(nrm, nrm)) for k in range(P.shape[0])])
     np.testing.assert_array_equal(slip_plane_nodes(n, dx, walls, tuple(nrm), d, scenes.WALL_SLIP), plane_only)
+
+
+# ----------------------------------------------------------------------------
+# Contact angle (section "Contact Angle"): Young's law as the minimum of the
+# surface energy of a resting drop
+# ----------------------------------------------------------------------------
+
+def _cap_energy(theta_deg, volume, k_sl, n, ncap=4000, nbase=2000):
+    """Surface energy at rest (F = I) of a spherical cap of the given volume that
+    meets a horizontal slip plane at theta: liquid-gas samples on the cap, and
+    samples on the wetted disk with area vectors into the plane, classified and
+    weighted by the oracle (reading R13: within dx of the plane is solid-liquid)."""
+    th = math.radians(theta_deg)
+    R = (volume / ((1 - math.cos(th)) ** 2 * (2 + math.cos(th)) * math.pi / 3)) ** (1 / 3)
+    h, a, z0 = R * (1 - math.cos(th)), R * math.sin(th), 0.3
+    c = np.array([0.5, 0.5, z0 - R * math.cos(th)])
+    sc = scenes.droplet(n=n, r_cells=2.0, seed=1, gamma=1.0, lambda_l=0.0)
+    sc.params.gamma_sl = k_sl
+    sc.plane_n, sc.plane_d, sc.plane_mode = (0.0, 0.0, 1.0), z0, scenes.WALL_SLIP
+    gold = math.pi * (3 - math.sqrt(5))
+    k = np.arange(ncap) + 0.5
+    zr = (z0 + k / ncap * h - c[2]) / R          # heights uniform in [z0, top]: uniform area
+    rr = np.sqrt(np.maximum(0.0, 1 - zr * zr))
+    nrm = np.stack([rr * np.cos(k * gold), rr * np.sin(k * gold), zr], -1)
+    kb = np.arange(nbase) + 0.5
+    rb = a * np.sqrt(kb / nbase)
+    base = np.stack([0.5 + rb * np.cos(kb * gold), 0.5 + rb * np.sin(kb * gold), np.full(nbase, z0)], -1)
+    sc.s = np.concatenate([c + R * nrm, base])
+    sc.dA = np.concatenate([nrm * (2 * math.pi * R * h / ncap), np.tile([0.0, 0.0, -math.pi * a * a / nbase], (nbase, 1))])
+    ns = sc.s.shape[0]
+    sc.kind, sc.b, sc.Tbar = np.zeros(ns, np.uint8), np.zeros(ns), np.zeros(ns)
+    rng = np.random.default_rng(0)
+    x = np.array([0.5, 0.5, z0 + 0.5 * h]) + rng.uniform(-0.2, 0.2, (20, 3)) * min(R, h)
+    for key, val in scenes._particles(x, 1.0, sc.dx, 8, rng).items():
+        setattr(sc, key, val)
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    st = sim.newton_state()
+    return st.energy(np.zeros_like(st.vn))      # at rest only the surface term remains
+
+
+@pytest.mark.parametrize("k_sl", [0.5, 0.0])
+def test_static_contact_angle_converges_to_youngs_law(k_sl):
+    """At fixed volume, gamma_LG A_cap + k_SL,eff A_wet is smallest where
+    cos theta = -k_SL,eff / gamma_LG. The oracle's discrete energy (samples,
+    interface kinds, coefficients) has its minimum there up to the width of the
+    solid-liquid band, which shrinks with dx: under 3 degrees at 17 cells of
+    radius. A flipped sign of the solid-liquid coefficient would put it at the
+    supplementary angle."""
+    young = math.degrees(math.acos(-k_sl))
+    volume = 2.0 / 3.0 * math.pi * (10 / 64) ** 3
+    errs = []
+    for n in (64, 128):
+        ths = young + np.arange(-10.0, 10.5, 5.0)
+        es = np.array([_cap_energy(t, volume, k_sl, n) for t in ths])
+        assert np.argmin(es) in (1, 2, 3)
+        q = np.polyfit(ths, es, 2)
+        errs.append(abs(-q[1] / (2 * q[0]) - young))
+    assert errs[1] < 3.0
+    assert errs[1] <= errs[0] + 0.1
