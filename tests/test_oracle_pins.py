@@ -710,11 +710,12 @@ def _one_sided_droplet(massless):
 def test_massless_samples_lose_momentum_only_through_massless_nodes():
     """The paper's point: with massless samples, surface forces that land on nodes
     without mass are dropped, so the step no longer conserves momentum; the
-    split-mass samples with balance particles conserve it."""
+    split-mass samples with balance particles conserve it. Explicit steps, as in
+    the paper's conservation example."""
     out = {}
     for massless in (False, True):
         sc = _one_sided_droplet(massless)
-        sim = oracle.OracleSim(sc)
+        sim = oracle.OracleSim(sc, explicit=True)
         sim.resample()
         sim.p2g()
         m_grid = sim.grid["m"]
