@@ -612,13 +612,22 @@ def test_projected_operator_psd_with_deformed_solids():
     v = st.vn * st.active[:, None]
     idx = np.flatnonzero(st.active)
     ncol = idx.size * 3
+    g = np.stack(np.unravel_index(idx, sc.n, order="F"), -1)
+    colour = (g % 5) @ np.array([1, 5, 25])
     ev = {}
     for mode in (HESS_EXACT, HESS_PROJECTED):
+        # nodes of one colour are 5 apart, farther than any two nodes sharing a
+        # particle (2), so one application per colour and component fills their columns
         H = np.zeros((ncol, ncol))
-        for c in range(ncol):
-            e = np.zeros((st.G, 3))
-            e[idx[c // 3], c % 3] = 1.0
-            H[:, c] = st.hessvec(v, e, mode)[idx].ravel()
+        for col in np.unique(colour):
+            members = np.flatnonzero(colour == col)
+            for q in range(3):
+                e = np.zeros((st.G, 3))
+                e[idx[members], q] = 1.0
+                he = st.hessvec(v, e, mode)
+                for j in members:
+                    near = np.flatnonzero(np.all(np.abs(g - g[j]) <= 2, axis=1))
+                    H[(3 * near[:, None] + np.arange(3)).ravel(), 3 * j + q] = he[idx[near]].ravel()
         np.testing.assert_allclose(H, H.T, atol=1e-10 * np.abs(H).max())
         ev[mode] = np.linalg.eigvalsh(0.5 * (H + H.T))
     mmin = st.m[idx].min()
