@@ -19,8 +19,24 @@ import numpy as np
 from .spline import node_positions
 
 
-def _node_classes(n, dx, walls, plane_n, plane_d, plane_mode):
-    """Fully fixed nodes (G,), slip axes (G, 3) and nodes below the plane (G,)."""
+def sphere_phi_normal(pos, sphere):
+    """Signed distance to a spherical solid and its unit normal into the liquid.
+
+    sphere = (cx, cy, cz, R, solid_outside): with solid_outside the solid is the
+    region |x - c| > R (a bowl holding the liquid), otherwise the ball
+    |x - c| < R. phi < 0 in the solid; the normal is grad phi.
+    """
+    c = np.asarray(sphere[:3], float)
+    R, outside = float(sphere[3]), bool(sphere[4])
+    d = np.asarray(pos, float) - c
+    r = np.linalg.norm(d, axis=-1)
+    u = np.where(r[..., None] > 1e-300, d / np.where(r > 1e-300, r, 1.0)[..., None], np.array([0.0, 0.0, 1.0]))
+    return (R - r, -u) if outside else (r - R, u)
+
+
+def _node_classes(n, dx, walls, plane_n, plane_d, plane_mode, sphere=None, sphere_mode=0):
+    """Fully fixed nodes (G,), slip axes (G, 3), nodes below the plane (G,) and
+    nodes inside the spherical solid (G,)."""
     n = tuple(int(v) for v in n)
     G = n[0] * n[1] * n[2]
     k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
@@ -43,14 +59,23 @@ def _node_classes(n, dx, walls, plane_n, plane_d, plane_mode):
         on_plane = phi < 0
         if plane_mode == 2:
             sticky |= on_plane
+    on_sphere = np.zeros(G, bool)
+    if sphere_mode:
+        phi_s, _ = sphere_phi_normal(node_positions(n, dx), sphere)
+        on_sphere = phi_s < 0
+        if sphere_mode == 2:
+            sticky |= on_sphere
     nslip = slip_axis.sum(1)
-    full = sticky | (on_plane & (nslip > 0)) | (nslip == 3)
-    return full, slip_axis, on_plane
+    # two independent solid normals at one node fix it (plane and sphere, or a solid and a wall)
+    full = (sticky | (on_plane & (nslip > 0)) | (on_sphere & (nslip > 0)) | (on_plane & on_sphere)
+            | (nslip == 3))
+    return full, slip_axis, on_plane, on_sphere
 
 
-def projector(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
+def projector(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0, sphere=None, sphere_mode=0):
     """Per-node projection matrices (G, 3, 3)."""
-    full, slip_axis, on_plane = _node_classes(n, dx, walls, plane_n, plane_d, plane_mode)
+    full, slip_axis, on_plane, on_sphere = _node_classes(n, dx, walls, plane_n, plane_d, plane_mode,
+                                                         sphere, sphere_mode)
     G = full.shape[0]
     P = np.broadcast_to(np.eye(3), (G, 3, 3)).copy()
     for a in range(3):
@@ -61,6 +86,10 @@ def projector(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
         nn = nn / np.linalg.norm(nn)
         sel = on_plane & ~full
         P[sel] = np.eye(3) - np.outer(nn, nn)
+    if sphere_mode == 1:
+        sel = on_sphere & ~full
+        _, nrm = sphere_phi_normal(node_positions(n, dx)[sel], sphere)
+        P[sel] = np.eye(3) - np.einsum("ga,gb->gab", nrm, nrm)
     P[full] = 0.0
     return P
 
@@ -69,10 +98,18 @@ def apply_projector(P, v):
     return np.einsum("gab,gb->ga", P, v)
 
 
-def slip_plane_nodes(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0):
+def slip_plane_nodes(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0, sphere=None,
+                     sphere_mode=0):
     """Nodes whose projection is the slip plane's, I - n n^T (G,) bool."""
-    full, _, on_plane = _node_classes(n, dx, walls, plane_n, plane_d, plane_mode)
+    full, _, on_plane, _ = _node_classes(n, dx, walls, plane_n, plane_d, plane_mode, sphere, sphere_mode)
     return on_plane & ~full if plane_mode == 1 else np.zeros_like(full)
+
+
+def slip_sphere_nodes(n, dx, walls, plane_n=(0.0, 1.0, 0.0), plane_d=0.0, plane_mode=0, sphere=None,
+                      sphere_mode=0):
+    """Nodes whose projection is the spherical solid's, I - n_i n_i^T (G,) bool."""
+    full, _, _, on_sphere = _node_classes(n, dx, walls, plane_n, plane_d, plane_mode, sphere, sphere_mode)
+    return on_sphere & ~full if sphere_mode == 1 else np.zeros_like(full)
 
 
 def coulomb_plane(v, nodes, plane_n, mu):
@@ -85,13 +122,20 @@ def coulomb_plane(v, nodes, plane_n, mu):
     projection. Other nodes are returned unchanged.
     """
     nn = np.asarray(plane_n, float)
-    nn = nn / np.linalg.norm(nn)
+    return coulomb(v, nodes, np.broadcast_to(nn / np.linalg.norm(nn), v.shape), mu)
+
+
+def coulomb(v, nodes, normals, mu):
+    """The same Coulomb rule with one unit solid normal per node (G, 3); the
+    normals of nodes outside `nodes` are not read."""
     out = v.copy()
-    vn = v @ nn
+    vn = np.zeros(v.shape[0])
+    vn[nodes] = np.einsum("ga,ga->g", v[nodes], normals[nodes])
     sel = nodes & (vn < 0.0)
-    t = v[sel] - vn[sel, None] * nn
+    nsel = normals[sel]
+    t = v[sel] - vn[sel, None] * nsel
     tl = np.linalg.norm(t, axis=1)
     lim = -mu * vn[sel]
     s = np.where(tl > lim, 1.0 - lim / np.where(tl > 0, tl, 1.0), 0.0)
-    out[sel] = s[:, None] * t + vn[sel, None] * nn
+    out[sel] = s[:, None] * t + vn[sel, None] * nsel
     return out

@@ -26,7 +26,7 @@ heat operator, initial guess T^n.
 """
 import numpy as np
 
-from .boundary import apply_projector, coulomb_plane
+from .boundary import apply_projector, coulomb
 from .energy import HESS_PROJECTED
 
 
@@ -62,8 +62,9 @@ def pcg(apply, b, precond, rtol, maxit, neg_curv_exit=True):
 def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False, friction=None):
     """Returns the end-of-step grid velocity and a stats dict.
 
-    friction: None, or (plane nodes (G,) bool, plane normal, mu) for the slip
-    plane's Coulomb friction on the end-of-step velocity before the projection.
+    friction: None, or (solid nodes (G,) bool, their unit normals (G, 3), mu) for
+    the slip solids' Coulomb friction on the end-of-step velocity before the
+    projection.
     """
     m = state.m
     act = state.active
@@ -113,8 +114,8 @@ def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False, fricti
     r = state.gradient(v)
     v = v - r * inv_m[:, None]
     if friction is not None:
-        nodes, nrm, mu = friction
-        v = coulomb_plane(v, nodes & act, nrm, mu)
+        nodes, normals, mu = friction
+        v = coulomb(v, nodes & act, normals, mu)
     v = proj(v)
     return v, stats
 

@@ -36,13 +36,13 @@ Readings:
 """
 import numpy as np
 
-from .boundary import projector, slip_plane_nodes
+from .boundary import projector, slip_plane_nodes, slip_sphere_nodes, sphere_phi_normal
 from .constitutive import cof
 from .energy import NewtonState, HESS_PROJECTED
 from .heat import HeatSystem
 from .resample import split
 from .solver import newton_solve, heat_solve
-from .spline import Stencil
+from .spline import Stencil, node_positions
 from .surface import generate
 from .transfer import p2g, g2p, grid_velocity
 
@@ -75,12 +75,20 @@ class OracleSim:
         self.hess_mode = hess_mode
         self.explicit = explicit
         sc = self.sc
-        self.P = projector(sc.n, sc.dx, sc.walls, sc.plane_n, sc.plane_d, sc.plane_mode)
+        solid = (sc.plane_n, sc.plane_d, sc.plane_mode, sc.sphere, sc.sphere_mode)
+        self.P = projector(sc.n, sc.dx, sc.walls, *solid)
         self.G = int(np.prod(sc.n))
         self.friction = None
-        if self.prm.friction > 0.0 and sc.plane_mode == 1:
-            nodes = slip_plane_nodes(sc.n, sc.dx, sc.walls, sc.plane_n, sc.plane_d, sc.plane_mode)
-            self.friction = (nodes, sc.plane_n, self.prm.friction)
+        if self.prm.friction > 0.0 and (sc.plane_mode == 1 or sc.sphere_mode == 1):
+            on_p = slip_plane_nodes(sc.n, sc.dx, sc.walls, *solid)
+            on_s = slip_sphere_nodes(sc.n, sc.dx, sc.walls, *solid)
+            normals = np.zeros((self.G, 3))
+            if sc.plane_mode == 1:
+                nn = np.asarray(sc.plane_n, float)
+                normals[on_p] = nn / np.linalg.norm(nn)
+            if sc.sphere_mode == 1:
+                normals[on_s] = sphere_phi_normal(node_positions(sc.n, sc.dx)[on_s], sc.sphere)[1]
+            self.friction = (on_p | on_s, normals, self.prm.friction)
         # the massless-sample variant: samples carry no mass, no balance particles
         self.massless = bool(self.prm.massless_surface)
 
@@ -97,9 +105,13 @@ class OracleSim:
     # (1) resample
     def resample(self):
         sc = self.sc
-        if sc.plane_mode:
-            phi = sc.s @ np.asarray(sc.plane_n) - sc.plane_d
-            sc.kind = np.where(phi < sc.dx, 1, 0).astype(np.uint8)
+        if sc.plane_mode or sc.sphere_mode:
+            near = np.zeros(sc.s.shape[0], bool)
+            if sc.plane_mode:
+                near |= sc.s @ np.asarray(sc.plane_n) - sc.plane_d < sc.dx
+            if sc.sphere_mode:
+                near |= sphere_phi_normal(sc.s, sc.sphere)[0] < sc.dx
+            sc.kind = near.astype(np.uint8)
         self.parent, self.count, self.mt, self.bpos = split(sc.x, sc.m, sc.s)
         if self.massless:
             self.mt = sc.m.copy()

@@ -143,6 +143,8 @@ def _f64(a):
 
 
 def scene_desc(sc, max_particles=None, max_surface=None, max_blocks=0):
+    if getattr(sc, "sphere_mode", 0):
+        raise NotImplementedError("spherical solids are not on the device path")
     p = sc.params
     d = SceneDesc()
     d.grid.n[:] = [int(v) for v in sc.n]

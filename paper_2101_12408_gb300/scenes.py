@@ -78,6 +78,10 @@ class Scene:
     plane_n: tuple = (0.0, 1.0, 0.0)  # solid plane phi(x) = n.x - d (solid where phi < 0)
     plane_d: float = 0.0
     plane_mode: int = WALL_NONE
+    # spherical solid (cx, cy, cz, R, solid_outside): a bowl when solid_outside, else a ball;
+    # the oracle takes it, the device path does not yet
+    sphere: tuple = None
+    sphere_mode: int = WALL_NONE
     # particles (float64)
     x: np.ndarray = None
     v: np.ndarray = None

@@ -93,3 +93,13 @@ def test_invalid_friction_and_massless_flag_rejected_without_gpu(lib):
         out = ctypes.c_void_p()
         assert lib.mpm_create(ctypes.byref(d), 1, 1, None, ctypes.byref(out)) == mpm.MPM_ERR_INVALID_ARG, field
         assert not out.value
+
+
+def test_spherical_solid_is_refused_by_the_device_binding():
+    """The spherical solid exists in the oracle only: the binding refuses it
+    instead of running the scene without it."""
+    from paper_2101_12408_gb300 import mpm, scenes
+    sc = scenes.droplet(n=8, r_cells=2.0, seed=1)
+    sc.sphere, sc.sphere_mode = (0.5, 0.5, 0.5, 0.3, True), scenes.WALL_SLIP
+    with pytest.raises(NotImplementedError):
+        mpm.scene_desc(sc)

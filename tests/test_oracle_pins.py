@@ -843,3 +843,80 @@ def test_static_contact_angle_converges_to_youngs_law(k_sl):
         errs.append(abs(-q[1] / (2 * q[0]) - young))
     assert errs[1] < 3.0
     assert errs[1] <= errs[0] + 0.1
+
+
+# ----------------------------------------------------------------------------
+# Curved solids (the glass of section "Examples"): a spherical level set
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("outside", [True, False])
+def test_sphere_projector_removes_the_local_normal(outside):
+    from oracle.boundary import projector, sphere_phi_normal
+    n, dx = (12, 12, 12), 1.0 / 12
+    sphere = (0.5, 0.52, 0.47, 0.31, outside)
+    walls = (scenes.WALL_SLIP,) + (scenes.WALL_NONE,) * 5
+    P = projector(n, dx, walls, sphere=sphere, sphere_mode=scenes.WALL_SLIP)
+    xi = oracle.node_positions(n, dx)
+    phi, nrm = sphere_phi_normal(xi, sphere)
+    g = np.stack(np.unravel_index(np.arange(P.shape[0]), n, order="F"), -1)
+    # the normal is the unit gradient of phi (central differences of the distance)
+    h = 1e-6
+    fd = np.stack([(sphere_phi_normal(xi + h * e, sphere)[0] - sphere_phi_normal(xi - h * e, sphere)[0]) / (2 * h)
+                   for e in np.eye(3)], -1)
+    np.testing.assert_allclose(fd, nrm, atol=1e-6)
+    solid = phi < 0
+    wall = g[:, 0] <= 1
+    assert solid.sum() > 50 and (~solid).sum() > 50
+    np.testing.assert_allclose(P, np.swapaxes(P, 1, 2), atol=1e-15)
+    np.testing.assert_allclose(np.einsum("gab,gbc->gac", P, P), P, atol=1e-14)
+    s = solid & ~wall
+    np.testing.assert_allclose(P[s], np.eye(3) - np.einsum("ga,gb->gab", nrm[s], nrm[s]), atol=1e-15)
+    np.testing.assert_array_equal(P[solid & wall], 0.0)
+    np.testing.assert_allclose(P[~solid & ~wall], np.broadcast_to(np.eye(3), P[~solid & ~wall].shape), atol=0)
+
+
+def _block_in_bowl(r_cells, mu, alpha_deg=30.0):
+    """A few particles inside a spherical bowl's wall, at polar angle alpha from
+    its lowest point, deep enough that every node of their stencils is solid."""
+    n = 64
+    dx = 1.0 / n
+    c = np.array([0.5, 0.5, 0.55])
+    R = r_cells * dx
+    sc = scenes.droplet(n=n, r_cells=1.0, seed=25, gravity=(0.0, 0.0, -9.8), lambda_l=0.0, gamma=0.0)
+    sc.sphere, sc.sphere_mode = (c[0], c[1], c[2], R, True), scenes.WALL_SLIP
+    sc.params.friction = mu
+    a = math.radians(alpha_deg)
+    p0 = c + (R + 4.0 * dx) * np.array([math.sin(a), 0.0, -math.cos(a)])
+    rng = np.random.default_rng(8)
+    x = p0 + rng.uniform(-0.3, 0.3, (8, 3)) * dx
+    for key, val in scenes._particles(x, 1.0, dx, 8, rng).items():
+        setattr(sc, key, val)
+    sc.s, sc.dA = np.zeros((0, 3)), np.zeros((0, 3))
+    sc.kind, sc.b, sc.Tbar = np.zeros(0, np.uint8), np.zeros(0), np.zeros(0)
+    return sc
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.2])
+def test_block_in_a_bowl_slides_as_on_its_tangent_plane(mu):
+    """One step from rest: each particle moves as a block on the incline tangent
+    to the bowl at its own position, a = g (sin alpha - mu cos alpha) down the
+    slope. The node normals vary over the stencil, but their first-order
+    variation cancels (the weights have zero first moment about the particle),
+    so the error falls with the square of dx / R."""
+    from oracle.boundary import sphere_phi_normal
+    err = []
+    for r_cells in (10.0, 20.0):
+        sc = _block_in_bowl(r_cells, mu)
+        sim = oracle.OracleSim(sc)
+        sim.step()
+        g = np.array(sc.params.gravity)
+        _, nrm = sphere_phi_normal(sc.x, sc.sphere)
+        gn = nrm @ g
+        gt = g - gn[:, None] * nrm
+        lt = np.linalg.norm(gt, axis=1)
+        expect = sc.params.dt * np.maximum(0.0, 1.0 - mu * np.abs(gn) / lt)[:, None] * gt
+        err.append(np.abs(sim.sc.v - expect).max() / (sc.params.dt * 9.8))
+    # the particles sit 4 cells into the wall: radii of curvature 14 and 24 cells, so
+    # second order gives a ratio (14/24)^2 = 0.34 (first order would give 0.58)
+    assert err[1] < 2e-3
+    assert err[1] < 0.45 * err[0]
