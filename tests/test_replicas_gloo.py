@@ -54,3 +54,21 @@ def test_job_rate_single_process_is_local():
     assert not dist.is_initialized()
     rate, t = bench.job_rate(3, 150.0)
     assert rate == pytest.approx(20.0) and t == 150.0
+
+
+def test_reference_arm_under_torchrun_prints_once_from_rank_zero():
+    """Launched like the multi-GPU bench (torchrun, two ranks), the oracle arm
+    runs on rank 0 alone and prints exactly one JSON line; rank 1 exits 0
+    without work."""
+    import json
+    import subprocess
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--workload", "droplet"]
+    res = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    lines = [ln for ln in res.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
