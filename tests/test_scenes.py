@@ -50,3 +50,13 @@ def test_film_steps_converge_and_stay_slow():
         assert sim.stats["residual"][-1] <= sc.params.newton_tol * sim.stats["residual"][0]
     vmax = np.abs(sim.sc.v).max()
     assert vmax * sc.params.dt < 0.01 * sc.dx
+
+
+def test_benchmark_inputs_have_the_documented_sizes():
+    """The seeded generators give the particle and sample counts the input
+    recipe states, so every measurement refers to the same inputs."""
+    d = scenes.config(0)
+    assert (d.n_particles, d.n_surface) == (17184, 1608)
+    f = scenes.config(1)
+    assert (f.n_particles, f.n_surface) == (738048, 31752)
+    assert f.params.rho == 1000.0 and f.params.lambda_l == 1e6
