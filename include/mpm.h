@@ -150,7 +150,11 @@ const char* mpm_last_error(const mpm_ctx* ctx);
 
 /* Interior particles of one scene (section "Discretization": x, J, v, A, V0, m,
  * T, grad T, plus F and the phase for solids). phase: 0 liquid, 1 solid.
- * Any pointer except x, m, V0 may be NULL (zeros; J = 1, F = I, phase liquid). */
+ * Any pointer except x, m, V0 may be NULL (zeros; J = 1, F = I, phase liquid).
+ * Arrays are row-major (x: n x 3, A and F: n x 3 x 3) in host or device memory;
+ * the call copies them and returns once the caller may reuse them. Host arrays
+ * in page-locked memory are copied by DMA at the link's speed, pageable ones
+ * through a staging copy. */
 mpm_status mpm_set_particles(mpm_ctx* ctx, int32_t scene, int64_t n, const double* x,
                              const double* v, const double* A, const double* m,
                              const double* V0, const double* J, const double* F,
