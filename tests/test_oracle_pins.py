@@ -920,3 +920,26 @@ def test_block_in_a_bowl_slides_as_on_its_tangent_plane(mu):
     # second order gives a ratio (14/24)^2 = 0.34 (first order would give 0.58)
     assert err[1] < 2e-3
     assert err[1] < 0.45 * err[0]
+
+
+def test_sphere_sticky_nodes_and_solid_liquid_samples():
+    """A sticky sphere fixes its solid nodes; samples within dx of the sphere's
+    solid are solid-liquid and take the effective coefficient (reading R13 with
+    the sphere's signed distance)."""
+    from oracle.boundary import projector, sphere_phi_normal
+    n, dx = (16, 16, 16), 1.0 / 16
+    sphere = (0.5, 0.5, 0.5, 0.35, True)
+    P = projector(n, dx, (scenes.WALL_NONE,) * 6, sphere=sphere, sphere_mode=scenes.WALL_STICKY)
+    phi, _ = sphere_phi_normal(oracle.node_positions(n, dx), sphere)
+    np.testing.assert_array_equal(P[phi < 0], 0.0)
+    np.testing.assert_array_equal(P[phi >= 0], np.broadcast_to(np.eye(3), P[phi >= 0].shape))
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=26, gamma=1.0)
+    sc.params.gamma_sl = 0.4
+    sc.sphere, sc.sphere_mode = (0.5 + 1.0 / 16, 0.5, 0.5, 5.0 / 16, True), scenes.WALL_SLIP
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    near = sphere_phi_normal(sc.s, sc.sphere)[0] < sc.dx
+    assert near.any() and (~near).any()
+    np.testing.assert_array_equal(sim.sc.kind, near.astype(np.uint8))
+    np.testing.assert_allclose(sim.gamma, np.where(near, 0.4, 1.0))
