@@ -943,3 +943,130 @@ def test_sphere_sticky_nodes_and_solid_liquid_samples():
     assert near.any() and (~near).any()
     np.testing.assert_array_equal(sim.sc.kind, near.astype(np.uint8))
     np.testing.assert_allclose(sim.gamma, np.where(near, 0.4, 1.0))
+
+
+# ----------------------------------------------------------------------------
+# The surface part of the definiteness fix (section "Momentum Update": the
+# projected Hessian keeps the Gauss-Newton term and the positive, conformal part
+# of the cofactor curvature). The split into conformal and anti-conformal parts
+# depends on the relative orientation of the frames of n and a: the pins below fail
+# if one frame is flipped, if the anti-conformal combination is kept, or if the
+# positive part is scaled wrongly (each checked by planting it in the oracle).
+# ----------------------------------------------------------------------------
+
+def _cof_apply(X, a):
+    """cof(X) a written as (X u) x (X w) for any u, w with u x w = a (no epsilon
+    tensor, no inverse, so it also holds for singular X)."""
+    an = np.linalg.norm(a)
+    u = np.cross(a, [1.0, 0.3, -0.2])
+    u /= np.linalg.norm(u)
+    w = np.cross(a / an, u) * an          # u x w = u x (a x u) |a|/|a| = a (u unit, u . a = 0)
+    return np.cross(X @ u, X @ w), u, w
+
+
+def _rotation(rng):
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    return q if np.linalg.det(q) > 0 else -q
+
+
+def _one_sample_state(Fh, a, gamma, dt=0.01):
+    """A NewtonState with one surface sample whose iterate gives F^ = Fh, and one
+    particle with no stiffness (so only the sample acts; the nodes carry no mass)."""
+    n, dx = (8, 8, 8), 1.0 / 8
+    s = np.array([[0.43, 0.51, 0.47]])
+    x = np.array([[0.5, 0.5, 0.5]])
+    one = np.ones(1)
+    st = oracle.NewtonState(n, dx, dt, np.zeros(3), np.zeros(512), np.zeros((512, 3)), x, one * dx ** 3,
+                            one, np.eye(3)[None], np.zeros(1, np.int64), 0.0, 0.0, np.zeros(1), np.zeros(1),
+                            s, a[None], np.array([gamma]))
+    xi = oracle.node_positions(n, dx)
+    v = (xi - s) @ ((Fh - np.eye(3)) / dt).T     # affine: F^ = I + dt L(s) = Fh exactly
+    return st, v, xi, s[0]
+
+
+def _sample_map(st, v, xi, s, X, mode):
+    """The sample's dG for dF^ = X: an affine direction dv_i = X (x_i - s) has
+    dF^ = X exactly, and sum_i out_i (x_i - s)^T = dt^2 dG because
+    sum_i gradN_i (x_i - s)^T = I (spline moment identity)."""
+    dv = (xi - s) @ X.T
+    out = st.hessvec(v, dv, mode)
+    return out.T @ (xi - s) / st.dt ** 2
+
+
+def test_conformal_frames_reproduce_the_cofactor_curvature():
+    """n . cof(X) a = |a| det[t_i . X s_j] with the oracle's right-handed frames."""
+    from oracle.energy import _frame
+    rng = np.random.default_rng(31)
+    for _ in range(50):
+        X = rng.standard_normal((3, 3))
+        nrm = rng.standard_normal(3)
+        nrm /= np.linalg.norm(nrm)
+        a = rng.standard_normal(3) * rng.uniform(0.1, 3.0)
+        lhs = nrm @ _cof_apply(X, a)[0]
+        t1, t2 = _frame(nrm[None])
+        s1, s2 = _frame((a / np.linalg.norm(a))[None])
+        x = np.array([[t[0] @ X @ sv[0] for sv in (s1, s2)] for t in (t1, t2)])
+        assert abs(lhs - np.linalg.norm(a) * np.linalg.det(x)) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_projected_surface_term_keeps_the_conformal_and_drops_the_anticonformal_curvature():
+    rng = np.random.default_rng(32)
+    for trial in range(6):
+        Fh = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+        a = rng.standard_normal(3) * 0.02
+        gamma = rng.uniform(0.2, 2.0)
+        st, v, xi, s = _one_sample_state(Fh, a, gamma)
+        c = _cof_apply(Fh, a)[0]
+        nrm = c / np.linalg.norm(c)
+        # tangential frames of n and a/|a|, built here from a random rotation (the
+        # conformal span does not depend on the in-plane angle, only on handedness)
+        R1, R2 = _rotation(rng), _rotation(rng)
+        t1 = np.cross(nrm, R1[0]); t1 /= np.linalg.norm(t1); t2 = np.cross(nrm, t1)
+        ah = a / np.linalg.norm(a)
+        s1 = np.cross(ah, R2[0]); s1 /= np.linalg.norm(s1); s2 = np.cross(ah, s1)
+        conf = [np.outer(t1, s1) + np.outer(t2, s2), np.outer(t1, s2) - np.outer(t2, s1)]
+        anti = [np.outer(t1, s1) - np.outer(t2, s2), np.outer(t1, s2) + np.outer(t2, s1)]
+        al, be = rng.standard_normal(2)
+        Xc = al * conf[0] + be * conf[1]
+        Xa = al * anti[0] + be * anti[1]
+        scale = gamma * np.linalg.norm(a) * np.linalg.norm(Xc)
+        # conformal directions: projected == exact
+        mE = _sample_map(st, v, xi, s, Xc, HESS_EXACT)
+        mP = _sample_map(st, v, xi, s, Xc, HESS_PROJECTED)
+        np.testing.assert_allclose(mP, mE, atol=1e-10 * scale)
+        # anti-conformal directions: projected == exact minus the whole curvature,
+        # gamma K[X] with K[X] = grad_X (n . cof(X) a) = ((X w) x n) u^T + (n x (X u)) w^T
+        _, u, w = _cof_apply(Xa, a)
+        K = np.outer(np.cross(Xa @ w, nrm), u) + np.outer(np.cross(nrm, Xa @ u), w)
+        mE = _sample_map(st, v, xi, s, Xa, HESS_EXACT)
+        mP = _sample_map(st, v, xi, s, Xa, HESS_PROJECTED)
+        np.testing.assert_allclose(mE - mP, gamma * K, atol=1e-10 * scale)
+        # ... and what remains is the Gauss-Newton form gamma |(I - n n^T) dc|^2 / |c|,
+        # dc = (X u) x (F^ w) + (F^ u) x (X w)
+        _, u, w = _cof_apply(Fh, a)
+        dc = np.cross(Xa @ u, Fh @ w) + np.cross(Fh @ u, Xa @ w)
+        dcp = dc - nrm * (nrm @ dc)
+        np.testing.assert_allclose(np.sum(Xa * mP), gamma * dcp @ dcp / np.linalg.norm(c),
+                                   rtol=1e-10, atol=1e-12 * scale * np.linalg.norm(Xa))
+
+
+def test_exact_minus_projected_surface_term_is_negative_semidefinite():
+    """Per sample, in dF^ space: exact - projected = -gamma |a| times the projector on
+    the anti-conformal plane, so two eigenvalues -gamma |a| and seven zeros."""
+    rng = np.random.default_rng(33)
+    for trial in range(4):
+        Fh = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+        a = rng.standard_normal(3) * 0.05
+        gamma = rng.uniform(0.2, 2.0)
+        st, v, xi, s = _one_sample_state(Fh, a, gamma)
+        D = np.zeros((9, 9))
+        for k in range(9):
+            E = np.zeros(9)
+            E[k] = 1.0
+            E = E.reshape(3, 3)
+            D[:, k] = (_sample_map(st, v, xi, s, E, HESS_EXACT) - _sample_map(st, v, xi, s, E, HESS_PROJECTED)).ravel()
+        ga = gamma * np.linalg.norm(a)
+        np.testing.assert_allclose(D, D.T, atol=1e-10 * ga)
+        ev = np.sort(np.linalg.eigvalsh(0.5 * (D + D.T)))
+        np.testing.assert_allclose(ev, [-ga, -ga] + [0.0] * 7, atol=1e-9 * ga)
