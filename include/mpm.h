@@ -63,8 +63,11 @@ typedef enum {
 
 typedef enum {
     MPM_HESS_EXACT = 0,      /* exact second derivative of the objective */
-    MPM_HESS_PROJECTED = 1   /* the operator the Newton-CG uses: surface term reduced to
-                                its positive semi-definite Gauss-Newton part */
+    MPM_HESS_PROJECTED = 1   /* the operator the Newton-CG uses (the paper's "definiteness
+                                fix"): each surface sample keeps its Gauss-Newton term and the
+                                positive (conformal) part of the cofactor curvature; each solid
+                                particle's 9x9 Hessian of psi(F) has its negative eigenvalues
+                                set to zero; liquid, viscous and mass terms are unchanged */
 } mpm_hess_mode;
 
 typedef enum { MPM_WALL_NONE = 0, MPM_WALL_SLIP = 1, MPM_WALL_STICKY = 2 } mpm_wall;
@@ -290,26 +293,30 @@ mpm_status mpm_get_profile(mpm_ctx* ctx, mpm_profile* out);
 /* Closest interior particle of each surface sample, computed without allocating.
  *
  * The paper has no counterpart of this entry point: it serves callers that cannot
- * allocate device memory (code inside a CUDA graph being captured, allocators that
- * forbid cudaMalloc after start-up, hosts that give the library a fixed memory
- * budget) and so cannot create a context. It returns the same parents as
- * mpm_resample: for sample r the index (into x) of the particle with the smallest
- * squared distance, formed as (dx^2 + dy^2) + dz^2 in float64, ties to the smaller
- * index, searched over the 27 cells around the sample.
+ * allocate device memory (allocators that forbid cudaMalloc after start-up, hosts
+ * that give the library a fixed memory budget) and so cannot create a context. It
+ * returns the same parents as mpm_resample: for sample r the index (into x) of the
+ * particle with the smallest squared distance, formed as (dx^2 + dy^2) + dz^2 in
+ * float64, ties to the smaller index, searched over the 27 cells around the sample
+ * and, when none of them holds a particle within dx, over the 125 cells around it.
  *
  * x: n_particles x 3 float64, s: n_samples x 3 float64, parent: n_samples int32, all
  * in memory the device can read / write (device memory, or host memory the device can
  * access); grid: only n, dx and origin are read. stream: a cudaStream_t or NULL.
  * Limits: n_particles <= 524288 and n0 n1 n2 <= 1048576 cells, else MPM_ERR_CAPACITY.
  * Particles must lie in cells 1 .. n-2 and every sample must have a particle within
- * dx, else MPM_ERR_DOMAIN (parent = -1 for such samples).
+ * 2 dx (the reach of mpm_resample), else MPM_ERR_DOMAIN (parent = -1 for such
+ * samples).
  *
  * Working memory is one fixed device array in the library (about 12.6 MB on every
  * GPU that loads the library, held until the process exits); nothing is allocated or
- * freed. The first call on a device looks up that array's device address; make that
- * first call before any stream capture. Every call reuses the same array, so calls
- * whose work overlaps on the GPU (different streams, or different host threads)
- * race: serialise them. The call synchronises `stream` before returning. */
+ * freed. The first call on a device looks up that array's device address and keeps it
+ * for the life of the process; make that first call before any stream capture, and
+ * do not call this entry point again after a reset of the device (cudaDeviceReset),
+ * which the kept address does not survive. Every call reuses the same array and
+ * clears the parts that must start at zero, so calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race: serialise them. The call
+ * reads a status word back and synchronises `stream` before returning. */
 mpm_status mpm_nearest_parent_noalloc(const mpm_grid_desc* grid, int64_t n_particles, const double* x,
                                       int64_t n_samples, const double* s, int32_t* parent, void* stream);
 

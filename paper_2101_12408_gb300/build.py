@@ -42,9 +42,7 @@ def _stale(obj, src, headers):
 def build(verbose=False, extra_flags=()):
     os.makedirs(BUILD, exist_ok=True)
     headers = _headers()
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--use_fast_math=false",
-             "-I", INCLUDE, *ARCH, *extra_flags]
-    flags = [f for f in flags if f != "--use_fast_math=false"]
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, *ARCH, *extra_flags]
     jobs = []
     objs = []
     for s in SOURCES:

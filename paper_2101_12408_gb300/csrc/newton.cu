@@ -103,16 +103,6 @@ __device__ __forceinline__ void add_conformal(R k, const R* n, const R* a, const
 }
 
 template <typename R>
-__device__ __forceinline__ void load_halo_vec(const int* __restrict__ nbr, int slot, const R* __restrict__ vec, R (*sh)[HN]) {
-    for (int t = threadIdx.x; t < 3 * HN; t += blockDim.x) {
-        int c = t / HN, h = t % HN;
-        int ns, loc;
-        halo_source(nbr, slot, h, ns, loc);
-        sh[c][h] = ns < 0 ? R(0) : vec[ns * 192 + c * 64 + loc];
-    }
-}
-
-template <typename R>
 __device__ __forceinline__ void load_halo_vec_d(const int* __restrict__ nbr, int slot, const double* __restrict__ vec, R (*sh)[HN]) {
     // The halo is stored relative to the velocity of the block's first node,
     // subtracted in float64: velocity gradients sum_i v_i gradN_i^T are unchanged
@@ -547,149 +537,6 @@ struct ApplyArgs {
     int mode;
     int check_done;
 };
-
-template <typename R>
-__global__ void __launch_bounds__(NT) k_apply(ApplyArgs<R> a) {
-    __shared__ R ph[3][HN];
-    __shared__ R ua[3][HN];
-    int w = blockIdx.x;
-    int slot = a.work[w];
-    long long gb = a.work_gb[w];
-    int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    if (a.check_done && a.scal[bc.w].cg_done) return;
-    load_halo_vec<R>(a.nbr, slot, a.p, ph);
-    for (int t = threadIdx.x; t < 3 * HN; t += NT) (&ua[0][0])[t] = R(0);
-    __syncthreads();
-    const R dt = (R)S.dt;
-    const R inv_dx = (R)S.inv_dx;
-    int beg = a.cell_start[gb * 64], end = a.cell_start[gb * 64 + 64];
-    for (int i = beg + threadIdx.x; i < end; i += NT) {
-        int lc[3];
-        R wgt[3][3], dw[3][3];
-        make_stencil_local<R>(a.pu.a[0][i], a.pu.a[1][i], a.pu.a[2][i], inv_dx, lc, wgt, dw);
-        bool liq = a.phase[i] == 0;
-        R cv = liq ? a.cvisc[i] : R(0);
-        bool full = !liq || cv != R(0);
-        R dL[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        R tr = 0;
-        if (full) {
-            for (int cz = 0; cz < 3; ++cz)
-                for (int cy = 0; cy < 3; ++cy)
-                    for (int cx = 0; cx < 3; ++cx) {
-                        int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                        R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                                   wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            R pq = ph[q][h];
-                            dL[3 * q] += pq * dN[0];
-                            dL[3 * q + 1] += pq * dN[1];
-                            dL[3 * q + 2] += pq * dN[2];
-                        }
-                    }
-            tr = dL[0] + dL[4] + dL[8];
-        } else {
-            for (int cz = 0; cz < 3; ++cz)
-                for (int cy = 0; cy < 3; ++cy)
-                    for (int cx = 0; cx < 3; ++cx) {
-                        int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                        tr += ph[0][h] * dw[0][cx] * wgt[1][cy] * wgt[2][cz] + ph[1][h] * wgt[0][cx] * dw[1][cy] * wgt[2][cz] +
-                              ph[2][h] * wgt[0][cx] * wgt[1][cy] * dw[2][cz];
-                    }
-        }
-        R M[9];
-        if (liq) {
-            R s = a.kappa[i] * tr;
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-#pragma unroll
-                for (int e = 0; e < 3; ++e) M[3 * q + e] = cv * R(0.5) * (dL[3 * q + e] + dL[3 * e + q]) + (q == e ? s : R(0));
-        } else {
-            R Fo[9], Fc[9], Rm[9], K[6], dF[9], dP[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                Fo[q] = a.Fn.a[q][i];
-                Fc[q] = a.scache.a[q][i];
-                Rm[q] = a.scache.a[9 + q][i];
-            }
-#pragma unroll
-            for (int q = 0; q < 6; ++q) K[q] = a.scache.a[18 + q][i];
-            matmul3<R>(dL, Fo, dF);
-            fcr_dP<R>(Fc, Rm, K, a.lmu[i], a.llam[i], dF, dP);
-            matmul3_bt<R>(dP, Fo, M);
-            R sc = dt * dt * (R)a.V0[i];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) M[q] *= sc;
-        }
-        for (int cz = 0; cz < 3; ++cz)
-            for (int cy = 0; cy < 3; ++cy)
-                for (int cx = 0; cx < 3; ++cx) {
-                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], M[3 * q] * dN[0] + M[3 * q + 1] * dN[1] + M[3 * q + 2] * dN[2]);
-                }
-    }
-    int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
-    for (int j = sbeg + threadIdx.x; j < send; j += NT) {
-        int lc[3];
-        R wgt[3][3], dw[3][3];
-        make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
-        R dFh[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int cz = 0; cz < 3; ++cz)
-            for (int cy = 0; cy < 3; ++cy)
-                for (int cx = 0; cx < 3; ++cx) {
-                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        R pq = ph[q][h];
-                        dFh[3 * q] += pq * dN[0];
-                        dFh[3 * q + 1] += pq * dN[1];
-                        dFh[3 * q + 2] += pq * dN[2];
-                    }
-                }
-        R Fh[9], av[3], nv[3];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) Fh[q] = a.sF.a[q][j];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            av[q] = a.sa.a[q][j];
-            nv[q] = a.sn.a[q][j];
-        }
-        R k = a.sg[j], ic = a.sic[j];
-        R dC[9];
-        dcofactor<R>(Fh, dFh, dC);
-        R dc[3] = {dC[0] * av[0] + dC[1] * av[1] + dC[2] * av[2], dC[3] * av[0] + dC[4] * av[1] + dC[5] * av[2],
-                   dC[6] * av[0] + dC[7] * av[1] + dC[8] * av[2]};
-        R nd = nv[0] * dc[0] + nv[1] * dc[1] + nv[2] * dc[2];
-        R dn[3] = {(dc[0] - nd * nv[0]) * ic, (dc[1] - nd * nv[1]) * ic, (dc[2] - nd * nv[2]) * ic};
-        R G[9];
-        surf_G<R>(k * dt * dt, dn, Fh, av, G);
-        if (a.mode == MPM_HESS_EXACT) {
-            R G2[9];
-            surf_G<R>(k * dt * dt, nv, dFh, av, G2);
-#pragma unroll
-            for (int q = 0; q < 9; ++q) G[q] += G2[q];
-        } else {
-            add_conformal<R>(k * dt * dt, nv, av, dFh, G);
-        }
-        for (int cz = 0; cz < 3; ++cz)
-            for (int cy = 0; cy < 3; ++cy)
-                for (int cx = 0; cx < 3; ++cx) {
-                    int h = halo_index(lc[0] + cx, lc[1] + cy, lc[2] + cz);
-                    R dN[3] = {dw[0][cx] * wgt[1][cy] * wgt[2][cz], wgt[0][cx] * dw[1][cy] * wgt[2][cz],
-                               wgt[0][cx] * wgt[1][cy] * dw[2][cz]};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) atomicAdd(&ua[q][h], G[3 * q] * dN[0] + G[3 * q + 1] * dN[1] + G[3 * q + 2] * dN[2]);
-                }
-    }
-    __syncthreads();
-    flush_halo_vec<R>(a.nbr, slot, ua, a.u);
-}
 
 // ======================================================================
 // Hessian-vector operator, thread per cell (the production kernel)

@@ -1,15 +1,17 @@
 // Closest-particle search without any allocation (mpm_nearest_parent_noalloc).
 //
-// For callers that cannot allocate device memory: code running inside a CUDA
-// graph that is being captured, allocators that forbid cudaMalloc after
-// start-up, or host programs that hand the library a fixed memory budget. It
-// computes what mpm_resample computes for the balance particles' parents -- for
-// every surface sample the closest interior particle (smallest squared distance
-// formed as (dx^2 + dy^2) + dz^2 in float64, ties to the smaller particle index),
-// searched over the 27 cells around the sample -- but it needs no context. Its
-// working memory (cell counts, cell starts, particles sorted by cell, scan
-// partials, an error word) is one file-scope device array of fixed size, so every
-// GPU that loads the library holds those bytes until the process exits.
+// For callers that cannot allocate device memory: allocators that forbid
+// cudaMalloc after start-up, or host programs that hand the library a fixed
+// memory budget, and so cannot create a context. It computes what mpm_resample
+// computes for the balance particles' parents -- for every surface sample the
+// closest interior particle (smallest squared distance formed as
+// (dx^2 + dy^2) + dz^2 in float64, ties to the smaller particle index), searched
+// over the 27 cells around the sample and, when none of those holds a particle
+// within dx, over the 125 cells around it (every particle within 2 dx) -- but it
+// needs no context. Its working memory (cell counts, cell starts, particles
+// sorted by cell, scan partials, an error word) is one file-scope device array of
+// fixed size, so every GPU that loads the library holds those bytes until the
+// process exits.
 #include <mutex>
 
 #include "ctx.h"
@@ -156,24 +158,33 @@ __global__ void na_search(Grid g, int ns, const double* __restrict__ s, const do
     na_cell(g, q[0], q[1], q[2], c);
     double best = 1e300;
     int bid = 0x7fffffff;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dxx = -1; dxx <= 1; ++dxx) {
-                long long k = na_key(g, c[0] + dxx, c[1] + dy, c[2] + dz);
-                int e = scratch[NA_OFF_START + k + 1];
-                for (int t = scratch[NA_OFF_START + k]; t < e; ++t) {
-                    int i = scratch[NA_OFF_SORTED + t];
-                    double d0 = __dsub_rn(q[0], x[3 * i]);
-                    double d1 = __dsub_rn(q[1], x[3 * i + 1]);
-                    double d2 = __dsub_rn(q[2], x[3 * i + 2]);
-                    double dist = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
-                    if (dist < best || (dist == best && i < bid)) {
-                        best = dist;
-                        bid = i;
+    // the 27 cells around the sample hold every particle within dx; when the
+    // nearest is farther (samples generated on the union-of-spheres surface reach
+    // ~1.1 dx), the shell of the 125 cells around it holds the rest within 2 dx
+    for (int reach = 1; reach <= 2; ++reach) {
+        if (reach == 2 && best <= g.dx * g.dx) break;
+        for (int dz = -reach; dz <= reach; ++dz)
+            for (int dy = -reach; dy <= reach; ++dy)
+                for (int dxx = -reach; dxx <= reach; ++dxx) {
+                    if (reach == 2 && dz > -2 && dz < 2 && dy > -2 && dy < 2 && dxx > -2 && dxx < 2) continue;
+                    const int cx = c[0] + dxx, cy = c[1] + dy, cz = c[2] + dz;
+                    if (cx < 0 || cy < 0 || cz < 0 || cx >= g.n[0] || cy >= g.n[1] || cz >= g.n[2]) continue;
+                    long long k = na_key(g, cx, cy, cz);
+                    int e = scratch[NA_OFF_START + k + 1];
+                    for (int t = scratch[NA_OFF_START + k]; t < e; ++t) {
+                        int i = scratch[NA_OFF_SORTED + t];
+                        double d0 = __dsub_rn(q[0], x[3 * i]);
+                        double d1 = __dsub_rn(q[1], x[3 * i + 1]);
+                        double d2 = __dsub_rn(q[2], x[3 * i + 2]);
+                        double dist = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+                        if (dist < best || (dist == best && i < bid)) {
+                            best = dist;
+                            bid = i;
+                        }
                     }
                 }
-            }
-    if (bid == 0x7fffffff || best > g.dx * g.dx) {
+    }
+    if (bid == 0x7fffffff || best > 4.0 * g.dx * g.dx) {
         atomicOr(err, NA_ERR_FAR);
         parent[j] = -1;
         return;
@@ -182,7 +193,8 @@ __global__ void na_search(Grid g, int ns, const double* __restrict__ s, const do
 }
 
 // One-time set-up per device, with that device current: the device address of
-// the scratch array. Returns null on failure.
+// the scratch array, kept for the life of the process (a device reset that
+// invalidates it is not detected). Returns null on failure.
 int* scratch_for_current_device() {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return nullptr;

@@ -379,8 +379,23 @@ def nearest_parent_noalloc(grid, x, s, parent, stream=None):
     """Closest particle of each sample without any allocation (see include/mpm.h).
 
     grid: a GridDesc (or a Scene); x (N, 3) and s (M, 3) float64 and parent (M,)
-    int32 must be device-accessible (torch CUDA tensors). Returns the status code.
+    int32 torch tensors, contiguous, on the current CUDA device (the library looks
+    up its fixed scratch array for the current device and cannot check where a
+    pointer lives). Returns the status code.
     """
+    import torch
+    dev = torch.cuda.current_device()
+    for name, a, dt, shape in (("x", x, torch.float64, (None, 3)), ("s", s, torch.float64, (None, 3)),
+                               ("parent", parent, torch.int32, (s.shape[0] if hasattr(s, "shape") else None,))):
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"{name}: need a torch CUDA tensor")
+        if a.dtype != dt or a.dim() != len(shape) or any(w is not None and a.shape[i] != w
+                                                          for i, w in enumerate(shape)):
+            raise ValueError(f"{name}: need a {dt} tensor of shape {shape}, got {a.dtype} {tuple(a.shape)}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if not a.is_cuda or a.device.index != dev:
+            raise ValueError(f"{name}: tensor must be on the current CUDA device cuda:{dev}, got {a.device}")
     if isinstance(grid, _scenes.Scene):
         grid = scene_desc(grid).grid
     return _lib.mpm_nearest_parent_noalloc(ctypes.byref(grid), int(x.shape[0]), _ptr(x), int(s.shape[0]), _ptr(s),

@@ -1,13 +1,17 @@
 """The allocation-free closest-particle search against the context path.
 
 mpm_nearest_parent_noalloc serves callers that cannot allocate device memory
-(graph capture in progress, allocators that forbid cudaMalloc, fixed memory
-budgets). Its parents must equal those mpm_resample finds, index for index, on
-two calls in a row (the calls share one fixed scratch array in the library).
+(allocators that forbid cudaMalloc after start-up, fixed memory budgets), so
+cannot create a context. Its parents must equal those mpm_resample finds, index
+for index, on two calls in a row (the calls share one fixed scratch array in the
+library), for samples on the analytic sphere and for samples generated on the
+particles' union-of-spheres surface (some lie farther than dx from every
+particle, so the search must reach 2 dx as mpm_resample's does).
 Collected last, so a failure here does not hide the other tests' results.
 """
 import numpy as np
 import pytest
+from scipy.spatial import cKDTree
 
 from paper_2101_12408_gb300 import scenes
 
@@ -35,10 +39,52 @@ def test_noalloc_parents_match_resample_twice():
         ref = _context_parents(sc)
         x = torch.tensor(sc.x, dtype=torch.float64, device=dev).contiguous()
         s = torch.tensor(sc.s, dtype=torch.float64, device=dev).contiguous()
-        parent = torch.full((sc.n_surface,), -7, dtype=torch.int32, device=dev)
-        status = mpm.nearest_parent_noalloc(sc, x, s, parent)
-        assert status == mpm.MPM_OK
+        for _ in range(2):
+            parent = torch.full((sc.n_surface,), -7, dtype=torch.int32, device=dev)
+            status = mpm.nearest_parent_noalloc(sc, x, s, parent)
+            assert status == mpm.MPM_OK
+            np.testing.assert_array_equal(parent.cpu().numpy(), ref)
+
+
+def test_noalloc_parents_match_resample_on_generated_surfaces():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda", 0)
+    sc = scenes.droplet(n=32, r_cells=7.0, seed=23)
+    ctx = mpm.Context(sc, precision=mpm.PREC_FP64, surface_capacity_factor=8.0)
+    ctx.load_scene(0)
+    ctx.generate_surface(seed=5)
+    ctx.resample()
+    surf = ctx.get_surface(0)
+    ctx.close()
+    ref, s_np = surf["parent"], surf["s"]
+    # the generated samples do include ones beyond dx of every particle
+    d = cKDTree(sc.x).query(s_np)[0]
+    assert np.any(d > sc.dx) and np.all(d <= 2 * sc.dx)
+    x = torch.tensor(sc.x, dtype=torch.float64, device=dev).contiguous()
+    s = torch.tensor(s_np, dtype=torch.float64, device=dev).contiguous()
+    for _ in range(2):
+        parent = torch.full((s_np.shape[0],), -7, dtype=torch.int32, device=dev)
+        assert mpm.nearest_parent_noalloc(sc, x, s, parent) == mpm.MPM_OK
         np.testing.assert_array_equal(parent.cpu().numpy(), ref)
+
+
+def test_noalloc_wrapper_rejects_wrong_dtypes_and_shapes():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda", 0)
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=24)
+    x = torch.tensor(sc.x, dtype=torch.float64, device=dev)
+    s = torch.tensor(sc.s, dtype=torch.float64, device=dev)
+    parent = torch.empty((sc.n_surface,), dtype=torch.int32, device=dev)
+    with pytest.raises(ValueError):
+        mpm.nearest_parent_noalloc(sc, x.float(), s, parent)
+    with pytest.raises(ValueError):
+        mpm.nearest_parent_noalloc(sc, x, s, parent[:-1])
+    with pytest.raises(ValueError):
+        mpm.nearest_parent_noalloc(sc, x.t(), s, parent)
+    with pytest.raises(ValueError):
+        mpm.nearest_parent_noalloc(sc, x.cpu(), s, parent)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
