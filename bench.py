@@ -19,13 +19,17 @@ Reported (one JSON line on rank 0):
   e2e          the same steps/s through the C ABI with host buffers: particle and
                surface state copied in from pinned host memory and back out into
                it every step
-  fp64_form    the all-float64 GPU form on the same workload (fewer steps)
-  cpu_baseline the FP64 numpy oracle on a bounded sample of the workload (a
-               16^3-cell window at the lower surface of its smallest droplet,
-               or around the centroid of a scene without droplets; same dx,
-               parameters and plane), scaled per particle to the full
-               workload; one host thread (BLAS pools pinned to 1)
-  --impl reference: the oracle alone, timed on the host, same metric.
+  fp64_form    the all-float64 GPU form on the same workload, the same warm-up
+               and the same number of timed steps from the same initial state
+  hessian_apply  the operator alone: 200 back-to-back applications on the
+               frozen Newton state after one more step, both forms
+  regenerated_surface  steps/s with a new surface generated before every step
+  cpu_baseline the FP64 numpy oracle on bounded samples of the workload (16^3-cell
+               windows around the lower surfaces of its droplets, or around the
+               centroid of a scene without droplets; same dx, parameters and
+               plane), one window per host core in separate processes, scaled
+               per particle to the full workload; the one-thread figure beside it
+  --impl reference: the oracle alone, timed the same way on the host cores.
 Multi-GPU (torchrun): replicas only -- every rank advances its own copy of the
 workload; value is the sum over ranks (weak scaling, no collective on the path).
 """
@@ -51,14 +55,25 @@ from paper_2101_12408_gb300 import scenes  # noqa: E402
 METRIC = "implicit steps/sec (float32 operator + float64 reductions)"
 UNIT = "steps/s"
 # ncu DRAM traffic (read + write bytes) of one Hessian-operator apply at the
-# full workload, from the 20-droplet capture in
-# profiles/apply_cg_kernels_incline20_fp32.md scaled by the units processed:
-# k_apply_cell (188.6 MB, particles and samples) x 8272476 / 5128948 particles
-# plus k_apply_general (0.07 MB) x 317603 / 185006 samples. k_apply_cell's code
-# is unchanged since that capture. k_apply_general has changed since (its
-# particle loop and the projected solid maps), but this workload gives it no
-# particles: its share is the scan of an empty list.
-NCU_TRAFFIC_BYTES = 304312853
+# full workload, with the SHA-256 of the operator's source files it was
+# measured on. When those files have changed since, the line reports no traffic.
+NCU_TRAFFIC = {"bytes_per_apply": None, "source_sha256": None}
+OPERATOR_SOURCES = ("paper_2101_12408_gb300/csrc/newton.cu", "paper_2101_12408_gb300/csrc/common.cuh")
+
+
+def operator_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in OPERATOR_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    if NCU_TRAFFIC["bytes_per_apply"] is None or NCU_TRAFFIC["source_sha256"] != operator_source_hash():
+        return None
+    return NCU_TRAFFIC["bytes_per_apply"]
 
 
 def make_workload(name, drops=40):
@@ -70,6 +85,8 @@ def make_workload(name, drops=40):
         return scenes.droplet()
     if name == "wax":
         return scenes.wax()
+    if name == "batch":
+        return scenes.batch()
     raise ValueError(name)
 
 
@@ -135,57 +152,109 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(ctx, sc, rsize):
+def algorithmic_bytes(ctx, rsize):
     """Bytes one Hessian-operator launch (projected form, as CG applies it) must
-    move: the packed record of a liquid particle (position in its block and
-    kappa, 4 values); a solid particle (position in its block and the iterate's
-    symmetric 9x9 projected-Hessian map, 3 + 45 values); a surface sample (position in its block and
-    the iterate's symmetric 9x9 Hessian map, 3 + 45 values); an active node (the
-    direction read and the product written, 3 components each)."""
-    p = ctx.get_particles(0)
-    nsol = int(np.sum(p["phase"] == 1))
-    nliq = ctx.np[0] - nsol
-    m = ctx.get_grid(0, 0)
-    g_active = int(np.sum(m > 0))
-    b = rsize * (nliq * 4 + nsol * (3 + 45) + ctx.ns[0] * (3 + 45) + g_active * 6)
-    return b, dict(liquid=nliq, solid=nsol, surface=ctx.ns[0], active_nodes=g_active)
+    move, over every scene of the context: the packed record of a liquid particle
+    (position in its block and kappa, 4 values); a solid particle (position in its
+    block and the iterate's symmetric 9x9 projected-Hessian map, 3 + 45 values); a
+    surface sample (position in its block and the iterate's symmetric 9x9 Hessian
+    map, 3 + 45 values); an active node (the direction read and the product
+    written, 3 components each)."""
+    nliq = nsol = nsurf = g_active = 0
+    for k in range(len(ctx.scenes)):
+        p = ctx.get_particles(k)
+        ns_ = int(np.sum(p["phase"] == 1))
+        nsol += ns_
+        nliq += ctx.np[k] - ns_
+        nsurf += ctx.ns[k]
+        g_active += int(np.sum(ctx.get_grid(k, 0) > 0))
+    b = rsize * (nliq * 4 + nsol * (3 + 45) + nsurf * (3 + 45) + g_active * 6)
+    return b, dict(liquid=nliq, solid=nsol, surface=nsurf, active_nodes=g_active)
 
 
-def run_oracle_sample(sc, steps):
-    """FP64 oracle on the workload's window sample; returns seconds per step and the sample."""
+SAMPLE_CELLS = 16
+
+
+def _scenes_of(sc):
+    return sc if isinstance(sc, list) else [sc]
+
+
+def total_particles(sc):
+    return sum(s.n_particles for s in _scenes_of(sc))
+
+
+def sample_where(sc):
+    """Where `sample_windows` puts its windows, in words."""
+    s0 = _scenes_of(sc)[0]
+    if "radii" in s0.meta:
+        return "at the lower surfaces of its droplets, smallest first"
+    return "around the particles' centroids"
+
+
+def sample_windows(sc, count, size=SAMPLE_CELLS):
+    """Bounded pieces of the workload for the CPU oracle: the particles and surface
+    samples in `size`^3-cell windows (same dx, parameters and plane), one around
+    the lower surface of each droplet (smallest first), or around the centroid of
+    each scene of a workload without droplets."""
+    out = []
+    for s in _scenes_of(sc):
+        if "radii" in s.meta:
+            for k in np.argsort(s.meta["radii"]):
+                c = s.meta["centers"][k] - np.array([0.0, s.meta["radii"][k] - 3 * s.dx, 0.0])
+                out.append(scenes.window(s, c, size, name=f"{s.name}_window{size}_{k}"))
+                if len(out) == count:
+                    return out
+        else:
+            out.append(scenes.window(s, s.x.mean(0), size, name=f"{s.name}_window{size}"))
+            if len(out) == count:
+                return out
+    while len(out) < count:   # fewer windows than cores: repeat them
+        out.append(out[len(out) % max(1, len(out))])
+    return out
+
+
+def _oracle_worker(job):
+    """One host process: the FP64 oracle on one window; seconds of each step."""
+    sample, steps = job
     import oracle
-    from scipy.spatial import cKDTree  # noqa: F401  (scipy present on both machines)
-    sample = sample_scene(sc)
     sim = oracle.OracleSim(sample)
     times = []
     for _ in range(steps):
         t = time.perf_counter()
         sim.step()
         times.append(time.perf_counter() - t)
-    return times, sample
+    return sample.n_particles, times
 
 
-SAMPLE_CELLS = 16
+def run_oracle(sc, steps, warmup, processes):
+    """The oracle as it stands on `processes` host cores at once, each process on
+    its own window (spawned processes, BLAS pools pinned to one thread each).
+    Returns (full-workload steps/s, per-process particle counts, mean step seconds)."""
+    import multiprocessing as mp
+    wins = sample_windows(sc, processes)
+    if processes == 1:
+        res = [_oracle_worker((wins[0], warmup + steps))]
+    else:
+        with mp.get_context("spawn").Pool(processes) as pool:
+            res = pool.map(_oracle_worker, [(w, warmup + steps) for w in wins])
+    counts = [n for n, _ in res]
+    secs = [float(np.mean(ts[warmup:])) if steps > 0 else float("nan") for _, ts in res]
+    # the processes run side by side: their particle rates add up
+    rate = sum(n / s for n, s in zip(counts, secs))
+    return rate / total_particles(sc), counts, secs
 
 
-def sample_where(sc):
-    """Where `sample_scene` puts its window, in words."""
-    if "radii" in sc.meta:
-        return "at the lower surface of the smallest droplet"
-    return "around the particles' centroid"
-
-
-def sample_scene(sc, size=SAMPLE_CELLS):
-    """A bounded piece of the workload for the CPU oracle: the particles and
-    surface samples in a `size`^3-cell window (same dx, parameters and plane)
-    around the lower surface of the smallest droplet, or around the particles'
-    centroid in a scene without droplets."""
-    if "radii" in sc.meta:
-        k = int(np.argmin(sc.meta["radii"]))
-        c = sc.meta["centers"][k] - np.array([0.0, sc.meta["radii"][k] - 3 * sc.dx, 0.0])
-        return scenes.window(sc, c, size, name=f"incline_window{size}")
-    c = sc.x.mean(0)
-    return scenes.window(sc, c, size, name=f"{sc.name}_window{size}")
+def oracle_baseline(sc, steps, warmup=0):
+    """cpu_baseline object: every host core, with the one-core figure beside it."""
+    cores = os.cpu_count() or 1
+    v1, c1, s1 = run_oracle(sc, steps, warmup, 1)
+    vn, cn, sn = run_oracle(sc, steps, warmup, cores) if cores > 1 else (v1, c1, s1)
+    return {"value": vn, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} host processes side by side, each the FP64 oracle on its own {SAMPLE_CELLS}^3-cell "
+                      f"window {sample_where(sc)} ({min(cn)}-{max(cn)} particles each, {steps} timed steps after "
+                      f"{warmup}); particle rates summed and scaled to the {total_particles(sc)}-particle workload",
+            "host_cpu_count": cores,
+            "one_core": {"value": v1, "cores": 1, "particles": c1[0], "sec_per_step": s1[0]}}
 
 
 def job_rate(units, elapsed_ms, device=None):
@@ -203,6 +272,28 @@ def job_rate(units, elapsed_ms, device=None):
     return float(u.item()) / (float(t.item()) * 1e-3), float(t.item())
 
 
+def _timed_steps(ctx, stream, steps):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [ctx.step() for _ in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), stats
+
+
+def _isolated_apply(ctx, n_applies):
+    """One more step's resample, P2G and Newton solve, then the operator alone on
+    that frozen state; the step is finished with G2P."""
+    ctx.resample()
+    ctx.p2g()
+    ctx.newton_step()
+    ms = ctx.profile_apply(n_applies)
+    ctx.g2p()
+    return ms
+
+
 def bench_ours(args, rank, world):
     import torch
     from paper_2101_12408_gb300 import mpm
@@ -210,11 +301,13 @@ def bench_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     sc = make_workload(args.workload, args.drops)
+    scl = _scenes_of(sc)
     stream = torch.cuda.current_stream()
     prec = mpm.PREC_FP32_FP64RED if args.precision == "fp32" else mpm.PREC_FP64
-    ctx = mpm.Context(sc, precision=prec, stream=stream.cuda_stream, max_blocks=args.max_blocks,
+    ctx = mpm.Context(scl, precision=prec, stream=stream.cuda_stream, max_blocks=args.max_blocks,
                       surface_capacity_factor=2.0)
-    ctx.load_scene(0)
+    for k in range(len(scl)):
+        ctx.load_scene(k)
     for _ in range(args.warmup):
         ctx.step()
     dist = world > 1
@@ -224,26 +317,19 @@ def bench_ours(args, rank, world):
     clocks = ClockSampler(dev.index)
     clocks.start()
     ctx.profile_enable(True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        stats.append(ctx.step()[0])
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    elapsed_ms, stats = _timed_steps(ctx, stream, args.steps)
     if dist:
         torch.distributed.barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     prof = ctx.profile()
     ctx.profile_enable(False)
     steps_per_s, elapsed_ms = job_rate(args.steps, elapsed_ms, dev)
     rsize = 4 if prec == mpm.PREC_FP32_FP64RED else 8
-    abytes, counts = algorithmic_bytes(ctx, sc, rsize)
+    abytes, counts = algorithmic_bytes(ctx, rsize)
     apply_avg_ms = prof["apply_ms"] / max(prof["apply_launches"], 1)
     peak, peak_kind = measured_peak()
     achieved = abytes / (apply_avg_ms * 1e-3) / 1e9
+    cnt = ctx.counts()
     out = {
         "steps_per_s": steps_per_s,
         "ms_per_step": elapsed_ms / args.steps,
@@ -251,12 +337,19 @@ def bench_ours(args, rank, world):
         "stats": stats,
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": NCU_TRAFFIC_BYTES, "peak_source": peak_kind, "kernel": "k_apply (Hessian-vector)",
-                     "bytes_per_launch": abytes, "launch_ms": apply_avg_ms,
-                     "launches": prof["apply_launches"]},
-        "counts": dict(counts, **{"grid_blocks": ctx.counts()["blocks"], "work_blocks": ctx.counts()["work_blocks"]}),
+                     "traffic": measured_traffic(), "peak_source": peak_kind,
+                     "kernel": "k_apply_cell + k_apply_general (Hessian-vector operator)",
+                     "bytes_per_launch": abytes, "launch_ms": apply_avg_ms, "launches": prof["apply_launches"]},
+        "counts": dict(counts, grid_blocks=cnt["blocks"], work_blocks=cnt["work_blocks"]),
         "applies_per_s": prof["apply_launches"] / (elapsed_ms * 1e-3),
     }
+    # the operator alone on a frozen Newton state
+    iso = {}
+    if args.apply_bench > 0:
+        ms = _isolated_apply(ctx, args.apply_bench)
+        iso["fp32" if rsize == 4 else "fp64"] = {
+            "ms_per_apply": ms, "applies_per_s": 1e3 / ms, "gbs": abytes / (ms * 1e-3) / 1e9,
+            "frac": abytes / (ms * 1e-3) / 1e9 / peak, "bytes_per_apply": abytes, "applies": args.apply_bench}
     # end to end through host buffers: state in from host memory, step, state back out
     if args.e2e_steps > 0:
         tdt = {np.dtype(np.float64): torch.float64, np.dtype(np.uint8): torch.uint8, np.dtype(np.int32): torch.int32}
@@ -267,68 +360,103 @@ def bench_ours(args, rank, world):
             buf[...] = a
             return buf
 
-        cur = sc.copy()
-        p = ctx.get_particles(0)
-        srf = ctx.get_surface(0)
         pf = ("x", "v", "A", "J", "F", "T", "gradT", "phase")
-        for f in pf:
-            setattr(cur, f, pinned(p[f]))
-        for f in ("m", "V0", "b", "Tbar"):
-            setattr(cur, f, pinned(np.ascontiguousarray(getattr(sc, f))))
-        cur.s, cur.dA, cur.kind = pinned(srf["s"]), pinned(srf["dA"]), pinned(srf["kind"])
-        # each step's outputs land in the arrays the next step loads
-        pout = {f: getattr(cur, f) for f in pf}
-        sout = dict(s=cur.s, dA=cur.dA, kind=cur.kind, gamma=pinned(srf["gamma"]), parent=pinned(srf["parent"]),
-                    b=pinned(srf["b"]))
+        curs, pouts, souts = [], [], []
+        for k, s0 in enumerate(scl):
+            cur = s0.copy()
+            p = ctx.get_particles(k)
+            srf = ctx.get_surface(k)
+            for f in pf:
+                setattr(cur, f, pinned(p[f]))
+            for f in ("m", "V0", "b", "Tbar"):
+                setattr(cur, f, pinned(np.ascontiguousarray(getattr(s0, f))))
+            cur.s, cur.dA, cur.kind = pinned(srf["s"]), pinned(srf["dA"]), pinned(srf["kind"])
+            curs.append(cur)
+            # each step's outputs land in the arrays the next step loads
+            pouts.append({f: getattr(cur, f) for f in pf})
+            souts.append(dict(s=cur.s, dA=cur.dA, kind=cur.kind, gamma=pinned(srf["gamma"]),
+                              parent=pinned(srf["parent"]), b=pinned(srf["b"])))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            ctx.load_scene(0, cur)
+            for k in range(len(scl)):
+                ctx.load_scene(k, curs[k])
             ctx.step()
-            ctx.get_particles(0, out=pout)
-            ctx.get_surface(0, out=sout)
+            for k in range(len(scl)):
+                ctx.get_particles(k, out=pouts[k])
+                ctx.get_surface(k, out=souts[k])
         torch.cuda.synchronize()
         e2e_rate, _ = job_rate(args.e2e_steps, (time.perf_counter() - t0) * 1e3, dev)
-        n, ns = ctx.np[0], ctx.ns[0]
+        n, ns = sum(ctx.np), sum(ctx.ns)
         h2d = n * (3 + 3 + 9 + 1 + 1 + 1 + 9 + 1 + 3) * 8 + n + ns * (3 + 3 + 1 + 1) * 8 + ns
         d2h = n * (3 + 3 + 9 + 1 + 9 + 1 + 3) * 8 + n + ns * (3 + 3 + 1 + 3) * 8 + ns + ns * 4
         out["e2e"] = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(d2h)}
-    # surface regeneration (mpm_generate_surface), timed once on the final state,
-    # outside the timed steps (the timed steps carry their samples)
+    # surface regeneration (mpm_generate_surface): once on its own, then steps
+    # that regenerate the surface before every step (section "Discretization",
+    # step 1); the headline steps carry their samples
     if args.surface_gen:
         ctx.generate_surface(1)   # warm-up (grows the triangle buffer)
         torch.cuda.synchronize()
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        cnt = ctx.generate_surface(2)
+        cnt_g = ctx.generate_surface(2)
         g1.record(stream)
         torch.cuda.synchronize()
-        out["surface_generation"] = {"ms": g0.elapsed_time(g1), "samples": int(cnt[0]),
-                                     "carried_samples": int(sc.n_surface)}
+        out["surface_generation"] = {"ms": g0.elapsed_time(g1), "samples": int(np.sum(cnt_g)),
+                                     "carried_samples": int(sum(s0.n_surface for s0 in scl))}
+    if args.regen_steps > 0:
+        ctx.step()   # warm-up on the regenerated surface
+        torch.cuda.synchronize()
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        rst = []
+        for k in range(args.regen_steps):
+            ctx.generate_surface(100 + k)
+            rst.append(ctx.step())
+        r1.record(stream)
+        torch.cuda.synchronize()
+        ms = r0.elapsed_time(r1)
+        out["regenerated_surface"] = {"steps_per_s": args.regen_steps / (ms * 1e-3),
+                                      "ms_per_step": ms / args.regen_steps, "steps": args.regen_steps,
+                                      "surface_samples": int(sum(ctx.ns)),
+                                      "newton_iters": [s[0]["newton_iters"] for s in rst],
+                                      "cg_iters": [s[0]["cg_iters"] for s in rst],
+                                      "residual_rel": [s[0]["residual"] / max(s[0]["residual0"], 1e-300)
+                                                       for s in rst]}
     ctx.close()
-    # all-float64 form on the same workload
-    if args.fp64_steps > 0 and prec == mpm.PREC_FP32_FP64RED:
-        ctx = mpm.Context(sc, precision=mpm.PREC_FP64, stream=stream.cuda_stream, max_blocks=args.max_blocks)
-        ctx.load_scene(0)
-        ctx.step()
+    # all-float64 form: same workload, warm-up and timed step count, from the same
+    # initial state
+    if args.fp64_steps != 0 and prec == mpm.PREC_FP32_FP64RED:
+        n64 = args.steps if args.fp64_steps < 0 else args.fp64_steps
+        w64 = args.warmup if args.fp64_steps < 0 else 1
+        ctx = mpm.Context(scl, precision=mpm.PREC_FP64, stream=stream.cuda_stream, max_blocks=args.max_blocks,
+                          surface_capacity_factor=2.0)
+        for k in range(len(scl)):
+            ctx.load_scene(k)
+        for _ in range(w64):
+            ctx.step()
+        torch.cuda.synchronize()
         ctx.profile_enable(True)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st64 = [ctx.step()[0] for _ in range(args.fp64_steps)]
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms, st64 = _timed_steps(ctx, stream, n64)
         p64 = ctx.profile()
-        out["fp64_form"] = {"steps_per_s": args.fp64_steps / (ms * 1e-3), "ms_per_step": ms / args.fp64_steps,
-                            "apply_launch_ms": p64["apply_ms"] / max(p64["apply_launches"], 1),
-                            "newton_iters": [s["newton_iters"] for s in st64],
-                            "cg_iters": [s["cg_iters"] for s in st64],
-                            "residual_rel": [s["residual"] / max(s["residual0"], 1e-300) for s in st64]}
+        ctx.profile_enable(False)
+        out["fp64_form"] = {"steps_per_s": n64 / (ms * 1e-3), "ms_per_step": ms / n64, "steps": n64,
+                            "warmup": w64, "apply_launch_ms": p64["apply_ms"] / max(p64["apply_launches"], 1),
+                            "newton_iters": [s[0]["newton_iters"] for s in st64],
+                            "cg_iters": [s[0]["cg_iters"] for s in st64],
+                            "residual_rel": [s[0]["residual"] / max(s[0]["residual0"], 1e-300) for s in st64]}
+        if args.apply_bench > 0:
+            ms = _isolated_apply(ctx, args.apply_bench)
+            b64, _ = algorithmic_bytes(ctx, 8)
+            iso["fp64"] = {"ms_per_apply": ms, "applies_per_s": 1e3 / ms, "gbs": b64 / (ms * 1e-3) / 1e9,
+                           "frac": b64 / (ms * 1e-3) / 1e9 / peak, "bytes_per_apply": b64,
+                           "applies": args.apply_bench}
         ctx.close()
+    if iso:
+        out["hessian_apply"] = iso
     return out, sc
 
 
@@ -338,12 +466,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="incline")
+    ap.add_argument("--workload", default="incline", choices=["incline", "film", "droplet", "wax", "batch"])
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=-1,
+                    help="timed steps of the all-float64 form (-1: as many as --steps, after as many warm-up steps; "
+                         "0: skip)")
+    ap.add_argument("--apply-bench", type=int, default=200, help="isolated operator applications (0: skip)")
+    ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--surface-gen", type=int, default=1, help="time one surface regeneration (0: skip)")
+    ap.add_argument("--regen-steps", type=int, default=3, help="steps with a regenerated surface (0: skip)")
     ap.add_argument("--drops", type=int, default=40, help="droplets in the incline workload")
     ap.add_argument("--max-blocks", type=int, default=0, help="grid block capacity (0: whole grid)")
     args = ap.parse_args()
@@ -355,19 +487,13 @@ def main():
         if rank != 0:
             return
         sc = make_workload(args.workload, args.drops)
-        times, sample = run_oracle_sample(sc, args.warmup + args.steps)
-        t = float(np.mean(times[args.warmup:])) if args.steps > 0 else float("nan")
-        scale = sample.n_particles / sc.n_particles
-        val = scale / t
+        cpu = oracle_baseline(sc, args.steps, args.warmup)
+        val = cpu["value"]
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": args.workload, "particles": sc.n_particles},
-                "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"{sample.n[0]}^3-cell window {sample_where(sc)} "
-                                           f"({sample.n_particles} of {sc.n_particles} particles, "
-                                           f"{sample.n_surface} samples) per step, seconds per step scaled by "
-                                           f"particle count ({scale:.5f})"},
+                "config": {"workload": args.workload, "particles": total_particles(sc)},
+                "cpu_baseline": cpu,
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -378,38 +504,42 @@ def main():
     res, sc = bench_ours(args, rank, world)
     if rank != 0:
         return
-    cpu = None
-    if args.cpu_steps > 0:
-        times, sample = run_oracle_sample(sc, args.cpu_steps)
-        t = float(np.mean(times))
-        scale = sample.n_particles / sc.n_particles
-        cpu = {"value": scale / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{sample.n[0]}^3-cell window {sample_where(sc)} "
-                         f"({sample.n_particles} of {sc.n_particles} particles, {sample.n_surface} samples, "
-                         f"{args.cpu_steps} steps), seconds per step scaled by particle count"}
+    cpu = oracle_baseline(sc, args.cpu_steps) if args.cpu_steps > 0 else None
     prof = res["prof"]
+    scl = _scenes_of(sc)
+    s0 = scl[0]
+    cfg = {"workload": args.workload, "scenes": len(scl), "particles": total_particles(sc),
+           "surface_samples": int(sum(s.n_surface for s in scl)), "dt": s0.params.dt,
+           "newton_tol": s0.params.newton_tol, "l2": "inputs larger than L2 (particle state ~2 GB)",
+           "parallelism": "replicas"}
+    if len(scl) == 1:
+        cfg.update(grid=list(s0.n), dx=s0.dx)
+    else:
+        cfg.update(grids=[list(s.n) for s in scl], particles_per_scene=[s.n_particles for s in scl])
     line = {
         "metric": METRIC, "value": res["steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "grid": list(sc.n), "dx": sc.dx, "particles": sc.n_particles,
-                   "surface_samples": sc.n_surface, "dt": sc.params.dt, "newton_tol": sc.params.newton_tol,
-                   "l2": "inputs larger than L2 (particle state ~2 GB)", "parallelism": "replicas"},
+        "config": cfg,
         "roofline": res["roofline"],
         "cpu_baseline": cpu,
         "e2e": res.get("e2e"),
         "gpu_launches": prof["kernel_launches"],
         "clocks": res["clocks"],
         "hessian_applies_per_s": res["applies_per_s"],
+        "hessian_apply": res.get("hessian_apply"),
         "fp64_form": res.get("fp64_form"),
+        "regenerated_surface": res.get("regenerated_surface"),
         "phases_ms_per_step": {k: v / args.steps for k, v in prof["phase_ms"].items()},
         "surface_generation": res.get("surface_generation"),
         "cg_launch": {"ctas_per_sm": prof["cg_ctas_per_sm"], "iters_per_check": prof["cg_chunk"],
                       "cuda_graphs": bool(prof["cg_graphs"]), "graph_error": prof["cg_graph_error"]},
-        "newton_iters": [s["newton_iters"] for s in res["stats"]],
-        "cg_iters": [s["cg_iters"] for s in res["stats"]],
-        "residual_rel": [s["residual"] / max(s["residual0"], 1e-300) for s in res["stats"]],
+        "newton_iters": [[s["newton_iters"] for s in st] for st in res["stats"]] if len(scl) > 1
+        else [st[0]["newton_iters"] for st in res["stats"]],
+        "cg_iters": [st[0]["cg_iters"] for st in res["stats"]] if len(scl) == 1
+        else [max(s["cg_iters"] for s in st) for st in res["stats"]],
+        "residual_rel": [max(s["residual"] / max(s["residual0"], 1e-300) for s in st) for st in res["stats"]],
         "counts": res["counts"],
     }
     print(json.dumps(line))

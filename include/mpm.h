@@ -290,6 +290,15 @@ typedef struct {
 mpm_status mpm_profile_enable(mpm_ctx* ctx, int32_t enable);
 mpm_status mpm_get_profile(mpm_ctx* ctx, mpm_profile* out);
 
+/* Timing of the Hessian-vector operator alone (not part of the paper's method):
+ * after one warm-up launch, n_applies back-to-back applications of the operator
+ * of mode `mode` (the launches mpm_apply_hessian makes, without its dense copies)
+ * to the solver's last CG direction at the iterate the last mpm_newton_step left
+ * (call it after mpm_newton_step and before mpm_g2p). *ms_per_apply receives the
+ * device time between CUDA events recorded on the context's stream around the
+ * n_applies launches, divided by n_applies. Synchronises the stream. */
+mpm_status mpm_profile_apply(mpm_ctx* ctx, int32_t n_applies, int32_t mode, double* ms_per_apply);
+
 /* Closest interior particle of each surface sample, computed without allocating.
  *
  * The paper has no counterpart of this entry point: it serves callers that cannot

@@ -826,6 +826,29 @@ mpm_status mpm_profile_enable(mpm_ctx* c, int32_t enable) {
     return MPM_OK;
 }
 
+mpm_status mpm_profile_apply(mpm_ctx* c, int32_t n_applies, int32_t mode, double* ms_per_apply) {
+    if (!c) return MPM_ERR_INVALID_ARG;
+    if (n_applies < 1 || !ms_per_apply || (mode != MPM_HESS_EXACT && mode != MPM_HESS_PROJECTED))
+        return fail(c, MPM_ERR_INVALID_ARG, "mpm_profile_apply: bad count, pointer or mode");
+    if (!c->step_ready) return fail(c, MPM_ERR_INVALID_ARG, "mpm_profile_apply: call mpm_newton_step first");
+    Dev& d = c->d;
+    cudaStream_t st = c->st;
+    // the solver's last CG direction at the frozen iterate; the products
+    // accumulate in the CG's product vector, which is cleared afterwards
+    MPM_CUDA(cudaMemsetAsync(d.cu, 0, (size_t)c->rsize * (size_t)c->NB * 192, st));
+    MPM_CUDA(launch_apply(c, d.cp, d.cu, mode));   // warm-up
+    MPM_CUDA(cudaEventRecord(c->ev[32], st));
+    for (int k = 0; k < n_applies; ++k) MPM_CUDA(launch_apply(c, d.cp, d.cu, mode));
+    MPM_CUDA(cudaEventRecord(c->ev[33], st));
+    MPM_CUDA(cudaEventSynchronize(c->ev[33]));
+    float ms = 0.f;
+    MPM_CUDA(cudaEventElapsedTime(&ms, c->ev[32], c->ev[33]));
+    *ms_per_apply = (double)ms / n_applies;
+    MPM_CUDA(cudaMemsetAsync(d.cu, 0, (size_t)c->rsize * (size_t)c->NB * 192, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+    return check_device_error(c);
+}
+
 mpm_status mpm_get_profile(mpm_ctx* c, mpm_profile* out) {
     if (!c || !out) return MPM_ERR_INVALID_ARG;
     *out = c->pr;

@@ -33,7 +33,7 @@ EXPORTED = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_particles", 
             "mpm_set_surface", "mpm_get_surface", "mpm_resample", "mpm_p2g", "mpm_get_grid", "mpm_set_velocity",
             "mpm_energy_gradient", "mpm_apply_hessian", "mpm_heat_apply", "mpm_newton_step", "mpm_g2p", "mpm_step",
             "mpm_sync", "mpm_counts", "mpm_profile_enable", "mpm_get_profile", "mpm_nearest_parent_noalloc",
-            "mpm_generate_surface"]
+            "mpm_generate_surface", "mpm_profile_apply"]
 
 
 class GridDesc(ctypes.Structure):
@@ -110,6 +110,7 @@ _lib.mpm_sync.argtypes = [_vp]
 _lib.mpm_counts.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int64)] * 4
 _lib.mpm_profile_enable.argtypes = [_vp, ctypes.c_int32]
 _lib.mpm_get_profile.argtypes = [_vp, ctypes.POINTER(Profile)]
+_lib.mpm_profile_apply.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
 _lib.mpm_nearest_parent_noalloc.argtypes = [ctypes.POINTER(GridDesc), ctypes.c_int64, _vp, ctypes.c_int64, _vp, _vp,
                                             _vp]
 for _name in EXPORTED:
@@ -335,6 +336,13 @@ class Context:
         p = Profile()
         self._check(_lib.mpm_get_profile(self.h, ctypes.byref(p)))
         return p.as_dict()
+
+    def profile_apply(self, n_applies=200, mode=HESS_PROJECTED):
+        """Mean device ms of one Hessian-operator application on the frozen Newton
+        state (after newton_step, before g2p)."""
+        ms = ctypes.c_double()
+        self._check(_lib.mpm_profile_apply(self.h, int(n_applies), int(mode), ctypes.byref(ms)))
+        return ms.value
 
     # ---- grid access / operators ----
     def _nodes(self, k):

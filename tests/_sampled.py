@@ -72,3 +72,37 @@ def nearest_parents(x, s, which, dx, n, reach_cells=3):
         local, _ = oracle.nearest_parent(x[cand], s[r][None, :])
         out[k] = cand[local[0]]
     return out
+
+
+def hessvec_at_nodes(n, dx, dt, x, V0, Jn, lam, s, dA, gamma, v, dv, m, nodes, mode, half=4):
+    """The oracle's Hessian-vector product (NewtonState.hessvec, liquid particles
+    and surface samples) at the linear node ids `nodes`, one node at a time.
+
+    A node's row gathers the particles and samples in the 27 cells around it;
+    their stencils read v and dv on the nodes within 2 of it. Each node is
+    evaluated on a (2 half)^3 window of the grid around it, with positions
+    shifted by whole cells, and the window's nodes carrying v, dv and m. Returns
+    the rows (len(nodes), 3) with the mass term m dv and without it."""
+    n = tuple(int(q) for q in n)
+    g = np.stack(np.unravel_index(np.asarray(nodes), n, order="F"), -1)
+    ix, isx = CellIndex(x, dx, n), CellIndex(s, dx, n)
+    w = 2 * half
+    loc = half + w * (half + w * half)
+    full = np.zeros((len(nodes), 3))
+    stiff = np.zeros((len(nodes), 3))
+    for k, gi in enumerate(g):
+        lo = gi - half
+        sel = ix.box(gi, 1)
+        ssel = isx.box(gi, 1)
+        win = np.stack(np.meshgrid(*[np.arange(lo[a], lo[a] + w) for a in range(3)], indexing="ij"), -1)
+        ids = (win[..., 0] + n[0] * (win[..., 1] + n[1] * win[..., 2])).transpose(2, 1, 0).ravel()
+        shift = lo * dx
+        np_ = sel.size
+        st = oracle.NewtonState((w, w, w), dx, dt, np.zeros(3), m[ids], np.zeros((w ** 3, 3)), x[sel] - shift,
+                                V0[sel], Jn[sel], np.broadcast_to(np.eye(3), (np_, 3, 3)).copy(),
+                                np.zeros(np_, np.int64), lam, 0.0, np.zeros(np_), np.zeros(np_),
+                                s[ssel] - shift, dA[ssel], gamma[ssel])
+        out = st.hessvec(v[ids], dv[ids], mode)
+        full[k] = out[loc]
+        stiff[k] = out[loc] - m[ids][loc] * dv[ids][loc]
+    return full, stiff

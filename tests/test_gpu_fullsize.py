@@ -14,7 +14,7 @@ import pytest
 import oracle
 from paper_2101_12408_gb300 import mpm, scenes
 
-from _sampled import nearest_parents, p2g_at_nodes
+from _sampled import hessvec_at_nodes, nearest_parents, p2g_at_nodes
 
 pytestmark = pytest.mark.gpu
 
@@ -72,6 +72,48 @@ def test_fullsize_operator_is_symmetric_and_positive(incline):
     assert a11 > 0 and a22 > 0
     # float32 operator arithmetic, float64 dots
     assert abs(a12 - a21) <= 1e-4 * np.sqrt(a11 * a22)
+
+
+@pytest.mark.parametrize("mode", [mpm.HESS_PROJECTED, mpm.HESS_EXACT])
+def test_fullsize_operator_at_sampled_nodes(incline, mode):
+    """mpm_apply_hessian at ~40 sampled free nodes against the oracle's
+    per-particle definition, evaluated one node at a time from the particles and
+    samples that reach it. The direction vanishes on the Dirichlet and massless
+    nodes, so P dv = dv, and the sampled nodes are free, so P acts as the
+    identity on their rows."""
+    sc, ctx, p, srf = incline
+    n = sc.n
+    m = ctx.get_grid(0, mpm.FIELD_MASS)
+    vn = ctx.get_grid(0, mpm.FIELD_VN)
+    ctx.set_velocity(0, vn)
+    xi = oracle.node_positions(n, sc.dx)
+    g = np.stack(np.unravel_index(np.arange(m.size), tuple(n), order="F"), -1)
+    inner = np.all((g >= 2) & (g <= np.array(n) - 3), axis=1)
+    free = inner & (xi @ np.asarray(sc.plane_n) - sc.plane_d >= 0.0) & (m > 0)
+    rng = np.random.default_rng(8)
+    dv = rng.standard_normal((m.size, 3)) * free[:, None]
+    dv = dv.astype(np.float32).astype(np.float64)
+    # free nodes in the bulk, next to surface samples, and next to the plane
+    st = oracle.Stencil(srf["s"][rng.choice(len(srf["s"]), 16, replace=False)], sc.dx, n)
+    plane_phi = xi @ np.asarray(sc.plane_n) - sc.plane_d
+    near_plane = np.flatnonzero(free & (plane_phi < 2 * sc.dx))
+    nodes = np.concatenate([rng.choice(np.flatnonzero(free), 16, replace=False), st.node[:, 13],
+                            rng.choice(near_plane, 8, replace=False)])
+    nodes = np.unique(nodes[free[nodes]])
+    assert nodes.size >= 30
+    # the surface coefficient by interface kind (solid-liquid within dx of the plane)
+    kind_sl = srf["s"] @ np.asarray(sc.plane_n) - sc.plane_d < sc.dx
+    gamma = np.where(kind_sl, sc.params.gamma_sl, sc.params.gamma_lg)
+    full, stiff = hessvec_at_nodes(n, sc.dx, sc.params.dt, p["x"], sc.V0, p["J"], sc.params.lambda_l, srf["s"],
+                                   srf["dA"], gamma, vn, dv, m, nodes,
+                                   oracle.energy.HESS_PROJECTED if mode == mpm.HESS_PROJECTED
+                                   else oracle.energy.HESS_EXACT)
+    out = ctx.apply_hessian(0, dv.astype(np.float32), mode=mode).astype(np.float64)
+    got = out[nodes]
+    assert np.max(np.abs(got - full)) <= 2e-5 * np.max(np.abs(full))
+    got_stiff = got - m[nodes, None] * dv[nodes]
+    assert np.max(np.abs(got_stiff - stiff)) <= 1e-4 * np.max(np.abs(stiff))
+    assert np.max(np.abs(stiff)) > 0
 
 
 def test_fullsize_step_hands_grid_momentum_to_particles(incline):

@@ -89,12 +89,30 @@ def _deformed_solids():
     return sc
 
 
+def _crowded_droplet():
+    """27 particles per cell (a 3x3x3 sub-cell lattice): every interior cell holds
+    more particles than the operator kernel stages in one chunk, so its record
+    loop runs over several chunks."""
+    sc = scenes.droplet(n=16, r_cells=4.5, seed=12, ppc_axis=3, lambda_l=60.0)
+    sc.J = np.random.default_rng(12).uniform(0.95, 1.05, sc.J.shape)
+    return sc
+
+
 SCENES = {
     "droplet": lambda: scenes.config(0),
     "mixed": _mixed_scene,
 }
-# the operator tests also take the deformed solids
-OP_SCENES = dict(SCENES, deformed=_deformed_solids)
+# the operator tests also take the deformed solids and the crowded cells
+OP_SCENES = dict(SCENES, deformed=_deformed_solids, crowded=_crowded_droplet)
+
+
+def test_crowded_scene_has_cells_beyond_one_staging_chunk():
+    sc = _crowded_droplet()
+    c = np.floor(sc.x / sc.dx).astype(np.int64)
+    per_cell = np.bincount(c[:, 0] + sc.n[0] * (c[:, 1] + sc.n[1] * c[:, 2]))
+    # the kernel stages the records of a block in chunks of 10 rows (one row per
+    # particle of a cell): 27 per cell needs three chunks
+    assert per_cell.max() == 27 and np.sum(per_cell > 20) > 50
 
 
 def _setup(sc, prec):

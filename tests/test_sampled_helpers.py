@@ -24,3 +24,31 @@ def test_sampled_p2g_and_parents_match_the_whole_grid_oracle():
     np.testing.assert_allclose(mv, sim.grid["mv"][nodes], rtol=1e-12, atol=1e-15 * np.abs(sim.grid["mv"]).max())
     which = rng.choice(sc.n_surface, 40, replace=False)
     np.testing.assert_array_equal(nearest_parents(sc.x, sc.s, which, sc.dx, sc.n), sim.parent[which])
+
+
+def test_sampled_hessvec_matches_the_whole_grid_oracle():
+    """hessvec_at_nodes (one node at a time, on a window around it) against the
+    oracle's whole-grid Hessian-vector product, in both modes, at bulk nodes and
+    nodes reached by surface samples."""
+    from oracle.energy import HESS_EXACT, HESS_PROJECTED
+    from _sampled import hessvec_at_nodes
+    sc = scenes.droplet(n=20, r_cells=5.0, seed=14, lambda_l=70.0)
+    rng = np.random.default_rng(3)
+    sc.J = rng.uniform(0.9, 1.1, sc.J.shape)
+    sc.params.dt = 0.02
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    st = sim.newton_state()
+    act = st.active
+    v = (st.vn + 0.5 * rng.standard_normal(st.vn.shape)) * act[:, None]
+    dv = rng.standard_normal(v.shape) * act[:, None]
+    ss = oracle.Stencil(sc.s[:12], sc.dx, sc.n)
+    nodes = np.unique(np.concatenate([rng.choice(np.flatnonzero(act), 20, replace=False), ss.node[:, 13]]))
+    for mode in (HESS_PROJECTED, HESS_EXACT):
+        ref = st.hessvec(v, dv, mode)
+        full, stiff = hessvec_at_nodes(sc.n, sc.dx, sc.params.dt, sc.x, sc.V0, sc.J, sc.params.lambda_l, sc.s,
+                                       sc.dA, st.gamma, v, dv, st.m, nodes, mode)
+        scale = np.abs(ref).max()
+        np.testing.assert_allclose(full, ref[nodes], rtol=0, atol=1e-12 * scale)
+        np.testing.assert_allclose(stiff, ref[nodes] - st.m[nodes, None] * dv[nodes], rtol=0, atol=1e-12 * scale)
