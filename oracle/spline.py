@@ -59,6 +59,8 @@ def scatter(G, node, vals):
     """Sum vals (P, 27, ...) into a (G, ...) array at node ids (P, 27)."""
     vals = np.asarray(vals, np.float64)
     tail = vals.shape[2:]
+    if node.size == 0:   # no points: nothing lands on the grid
+        return np.zeros((G,) + tail)
     flat = vals.reshape(node.size, -1)
     out = np.zeros((G, flat.shape[1]))
     idx = node.ravel()

@@ -52,3 +52,20 @@ def test_sampled_hessvec_matches_the_whole_grid_oracle():
         scale = np.abs(ref).max()
         np.testing.assert_allclose(full, ref[nodes], rtol=0, atol=1e-12 * scale)
         np.testing.assert_allclose(stiff, ref[nodes] - st.m[nodes, None] * dv[nodes], rtol=0, atol=1e-12 * scale)
+
+
+def test_hessvec_with_only_surface_samples_near_the_node():
+    """A node whose mass comes from samples alone: the particle set of its window
+    is empty, and the row is the mass term plus the samples' terms."""
+    from oracle.energy import HESS_EXACT, HESS_PROJECTED
+    n, dx = (8, 8, 8), 1.0 / 8
+    m = np.zeros(512)
+    m[4 + 8 * (4 + 8 * 4)] = 0.3
+    s = np.array([[0.55, 0.55, 0.55]])
+    st = oracle.NewtonState(n, dx, 0.01, np.zeros(3), m, np.zeros((512, 3)), np.zeros((0, 3)), np.zeros(0),
+                            np.zeros(0), np.zeros((0, 3, 3)), np.zeros(0, np.int64), 50.0, 0.0, np.zeros(0),
+                            np.zeros(0), s, np.array([[0.0, 0.0, 0.01]]), np.array([1.0]))
+    dv = np.random.default_rng(1).standard_normal((512, 3))
+    for mode in (HESS_PROJECTED, HESS_EXACT):
+        out = st.hessvec(np.zeros((512, 3)), dv, mode)
+        assert np.all(np.isfinite(out)) and np.any(out != 0.0)
