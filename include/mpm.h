@@ -75,7 +75,15 @@ typedef enum { MPM_GAMMA_CONST = 0, MPM_GAMMA_LINEAR = 1 } mpm_gamma_law;
 
 /* Grid of one scene. Dirichlet velocity conditions (Eq. vbc): the two outer node
  * layers of face f (order x-, x+, y-, y+, z-, z+) follow walls[f]; nodes where the
- * plane's signed distance plane_n . x - plane_d is negative follow plane_mode. */
+ * plane's signed distance plane_n . x - plane_d is negative follow plane_mode;
+ * nodes inside the spherical solid follow sphere_mode. The sphere (the curved
+ * solids of section "Examples") has centre sphere[0..2] and radius sphere[3]; with
+ * sphere_outside = 1 the solid is |x - c| > R (a bowl holding the liquid), else
+ * |x - c| < R (a ball). A slip node of either solid loses the velocity component
+ * along that solid's unit normal at the node (the plane's normal, or (x - c)/|x - c|
+ * pointing into the liquid); a sticky node is fixed; a node in both solids, or in
+ * a solid and a wall layer, is fixed. Surface samples closer than dx to either
+ * solid are solid-liquid. */
 typedef struct {
     int32_t n[3];
     double dx;
@@ -85,6 +93,9 @@ typedef struct {
     double plane_d;
     int32_t plane_mode;
     int32_t pad_;
+    double sphere[4];
+    int32_t sphere_outside;
+    int32_t sphere_mode;
 } mpm_grid_desc;
 
 /* Physical and solver parameters of one scene (sections "Constitutive Models",
@@ -110,9 +121,10 @@ typedef struct {
     double heat_rtol;           /* heat CG tolerance relative to |rhs| */
     int32_t max_newton, max_cg, max_ls;
     int32_t phase_change;       /* 1: melt / freeze at T_melt after G2P */
-    double friction;            /* Coulomb coefficient mu_f >= 0 at the nodes of a slip plane, applied
-                                   to the end-of-step grid velocity (section "Examples", inclined
-                                   ramps): with v~ = v - r/m and v_n = v~ . n < 0 the tangential part t
+    double friction;            /* Coulomb coefficient mu_f >= 0 at the slip nodes of the plane and of
+                                   the sphere, applied to the end-of-step grid velocity (section
+                                   "Examples", inclined ramps): with v~ = v - r/m, n the solid's unit
+                                   normal at the node and v_n = v~ . n < 0, the tangential part t
                                    becomes max(0, 1 - mu_f |v_n| / |t|) t; 0 is the frictionless slip */
     int32_t massless_surface;   /* 1: the massless-sample variant the paper compares against (section
                                    "Surface Particle Sampling"): samples carry no mass, no balance

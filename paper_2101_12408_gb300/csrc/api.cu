@@ -291,6 +291,15 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
         for (int a = 0; a < 3; ++a) S.plane_n[a] = G.plane_mode ? G.plane_n[a] / nn : 0.0;
         for (int a = 0; a < 3; ++a) S.plane_nf[a] = (float)S.plane_n[a];
         S.plane_d = G.plane_mode ? G.plane_d / nn : 0.0;
+        S.sphere_mode = G.sphere_mode;
+        S.sphere_outside = G.sphere_outside ? 1 : 0;
+        for (int a = 0; a < 3; ++a) S.sphere_c[a] = G.sphere_mode ? G.sphere[a] : 0.0;
+        S.sphere_R = G.sphere_mode ? G.sphere[3] : 0.0;
+        if (G.sphere_mode < 0 || G.sphere_mode > 2 || (G.sphere_mode && !(G.sphere[3] > 0.0)) ||
+            (G.sphere_mode && !(std::isfinite(G.sphere[0]) && std::isfinite(G.sphere[1]) && std::isfinite(G.sphere[2])))) {
+            delete c;
+            return MPM_ERR_INVALID_ARG;
+        }
         S.newton_tol = P.newton_tol;
         S.cg_rtol = P.cg_rtol;
         S.heat_rtol = P.heat_rtol;
@@ -298,7 +307,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
         S.max_cg = P.max_cg;
         S.max_ls = P.max_ls;
         S.massless = P.massless_surface;
-        S.friction = G.plane_mode == MPM_WALL_SLIP ? P.friction : 0.0;
+        S.friction = (G.plane_mode == MPM_WALL_SLIP || G.sphere_mode == MPM_WALL_SLIP) ? P.friction : 0.0;
         S.p_begin = pb;
         S.p_end = pb + D.max_particles;
         S.s_begin = sb;
@@ -348,8 +357,7 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     A_(d.kind, uint8_t, Sn);
     A_(d.sid, int, Sn); A_(d.ssc, int, Sn); A_(d.parent, int, Sn);
     R_(d.sg, Sn); R_(d.sic, Sn); R_(d.swn, Sn);
-    R_(d.sK[0], 45 * Sn);   // one allocation: the 45 entries of a sample's map are Sn apart
-    for (int q = 1; q < 45; ++q) d.sK[q] = (char*)d.sK[0] + (size_t)q * Sn * c->rsize;
+    R_(d.sKa, (size_t)SREC * Sn);   // sample j's record at j * SREC
     A_(d.key, long long, P); A_(d.rank, int, P); A_(d.perm, int, P);
     A_(d.skey, long long, Sn); A_(d.srank, int, Sn); A_(d.sperm, int, Sn);
     A_(d.cell_count, int, c->total_cells + 1); A_(d.cell_start, int, c->total_cells + 1);

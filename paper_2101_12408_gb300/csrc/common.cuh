@@ -34,9 +34,11 @@ struct SceneDev {
     int walls[6];
     double plane_n[3], plane_d;
     float plane_nf[3], pad_f_;      // plane normal in float32 (the float32 projections)
+    double sphere_c[3], sphere_R;   // spherical solid: centre and radius
+    int sphere_outside, sphere_mode;
     double newton_tol, cg_rtol, heat_rtol;
     int max_newton, max_cg, max_ls, massless;
-    double friction;             // Coulomb coefficient at slip-plane nodes
+    double friction;             // Coulomb coefficient at slip nodes of the plane and the sphere
     long long p_begin, p_end;    // interior particles (set order == storage offset)
     long long s_begin, s_end;    // surface samples
 };
@@ -125,6 +127,30 @@ __device__ __forceinline__ void make_stencil_local(R ux, R uy, R uz, R inv_dx, i
     }
 }
 
+// Signed distance of x to the spherical solid (negative inside the solid) and
+// its unit normal (the gradient, pointing into the liquid); the direction is
+// (0, 0, 1) from (x - c) at the centre itself.
+__device__ __forceinline__ double sphere_phi_normal(const SceneDev& S, const double x[3], double n[3]) {
+    double d[3] = {x[0] - S.sphere_c[0], x[1] - S.sphere_c[1], x[2] - S.sphere_c[2]};
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double u[3] = {0.0, 0.0, 1.0};
+    if (r > 1e-300) {
+        u[0] = d[0] / r;
+        u[1] = d[1] / r;
+        u[2] = d[2] / r;
+    }
+    const double sgn = S.sphere_outside ? -1.0 : 1.0;
+    for (int a = 0; a < 3; ++a) n[a] = sgn * u[a];
+    return S.sphere_outside ? S.sphere_R - r : r - S.sphere_R;
+}
+
+// position of node l (0..63) of the block at bc
+__device__ __forceinline__ void node_position(const SceneDev& S, int4 bc, int l, double x[3]) {
+    x[0] = S.origin[0] + ((double)(bc.x * BS + (l & 3)) + 0.5) * S.dx;
+    x[1] = S.origin[1] + ((double)(bc.y * BS + ((l >> 2) & 3)) + 0.5) * S.dx;
+    x[2] = S.origin[2] + ((double)(bc.z * BS + (l >> 4)) + 0.5) * S.dx;
+}
+
 __device__ __forceinline__ int halo_index(int hx, int hy, int hz) { return hx + HE * (hy + HE * hz); }
 
 // Halo node h (0..215) of block `slot`: which neighbour slot and which local node.
@@ -188,6 +214,19 @@ __device__ __forceinline__ void matmul3_bt(const R* A, const R* B, R* C) {
 #pragma unroll
         for (int j = 0; j < 3; ++j)
             C[3 * i + j] = A[3 * i] * B[3 * j] + A[3 * i + 1] * B[3 * j + 1] + A[3 * i + 2] * B[3 * j + 2];
+}
+
+// Record of one surface sample for the Hessian operator: its projected-Hessian
+// map K (symmetric 9x9 on dF^ flattened row-major, rows 3q..3q+2 belong to
+// component q) grouped in 3x3 blocks, then its position in its block:
+//   [0, 6)   D0 = K(0,0) upper triangle (00 01 02 11 12 22), [6, 12) D1, [12, 18) D2,
+//   [18, 27) O01 = K(0,1) row-major, [27, 36) O02, [36, 45) O12, [45, 48) position.
+// The lane computing row block q of G = K dF^ reads D_q and the two off-diagonal
+// blocks of its rows (transposed where they lie below the diagonal).
+constexpr int SREC = 48;
+__host__ __device__ constexpr int sample_map_index(int m, int l) {   // m <= l
+    return (m / 3 == l / 3) ? 6 * (m / 3) + (m % 3) * 3 - (m % 3) * ((m % 3) - 1) / 2 + (l % 3 - m % 3)
+                            : (m / 3 == 0 ? (l / 3 == 1 ? 18 : 27) : 36) + 3 * (m % 3) + (l % 3);
 }
 
 // Four values of one type, 16- (float) or 32-byte (double) aligned: the packed

@@ -12,7 +12,7 @@
 namespace mpm {
 
 // Node projection codes (grid Dirichlet conditions, massless nodes).
-enum : uint8_t { PC_FIXED = 1, PC_SLIPX = 2, PC_SLIPY = 4, PC_SLIPZ = 8, PC_PLANE = 16 };
+enum : uint8_t { PC_FIXED = 1, PC_SLIPX = 2, PC_SLIPY = 4, PC_SLIPZ = 8, PC_PLANE = 16, PC_SPHERE = 32 };
 
 struct Dev {
     // ---- interior particles, float64, sorted by cell (SoA) ----
@@ -51,7 +51,9 @@ struct Dev {
     void* sn[3];                    // unit c (R)
     void* sic;                      // 1/|c| (R)
     void* swn;                      // Robin normaliser 1/sum_j N_j [m^T_j > 0] (R)
-    void* sK[45];                   // per-iterate symmetric 9x9 projected-Hessian map of a sample (R)
+    void* sKa;                      // per sample j, SREC values of R at j * SREC: the per-iterate symmetric
+                                    // 9x9 projected-Hessian map in 3x3 blocks (sample_map_index), then the
+                                    // sample's position in its block (cells) at 45..47
     void* pK[45];                   // the same for a solid particle (R, solid buffers only)
     // ---- sort / blocks ----
     long long* key;                 // interior cell keys
@@ -109,7 +111,7 @@ struct mpm_ctx {
     long long block_cap = 0;        // capacity of active blocks (grid slots)
     long long opk_cap = 0;          // capacity of d.opk in records (grown by the per-step pack)
     bool has_solids = false;        // solid-only buffers allocated
-    bool sK_valid = false;          // d.sK holds the maps of the cached iterate
+    bool sK_valid = false;          // d.sKa holds the maps of the cached iterate
     bool pK_valid = false;          // d.pK holds the solids' maps of the cached iterate
     bool use_graphs = true;         // CG chunks as CUDA graphs (cleared if capture is refused)
     int graph_error = 0;            // the refusal's error code
@@ -125,6 +127,7 @@ struct mpm_ctx {
     std::vector<unsigned long long> hscene_cnt;
     std::vector<long long> hscene_first;
     int NB = 0, NW = 0;
+    int n_gen = 0, n_gen_g = 0;     // work blocks in the general kernel's lists (with / without samples)
     bool resampled = false, p2g_done = false, step_ready = false;
     mpm::Dev d{};
     mpm::SceneScal* hscal = nullptr;   // pinned mirror

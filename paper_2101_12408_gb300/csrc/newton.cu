@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(NT) k_eval(EvalArgs<RS> a) {
 }
 
 // node part of the gradient: m (v - v^n) - dt m g; |P grad|^2 and the kinetic energy
-__device__ __forceinline__ void project3(double* v, uint8_t code, const SceneDev& S) {
+__device__ __forceinline__ void project3(double* v, uint8_t code, const SceneDev& S, int4 bc, int l) {
     if (code & PC_FIXED) {
         v[0] = v[1] = v[2] = 0.0;
         return;
@@ -438,10 +438,17 @@ __device__ __forceinline__ void project3(double* v, uint8_t code, const SceneDev
         double d = v[0] * S.plane_n[0] + v[1] * S.plane_n[1] + v[2] * S.plane_n[2];
         for (int q = 0; q < 3; ++q) v[q] -= d * S.plane_n[q];
     }
+    if (code & PC_SPHERE) {
+        double x[3], n[3];
+        node_position(S, bc, l, x);
+        sphere_phi_normal(S, x, n);
+        double d = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+        for (int q = 0; q < 3; ++q) v[q] -= d * n[q];
+    }
 }
 
 template <typename R>
-__device__ __forceinline__ void project3r(R* v, uint8_t code, const SceneDev& S) {
+__device__ __forceinline__ void project3r(R* v, uint8_t code, const SceneDev& S, int4 bc, int l) {
     if (code & PC_FIXED) {
         v[0] = v[1] = v[2] = R(0);
         return;
@@ -449,9 +456,17 @@ __device__ __forceinline__ void project3r(R* v, uint8_t code, const SceneDev& S)
     if (code & PC_SLIPX) v[0] = R(0);
     if (code & PC_SLIPY) v[1] = R(0);
     if (code & PC_SLIPZ) v[2] = R(0);
-    if (code & PC_PLANE) {
+    if (code & (PC_PLANE | PC_SPHERE)) {
         R n0, n1, n2;
-        if constexpr (sizeof(R) == 4) {
+        if (code & PC_SPHERE) {
+            // the sphere's normal at the node, rounded to R
+            double x[3], n[3];
+            node_position(S, bc, l, x);
+            sphere_phi_normal(S, x, n);
+            n0 = (R)n[0];
+            n1 = (R)n[1];
+            n2 = (R)n[2];
+        } else if constexpr (sizeof(R) == 4) {
             n0 = S.plane_nf[0];
             n1 = S.plane_nf[1];
             n2 = S.plane_nf[2];
@@ -487,7 +502,7 @@ __global__ void k_node_grad(const int4* __restrict__ coord, const SceneDev* __re
             grad[k] = gr[q];
             ek += 0.5 * m * dv * dv - S.dt * m * S.g[q] * v;
         }
-        project3(gr, pcode[t], S);
+        project3(gr, pcode[t], S, bc, l);
         rr = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
     }
     rr = warp_sum(rr);
@@ -508,7 +523,7 @@ struct ApplyArgs {
     const int *work, *work_gb, *nbr, *cell_start, *scell_start;
     const int4* coord;
     const SceneDev* sc;
-    const SceneScal* scal;
+    SceneScal* scal;
     const R* p;
     R* u;
     const uint8_t* phase;
@@ -523,11 +538,9 @@ struct ApplyArgs {
     RPtr9<R> sF;
     RPtr3<R> sn;
     const R* sic;
-    RPtr45<R> sK;             // surface: symmetric 9x9 map dF^ -> G of the projected Hessian (per iterate)
+    const R* sKa;             // surface: per-sample records (SREC values: the projected-Hessian map, position)
     RPtr45<R> pK;             // solid: symmetric 9x9 map dL -> M of the projected Hessian (per iterate)
     int use_pK;
-    const R* sK0;             // the same 45 arrays, contiguous: entry e of sample j at sK0[e * sKs + j]
-    long long sKs;
     int samples_in_cell;      // projected mode with current maps: k_apply_cell applies the samples
     const int* slot_gen;      // general particles per slot
     const R4<R>* opk;         // rank-major records: position in the block (cells), kappa (< 0: general)
@@ -536,6 +549,7 @@ struct ApplyArgs {
     int* err;
     int mode;
     int check_done;
+    int pap;                  // 1: add p . (H - M) p of the launch to the scene's pAp (p the direction)
 };
 
 // ======================================================================
@@ -771,22 +785,6 @@ __device__ __forceinline__ void gather_grad_row(const R* ph, const int* lc, cons
 }
 
 template <typename R>
-__device__ __forceinline__ void scatter_row(R* ua, const int* lc, const R (*w)[3], const R (*dw)[3], const R* m) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        R A0 = m[0] * dw[0][a], A1 = m[1] * w[0][a], A2 = m[2] * w[0][a];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            R B0 = A0 * w[1][b] + A1 * dw[1][b];
-            R B1 = A2 * w[1][b];
-            R* row = &ua[pidx(lc[0] + a, lc[1] + b, lc[2])];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) atomicAdd(row + c * PZ, B0 * w[2][c] + B1 * dw[2][c]);
-        }
-    }
-}
-
-template <typename R>
 __device__ __forceinline__ void scatter_sep(R (*ua)[PN], const int* lc, const R (*w)[3], const R (*dw)[3], const R* M) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -805,9 +803,48 @@ __device__ __forceinline__ void scatter_sep(R (*ua)[PN], const int* lc, const R 
     }
 }
 
-// general per-particle operator (solid or viscous liquid) on the padded layout
+// A thread's running sum of products formed in R: compensated (Kahan) in
+// float32, plain in float64, handed on in float64 (the CG reductions and the
+// operator's p . H p use it).
 template <typename R>
-__device__ __forceinline__ void particle_general(const ApplyArgs<R>& a, int i, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
+struct KSum {
+    R s = R(0), c = R(0);   // value s - c
+    __device__ void add(R x) {
+        if constexpr (sizeof(R) == 4) {
+            R y = x - c;
+            R t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    // sum over the warp (valid in lane 0), float32 pairs combined with an
+    // error-free two-sum, so the float64 pipe only sees lane 0's conversion
+    __device__ double warp_total() const {
+        if constexpr (sizeof(R) == 4) {
+            R hs = s, hc = c;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                R os = __shfl_down_sync(0xffffffffu, hs, o), oc = __shfl_down_sync(0xffffffffu, hc, o);
+                R t = hs + os;
+                R bb = t - hs;
+                R err = (hs - (t - bb)) + (os - bb);   // hs + os = t + err exactly
+                hs = t;
+                hc = hc + oc - err;
+            }
+            return (threadIdx.x & 31) == 0 ? (double)hs - (double)hc : 0.0;
+        } else {
+            return warp_sum((double)s);
+        }
+    }
+    __device__ void clear() { s = c = R(0); }
+};
+
+// general per-particle operator (solid or viscous liquid) on the padded layout
+// returns M : dL, the particle's share of p . (H - M) p
+template <typename R>
+__device__ __forceinline__ R particle_general(const ApplyArgs<R>& a, int i, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
     int lc[3];
     R wgt[3][3], dw[3][3];
     make_stencil_local<R>(a.pu.a[0][i], a.pu.a[1][i], a.pu.a[2][i], inv_dx, lc, wgt, dw);
@@ -851,10 +888,15 @@ __device__ __forceinline__ void particle_general(const ApplyArgs<R>& a, int i, R
         for (int q = 0; q < 9; ++q) M[q] *= sc;
     }
     scatter_sep<R>(ua, lc, wgt, dw, M);
+    R md = R(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) md += M[q] * dL[q];
+    return md;
 }
 
+// returns G : dF^, the sample's share of p . (H - M) p
 template <typename R>
-__device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
+__device__ __forceinline__ R sample_general(const ApplyArgs<R>& a, int j, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
     int lc[3];
     R wgt[3][3], dw[3][3];
     make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
@@ -886,12 +928,14 @@ __device__ __forceinline__ void sample_general(const ApplyArgs<R>& a, int j, R (
         add_conformal<R>(k * dt * dt, nv, av, dFh, G);
     }
     scatter_sep<R>(ua, lc, wgt, dw, G);
+    R gd = R(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) gd += G[q] * dFh[q];
+    return gd;
 }
 
 constexpr int NT_CELL = 64;
 constexpr int NT_GEN = 32;  // one warp: a block holds ~20-40 surface samples
-constexpr int KROWS = 10;   // record rows staged per chunk
-constexpr int MAXP = KROWS * 64;
 
 // Halo rows along x: the four middle nodes of a row belong to one neighbour block
 // and are contiguous there (x fastest), so they move as one vector; the two end
@@ -962,11 +1006,144 @@ __device__ __forceinline__ void flush_halo_rows(const int* __restrict__ nbr, int
     }
 }
 
+
+// ----------------------------------------------------------------------
+// Scatter without shared atomics. Each warp owns 32 cells forming a 4x4x2 brick
+// and accumulates into its own z-range of the halo (warp 0: node levels 0..3,
+// warp 1: levels 2..5, stored at 4..7), so the two warps never touch the same
+// word. Within a warp, for one stencil offset the 32 lanes write 32 distinct
+// nodes, and offsets whose z differs by 2 never meet (a warp's cells span two z
+// levels), so each phase below is a plain read-add-write by every lane with no
+// two lanes on one node; __syncwarp orders the phases.
+constexpr int UZ = 8;
+constexpr int UN = PZ * UZ;
+constexpr int KR2 = 8;   // record rows staged per chunk
+
+// every lane of the warp calls it; lanes with act = false only take part in the
+// phase ordering (two lanes may never write one node in one phase)
+template <typename R>
+__device__ __forceinline__ void rmw_phases(R* uq, const R (&N)[3][3][3], int lx, int ly, int zb, bool act = true) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            __syncwarp();
+            if (act) {
+                R* p0 = uq + pidx(lx + a, ly + b, zb);
+                R* p2 = uq + pidx(lx + a, ly + b, zb + 2);
+                const R v0 = *p0, v2 = *p2;
+                *p0 = v0 + N[a][b][0];
+                *p2 = v2 + N[a][b][2];
+            }
+        }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            __syncwarp();
+            if (act) {
+                R* p1 = uq + pidx(lx + a, ly + b, zb + 1);
+                *p1 += N[a][b][1];
+            }
+        }
+    __syncwarp();
+}
+
+// node values (without the 1/dx factor) of the cell's moments, component by
+// component, added to the warp's accumulation halo (every lane of the warp calls it)
+template <typename R>
+__device__ __forceinline__ void cell_scatter_warp(const R (&M)[3][3][3], R (*ua)[UN], int lx, int ly, int zb) {
+    R N[3][3][3];
+    {
+        R T1[2][3][3], T2[2][3][3];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) wN<R>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) wN<R>(T1[i][0][c], T1[i][1][c], T1[i][2][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dN<R>(T2[0][b][c], T2[1][b][c], N[0][b][c], N[1][b][c], N[2][b][c]);
+    }
+    rmw_phases<R>(ua[0], N, lx, ly, zb);
+    {
+        R T1[3][2][3], T2[3][3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) wN<R>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dN<R>(T1[i][0][c], T1[i][1][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) wN<R>(T2[0][b][c], T2[1][b][c], T2[2][b][c], N[0][b][c], N[1][b][c], N[2][b][c]);
+    }
+    rmw_phases<R>(ua[1], N, lx, ly, zb);
+    {
+        R T1[3][3][3], T2[3][3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) dN<R>(M[i][j][0], M[i][j][1], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) wN<R>(T1[i][0][c], T1[i][1][c], T1[i][2][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) wN<R>(T2[0][b][c], T2[1][b][c], T2[2][b][c], N[0][b][c], N[1][b][c], N[2][b][c]);
+    }
+    rmw_phases<R>(ua[2], N, lx, ly, zb);
+}
+
+template <typename R>
+__device__ __forceinline__ void flush_halo_rows_u(const int* __restrict__ nbr, int slot, R (*ua)[UN], R* __restrict__ u) {
+    for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
+        int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<R>(nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        R v[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = R(0);
+        if (hz <= 3) {
+            const R* s = &ua[c][pidx(0, hy, hz)];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] += s[k];
+        }
+        if (hz >= 2) {
+            const R* s = &ua[c][pidx(0, hy, hz + 2)];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] += s[k];
+        }
+        if (nlo >= 0 && v[0] != R(0)) atomicAdd(&u[nlo * 192 + c * 64 + base + 3], v[0]);
+        if (nhi >= 0 && v[5] != R(0)) atomicAdd(&u[nhi * 192 + c * 64 + base], v[5]);
+        if (nmid >= 0 && (v[1] != R(0) || v[2] != R(0) || v[3] != R(0) || v[4] != R(0))) {
+            R* dst = u + nmid * 192 + c * 64 + base;
+            if constexpr (sizeof(R) == 4) {
+                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[1], v[2], v[3], v[4]));
+            } else {
+                atomicAdd(dst, v[1]);
+                atomicAdd(dst + 1, v[2]);
+                atomicAdd(dst + 2, v[3]);
+                atomicAdd(dst + 3, v[4]);
+            }
+        }
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
-    __shared__ R ua[3][PN];
-    __shared__ R4<R> sp[MAXP];
+    __shared__ R ua[3][UN];
+    __shared__ R4<R> sp[KR2 * 64];
     __shared__ __align__(8) uint64_t bar;
     int w = blockIdx.x;
     int slot = a.work[w];
@@ -974,139 +1151,250 @@ __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell
     int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
     if (a.check_done && a.scal[bc.w].cg_done) return;
-    // rank-major records: row r holds the r-th particle of each of the 64 cells,
-    // so a warp reads 32 consecutive records (no bank conflicts)
     const int rows = a.wrows[w];
     const R4<R>* recs = a.opk + (long long)a.wroff[w] * 64;
-    const int nchunk = (rows + KROWS - 1) / KROWS;
+    const int nchunk = (rows + KR2 - 1) / KR2;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
+    for (int i = threadIdx.x; i < 3 * UN; i += blockDim.x) (&ua[0][0])[i] = R(0);
     __syncthreads();
-    // the block's records stream into shared memory (TMA bulk copy) while the
-    // threads stage the direction's halo
     if (threadIdx.x == 0 && nchunk > 0) {
-        uint32_t cnt = (uint32_t)min(KROWS, rows) * 64u;
+        uint32_t cnt = (uint32_t)min(KR2, rows) * 64u;
         mbar_expect_tx(&bar, cnt * (uint32_t)sizeof(R4<R>));
         bulk_g2s(sp, recs, cnt * (uint32_t)sizeof(R4<R>), &bar);
     }
-    load_halo_rows<R>(a.nbr, slot, a.p, ph, ua);
+    {
+        // the direction's halo
+        for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
+            int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+            int nmid, nlo, nhi, base;
+            halo_row<R>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
+            R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
+            if (nmid >= 0) {
+                const R* src = a.p + nmid * 192 + c * 64 + base;
+                if constexpr (sizeof(R) == 4) {
+                    float4 v = *reinterpret_cast<const float4*>(src);
+                    m0 = v.x; m1 = v.y; m2 = v.z; m3 = v.w;
+                } else {
+                    m0 = src[0]; m1 = src[1]; m2 = src[2]; m3 = src[3];
+                }
+            }
+            int h0 = pidx(0, hy, hz);
+            ph[c][h0] = nlo >= 0 ? a.p[nlo * 192 + c * 64 + base + 3] : R(0);
+            ph[c][h0 + 1] = m0;
+            ph[c][h0 + 2] = m1;
+            ph[c][h0 + 3] = m2;
+            ph[c][h0 + 4] = m3;
+            ph[c][h0 + 5] = nhi >= 0 ? a.p[nhi * 192 + c * 64 + base] : R(0);
+        }
+    }
     __syncthreads();
     const R inv_dx = (R)S.inv_dx;
     const R s2 = inv_dx * inv_dx;
     const int cell = threadIdx.x;
     const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
+    const int wid = threadIdx.x >> 5;
     const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
     R C[3][3][3], M[3][3][3];
-    if (cend > cbeg) {
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            (&C[0][0][0])[q] = R(0);
-            (&M[0][0][0])[q] = R(0);
-        }
-        cell_coefficients<R>(ph, lx, ly, lz, C);
+    for (int q = 0; q < 27; ++q) {
+        (&C[0][0][0])[q] = R(0);
+        (&M[0][0][0])[q] = R(0);
     }
+    if (cend > cbeg) cell_coefficients<R>(ph, lx, ly, lz, C);
+    KSum<R> pap;   // p . (H - M) p of this block's particles and samples
     bool any = false, timed_out = false;
     uint32_t parity_left = 0;
     const int ncell = cend - cbeg;
     for (int k = 0; k < nchunk; ++k) {
-        const int r0 = k * KROWS;
-        // bounded wait; the CTA agrees on the outcome so that no thread is left at a barrier
+        const int r0 = k * KR2;
         bool ok = mbar_wait_bounded(&bar, (uint32_t)(k & 1), 1LL << 26);
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             parity_left = (uint32_t)(k & 1);
             break;
         }
-        const int rhi = min(ncell, r0 + KROWS);
+        const int rhi = min(ncell, r0 + KR2);
         for (int r = r0; r < rhi; ++r) {
             R4<R> rec = sp[(r - r0) * 64 + cell];
             if (rec.w < R(0)) continue;   // general particle: k_apply_general
             any = true;
-            R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
-            R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
-            R tz = fmin(fmax(rec.z - R(lz), R(0)), R(1));
-            R px[3] = {R(1), tx, tx * tx};
-            R py[3] = {R(1), ty, ty * ty}, pz[3] = {R(1), tz, tz * tz};
-            R yz[3][3];
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-#pragma unroll
-                for (int kk = 0; kk < 3; ++kk) yz[j][kk] = py[j] * pz[kk];
-            R tr = R(0);
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-#pragma unroll
-                    for (int kk = 0; kk < 3; ++kk)
-                        if (!(ii == 2 && j == 2 && kk == 2)) tr += C[ii][j][kk] * px[ii] * yz[j][kk];
-            R s = rec.w * s2 * tr;
+            const R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
+            const R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
+            const R tz = fmin(fmax(rec.z - R(lz), R(0)), R(1));
+            // tr(dL)(t) by Horner's rule, z then y then x (no t^2 t^2 t^2 term)
+            R E[3];
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii) {
-                R sx = s * px[ii];
+                R D[3];
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
+                    D[j] = (ii == 2 && j == 2) ? C[2][2][0] + tz * C[2][2][1] : C[ii][j][0] + tz * (C[ii][j][1] + tz * C[ii][j][2]);
+                E[ii] = D[0] + ty * (D[1] + ty * D[2]);
+            }
+            const R tr = E[0] + tx * (E[1] + tx * E[2]);
+            const R s = rec.w * s2 * tr;
+            pap.add(s * tr);
+            const R tz2 = tz * tz;
+            R sx = s;
 #pragma unroll
-                    for (int kk = 0; kk < 3; ++kk)
-                        if (!(ii == 2 && j == 2 && kk == 2)) M[ii][j][kk] += sx * yz[j][kk];
+            for (int ii = 0; ii < 3; ++ii) {
+                R sxy = sx;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    M[ii][j][0] += sxy;
+                    M[ii][j][1] += sxy * tz;
+                    if (!(ii == 2 && j == 2)) M[ii][j][2] += sxy * tz2;
+                    sxy *= ty;
+                }
+                sx *= tx;
             }
         }
-        __syncthreads();   // every thread is done with this chunk
+        __syncthreads();
         if (k + 1 < nchunk && threadIdx.x == 0) {
-            uint32_t cnt2 = (uint32_t)min(KROWS, rows - (r0 + KROWS)) * 64u;
+            uint32_t cnt2 = (uint32_t)min(KR2, rows - (r0 + KR2)) * 64u;
             mbar_expect_tx(&bar, cnt2 * (uint32_t)sizeof(R4<R>));
-            bulk_g2s(sp, recs + (long long)(r0 + KROWS) * 64, cnt2 * (uint32_t)sizeof(R4<R>), &bar);
+            bulk_g2s(sp, recs + (long long)(r0 + KR2) * 64, cnt2 * (uint32_t)sizeof(R4<R>), &bar);
         }
     }
     if (timed_out) {
-        // record the failure; wait once more (bounded) for the copy in flight, then leave
         if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
         mbar_wait_bounded(&bar, parity_left, 1LL << 20);
         return;
     }
-    if (any) cell_scatter<R>(M, ua, lx, ly, lz);
-    if (a.samples_in_cell) {
-        // The block's surface samples share the halo already staged for its
-        // particles. Three lanes per sample, one per component: lane q gathers row q
-        // of dF^, the rows are exchanged within the lane triple, lane q forms row q of
-        // G = K dF^ and scatters it (10 samples per warp, lanes 30 and 31 idle).
-        const int sbeg = a.scell_start[gb * 64], nsm = a.scell_start[gb * 64 + 64] - sbeg;
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        const int si = lane / 3, q = lane - 3 * (lane / 3);
-        for (int base = 0; base < nsm; base += 10 * (NT_CELL / 32)) {
-            const int k = base + wid * 10 + si;
-            const bool act = lane < 30 && k < nsm;
-            const int j = sbeg + (act ? k : 0);
-            int lc[3];
-            R wgt[3][3], dw[3][3];
-            make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
-            R g[3] = {R(0), R(0), R(0)};
-            if (act) gather_grad_row<R>(ph[q], lc, wgt, dw, g);
-            R dF[9];
-            const int l0 = 3 * si < 30 ? 3 * si : 0;
+    // The block's surface samples (projected mode with current maps): their
+    // records (map and position, SREC values each) are staged into the record
+    // buffer by one bulk copy per chunk, the first issued here so that it lands
+    // while the warps scatter their cells.
+    const int sbeg = a.scell_start[gb * 64], nsm = a.samples_in_cell ? a.scell_start[gb * 64 + 64] - sbeg : 0;
+    constexpr int SCAP = (KR2 * 64 * 4) / SREC;   // samples per staged chunk
+    R* sbuf = reinterpret_cast<R*>(sp);
+    uint32_t phase = (uint32_t)nchunk;          // bulk copies completed on `bar` so far
+    if (nsm > 0 && threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)(min(nsm, SCAP) * SREC * sizeof(R));
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(sbuf, a.sKa + (long long)sbeg * SREC, bytes, &bar);
+    }
+    // every lane of a warp takes part in its scatter phases (empty cells add zeros)
+    if (__any_sync(0xffffffffu, any)) cell_scatter_warp<R>(M, ua, lx, ly, lz + 2 * wid);
+    if (nsm > 0) {
+        // A warp takes the samples of its own 32 cells, in rank order: pass r holds
+        // the r-th sample of every cell that has one, so the (up to ten) samples of
+        // one iteration lie in distinct cells and, per stencil offset, write
+        // distinct nodes. Each sample's stencil is taken relative to its sorted
+        // cell (t clamped to [0, 1]: the weights agree with the rounded position's),
+        // which keeps its nodes inside the warp's accumulation levels. Three lanes
+        // per sample: lane q gathers row q of dF^, forms row block q of G = K dF^
+        // from D_q and its two off-diagonal blocks, and adds row q of G gradN.
+        __shared__ int stab[NT_CELL / 32][32];
+        const int lane = threadIdx.x & 31;
+        const int si = lane / 3, q = lane - 3 * si;
+        const int qa = q == 0 ? 1 : 0, qb = q == 2 ? 1 : 2;                 // the other two row blocks
+        const int offA = q == 2 ? 27 : 18, offB = q == 0 ? 27 : 36;        // their 3x3 blocks
+        const bool trA = q != 0, trB = q == 2;                              // below the diagonal: transposed
+        const int scs = a.scell_start[gb * 64 + cell] - sbeg, sce = a.scell_start[gb * 64 + cell + 1] - sbeg;
+        for (int c0 = 0; c0 < nsm; c0 += SCAP) {
+            const int c1 = min(nsm, c0 + SCAP);
+            const bool ok = mbar_wait_bounded(&bar, phase & 1u, 1LL << 26);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
+                mbar_wait_bounded(&bar, phase & 1u, 1LL << 20);
+                return;
+            }
+            ++phase;
+            const int cs = max(scs, c0), cnt = max(0, min(sce, c1) - cs);
+            const int maxcnt = __reduce_max_sync(0xffffffffu, cnt);
+            for (int r = 0; r < maxcnt; ++r) {
+                const unsigned mask = __ballot_sync(0xffffffffu, cnt > r);
+                const int n = __popc(mask);
+                if (cnt > r) stab[wid][__popc(mask & ((1u << lane) - 1u))] = lane;
+                __syncwarp();
+                for (int base = 0; base < n; base += 10) {
+                    const int k = base + si;
+                    const bool act = lane < 30 && k < n;
+                    const int cl = act ? stab[wid][k] : 0;
+                    const int jr = __shfl_sync(0xffffffffu, cs, cl) + r - c0;   // record in the chunk
+                    const int sc = wid * 32 + cl;
+                    const int sx = sc & 3, sy = (sc >> 2) & 3, sz = sc >> 4;
+                    const R* rec = sbuf + (act ? jr : 0) * SREC;
+                    R wgt[3][3], dw[3][3];
+                    {
+                        const R tt[3] = {fmin(fmax(rec[45] - R(sx), R(0)), R(1)), fmin(fmax(rec[46] - R(sy), R(0)), R(1)),
+                                         fmin(fmax(rec[47] - R(sz), R(0)), R(1))};
 #pragma unroll
-            for (int qq = 0; qq < 3; ++qq)
+                        for (int ax = 0; ax < 3; ++ax) {
+                            bspline<R>(tt[ax] + R(0.5), wgt[ax], dw[ax]);
 #pragma unroll
-                for (int e = 0; e < 3; ++e) dF[3 * qq + e] = __shfl_sync(0xffffffffu, g[e], l0 + qq);
-            if (act) {
-                R m3[3];
-#pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    const int row = 3 * q + e;
-                    R acc = R(0);
-#pragma unroll
-                    for (int l = 0; l < 9; ++l) {
-                        const int lo = row < l ? row : l, hi = row < l ? l : row;
-                        acc += a.sK0[(long long)sym9(lo, hi) * a.sKs + j] * dF[l];
+                            for (int kk = 0; kk < 3; ++kk) dw[ax][kk] *= inv_dx;
+                        }
                     }
-                    m3[e] = acc;
+                    const int lc[3] = {sx, sy, sz};
+                    R g[3] = {R(0), R(0), R(0)};
+                    if (act) gather_grad_row<R>(ph[q], lc, wgt, dw, g);
+                    const int l0 = 3 * si < 30 ? 3 * si : 0;
+                    R gA[3], gB[3];
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        gA[e] = __shfl_sync(0xffffffffu, g[e], l0 + qa);
+                        gB[e] = __shfl_sync(0xffffffffu, g[e], l0 + qb);
+                    }
+                    R N[3][3][3];
+                    if (act) {
+                        const R* Dq = rec + 6 * q;
+                        const R DM[3][3] = {{Dq[0], Dq[1], Dq[2]}, {Dq[1], Dq[3], Dq[4]}, {Dq[2], Dq[4], Dq[5]}};
+                        R bA[9], bB[9];
+#pragma unroll
+                        for (int m = 0; m < 9; ++m) {
+                            bA[m] = rec[offA + m];
+                            bB[m] = rec[offB + m];
+                        }
+                        R m3[3];
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) {
+                            R acc = R(0);
+#pragma unroll
+                            for (int f = 0; f < 3; ++f) {
+                                const R ka = trA ? bA[3 * f + e] : bA[3 * e + f];
+                                const R kb = trB ? bB[3 * f + e] : bB[3 * e + f];
+                                acc += DM[e][f] * g[f] + ka * gA[f] + kb * gB[f];
+                            }
+                            m3[e] = acc;
+                        }
+                        pap.add(m3[0] * g[0] + m3[1] * g[1] + m3[2] * g[2]);
+#pragma unroll
+                        for (int aa = 0; aa < 3; ++aa) {
+                            const R A0 = m3[0] * dw[0][aa], A1 = m3[1] * wgt[0][aa], A2 = m3[2] * wgt[0][aa];
+#pragma unroll
+                            for (int bb = 0; bb < 3; ++bb) {
+                                const R B0 = A0 * wgt[1][bb] + A1 * dw[1][bb], B1 = A2 * wgt[1][bb];
+#pragma unroll
+                                for (int cc = 0; cc < 3; ++cc) N[aa][bb][cc] = B0 * wgt[2][cc] + B1 * dw[2][cc];
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 27; ++m) (&N[0][0][0])[m] = R(0);
+                    }
+                    // component q's accumulation levels of this warp
+                    rmw_phases<R>(ua[q], N, sx, sy, sz + 2 * wid, act);
                 }
-                scatter_row<R>(ua[q], lc, wgt, dw, m3);
+                __syncwarp();   // stab is rewritten by the next pass
+            }
+            __syncthreads();   // both warps are done with this chunk
+            if (c1 < nsm && threadIdx.x == 0) {
+                const uint32_t bytes = (uint32_t)(min(nsm - c1, SCAP) * SREC * sizeof(R));
+                mbar_expect_tx(&bar, bytes);
+                bulk_g2s(sbuf, a.sKa + (long long)(sbeg + c1) * SREC, bytes, &bar);
             }
         }
     }
+    if (a.pap) {
+        const double v = pap.warp_total();
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&a.scal[bc.w].pAp, v);
+    }
     __syncthreads();
-    flush_halo_rows<R>(a.nbr, slot, ua, a.u);
+    flush_halo_rows_u<R>(a.nbr, slot, ua, a.u);
 }
+
 
 // Per-iterate projected Hessian of each solid particle (the reading of the
 // paper's "definiteness fix" for solids): the 9x9 Hessian of psi(F) from the
@@ -1213,7 +1501,8 @@ __global__ void k_solid_hess(int np, const uint8_t* __restrict__ phase, const in
 // per sample instead of re-deriving frames and cofactor derivatives.
 template <typename R>
 __global__ void k_surf_hess(int ns, const int* __restrict__ ssc, const SceneDev* __restrict__ sc, RPtr9<R> sF,
-                            RPtr3<R> sa, RPtr3<R> sn, const R* __restrict__ sic, const R* __restrict__ sg, RPtr45<R> K) {
+                            RPtr3<R> sa, RPtr3<R> sn, const R* __restrict__ sic, const R* __restrict__ sg, RPtr3<R> su,
+                            R* __restrict__ K) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ns) return;
     const SceneDev& S = sc[ssc[j]];
@@ -1239,8 +1528,9 @@ __global__ void k_surf_hess(int ns, const int* __restrict__ ssc, const SceneDev*
         R G[9];
         surf_G<R>(k, dn, Fh, av, G);
         add_conformal<R>(k, nv, av, X, G);
-        for (int m = 0; m <= l; ++m) K.a[sym9(m, l)][j] = G[m];
+        for (int m = 0; m <= l; ++m) K[(long long)j * SREC + sample_map_index(m, l)] = G[m];
     }
+    for (int q = 0; q < 3; ++q) K[(long long)j * SREC + 45 + q] = su.a[q][j];
 }
 
 // Solids, viscous liquids and surface samples: one thread per particle or
@@ -1282,6 +1572,7 @@ __global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_gener
     for (int b = 0; b < GEN_B; ++b)
         if (act[b]) load_halo_rows<R>(a.nbr, slot[b], a.p, ph[b], ua[b]);
     __syncthreads();
+    KSum<R> pap[GEN_B];
 #pragma unroll
     for (int b = 0; b < GEN_B; ++b) {
         if (!act[b] || a.slot_gen[slot[b]] == 0) continue;
@@ -1295,7 +1586,7 @@ __global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_gener
             const int cb = a.cell_start[gb * 64 + c], ce = a.cell_start[gb * 64 + c + 1];
             for (int i = cb; i < ce; ++i)
                 if (a.phase[i] != 0 || a.cvisc[i] != R(0))
-                    particle_general<R>(a, i, ph[b], ua[b], (R)S.dt, (R)S.inv_dx);
+                    pap[b].add(particle_general<R>(a, i, ph[b], ua[b], (R)S.dt, (R)S.inv_dx));
         }
     }
     static_assert(GEN_B == 2, "the sample loop below selects between two blocks");
@@ -1303,7 +1594,16 @@ __global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_gener
         const bool second = k >= nsm[0];
         const int j = second ? sbeg[1] + (k - nsm[0]) : sbeg[0] + k;
         const SceneDev& S = a.sc[second ? scene[1] : scene[0]];
-        sample_general<R>(a, j, second ? ph[1] : ph[0], second ? ua[1] : ua[0], (R)S.dt, (R)S.inv_dx);
+        const R gd = sample_general<R>(a, j, second ? ph[1] : ph[0], second ? ua[1] : ua[0], (R)S.dt, (R)S.inv_dx);
+        if (second) pap[1].add(gd);
+        else pap[0].add(gd);
+    }
+    if (a.pap) {
+#pragma unroll
+        for (int b = 0; b < GEN_B; ++b) {
+            const double v = pap[b].warp_total();   // one warp per CTA
+            if (act[b] && threadIdx.x == 0 && v != 0.0) atomicAdd(&a.scal[scene[b]].pAp, v);
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -1591,7 +1891,7 @@ __device__ __forceinline__ R cg_prec(const CGArgs<R, NC>& a, int slot, int c, in
 
 template <typename R, int NC>
 __device__ __forceinline__ void cg_proj(R* v, const CGArgs<R, NC>& a, int t, const SceneDev& S) {
-    if (NC == 3) project3r<R>(v, a.pcode[t], S);
+    if (NC == 3) project3r<R>(v, a.pcode[t], S, a.coord[t >> 6], t & 63);
     else if (a.inv[t] == R(0)) v[0] = R(0);
 }
 
@@ -1646,7 +1946,7 @@ __device__ __forceinline__ void cta_scene_sum2_warp(double v1, double v2, int sc
 
 // r = P b, x = 0, z = P(inv r), p = z, u = 0; rz, bnorm (if requested)
 template <typename R, int NC>
-__global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int set_bnorm) {
+__global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int set_bnorm, int fused_pap) {
     int slot = blockIdx.x * CG_SLOTS + (threadIdx.x >> 6), l = threadIdx.x & 63;
     int scene = -1;
     double bb = 0.0, rz = 0.0;
@@ -1679,50 +1979,30 @@ __global__ void __launch_bounds__(CG_NT) k_cg_init(CGArgs<R, NC> a, int nb, int 
         }
     }
     cta_scene_sum2(rz, bb, scene, a.scal, OFF_RZ, set_bnorm ? OFF_BN : -1);
+    if (NC == 3 && fused_pap) {
+        // p . M p of the first direction p = z (the operator adds p . (H - M) p)
+        double mpp = 0.0;
+        if (slot < nb && !a.scal[scene].cg_done) {
+            const int t = slot * 64 + l;
+            R s = R(0);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                const R pv = a.p[vidx<R, NC>(slot, q, l)];
+                s += a.mR[t] * pv * pv;
+            }
+            mpp = (double)s;
+        }
+        __syncthreads();
+        cta_scene_sum2(mpp, 0.0, scene, a.scal, OFF_PAP, -1);
+    }
 }
 
-// ---- one CG iteration's vector work as a single cooperative launch ----
-// Each thread sums the per-node products (formed in R) of the nodes it visits:
-// compensated (Kahan) in float32, plain in float64, and hands the sum on in
-// float64. Warps stay scene-uniform (a warp covers 32 nodes of one slot and all
-// lanes visit the same slots), so a change of scene flushes the warp's sums
-// with one atomic; the last scene's sums go through the CTA reduction
-// (cta_scene_sum2).
-template <typename R>
-struct KSum {
-    R s = R(0), c = R(0);   // value s - c
-    __device__ void add(R x) {
-        if constexpr (sizeof(R) == 4) {
-            R y = x - c;
-            R t = s + y;
-            c = (t - s) - y;
-            s = t;
-        } else {
-            s += x;
-        }
-    }
-    // sum over the warp (valid in lane 0), float32 pairs combined with an
-    // error-free two-sum, so the float64 pipe only sees lane 0's conversion
-    __device__ double warp_total() const {
-        if constexpr (sizeof(R) == 4) {
-            R hs = s, hc = c;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                R os = __shfl_down_sync(0xffffffffu, hs, o), oc = __shfl_down_sync(0xffffffffu, hc, o);
-                R t = hs + os;
-                R bb = t - hs;
-                R err = (hs - (t - bb)) + (os - bb);   // hs + os = t + err exactly
-                hs = t;
-                hc = hc + oc - err;
-            }
-            return (threadIdx.x & 31) == 0 ? (double)hs - (double)hc : 0.0;
-        } else {
-            return warp_sum((double)s);
-        }
-    }
-    __device__ void clear() { s = c = R(0); }
-};
 
+// ---- one CG iteration's vector work as a single cooperative launch ----
+// Each thread sums the per-node products of the nodes it visits (KSum). Warps
+// stay scene-uniform (a warp covers 32 nodes of one slot and all lanes visit the
+// same slots), so a change of scene flushes the warp's sums with one atomic; the
+// last scene's sums go through the CTA reduction (cta_scene_sum2).
 template <typename R>
 struct SceneAcc {
     KSum<R> a1, a2;
@@ -1920,6 +2200,119 @@ __global__ void __launch_bounds__(CG_NT, 3) k_cg_iter(CGArgs<R, NC> a, int nb, i
     }
 }
 
+// The momentum CG iteration with p . A p already summed: the operator kernels
+// add p . (H - M) p per particle and sample, and the step that formed p (the
+// previous iteration's phase D, or k_cg_init) added p . M p, so the iteration
+// starts at B:
+//   B: q = P (M p + u) on the fly, x += alpha p, r -= alpha q, u = 0,
+//      z = P(inv r); rz_new, rr
+//   C: per-scene control (zeroes pAp)
+//   D: p = z + beta p, and p . M p of the new p into pAp
+template <typename R>
+__global__ void __launch_bounds__(CG_NT, 3) k_cg_iter2(CGArgs<R, 3> a, int nb, int nsc, unsigned* bar, int* err) {
+    const int nchunks = (nb + CG_SLOTS - 1) / CG_SLOTS;
+    const int l = threadIdx.x & 63;
+    SceneAcc<R> acc;
+    int ascene = -1;
+    R alpha = R(0);
+    bool curv_ok = true;
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
+        if (slot >= nb) continue;
+        const int scene = a.coord[slot].w;
+        const SceneDev& S = a.sc[scene];
+        const SceneScal& sc = a.scal[scene];
+        R rzl = R(0), rrl = R(0);
+        if (!sc.cg_done) {
+            const int t = slot * 64 + l;
+            if (scene != ascene) {   // once per scene change, not per node
+                const double pAp = sc.pAp;
+                curv_ok = pAp > 0.0;
+                alpha = curv_ok ? (R)sc.rz / (R)pAp : R(0);
+                ascene = scene;
+            }
+            if (!curv_ok) {
+                if (sc.cg_it == 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const int k = slot * 192 + c * 64 + l;
+                        a.x[k] = a.p[k];
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a.u[slot * 192 + c * 64 + l] = R(0);
+            } else {
+                const R mr = a.mR[t];
+                R pv[3], q[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int k = slot * 192 + c * 64 + l;
+                    pv[c] = a.p[k];
+                    q[c] = mr * pv[c] + a.u[k];
+                }
+                cg_proj<R, 3>(q, a, t, S);
+                R r[3], z[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int k = slot * 192 + c * 64 + l;
+                    a.x[k] += alpha * pv[c];
+                    r[c] = a.r[k] - alpha * q[c];
+                    a.r[k] = r[c];
+                    a.u[k] = R(0);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) z[c] = r[c] * cg_prec<R, 3>(a, slot, c, l, t);
+                cg_proj<R, 3>(z, a, t, S);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    rzl += r[c] * z[c];
+                    rrl += r[c] * r[c];
+                }
+            }
+        }
+        acc.add(scene, rzl, rrl, a.scal, OFF_RZN, OFF_RR);
+    }
+    cta_scene_sum2_warp(acc.a1.warp_total(), acc.a2.warp_total(), acc.cur, a.scal, OFF_RZN, OFF_RR);
+    if (!grid_barrier(bar, err)) return;
+    if (blockIdx.x == 0)
+        for (int s = threadIdx.x; s < nsc; s += blockDim.x) cg_check_scene(a.scal[s], a.sc[s], 0);
+    if (!grid_barrier(bar, err)) return;
+    acc.a1.clear();
+    acc.a2.clear();
+    acc.cur = -1;
+    int bscene = -1;
+    R beta = R(0);
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+        const int slot = ch * CG_SLOTS + (threadIdx.x >> 6);
+        if (slot >= nb) continue;
+        const int scene = a.coord[slot].w;
+        const SceneDev& S = a.sc[scene];
+        const SceneScal& sc = a.scal[scene];
+        R mpp = R(0);
+        if (!sc.cg_done) {
+            if (scene != bscene) {
+                beta = (R)sc.alpha;   // holds beta here (set by the control phase)
+                bscene = scene;
+            }
+            const int t = slot * 64 + l;
+            R z[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) z[c] = a.r[slot * 192 + c * 64 + l] * cg_prec<R, 3>(a, slot, c, l, t);
+            cg_proj<R, 3>(z, a, t, S);
+            const R mr = a.mR[t];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int k = slot * 192 + c * 64 + l;
+                const R pn = z[c] + beta * a.p[k];
+                a.p[k] = pn;
+                mpp += mr * pn * pn;
+            }
+        }
+        acc.add(scene, mpp, R(0), a.scal, OFF_PAP, -1);
+    }
+    cta_scene_sum2_warp(acc.a1.warp_total(), acc.a2.warp_total(), acc.cur, a.scal, OFF_PAP, -1);
+}
+
 __global__ void k_cg_begin(SceneScal* scal, int nsc, int from_newton) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsc) return;
@@ -1984,7 +2377,7 @@ __global__ void k_newton_init_v(const int4* __restrict__ coord, const SceneDev* 
     int t = slot * 64 + l;
     double v[3];
     for (int q = 0; q < 3; ++q) v[q] = gvn[slot * 192 + q * 64 + l] + S.dt * S.g[q];
-    project3(v, pcode[t], S);
+    project3(v, pcode[t], S, bc, l);
     for (int q = 0; q < 3; ++q) gv[slot * 192 + q * 64 + l] = v[q];
 }
 
@@ -2333,13 +2726,12 @@ __global__ void k_newton_update(const int4* __restrict__ coord, const SceneScal*
 // m |v_n| bounds the tangential one by mu_f m |v_n|, so the tangential part t
 // shrinks by mu_f |v_n| or stops (|t| <= mu_f |v_n|). The normal part is left
 // for the slip projection.
-__device__ __forceinline__ void coulomb_plane(double* v, const SceneDev& S) {
-    const double* n = S.plane_n;
+__device__ __forceinline__ void coulomb_node(double* v, const double* n, double mu) {
     double vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
     if (!(vn < 0.0)) return;
     double t[3] = {v[0] - vn * n[0], v[1] - vn * n[1], v[2] - vn * n[2]};
     double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-    double lim = -S.friction * vn;
+    double lim = -mu * vn;
     double s = tn > lim ? 1.0 - lim / tn : 0.0;
     for (int q = 0; q < 3; ++q) v[q] = s * t[q] + vn * n[q];
 }
@@ -2361,8 +2753,16 @@ __global__ void k_newton_final(const int4* __restrict__ coord, const SceneDev* _
             v[q] = gv[k] - grad[k] / m;
         }
         const uint8_t code = pcode[t];
-        if ((code & PC_PLANE) && !(code & PC_FIXED) && S.friction > 0.0) coulomb_plane(v, S);
-        project3(v, code, S);
+        if (!(code & PC_FIXED) && S.friction > 0.0) {
+            if (code & PC_PLANE) coulomb_node(v, S.plane_n, S.friction);
+            if (code & PC_SPHERE) {
+                double x[3], n[3];
+                node_position(S, bc, l, x);
+                sphere_phi_normal(S, x, n);
+                coulomb_node(v, n, S.friction);
+            }
+        }
+        project3(v, code, S, bc, l);
     }
     for (int q = 0; q < 3; ++q) {
         gvhat[slot * 192 + q * 64 + l] = v[q];
@@ -2433,7 +2833,7 @@ __global__ void k_project_vec(int nb, const int4* __restrict__ coord, const Scen
     const SceneDev& S = sc[coord[slot].w];
     R v[3];
     for (int q = 0; q < 3; ++q) v[q] = vec[slot * 192 + q * 64 + l];
-    project3r<R>(v, pcode[t], S);
+    project3r<R>(v, pcode[t], S, coord[slot], l);
     for (int q = 0; q < 3; ++q) vec[slot * 192 + q * 64 + l] = v[q];
 }
 
@@ -2452,7 +2852,7 @@ __global__ void k_mass_term(int nb, const int4* __restrict__ coord, const SceneD
         int k = slot * 192 + q * 64 + l;
         v[q] = m * p[k] + u[k];
     }
-    project3r<R>(v, pcode[t], S);
+    project3r<R>(v, pcode[t], S, coord[slot], l);
     for (int q = 0; q < 3; ++q) u[slot * 192 + q * 64 + l] = v[q];
 }
 
@@ -2502,6 +2902,7 @@ template <typename R>
 ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int check_done) {
     Dev& d = c->d;
     ApplyArgs<R> a;
+    a.pap = 0;
     a.work = d.work;
     a.work_gb = d.work_gb;
     a.nbr = d.nbr;
@@ -2532,11 +2933,9 @@ ApplyArgs<R> make_apply_args(mpm_ctx* c, const void* p, void* u, int mode, int c
     a.sg = (const R*)d.sg;
     a.sic = (const R*)d.sic;
     a.slot_gen = d.slot_gen;
-    for (int q = 0; q < 45; ++q) a.sK.a[q] = (R*)d.sK[q];
-    a.sK0 = (const R*)d.sK[0];
+    a.sKa = (const R*)d.sKa;
     for (int q = 0; q < 45; ++q) a.pK.a[q] = (R*)d.pK[q];
     a.use_pK = (c->pK_valid && mode == MPM_HESS_PROJECTED) ? 1 : 0;
-    a.sKs = c->Scap;
     a.samples_in_cell = (c->sK_valid && mode == MPM_HESS_PROJECTED) ? 1 : 0;
     a.opk = (const R4<R>*)d.opk;
     a.wrows = d.wrows;
@@ -2664,6 +3063,15 @@ cudaError_t pack_step_t(mpm_ctx* c) {
         MPM_LAUNCH k_gen_list<<<nblk(c->NW, 256), 256, 0, st>>>(c->NW, d.gen_flag, d.gen_pos, d.gen_list);
         launch_exclusive_scan(c, d.gen_flag_g, d.gen_pos_g, c->NW, d.scan_tmp, st);
         MPM_LAUNCH k_gen_list<<<nblk(c->NW, 256), 256, 0, st>>>(c->NW, d.gen_flag_g, d.gen_pos_g, d.gen_list_g);
+        // the lists' lengths size the general kernel's grid (none: no launch)
+        cudaMemcpyAsync(c->hcounts + 5, d.gen_pos + c->NW, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(c->hcounts + 6, d.gen_pos_g + c->NW, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        c->n_gen = c->hcounts[5];
+        c->n_gen_g = c->hcounts[6];
+    } else {
+        c->n_gen = c->n_gen_g = 0;
     }
     return cudaGetLastError();
 }
@@ -2680,7 +3088,9 @@ cudaError_t cg_iter_capacity(int& grid, int per_sm_cap = 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_iter<R, NC>, CG_NT, 0);
+        // the momentum CG runs the iteration that starts from a summed p . A p
+        const void* fn = NC == 3 ? (const void*)k_cg_iter2<R> : (const void*)k_cg_iter<R, NC>;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, CG_NT, 0);
         if (e != cudaSuccess) return e;
         if (occ < 1) return cudaErrorInvalidConfiguration;
     }
@@ -2700,6 +3110,7 @@ cudaError_t launch_cg_iter(mpm_ctx* c, CGArgs<R, NC>& a, int heat) {
     unsigned* bar = c->d.cg_bar;
     int* err = c->d.err;
     void* args[] = {(void*)&a, (void*)&nb, (void*)&ns, (void*)&heat, (void*)&bar, (void*)&err};
+    void* args2[] = {(void*)&a, (void*)&nb, (void*)&ns, (void*)&bar, (void*)&err};
     // a cooperative launch (all CTAs co-resident), expressed as a launch attribute
     // so that it can also be captured into a CUDA graph
     cudaLaunchAttribute attr[1];
@@ -2713,6 +3124,7 @@ cudaError_t launch_cg_iter(mpm_ctx* c, CGArgs<R, NC>& a, int heat) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     c->launches++;
+    if constexpr (NC == 3) return cudaLaunchKernelExC(&cfg, (const void*)k_cg_iter2<R>, args2);
     return cudaLaunchKernelExC(&cfg, (const void*)k_cg_iter<R, NC>, args);
 }
 
@@ -2743,7 +3155,7 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     if (e0 != cudaSuccess) return e0;
     if (NC_is_heat) {
         auto a = make_cg_args<R, 1>(c);
-        MPM_LAUNCH k_cg_init<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init);
+        MPM_LAUNCH k_cg_init<R, 1><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init, 0);
         for (int it = 0; it < maxit; it += chunk) {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
@@ -2763,13 +3175,15 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
     } else {
         auto a = make_cg_args<R, 3>(c);
         auto ap = make_apply_args<R>(c, d.cp, d.cu, MPM_HESS_PROJECTED, 1);
-        MPM_LAUNCH k_cg_init<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init);
+        ap.pap = 1;   // the operator kernels sum p . (H - M) p for the iteration
+        MPM_LAUNCH k_cg_init<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init, 1);
         // one chunk of CG iterations: operator apply, then the cooperative vector kernel
         auto enqueue_chunk = [&]() -> cudaError_t {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
                 if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
-                if (c->NW > 0) MPM_LAUNCH k_apply_general<R><<<nblk(c->NW, GEN_B), NT_GEN, 0, st>>>(ap);
+                const int ng = ap.samples_in_cell ? c->n_gen_g : c->n_gen;
+                if (ng > 0) MPM_LAUNCH k_apply_general<R><<<nblk(ng, GEN_B), NT_GEN, 0, st>>>(ap);
                 prof_mark_apply(c, false);
                 cudaError_t e = launch_cg_iter<R, 3>(c, a, 0);
                 if (e != cudaSuccess) return e;
@@ -2867,15 +3281,16 @@ cudaError_t eval_t(mpm_ctx* c, bool want_grad, bool want_cache, bool skip_done) 
             Dev& dd = c->d;
             RPtr9<RS> sF;
             RPtr3<RS> sa, sn;
-            RPtr45<RS> K;
+            RPtr3<RS> su;
             for (int q = 0; q < 9; ++q) sF.a[q] = (RS*)dd.sF[q];
             for (int q = 0; q < 3; ++q) {
                 sa.a[q] = (RS*)dd.sa[q];
                 sn.a[q] = (RS*)dd.sn[q];
+                su.a[q] = (RS*)dd.su[q];
             }
-            for (int q = 0; q < 45; ++q) K.a[q] = (RS*)dd.sK[q];
             MPM_LAUNCH k_surf_hess<RS><<<nblk(c->ns, 128), 128, 0, c->st>>>((int)c->ns, dd.ssc, dd.sc, sF, sa, sn,
-                                                                        (const RS*)dd.sic, (const RS*)dd.sg, K);
+                                                                        (const RS*)dd.sic, (const RS*)dd.sg, su,
+                                                                        (RS*)dd.sKa);
             c->sK_valid = true;
         }
     }
@@ -3013,11 +3428,13 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
     if (c->rsize == 4) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
-        MPM_LAUNCH k_apply_general<float><<<nblk(c->NW, GEN_B), NT_GEN, 0, c->st>>>(a);
+        const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
+        if (ng > 0) MPM_LAUNCH k_apply_general<float><<<nblk(ng, GEN_B), NT_GEN, 0, c->st>>>(a);
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
-        MPM_LAUNCH k_apply_general<double><<<nblk(c->NW, GEN_B), NT_GEN, 0, c->st>>>(a);
+        const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
+        if (ng > 0) MPM_LAUNCH k_apply_general<double><<<nblk(ng, GEN_B), NT_GEN, 0, c->st>>>(a);
     }
     return cudaGetLastError();
 }

@@ -85,9 +85,15 @@ __global__ void k_nearest(int ns, P3 s, const int* __restrict__ ssc, P3 x, const
     atomicAdd(&gcount[bi], 1);
 #pragma unroll
     for (int a = 0; a < 3; ++a) bpos.a[a][j] = __dadd_rn(q[a], 2.0 * __dsub_rn(x.a[a][bi], q[a]));
-    if (S.plane_mode) {
-        double phi = S.plane_n[0] * q[0] + S.plane_n[1] * q[1] + S.plane_n[2] * q[2] - S.plane_d;
-        kind[j] = phi < S.dx ? 1 : 0;
+    // solid-liquid: closer than dx to the plane or to the sphere
+    if (S.plane_mode || S.sphere_mode) {
+        bool near = false;
+        if (S.plane_mode) near = S.plane_n[0] * q[0] + S.plane_n[1] * q[1] + S.plane_n[2] * q[2] - S.plane_d < S.dx;
+        if (S.sphere_mode) {
+            double nrm[3];
+            near = near || sphere_phi_normal(S, q, nrm) < S.dx;
+        }
+        kind[j] = near ? 1 : 0;
     }
 }
 
@@ -267,14 +273,26 @@ __global__ void k_grid_final(int nb, const int4* __restrict__ coord, const Scene
         on_plane = xn - S.plane_d < 0.0;
         if (on_plane && S.plane_mode == 2) sticky = true;
     }
+    bool on_sphere = false;
+    if (S.sphere_mode) {
+        double xi[3], nrm[3];
+        for (int q = 0; q < 3; ++q) xi[q] = (g[q] + 0.5) * S.dx + S.origin[q];
+        on_sphere = sphere_phi_normal(S, xi, nrm) < 0.0;
+        if (on_sphere && S.sphere_mode == 2) sticky = true;
+    }
     int nslip = __popc(slip);
     uint8_t code = 0;
-    if (sticky || (on_plane && nslip > 0) || nslip == 3 || !(m > 0.0)) code = PC_FIXED;
+    // two independent solid normals at one node fix it (plane and sphere, or a
+    // solid and a wall)
+    if (sticky || (on_plane && nslip > 0) || (on_sphere && nslip > 0) || (on_plane && on_sphere) || nslip == 3 ||
+        !(m > 0.0))
+        code = PC_FIXED;
     else {
         if (slip & 1) code |= PC_SLIPX;
         if (slip & 2) code |= PC_SLIPY;
         if (slip & 4) code |= PC_SLIPZ;
         if (on_plane) code |= PC_PLANE;
+        if (on_sphere) code |= PC_SPHERE;
     }
     pcode[t] = code;
     invm[t] = (m > 0.0 && code != PC_FIXED) ? (R)(1.0 / m) : R(0);

@@ -39,7 +39,8 @@ EXPORTED = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_particles", 
 class GridDesc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32 * 3), ("dx", ctypes.c_double), ("origin", ctypes.c_double * 3),
                 ("walls", ctypes.c_int32 * 6), ("plane_n", ctypes.c_double * 3), ("plane_d", ctypes.c_double),
-                ("plane_mode", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("plane_mode", ctypes.c_int32), ("pad_", ctypes.c_int32), ("sphere", ctypes.c_double * 4),
+                ("sphere_outside", ctypes.c_int32), ("sphere_mode", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
@@ -144,8 +145,6 @@ def _f64(a):
 
 
 def scene_desc(sc, max_particles=None, max_surface=None, max_blocks=0):
-    if getattr(sc, "sphere_mode", 0):
-        raise NotImplementedError("spherical solids are not on the device path")
     p = sc.params
     d = SceneDesc()
     d.grid.n[:] = [int(v) for v in sc.n]
@@ -155,6 +154,10 @@ def scene_desc(sc, max_particles=None, max_surface=None, max_blocks=0):
     d.grid.plane_n[:] = list(sc.plane_n)
     d.grid.plane_d = sc.plane_d
     d.grid.plane_mode = int(sc.plane_mode)
+    d.grid.sphere_mode = int(getattr(sc, "sphere_mode", 0))
+    if d.grid.sphere_mode:
+        d.grid.sphere[:] = [float(v) for v in sc.sphere[:4]]
+        d.grid.sphere_outside = int(bool(sc.sphere[4]))
     P = d.params
     P.dt = p.dt
     P.gravity[:] = list(p.gravity)

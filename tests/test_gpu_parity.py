@@ -98,12 +98,28 @@ def _crowded_droplet():
     return sc
 
 
+def _dense_samples():
+    """Many surface samples per block: the operator stages a block's samples in
+    chunks of 42 records, so these blocks take several chunks."""
+    sc = scenes.droplet(n=16, r_cells=4.5, seed=13, surf_per_cell=14.0, lambda_l=60.0)
+    sc.v = np.random.default_rng(13).standard_normal(sc.v.shape) * 0.2
+    return sc
+
+
 SCENES = {
     "droplet": lambda: scenes.config(0),
     "mixed": _mixed_scene,
 }
 # the operator tests also take the deformed solids and the crowded cells
-OP_SCENES = dict(SCENES, deformed=_deformed_solids, crowded=_crowded_droplet)
+OP_SCENES = dict(SCENES, deformed=_deformed_solids, crowded=_crowded_droplet, dense_samples=_dense_samples)
+
+
+def test_dense_sample_scene_has_blocks_beyond_one_sample_chunk():
+    sc = _dense_samples()
+    c = np.floor(sc.s / sc.dx).astype(np.int64) // 4
+    nb = np.array(sc.n) // 4
+    per_block = np.bincount(c[:, 0] + nb[0] * (c[:, 1] + nb[1] * c[:, 2]))
+    assert per_block.max() > 42
 
 
 def test_crowded_scene_has_cells_beyond_one_staging_chunk():
@@ -320,8 +336,43 @@ def _massless_droplet():
     return sc
 
 
+def _bowl_friction():
+    # a curved solid (reading R29): a droplet just above the bottom of a spherical
+    # bowl (solid outside the sphere), slip with the ramp's Coulomb coefficient
+    sc = scenes.droplet(n=20, r_cells=4.0, seed=45, center=(0.5, 0.52, 0.42), gravity=(0.0, 0.0, -9.8),
+                        v0=(0.4, 0.0, -0.3), lambda_l=80.0)
+    sc.sphere, sc.sphere_mode = (0.47, 0.5, 0.55, 0.36, True), scenes.WALL_SLIP
+    sc.params.friction = 0.2
+    sc.params.gamma_sl = 0.5
+    return sc
+
+
+def _sticky_ball():
+    # a droplet falling onto a sticky ball (solid inside the sphere)
+    sc = scenes.droplet(n=20, r_cells=4.0, seed=46, center=(0.52, 0.5, 0.58), gravity=(0.0, 0.0, -9.8),
+                        v0=(0.0, 0.1, -0.5), lambda_l=80.0)
+    sc.sphere, sc.sphere_mode = (0.5, 0.5, 0.2, 0.15, False), scenes.WALL_STICKY
+    sc.params.gamma_sl = -0.2
+    return sc
+
+
 WORKLOADS = {"film": _small_film, "wax": _small_wax, "incline": _small_incline,
-             "incline_friction": _small_incline_friction, "massless": _massless_droplet}
+             "incline_friction": _small_incline_friction, "massless": _massless_droplet,
+             "bowl_friction": _bowl_friction, "sticky_ball": _sticky_ball}
+
+
+@pytest.mark.parametrize("name", ["bowl_friction", "sticky_ball"])
+def test_sphere_scenes_reach_the_solid(name):
+    """The sphere scenes put solid nodes in the particles' stencils and
+    solid-liquid samples on the droplet (host-side check of the inputs)."""
+    from oracle.boundary import sphere_phi_normal
+    sc = WORKLOADS[name]()
+    phi_s, _ = sphere_phi_normal(sc.s, sc.sphere)
+    assert np.any(phi_s < sc.dx) and np.any(phi_s >= sc.dx)
+    st = oracle.Stencil(sc.x, sc.dx, sc.n)
+    phi_n, _ = sphere_phi_normal(st.xi.reshape(-1, 3), sc.sphere)
+    assert np.any(phi_n < 0.0)
+    assert np.all(sphere_phi_normal(sc.x, sc.sphere)[0] > 0.0)
 
 
 def _tight(sc):
