@@ -46,9 +46,9 @@ def test_binding_names_match_header(lib):
 def test_struct_sizes_match_c_layout(lib):
     from paper_2101_12408_gb300 import mpm
     # sizes follow the C rules for the header's field order (8-byte aligned doubles)
-    assert ctypes.sizeof(mpm.GridDesc) == 112
+    assert ctypes.sizeof(mpm.GridDesc) == 152
     assert ctypes.sizeof(mpm.Params) == 232
-    assert ctypes.sizeof(mpm.SceneDesc) == 368
+    assert ctypes.sizeof(mpm.SceneDesc) == 408
     assert ctypes.sizeof(mpm.Stats) == 64
 
 
@@ -63,14 +63,16 @@ def test_struct_layout_matches_the_header_compiled(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "mpm.h"\n'
-        'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(mpm_params), sizeof(mpm_scene_desc),'
+        'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mpm_params), sizeof(mpm_scene_desc),'
         ' offsetof(mpm_params, phase_change), offsetof(mpm_params, friction),'
-        ' offsetof(mpm_params, massless_surface)); return 0; }\n')
+        ' offsetof(mpm_params, massless_surface), sizeof(mpm_grid_desc), offsetof(mpm_grid_desc, sphere),'
+        ' offsetof(mpm_grid_desc, sphere_mode)); return 0; }\n')
     exe = tmp_path / "layout"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == [ctypes.sizeof(mpm.Params), ctypes.sizeof(mpm.SceneDesc), mpm.Params.phase_change.offset,
-                   mpm.Params.friction.offset, mpm.Params.massless_surface.offset]
+                   mpm.Params.friction.offset, mpm.Params.massless_surface.offset, ctypes.sizeof(mpm.GridDesc),
+                   mpm.GridDesc.sphere.offset, mpm.GridDesc.sphere_mode.offset]
 
 
 def test_invalid_arguments_rejected_without_gpu(lib):
@@ -95,11 +97,23 @@ def test_invalid_friction_and_massless_flag_rejected_without_gpu(lib):
         assert not out.value
 
 
-def test_spherical_solid_is_refused_by_the_device_binding():
-    """The spherical solid exists in the oracle only: the binding refuses it
-    instead of running the scene without it."""
+def test_spherical_solid_reaches_the_descriptor_and_bad_spheres_are_rejected(lib):
+    """The binding passes the spherical solid to mpm_grid_desc; mpm_create rejects
+    a non-positive or non-finite radius, a non-finite centre and an unknown mode
+    before any CUDA call."""
     from paper_2101_12408_gb300 import mpm, scenes
     sc = scenes.droplet(n=8, r_cells=2.0, seed=1)
-    sc.sphere, sc.sphere_mode = (0.5, 0.5, 0.5, 0.3, True), scenes.WALL_SLIP
-    with pytest.raises(NotImplementedError):
-        mpm.scene_desc(sc)
+    sc.sphere, sc.sphere_mode = (0.5, 0.45, 0.55, 0.3, True), scenes.WALL_SLIP
+    d = mpm.scene_desc(sc)
+    assert list(d.grid.sphere) == [0.5, 0.45, 0.55, 0.3]
+    assert d.grid.sphere_outside == 1 and d.grid.sphere_mode == scenes.WALL_SLIP
+    for field, idx, bad in (("sphere", 3, 0.0), ("sphere", 3, -0.2), ("sphere", 3, float("nan")),
+                            ("sphere", 0, float("inf")), ("sphere_mode", None, 3)):
+        d = mpm.scene_desc(sc)
+        if idx is None:
+            setattr(d.grid, field, bad)
+        else:
+            getattr(d.grid, field)[idx] = bad
+        out = ctypes.c_void_p()
+        assert lib.mpm_create(ctypes.byref(d), 1, 1, None, ctypes.byref(out)) == mpm.MPM_ERR_INVALID_ARG, (field, bad)
+        assert not out.value
