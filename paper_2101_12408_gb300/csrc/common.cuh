@@ -220,10 +220,13 @@ __device__ __forceinline__ void matmul3_bt(const R* A, const R* B, R* C) {
 // map K (symmetric 9x9 on dF^ flattened row-major, rows 3q..3q+2 belong to
 // component q) grouped in 3x3 blocks, then its position in its block:
 //   [0, 6)   D0 = K(0,0) upper triangle (00 01 02 11 12 22), [6, 12) D1, [12, 18) D2,
-//   [18, 27) O01 = K(0,1) row-major, [27, 36) O02, [36, 45) O12, [45, 48) position.
+//   [18, 27) O01 = K(0,1) row-major, [27, 36) O02, [36, 45) O12, [45, 48) position,
+//   [48, 52) unused: a stride of 52 values puts the records of the samples read
+//   together on 8 different shared-memory banks (48 would give 2) and keeps every
+//   record 16-byte aligned for the bulk copy.
 // The lane computing row block q of G = K dF^ reads D_q and the two off-diagonal
 // blocks of its rows (transposed where they lie below the diagonal).
-constexpr int SREC = 48;
+constexpr int SREC = 52;
 __host__ __device__ constexpr int sample_map_index(int m, int l) {   // m <= l
     return (m / 3 == l / 3) ? 6 * (m / 3) + (m % 3) * 3 - (m % 3) * ((m % 3) - 1) / 2 + (l % 3 - m % 3)
                             : (m / 3 == 0 ? (l / 3 == 1 ? 18 : 27) : 36) + 3 * (m % 3) + (l % 3);

@@ -1106,34 +1106,37 @@ __device__ __forceinline__ void cell_scatter_warp(const R (&M)[3][3][3], R (*ua)
 
 template <typename R>
 __device__ __forceinline__ void flush_halo_rows_u(const int* __restrict__ nbr, int slot, R (*ua)[UN], R* __restrict__ u) {
-    for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
-        int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+    for (int yz = threadIdx.x; yz < HE * HE; yz += blockDim.x) {
+        const int hy = yz % HE, hz = yz / HE;
         int nmid, nlo, nhi, base;
         halo_row<R>(nbr, slot, hy, hz, nmid, nlo, nhi, base);
-        R v[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) v[k] = R(0);
-        if (hz <= 3) {
-            const R* s = &ua[c][pidx(0, hy, hz)];
+        for (int c = 0; c < 3; ++c) {
+            R v[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] += s[k];
-        }
-        if (hz >= 2) {
-            const R* s = &ua[c][pidx(0, hy, hz + 2)];
+            for (int k = 0; k < 6; ++k) v[k] = R(0);
+            if (hz <= 3) {
+                const R* s = &ua[c][pidx(0, hy, hz)];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] += s[k];
-        }
-        if (nlo >= 0 && v[0] != R(0)) atomicAdd(&u[nlo * 192 + c * 64 + base + 3], v[0]);
-        if (nhi >= 0 && v[5] != R(0)) atomicAdd(&u[nhi * 192 + c * 64 + base], v[5]);
-        if (nmid >= 0 && (v[1] != R(0) || v[2] != R(0) || v[3] != R(0) || v[4] != R(0))) {
-            R* dst = u + nmid * 192 + c * 64 + base;
-            if constexpr (sizeof(R) == 4) {
-                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[1], v[2], v[3], v[4]));
-            } else {
-                atomicAdd(dst, v[1]);
-                atomicAdd(dst + 1, v[2]);
-                atomicAdd(dst + 2, v[3]);
-                atomicAdd(dst + 3, v[4]);
+                for (int k = 0; k < 6; ++k) v[k] += s[k];
+            }
+            if (hz >= 2) {
+                const R* s = &ua[c][pidx(0, hy, hz + 2)];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) v[k] += s[k];
+            }
+            if (nlo >= 0 && v[0] != R(0)) atomicAdd(&u[nlo * 192 + c * 64 + base + 3], v[0]);
+            if (nhi >= 0 && v[5] != R(0)) atomicAdd(&u[nhi * 192 + c * 64 + base], v[5]);
+            if (nmid >= 0 && (v[1] != R(0) || v[2] != R(0) || v[3] != R(0) || v[4] != R(0))) {
+                R* dst = u + nmid * 192 + c * 64 + base;
+                if constexpr (sizeof(R) == 4) {
+                    atomicAdd(reinterpret_cast<float4*>(dst), make_float4(v[1], v[2], v[3], v[4]));
+                } else {
+                    atomicAdd(dst, v[1]);
+                    atomicAdd(dst + 1, v[2]);
+                    atomicAdd(dst + 2, v[3]);
+                    atomicAdd(dst + 3, v[4]);
+                }
             }
         }
     }
@@ -1142,7 +1145,7 @@ __device__ __forceinline__ void flush_halo_rows_u(const int* __restrict__ nbr, i
 template <typename R>
 __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell(ApplyArgs<R> a) {
     __shared__ R ph[3][PN];
-    __shared__ R ua[3][UN];
+    __shared__ __align__(16) R ua[3][UN];
     __shared__ R4<R> sp[KR2 * 64];
     __shared__ __align__(8) uint64_t bar;
     int w = blockIdx.x;
@@ -1155,7 +1158,8 @@ __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell
     const R4<R>* recs = a.opk + (long long)a.wroff[w] * 64;
     const int nchunk = (rows + KR2 - 1) / KR2;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
-    for (int i = threadIdx.x; i < 3 * UN; i += blockDim.x) (&ua[0][0])[i] = R(0);
+    for (int i = threadIdx.x; i < (int)(3 * UN * sizeof(R) / 16); i += blockDim.x)
+        reinterpret_cast<int4*>(&ua[0][0])[i] = make_int4(0, 0, 0, 0);
     __syncthreads();
     if (threadIdx.x == 0 && nchunk > 0) {
         uint32_t cnt = (uint32_t)min(KR2, rows) * 64u;
@@ -1163,28 +1167,31 @@ __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell
         bulk_g2s(sp, recs, cnt * (uint32_t)sizeof(R4<R>), &bar);
     }
     {
-        // the direction's halo
-        for (int r = threadIdx.x; r < 3 * HE * HE; r += blockDim.x) {
-            int c = r / (HE * HE), yz = r % (HE * HE), hy = yz % HE, hz = yz / HE;
+        // the direction's halo: one neighbour lookup per (y, z) row, three components
+        for (int yz = threadIdx.x; yz < HE * HE; yz += blockDim.x) {
+            const int hy = yz % HE, hz = yz / HE;
             int nmid, nlo, nhi, base;
             halo_row<R>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
-            R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
-            if (nmid >= 0) {
-                const R* src = a.p + nmid * 192 + c * 64 + base;
-                if constexpr (sizeof(R) == 4) {
-                    float4 v = *reinterpret_cast<const float4*>(src);
-                    m0 = v.x; m1 = v.y; m2 = v.z; m3 = v.w;
-                } else {
-                    m0 = src[0]; m1 = src[1]; m2 = src[2]; m3 = src[3];
+            const int h0 = pidx(0, hy, hz);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
+                if (nmid >= 0) {
+                    const R* src = a.p + nmid * 192 + c * 64 + base;
+                    if constexpr (sizeof(R) == 4) {
+                        float4 v = *reinterpret_cast<const float4*>(src);
+                        m0 = v.x; m1 = v.y; m2 = v.z; m3 = v.w;
+                    } else {
+                        m0 = src[0]; m1 = src[1]; m2 = src[2]; m3 = src[3];
+                    }
                 }
+                ph[c][h0] = nlo >= 0 ? a.p[nlo * 192 + c * 64 + base + 3] : R(0);
+                ph[c][h0 + 1] = m0;
+                ph[c][h0 + 2] = m1;
+                ph[c][h0 + 3] = m2;
+                ph[c][h0 + 4] = m3;
+                ph[c][h0 + 5] = nhi >= 0 ? a.p[nhi * 192 + c * 64 + base] : R(0);
             }
-            int h0 = pidx(0, hy, hz);
-            ph[c][h0] = nlo >= 0 ? a.p[nlo * 192 + c * 64 + base + 3] : R(0);
-            ph[c][h0 + 1] = m0;
-            ph[c][h0 + 2] = m1;
-            ph[c][h0 + 3] = m2;
-            ph[c][h0 + 4] = m3;
-            ph[c][h0 + 5] = nhi >= 0 ? a.p[nhi * 192 + c * 64 + base] : R(0);
         }
     }
     __syncthreads();
