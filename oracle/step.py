@@ -17,8 +17,11 @@ Readings:
 * solid-liquid samples: with a solid plane, s_r is solid-liquid when its signed
   distance to the plane is below dx;
 * the heat solve and the momentum solve are independent within a step;
-* E(T) = E0 max(0, (T_melt - T)/(T_melt - T0)) per particle from T^n_p, Lame
-  mu = E / (2 (1 + nu)), lambda = E nu / ((1 + nu)(1 - 2 nu));
+* E(T) = E0 max(0, (T_melt - T)/(T_melt - T0)) per particle from T^n_p and the
+  shear Lame coefficient mu = E / (2 (1 + nu)); the volumetric coefficient of the
+  solid is the scene's bulk modulus lambda_l at every temperature (the paper's
+  candle example gives one bulk modulus for the liquid and solid phases), so a
+  solid at the melting point (E = 0) stores the liquid's energy lambda_l/2 (J-1)^2;
 * without surface regeneration, the surface samples of the next step are the
   current ones carried by the grid velocity: s <- s + dt sum_i N_i(s) v_i and
   dA <- cof(I + dt sum_i v_i gradN_i(s)^T) dA (the updated-Lagrangian area map
@@ -47,8 +50,9 @@ from .surface import generate
 from .transfer import p2g, g2p, grid_velocity
 
 
-def lame(E, nu):
-    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+def solid_lame(T, prm):
+    """Lame coefficients (mu, lambda) of the solid at temperatures T."""
+    return youngs(T, prm) / (2.0 * (1.0 + prm.nu)), np.full(np.shape(T), float(prm.lambda_l))
 
 
 def youngs(T, prm):
@@ -142,7 +146,7 @@ class OracleSim:
 
     def newton_state(self):
         sc, prm = self.sc, self.prm
-        mu_h, lam_h = lame(youngs(sc.T, prm), prm.nu)
+        mu_h, lam_h = solid_lame(sc.T, prm)
         return NewtonState(sc.n, sc.dx, prm.dt, prm.gravity, self.grid["m"], self.vn, sc.x, sc.V0,
                            sc.J, sc.F, sc.phase, prm.lambda_l, prm.mu_l, mu_h, lam_h,
                            sc.s, sc.dA, self.gamma)

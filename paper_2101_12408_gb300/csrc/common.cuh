@@ -127,6 +127,42 @@ __device__ __forceinline__ void make_stencil_local(R ux, R uy, R uz, R inv_dx, i
     }
 }
 
+// Padded shared-memory layout of a block's 6x6x6 halo: x + 8 y + 52 z, so the 32
+// cells of a warp (a 4x4x2 brick) read or write 32 distinct banks.
+constexpr int PY = 8, PZ = 52, PN = 312;
+__device__ __forceinline__ int pidx(int x, int y, int z) { return x + PY * y + PZ * z; }
+// Accumulation halo of a block written by its two warps: warp 0's node levels
+// 0..3 at levels 0..3, warp 1's levels 2..5 at 4..7 (the warps never share a word).
+constexpr int UZ = 8;
+constexpr int UN = PZ * UZ;
+
+// Halo rows along x: the four middle nodes of a row belong to one neighbour block
+// and are contiguous there (x fastest), so they move as one vector; the two end
+// nodes belong to the x-neighbours.
+template <typename R>
+__device__ __forceinline__ void halo_row(const int* __restrict__ nbr, int slot, int hy, int hz, int& nmid, int& nlo,
+                                         int& nhi, int& base) {
+    int oy = hy - 1, oz = hz - 1;
+    int by = oy < 0 ? -1 : (oy >= BS ? 1 : 0), bz = oz < 0 ? -1 : (oz >= BS ? 1 : 0);
+    const int* nb = nbr + slot * 27 + 3 * (by + 1) + 9 * (bz + 1);
+    nlo = nb[0];
+    nmid = nb[1];
+    nhi = nb[2];
+    base = BS * ((oy - BS * by) + BS * (oz - BS * bz));   // local index of x = 0 in the row
+}
+
+// Lame coefficients of the solid at temperature T (section "Thermomechanical
+// Material Dependence and Phase Change"): shear mu = E(T) / (2 (1 + nu)) with
+// E(T) = E0 max(0, (T_melt - T)/(T_melt - T0)); the volumetric coefficient is the
+// scene's bulk modulus lambda_l at every temperature (one bulk modulus for the
+// liquid and solid phases), so a solid at the melting point stores the liquid's
+// energy.
+__device__ __forceinline__ void solid_lame(const SceneDev& S, double T, double& mu, double& lam) {
+    const double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - T) / (S.T_melt - S.T0));
+    mu = E / (2.0 * (1.0 + S.nu));
+    lam = S.lambda_l;
+}
+
 // Signed distance of x to the spherical solid (negative inside the solid) and
 // its unit normal (the gradient, pointing into the liquid); the direction is
 // (0, 0, 1) from (x - c) at the centre itself.

@@ -200,9 +200,10 @@ __global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptr
     }
     if (!liq) {
         for (int q = 0; q < 9; ++q) Fn.a[q][i] = (R)Fd[q];
-        double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - T[i]) / (S.T_melt - S.T0));
-        lmu[i] = (R)(E / (2.0 * (1.0 + S.nu)));
-        llam[i] = (R)(E * S.nu / ((1.0 + S.nu) * (1.0 - 2.0 * S.nu)));
+        double mu_h, lam_h;
+        solid_lame(S, T[i], mu_h, lam_h);
+        lmu[i] = (R)mu_h;
+        llam[i] = (R)lam_h;
     }
 }
 
@@ -327,9 +328,9 @@ __global__ void __launch_bounds__(NT) k_eval(EvalArgs<RS> a) {
             R Rm[9], K[6], sg[3];
             polar3<R>(Fc, Rm, K, sg);
             double Tn = a.T[i];
-            double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - Tn) / (S.T_melt - S.T0));
-            R mu = (R)(E / (2.0 * (1.0 + S.nu)));
-            R lam = (R)(E * S.nu / ((1.0 + S.nu) * (1.0 - 2.0 * S.nu)));
+            double mu_h, lam_h;
+            solid_lame(S, Tn, mu_h, lam_h);
+            const R mu = (R)mu_h, lam = (R)lam_h;
             R J = det3<R>(Fc);
             esum += ((double)mu * ((double)(sg[0] - 1) * (sg[0] - 1) + (double)(sg[1] - 1) * (sg[1] - 1) +
                                    (double)(sg[2] - 1) * (sg[2] - 1)) +
@@ -568,8 +569,6 @@ struct ApplyArgs {
 // surface samples take the general per-particle path in the same CTA.
 // Shared layout x + 8 y + 52 z: the 32 cells of a warp hit 32 distinct banks.
 // ======================================================================
-constexpr int PY = 8, PZ = 52, PN = 312;
-__device__ __forceinline__ int pidx(int x, int y, int z) { return x + PY * y + PZ * z; }
 
 // power coefficients -> from node values (out_k = sum_c v_c W[c][k]) and derivatives
 template <typename R>
@@ -662,69 +661,6 @@ __device__ __forceinline__ void cell_coefficients(R (*ph)[PN], int lx, int ly, i
             C[0][j][k] += g0;
             C[1][j][k] += g1;
             C[2][j][k] += g2;
-        }
-}
-
-// ua += node values of the cell's moments (without the 1/dx factor)
-template <typename R>
-__device__ __forceinline__ void cell_scatter(R M[3][3][3], R (*ua)[PN], int lx, int ly, int lz) {
-    R T1[3][3][3], T2[3][3][3];
-    // x component: D along x, W along y, z
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) wN<R>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) wN<R>(T1[i][0][c], T1[i][1][c], T1[i][2][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            R n0, n1, n2;
-            dN<R>(T2[0][b][c], T2[1][b][c], n0, n1, n2);
-            atomicAdd(&ua[0][pidx(lx, ly + b, lz + c)], n0);
-            atomicAdd(&ua[0][pidx(lx + 1, ly + b, lz + c)], n1);
-            atomicAdd(&ua[0][pidx(lx + 2, ly + b, lz + c)], n2);
-        }
-    // y component: W along x, D along y, W along z
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) wN<R>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dN<R>(T1[i][0][c], T1[i][1][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            R n0, n1, n2;
-            wN<R>(T2[0][b][c], T2[1][b][c], T2[2][b][c], n0, n1, n2);
-            atomicAdd(&ua[1][pidx(lx, ly + b, lz + c)], n0);
-            atomicAdd(&ua[1][pidx(lx + 1, ly + b, lz + c)], n1);
-            atomicAdd(&ua[1][pidx(lx + 2, ly + b, lz + c)], n2);
-        }
-    // z component: W along x, y, D along z
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) dN<R>(M[i][j][0], M[i][j][1], T1[i][j][0], T1[i][j][1], T1[i][j][2]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) wN<R>(T1[i][0][c], T1[i][1][c], T1[i][2][c], T2[i][0][c], T2[i][1][c], T2[i][2][c]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            R n0, n1, n2;
-            wN<R>(T2[0][b][c], T2[1][b][c], T2[2][b][c], n0, n1, n2);
-            atomicAdd(&ua[2][pidx(lx, ly + b, lz + c)], n0);
-            atomicAdd(&ua[2][pidx(lx + 1, ly + b, lz + c)], n1);
-            atomicAdd(&ua[2][pidx(lx + 2, ly + b, lz + c)], n2);
         }
 }
 
@@ -842,66 +778,10 @@ struct KSum {
 };
 
 // general per-particle operator (solid or viscous liquid) on the padded layout
-// returns M : dL, the particle's share of p . (H - M) p
-template <typename R>
-__device__ __forceinline__ R particle_general(const ApplyArgs<R>& a, int i, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
-    int lc[3];
-    R wgt[3][3], dw[3][3];
-    make_stencil_local<R>(a.pu.a[0][i], a.pu.a[1][i], a.pu.a[2][i], inv_dx, lc, wgt, dw);
-    R dL[9];
-    gather_grad_sep<R>(ph, lc, wgt, dw, dL);
-    R M[9];
-    if (a.phase[i] == 0) {
-        R s = a.kappa[i] * (dL[0] + dL[4] + dL[8]);
-        R cv = a.cvisc[i];
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) M[3 * q + e] = cv * R(0.5) * (dL[3 * q + e] + dL[3 * e + q]) + (q == e ? s : R(0));
-    } else if (a.use_pK) {
-        // projected: the particle's per-iterate 9x9 map
-#pragma unroll
-        for (int m = 0; m < 9; ++m) M[m] = R(0);
-#pragma unroll
-        for (int m = 0; m < 9; ++m)
-#pragma unroll
-            for (int l = m; l < 9; ++l) {
-                const R kml = a.pK.a[sym9(m, l)][i];
-                M[m] += kml * dL[l];
-                if (l != m) M[l] += kml * dL[m];
-            }
-    } else {
-        R Fo[9], Fc[9], Rm[9], K[6], dF[9], dP[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            Fo[q] = a.Fn.a[q][i];
-            Fc[q] = a.scache.a[q][i];
-            Rm[q] = a.scache.a[9 + q][i];
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) K[q] = a.scache.a[18 + q][i];
-        matmul3<R>(dL, Fo, dF);
-        fcr_dP<R>(Fc, Rm, K, a.lmu[i], a.llam[i], dF, dP);
-        matmul3_bt<R>(dP, Fo, M);
-        R sc = dt * dt * (R)a.V0[i];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) M[q] *= sc;
-    }
-    scatter_sep<R>(ua, lc, wgt, dw, M);
-    R md = R(0);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) md += M[q] * dL[q];
-    return md;
-}
 
-// returns G : dF^, the sample's share of p . (H - M) p
+// the exact or projected surface term of sample j for a gathered dF^: G (3x3)
 template <typename R>
-__device__ __forceinline__ R sample_general(const ApplyArgs<R>& a, int j, R (*ph)[PN], R (*ua)[PN], R dt, R inv_dx) {
-    int lc[3];
-    R wgt[3][3], dw[3][3];
-    make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, lc, wgt, dw);
-    R dFh[9];
-    gather_grad_sep<R>(ph, lc, wgt, dw, dFh);
+__device__ __forceinline__ void sample_G(const ApplyArgs<R>& a, int j, const R* dFh, R dt, R* G) {
     R Fh[9], av[3], nv[3];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Fh[q] = a.sF.a[q][j];
@@ -917,7 +797,6 @@ __device__ __forceinline__ R sample_general(const ApplyArgs<R>& a, int j, R (*ph
                dC[6] * av[0] + dC[7] * av[1] + dC[8] * av[2]};
     R nd = nv[0] * dc[0] + nv[1] * dc[1] + nv[2] * dc[2];
     R dn[3] = {(dc[0] - nd * nv[0]) * ic, (dc[1] - nd * nv[1]) * ic, (dc[2] - nd * nv[2]) * ic};
-    R G[9];
     surf_G<R>(k * dt * dt, dn, Fh, av, G);
     if (a.mode == MPM_HESS_EXACT) {
         R G2[9];
@@ -927,30 +806,10 @@ __device__ __forceinline__ R sample_general(const ApplyArgs<R>& a, int j, R (*ph
     } else {
         add_conformal<R>(k * dt * dt, nv, av, dFh, G);
     }
-    scatter_sep<R>(ua, lc, wgt, dw, G);
-    R gd = R(0);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) gd += G[q] * dFh[q];
-    return gd;
 }
 
 constexpr int NT_CELL = 64;
-constexpr int NT_GEN = 32;  // one warp: a block holds ~20-40 surface samples
 
-// Halo rows along x: the four middle nodes of a row belong to one neighbour block
-// and are contiguous there (x fastest), so they move as one vector; the two end
-// nodes belong to the x-neighbours.
-template <typename R>
-__device__ __forceinline__ void halo_row(const int* __restrict__ nbr, int slot, int hy, int hz, int& nmid, int& nlo,
-                                         int& nhi, int& base) {
-    int oy = hy - 1, oz = hz - 1;
-    int by = oy < 0 ? -1 : (oy >= BS ? 1 : 0), bz = oz < 0 ? -1 : (oz >= BS ? 1 : 0);
-    const int* nb = nbr + slot * 27 + 3 * (by + 1) + 9 * (bz + 1);
-    nlo = nb[0];
-    nmid = nb[1];
-    nhi = nb[2];
-    base = BS * ((oy - BS * by) + BS * (oz - BS * bz));   // local index of x = 0 in the row
-}
 
 template <typename R>
 __device__ __forceinline__ void load_halo_rows(const int* __restrict__ nbr, int slot, const R* __restrict__ p,
@@ -1015,8 +874,6 @@ __device__ __forceinline__ void flush_halo_rows(const int* __restrict__ nbr, int
 // nodes, and offsets whose z differs by 2 never meet (a warp's cells span two z
 // levels), so each phase below is a plain read-add-write by every lane with no
 // two lanes on one node; __syncwarp orders the phases.
-constexpr int UZ = 8;
-constexpr int UN = PZ * UZ;
 constexpr int KR2 = 8;   // record rows staged per chunk
 
 // every lane of the warp calls it; lanes with act = false only take part in the
@@ -1540,82 +1397,175 @@ __global__ void k_surf_hess(int ns, const int* __restrict__ ssc, const SceneDev*
     for (int q = 0; q < 3; ++q) K[(long long)j * SREC + 45 + q] = su.a[q][j];
 }
 
-// Solids, viscous liquids and surface samples: one thread per particle or
-// sample, shared-memory accumulation on the padded halo. A CTA is one warp and
-// takes GEN_B blocks of the compact list of blocks that hold any of them
-// (a block holds ~10-40 samples: one block per warp left most lanes idle);
-// the warp's lanes run over the concatenated samples of its blocks.
-constexpr int GEN_B = 2;
+// level of halo node level z in the two-warp accumulation halo, for writes made
+// after both warps finished their phases: levels 0..3 are warp 0's, 4..5 warp 1's
+__device__ __forceinline__ int ulevel(int z) { return z <= 3 ? z : z + 2; }
+
+// separable scatter of a 3x3 M (u_q += sum_e M_qe dN/dx_e) into the two-warp
+// accumulation halo with shared atomics (samples in the exact mode only)
 template <typename R>
-__global__ void __launch_bounds__(NT_GEN, sizeof(R) == 4 ? 16 : 8) k_apply_general(ApplyArgs<R> a) {
-    __shared__ R ph[GEN_B][3][PN];
-    __shared__ R ua[GEN_B][3][PN];
-    const int g0 = blockIdx.x * GEN_B;
-    const int ng = *a.gen_count;
-    if (g0 >= ng) return;
-    int slot[GEN_B], sbeg[GEN_B], nsm[GEN_B], scene[GEN_B];
-    bool act[GEN_B];
-    int total = 0;
+__device__ __forceinline__ void scatter_sep_u(R (*ua)[UN], const int* lc, const R (*w)[3], const R (*dw)[3], const R* M) {
 #pragma unroll
-    for (int b = 0; b < GEN_B; ++b) {
-        act[b] = false;
-        slot[b] = -1;
-        sbeg[b] = nsm[b] = 0;
-        scene[b] = 0;
-        if (g0 + b < ng) {
-            const int w = a.gen_list[g0 + b];
-            slot[b] = a.work[w];
-            const long long gb = a.work_gb[w];
-            scene[b] = a.coord[slot[b]].w;
-            act[b] = !(a.check_done && a.scal[scene[b]].cg_done);
-            if (act[b] && !a.samples_in_cell) {
-                sbeg[b] = a.scell_start[gb * 64];
-                nsm[b] = a.scell_start[gb * 64 + 64] - sbeg[b];
-                total += nsm[b];
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R A0 = M[3 * q] * dw[0][a], A1 = M[3 * q + 1] * w[0][a], A2 = M[3 * q + 2] * w[0][a];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const R B0 = A0 * w[1][b] + A1 * dw[1][b], B1 = A2 * w[1][b];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    atomicAdd(&ua[q][pidx(lc[0] + a, lc[1] + b, ulevel(lc[2] + c))], B0 * w[2][c] + B1 * dw[2][c]);
             }
         }
-    }
+}
+
+// Solid particles, viscous liquid particles, and (in the exact mode) surface
+// samples. One CTA per block of the compact list, one thread per cell, two warps:
+// a thread's general particles share its cell's 27 nodes, so their node values
+// add up in registers (the stencil is taken relative to the cell, t clamped to
+// [0, 1], as in k_apply_cell), and each warp writes them once per cell into its
+// own accumulation levels in conflict-free phases. EXACT_SOLID: solids take the
+// exact dP (exact mode with solid buffers), else their projected 9x9 map.
+template <typename R, bool EXACT_SOLID>
+__global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 8 : 4) k_apply_general(ApplyArgs<R> a) {
+    __shared__ R ph[3][PN];
+    __shared__ __align__(16) R ua[3][UN];
+    const int w = a.gen_list[blockIdx.x];
+    const int slot = a.work[w];
+    const long long gb = a.work_gb[w];
+    const int4 bc = a.coord[slot];
+    if (a.check_done && a.scal[bc.w].cg_done) return;
+    const SceneDev& S = a.sc[bc.w];
+    for (int i = threadIdx.x; i < (int)(3 * UN * sizeof(R) / 16); i += blockDim.x)
+        reinterpret_cast<int4*>(&ua[0][0])[i] = make_int4(0, 0, 0, 0);
+    for (int yz = threadIdx.x; yz < HE * HE; yz += blockDim.x) {
+        const int hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<R>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        const int h0 = pidx(0, hy, hz);
 #pragma unroll
-    for (int b = 0; b < GEN_B; ++b)
-        if (act[b]) load_halo_rows<R>(a.nbr, slot[b], a.p, ph[b], ua[b]);
-    __syncthreads();
-    KSum<R> pap[GEN_B];
+        for (int c = 0; c < 3; ++c) {
+            const R* src = a.p + nmid * 192 + c * 64 + base;
+            ph[c][h0] = nlo >= 0 ? a.p[nlo * 192 + c * 64 + base + 3] : R(0);
 #pragma unroll
-    for (int b = 0; b < GEN_B; ++b) {
-        if (!act[b] || a.slot_gen[slot[b]] == 0) continue;
-        const SceneDev& S = a.sc[scene[b]];
-        const int4 bc = a.coord[slot[b]];
-        const long long gb = S.block_base + bc.x + (long long)S.nb[0] * (bc.y + (long long)S.nb[1] * bc.z);
-        // lanes take cells, not consecutive particles: particles of one cell share
-        // their 27 nodes, so a warp over consecutive particles would serialise its
-        // shared atomics; 32 distinct cells hit 32 distinct nodes per offset
-        for (int c = threadIdx.x; c < 64; c += blockDim.x) {
-            const int cb = a.cell_start[gb * 64 + c], ce = a.cell_start[gb * 64 + c + 1];
-            for (int i = cb; i < ce; ++i)
-                if (a.phase[i] != 0 || a.cvisc[i] != R(0))
-                    pap[b].add(particle_general<R>(a, i, ph[b], ua[b], (R)S.dt, (R)S.inv_dx));
+            for (int k = 0; k < 4; ++k) ph[c][h0 + 1 + k] = nmid >= 0 ? src[k] : R(0);
+            ph[c][h0 + 5] = nhi >= 0 ? a.p[nhi * 192 + c * 64 + base] : R(0);
         }
     }
-    static_assert(GEN_B == 2, "the sample loop below selects between two blocks");
-    for (int k = threadIdx.x; k < total; k += blockDim.x) {
-        const bool second = k >= nsm[0];
-        const int j = second ? sbeg[1] + (k - nsm[0]) : sbeg[0] + k;
-        const SceneDev& S = a.sc[second ? scene[1] : scene[0]];
-        const R gd = sample_general<R>(a, j, second ? ph[1] : ph[0], second ? ua[1] : ua[0], (R)S.dt, (R)S.inv_dx);
-        if (second) pap[1].add(gd);
-        else pap[0].add(gd);
+    __syncthreads();
+    const R dt = (R)S.dt, inv_dx = (R)S.inv_dx;
+    const int cell = threadIdx.x, wid = threadIdx.x >> 5;
+    const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
+    const int lc[3] = {lx, ly, lz};
+    KSum<R> pap;
+    R acc[3][3][3][3];
+#pragma unroll
+    for (int m = 0; m < 81; ++m) (&acc[0][0][0][0])[m] = R(0);
+    bool any = false;
+    if (a.slot_gen[slot] > 0) {
+        const int cb = a.cell_start[gb * 64 + cell], ce = a.cell_start[gb * 64 + cell + 1];
+        for (int i = cb; i < ce; ++i) {
+            if (!(a.phase[i] != 0 || a.cvisc[i] != R(0))) continue;
+            any = true;
+            R wgt[3][3], dw[3][3];
+            {
+                const R tt[3] = {fmin(fmax(a.pu.a[0][i] - R(lx), R(0)), R(1)), fmin(fmax(a.pu.a[1][i] - R(ly), R(0)), R(1)),
+                                 fmin(fmax(a.pu.a[2][i] - R(lz), R(0)), R(1))};
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    bspline<R>(tt[ax] + R(0.5), wgt[ax], dw[ax]);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) dw[ax][k] *= inv_dx;
+                }
+            }
+            R dL[9];
+            gather_grad_sep<R>(ph, lc, wgt, dw, dL);
+            R M[9];
+            if (a.phase[i] == 0) {
+                const R s = a.kappa[i] * (dL[0] + dL[4] + dL[8]);
+                const R cv = a.cvisc[i];
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) M[3 * q + e] = cv * R(0.5) * (dL[3 * q + e] + dL[3 * e + q]) + (q == e ? s : R(0));
+            } else if (!EXACT_SOLID) {
+                // projected: the particle's per-iterate 9x9 map
+#pragma unroll
+                for (int m = 0; m < 9; ++m) M[m] = R(0);
+#pragma unroll
+                for (int m = 0; m < 9; ++m)
+#pragma unroll
+                    for (int l = m; l < 9; ++l) {
+                        const R kml = a.pK.a[sym9(m, l)][i];
+                        M[m] += kml * dL[l];
+                        if (l != m) M[l] += kml * dL[m];
+                    }
+            } else {
+                R Fo[9], Fc[9], Rm[9], K[6], dF[9], dP[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    Fo[q] = a.Fn.a[q][i];
+                    Fc[q] = a.scache.a[q][i];
+                    Rm[q] = a.scache.a[9 + q][i];
+                }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) K[q] = a.scache.a[18 + q][i];
+                matmul3<R>(dL, Fo, dF);
+                fcr_dP<R>(Fc, Rm, K, a.lmu[i], a.llam[i], dF, dP);
+                matmul3_bt<R>(dP, Fo, M);
+                const R sc = dt * dt * (R)a.V0[i];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) M[q] *= sc;
+            }
+            R md = R(0);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) md += M[q] * dL[q];
+            pap.add(md);
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa) {
+                    const R A0 = M[3 * q] * dw[0][aa], A1 = M[3 * q + 1] * wgt[0][aa], A2 = M[3 * q + 2] * wgt[0][aa];
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb) {
+                        const R B0 = A0 * wgt[1][bb] + A1 * dw[1][bb], B1 = A2 * wgt[1][bb];
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) acc[q][aa][bb][cc] += B0 * wgt[2][cc] + B1 * dw[2][cc];
+                    }
+                }
+        }
+    }
+    if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) rmw_phases<R>(ua[q], acc[q], lx, ly, lz + 2 * wid);
+    }
+    if (!a.samples_in_cell) {
+        // samples (exact mode, or maps not current), after both warps' phases
+        __syncthreads();
+        const int sbeg = a.scell_start[gb * 64], nsm = a.scell_start[gb * 64 + 64] - sbeg;
+        for (int k = threadIdx.x; k < nsm; k += blockDim.x) {
+            const int j = sbeg + k;
+            int slc[3];
+            R wgt[3][3], dw[3][3];
+            make_stencil_local<R>(a.su.a[0][j], a.su.a[1][j], a.su.a[2][j], inv_dx, slc, wgt, dw);
+            R dFh[9];
+            gather_grad_sep<R>(ph, slc, wgt, dw, dFh);
+            R G[9];
+            sample_G<R>(a, j, dFh, dt, G);
+            R gd = R(0);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) gd += G[q] * dFh[q];
+            pap.add(gd);
+            scatter_sep_u<R>(ua, slc, wgt, dw, G);
+        }
     }
     if (a.pap) {
-#pragma unroll
-        for (int b = 0; b < GEN_B; ++b) {
-            const double v = pap[b].warp_total();   // one warp per CTA
-            if (act[b] && threadIdx.x == 0 && v != 0.0) atomicAdd(&a.scal[scene[b]].pAp, v);
-        }
+        const double v = pap.warp_total();
+        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&a.scal[bc.w].pAp, v);
     }
     __syncthreads();
-#pragma unroll
-    for (int b = 0; b < GEN_B; ++b)
-        if (act[b]) flush_halo_rows<R>(a.nbr, slot[b], ua[b], a.u);
+    flush_halo_rows_u<R>(a.nbr, slot, ua, a.u);
 }
 
 // Compact list of the work blocks that hold surface samples or general particles.
@@ -1724,7 +1674,7 @@ __device__ __forceinline__ void cell_t(const SceneDev& S, int4 bc, int lx, int l
 
 __global__ void __launch_bounds__(NT_CELL) k_eval_cell(EvalCellArgs a) {
     __shared__ double ph[3][PN];
-    __shared__ double ga[3][PN];
+    __shared__ __align__(16) double ga[3][UN];
     __shared__ double red[NT_CELL / 32];
     int w = blockIdx.x;
     int slot = a.work[w];
@@ -1733,22 +1683,36 @@ __global__ void __launch_bounds__(NT_CELL) k_eval_cell(EvalCellArgs a) {
     const SceneDev& S = a.sc[bc.w];
     if (a.skip_done && a.scal[bc.w].newton_done) return;
     if (S.mu_l != 0.0) return;   // viscous scene: k_eval takes every particle
-    load_halo_rows<double>(a.nbr, slot, a.gv, ph, ga);
+    for (int i = threadIdx.x; i < (int)(3 * UN * sizeof(double) / 16); i += blockDim.x)
+        reinterpret_cast<int4*>(&ga[0][0])[i] = make_int4(0, 0, 0, 0);
+    for (int yz = threadIdx.x; yz < HE * HE; yz += blockDim.x) {
+        const int hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<double>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        const int h0 = pidx(0, hy, hz);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ph[c][h0] = nlo >= 0 ? a.gv[nlo * 192 + c * 64 + base + 3] : 0.0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) ph[c][h0 + 1 + m] = nmid >= 0 ? a.gv[nmid * 192 + c * 64 + base + m] : 0.0;
+            ph[c][h0 + 5] = nhi >= 0 ? a.gv[nhi * 192 + c * 64 + base] : 0.0;
+        }
+    }
     __syncthreads();
     const int cell = threadIdx.x;
     const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
     const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
     const double dt = S.dt, lam = S.lambda_l, inv_dx = S.inv_dx;
     double esum = 0.0;
-    if (cend > cbeg) {
-        double C[3][3][3], M[3][3][3];
+    double M[3][3][3];
 #pragma unroll
-        for (int q = 0; q < 27; ++q) {
-            (&C[0][0][0])[q] = 0.0;
-            (&M[0][0][0])[q] = 0.0;
-        }
+    for (int q = 0; q < 27; ++q) (&M[0][0][0])[q] = 0.0;
+    bool any = false;
+    if (cend > cbeg) {
+        double C[3][3][3];
+#pragma unroll
+        for (int q = 0; q < 27; ++q) (&C[0][0][0])[q] = 0.0;
         cell_coefficients<double>(ph, lx, ly, lz, C);
-        bool any = false;
         for (int i = cbeg; i < cend; ++i) {
             if (a.phase[i] != 0) continue;
             any = true;
@@ -1784,13 +1748,14 @@ __global__ void __launch_bounds__(NT_CELL) k_eval_cell(EvalCellArgs a) {
                     for (int k = 0; k < 3; ++k)
                         if (!(ii == 2 && j == 2 && k == 2)) M[ii][j][k] += sx[ii] * yz[j][k];
         }
-        if (any && a.grad) cell_scatter<double>(M, ga, lx, ly, lz);
     }
+    // every lane of a warp takes part in its scatter phases (empty cells add zeros)
+    if (a.grad && __any_sync(0xffffffffu, any)) cell_scatter_warp<double>(M, ga, lx, ly, lz + 2 * (threadIdx.x >> 5));
     block_atomic_sum<NT_CELL>(esum, &a.scal[bc.w].phi_part, red);
     if (a.grad) {
         __syncthreads();
-        flush_halo_rows<double>(a.nbr, slot, ga, a.grad);
-        if (a.grad_l) flush_halo_rows<double>(a.nbr, slot, ga, a.grad_l);
+        flush_halo_rows_u<double>(a.nbr, slot, ga, a.grad);
+        if (a.grad_l) flush_halo_rows_u<double>(a.nbr, slot, ga, a.grad_l);
     }
 }
 
@@ -2497,9 +2462,9 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
             }
             matmul3<R>(A1, Fo, Fc);
             double Tn = a.T[i];
-            double E = S.E0 == 0.0 ? 0.0 : S.E0 * fmax(0.0, (S.T_melt - Tn) / (S.T_melt - S.T0));
-            R mu = (R)(E / (2.0 * (1.0 + S.nu)));
-            R lam = (R)(E * S.nu / ((1.0 + S.nu) * (1.0 - 2.0 * S.nu)));
+            double mu_h, lam_h;
+            solid_lame(S, Tn, mu_h, lam_h);
+            const R mu = (R)mu_h, lam = (R)lam_h;
             R psi0 = fcr_psi<R>(Fc, mu, lam);
             R alpha = 1;
             for (int k = 0; k < nls; ++k) {
@@ -3190,7 +3155,10 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
                 prof_mark_apply(c, true);
                 if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
                 const int ng = ap.samples_in_cell ? c->n_gen_g : c->n_gen;
-                if (ng > 0) MPM_LAUNCH k_apply_general<R><<<nblk(ng, GEN_B), NT_GEN, 0, st>>>(ap);
+                if (ng > 0) {
+                    if (ap.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<R, false><<<ng, NT_CELL, 0, st>>>(ap);
+                    else MPM_LAUNCH k_apply_general<R, true><<<ng, NT_CELL, 0, st>>>(ap);
+                }
                 prof_mark_apply(c, false);
                 cudaError_t e = launch_cg_iter<R, 3>(c, a, 0);
                 if (e != cudaSuccess) return e;
@@ -3436,12 +3404,18 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
         const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
-        if (ng > 0) MPM_LAUNCH k_apply_general<float><<<nblk(ng, GEN_B), NT_GEN, 0, c->st>>>(a);
+        if (ng > 0) {
+            if (a.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<float, false><<<ng, NT_CELL, 0, c->st>>>(a);
+            else MPM_LAUNCH k_apply_general<float, true><<<ng, NT_CELL, 0, c->st>>>(a);
+        }
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
         MPM_LAUNCH k_apply_cell<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
         const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
-        if (ng > 0) MPM_LAUNCH k_apply_general<double><<<nblk(ng, GEN_B), NT_GEN, 0, c->st>>>(a);
+        if (ng > 0) {
+            if (a.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<double, false><<<ng, NT_CELL, 0, c->st>>>(a);
+            else MPM_LAUNCH k_apply_general<double, true><<<ng, NT_CELL, 0, c->st>>>(a);
+        }
     }
     return cudaGetLastError();
 }

@@ -121,83 +121,114 @@ struct P2GArgs {
     double *gm, *gmv, *gmT, *gmTT;
 };
 
-// One CTA per work block, one thread per cell: a thread walks its cell's
-// particles, so the 32 lanes of a warp write 32 distinct halo nodes for each
-// stencil offset (sorted particles of one cell would otherwise hit the same
-// nodes from many lanes at once).
+// One CTA per work block, one thread per cell, two warps. The cells' particles
+// are taken in rows: pass r takes the r-th particle of every cell, so within a
+// warp the 32 particles of a pass lie in 32 distinct cells and, for one stencil
+// offset, add to 32 distinct nodes. Each warp accumulates into its own z-range of
+// the halo (the two-warp layout of common.cuh), and offsets whose z differs by 2
+// never meet within a warp, so a pass's 27 offsets go out in 18 phases of plain
+// read-add-write ordered by __syncwarp; no shared-memory atomics (float64 atomics
+// on shared memory are compare-and-swap loops on this GPU).
 __global__ void __launch_bounds__(64) k_p2g_volume(P2GArgs a) {
-    __shared__ double acc[6][HN];
+    __shared__ __align__(16) double acc[6][UN];
     const int w = blockIdx.x;
     const int slot = a.work[w];
     const long long gb = a.work_gb[w];
     const int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
-    for (int t = threadIdx.x; t < 6 * HN; t += blockDim.x) (&acc[0][0])[t] = 0.0;
+    const int nf = S.thermal ? 6 : 4;
+    for (int t = threadIdx.x; t < (int)(6 * UN * sizeof(double) / 16); t += blockDim.x)
+        reinterpret_cast<int4*>(&acc[0][0])[t] = make_int4(0, 0, 0, 0);
     __syncthreads();
-    const int cell = threadIdx.x;
+    const int cell = threadIdx.x, wid = threadIdx.x >> 5;
+    const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
+    const int zb = lz + 2 * wid;
     const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
-    const int ob[3] = {bc.x * BS, bc.y * BS, bc.z * BS};
+    const int rows = __reduce_max_sync(0xffffffffu, cend - cbeg);
     const double dx = S.dx;
-    for (int i = cbeg; i < cend; ++i) {
-        double u[3];
-        for (int q = 0; q < 3; ++q) u[q] = (a.x.a[q][i] - S.origin[q]) * S.inv_dx;
-        Stencil<double> st;
-        make_stencil<double>(u, S.inv_dx, st);
-        double f[3];
-        for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
-        const double mt = a.mt[i];
-        // node (cx, cy, cz) receives mt N (v + A (x_i - x_p)) with x_i - x_p = (c - f) dx,
-        // i.e. N (B + E c): B = mt (v - dx A f), E = mt dx A
-        double B[3], E[9];
+    for (int r = 0; r < rows; ++r) {
+        const int i = cbeg + r;
+        const bool act = i < cend;
+        double wx[3] = {0, 0, 0}, wy[3] = {0, 0, 0}, wz[3] = {0, 0, 0};
+        double mt = 0.0, B[3] = {0, 0, 0}, E[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        double mp = 0.0, TB = 0.0, TE[3] = {0, 0, 0};
+        if (act) {
+            double u[3];
+            for (int q = 0; q < 3; ++q) u[q] = (a.x.a[q][i] - S.origin[q]) * S.inv_dx;
+            Stencil<double> st;
+            make_stencil<double>(u, S.inv_dx, st);
+            double f[3];
+            for (int q = 0; q < 3; ++q) f[q] = u[q] - 0.5 - (st.c[q] - 1);
+            for (int k = 0; k < 3; ++k) {
+                wx[k] = st.w[0][k];
+                wy[k] = st.w[1][k];
+                wz[k] = st.w[2][k];
+            }
+            mt = a.mt[i];
+            // node (cx, cy, cz) receives mt N (v + A (x_i - x_p)) with x_i - x_p = (c - f) dx,
+            // i.e. N (B + E c): B = mt (v - dx A f), E = mt dx A
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            double Aq[3] = {a.A.a[3 * q][i], a.A.a[3 * q + 1][i], a.A.a[3 * q + 2][i]};
-            B[q] = mt * (a.v.a[q][i] - dx * (Aq[0] * f[0] + Aq[1] * f[1] + Aq[2] * f[2]));
+            for (int q = 0; q < 3; ++q) {
+                double Aq[3] = {a.A.a[3 * q][i], a.A.a[3 * q + 1][i], a.A.a[3 * q + 2][i]};
+                B[q] = mt * (a.v.a[q][i] - dx * (Aq[0] * f[0] + Aq[1] * f[1] + Aq[2] * f[2]));
 #pragma unroll
-            for (int e = 0; e < 3; ++e) E[3 * q + e] = mt * dx * Aq[e];
+                for (int e = 0; e < 3; ++e) E[3 * q + e] = mt * dx * Aq[e];
+            }
+            if (S.thermal) {
+                mp = a.m[i];
+                double g[3] = {a.gT.a[0][i], a.gT.a[1][i], a.gT.a[2][i]};
+                TB = mp * (a.T[i] - dx * (g[0] * f[0] + g[1] * f[1] + g[2] * f[2]));
+                for (int e = 0; e < 3; ++e) TE[e] = mp * dx * g[e];
+            }
         }
-        double TB = 0.0, TE[3] = {0, 0, 0}, mp = 0.0;
-        if (S.thermal) {
-            mp = a.m[i];
-            double g[3] = {a.gT.a[0][i], a.gT.a[1][i], a.gT.a[2][i]};
-            TB = mp * (a.T[i] - dx * (g[0] * f[0] + g[1] * f[1] + g[2] * f[2]));
-            for (int e = 0; e < 3; ++e) TE[e] = mp * dx * g[e];
-        }
-        double wyz[3][3];
+        // phases: (cx, cy) with cz in {0, 2}, then (cx, cy) with cz = 1
 #pragma unroll
-        for (int cy = 0; cy < 3; ++cy)
-#pragma unroll
-            for (int cz = 0; cz < 3; ++cz) wyz[cy][cz] = st.w[1][cy] * st.w[2][cz];
-        const int lx = st.c[0] - ob[0], ly = st.c[1] - ob[1], lz = st.c[2] - ob[2];
-#pragma unroll
-        for (int cz = 0; cz < 3; ++cz)
+        for (int ph = 0; ph < 2; ++ph)
 #pragma unroll
             for (int cy = 0; cy < 3; ++cy)
 #pragma unroll
                 for (int cx = 0; cx < 3; ++cx) {
-                    const double N = st.w[0][cx] * wyz[cy][cz];
-                    const int h = halo_index(lx + cx, ly + cy, lz + cz);
-                    atomicAdd(&acc[0][h], mt * N);
+                    __syncwarp();
+                    if (act) {
 #pragma unroll
-                    for (int q = 0; q < 3; ++q)
-                        atomicAdd(&acc[1 + q][h], N * (B[q] + E[3 * q] * cx + E[3 * q + 1] * cy + E[3 * q + 2] * cz));
-                    if (S.thermal) {
-                        atomicAdd(&acc[4][h], mp * N);
-                        atomicAdd(&acc[5][h], N * (TB + TE[0] * cx + TE[1] * cy + TE[2] * cz));
+                        for (int h = 0; h < 2; ++h) {
+                            const int cz = ph == 0 ? 2 * h : 1;
+                            const double N = wx[cx] * (wy[cy] * wz[cz]);
+                            const int k = pidx(lx + cx, ly + cy, zb + cz);
+                            acc[0][k] += mt * N;
+#pragma unroll
+                            for (int q = 0; q < 3; ++q)
+                                acc[1 + q][k] += N * (B[q] + E[3 * q] * cx + E[3 * q + 1] * cy + E[3 * q + 2] * cz);
+                            if (nf == 6) {
+                                acc[4][k] += mp * N;
+                                acc[5][k] += N * (TB + TE[0] * cx + TE[1] * cy + TE[2] * cz);
+                            }
+                            if (ph == 1) break;
+                        }
                     }
                 }
+        __syncwarp();
     }
     __syncthreads();
+    // the two warps' levels summed per halo node, then added to the grid
     for (int h = threadIdx.x; h < HN; h += blockDim.x) {
-        if (acc[0][h] == 0.0 && acc[4][h] == 0.0) continue;
+        const int hx = h % HE, hy = (h / HE) % HE, hz = h / (HE * HE);
+        double v[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            v[f] = 0.0;
+            if (hz <= 3) v[f] += acc[f][pidx(hx, hy, hz)];
+            if (hz >= 2) v[f] += acc[f][pidx(hx, hy, hz + 2)];
+        }
+        if (v[0] == 0.0 && v[4] == 0.0) continue;
         int ns, loc;
         halo_source(a.nbr, slot, h, ns, loc);
         if (ns < 0) continue;
-        atomicAdd(&a.gm[ns * 64 + loc], acc[0][h]);
-        for (int q = 0; q < 3; ++q) atomicAdd(&a.gmv[ns * 192 + q * 64 + loc], acc[1 + q][h]);
-        if (S.thermal) {
-            atomicAdd(&a.gmT[ns * 64 + loc], acc[4][h]);
-            atomicAdd(&a.gmTT[ns * 64 + loc], acc[5][h]);
+        atomicAdd(&a.gm[ns * 64 + loc], v[0]);
+        for (int q = 0; q < 3; ++q) atomicAdd(&a.gmv[ns * 192 + q * 64 + loc], v[1 + q]);
+        if (nf == 6) {
+            atomicAdd(&a.gmT[ns * 64 + loc], v[4]);
+            atomicAdd(&a.gmTT[ns * 64 + loc], v[5]);
         }
     }
 }

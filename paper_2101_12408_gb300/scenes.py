@@ -365,8 +365,9 @@ def wax(nx=256, ny=256, nz=128, cube_cells=96, seed=1004, ppc_axis=2, surf_per_c
         K=0.1, cp=1.0, mu_l=1e-3) -> Scene:
     """Melting wax block: a fixed-corotated cube on a sticky floor, heated on -x.
 
-    E(T) falls linearly from E0 at T0 to 0 at T_melt; liquid bulk modulus
-    E0 / (3 (1 - 2 nu)); gamma(T) = clamp(0.1 - 0.01 (T - T0), 0, 0.1).
+    E(T) falls linearly from E0 at T0 to 0 at T_melt and sets the solid's shear
+    modulus; the bulk modulus E0 / (3 (1 - 2 nu)) serves the liquid and the solid
+    phases; gamma(T) = clamp(0.1 - 0.01 (T - T0), 0, 0.1).
     Surface samples cover the five free faces; the -x face carries the heating
     rate b, every face Robin convection h towards T0.
     """

@@ -1070,3 +1070,37 @@ def test_exact_minus_projected_surface_term_is_negative_semidefinite():
         np.testing.assert_allclose(D, D.T, atol=1e-10 * ga)
         ev = np.sort(np.linalg.eigvalsh(0.5 * (D + D.T)))
         np.testing.assert_allclose(ev, [-ga, -ga] + [0.0] * 7, atol=1e-9 * ga)
+
+
+def test_solid_at_the_melting_point_stores_the_liquids_energy():
+    """Reading of section "Thermomechanical Material Dependence and Phase Change"
+    with the candle example's single bulk modulus for both phases: E(T) reaches 0
+    at T_melt and sets the shear modulus only, so a solid at the melting point with
+    F = c I has the liquid's energy lambda_l/2 (J - 1)^2 and force at J = c^3 (at
+    the step's start, v = 0, where the liquid's J and the solid's det F agree)."""
+    base = scenes.droplet(n=12, r_cells=3.0, seed=31, lambda_l=70.0, gamma=0.0)
+    base.params.E0 = 500.0
+    base.params.T0, base.params.T_melt = 0.0, 10.0
+    c = 0.97
+    liq = base.copy()
+    liq.J = np.full(liq.J.shape, c ** 3)
+    sol = base.copy()
+    sol.phase[:] = scenes.PHASE_SOLID
+    sol.F = np.broadcast_to(c * np.eye(3), sol.F.shape).copy()
+    sol.T = np.full(sol.T.shape, 10.0)       # at the melting point: E = 0
+    st = []
+    for sc in (liq, sol):
+        sim, s = _state(sc)
+        st.append(s)
+    v0 = np.zeros((st[0].G, 3))
+    e_liq, e_sol = st[0].energy(v0), st[1].energy(v0)
+    assert e_liq > 0
+    np.testing.assert_allclose(e_sol, e_liq, rtol=1e-12)
+    g_liq, g_sol = st[0].gradient(v0), st[1].gradient(v0)
+    np.testing.assert_allclose(g_sol, g_liq, rtol=0, atol=1e-12 * np.abs(g_liq).max())
+    # below the melting point the shear modulus adds energy for a sheared F
+    sol2 = sol.copy()
+    sol2.T = np.full(sol.T.shape, 5.0)
+    sol2.F = np.broadcast_to(np.array([[1.0, 0.1, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]), sol.F.shape).copy()
+    _, s2 = _state(sol2)
+    assert s2.energy(v0) > 0
