@@ -62,7 +62,16 @@ def test_steps_with_generated_surface_match_oracle():
         sim.p2g()
         sim.grid_update()
         np.testing.assert_array_equal(ctx.get_surface(0)["parent"], sim.parent)
-        assert relerr(ctx.get_grid(0, mpm.FIELD_VHAT), sim.vhat) < 1e-8
+        # Both sides stop Newton at a 1e-10 relative residual. The end-of-step
+        # velocity v - r/m (reading R17 of the final force evaluation) carries
+        # the leftover residual divided by the node mass, so nodes with little
+        # mass (balance particles just outside the surface) hold the largest
+        # differences, ~1e-8 of the largest velocity; weighted by mass they are
+        # a few 1e-9 (measured 2.9e-9)
+        vg, vo = ctx.get_grid(0, mpm.FIELD_VHAT), sim.vhat
+        assert relerr(vg, vo) < 3e-8
+        m = sim.grid["m"][:, None]
+        assert np.sum(m * np.abs(vg - vo)) <= 1e-8 * np.sum(m * np.abs(vo))
         ctx.g2p()
         sim.g2p()
     # Balance particles put small masses on nodes just outside the surface; the
