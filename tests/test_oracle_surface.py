@@ -109,3 +109,59 @@ def test_osada_points_uniform_and_poisson_counts():
     # area 0.45, density 60: Poisson mean 27 per triangle
     assert abs(s.shape[0] / 400.0 - 27.0) < 0.8
     assert np.allclose(dA[:, 2], 1.0 / 60.0, rtol=1e-12) and np.all(dA[:, :2] == 0.0)
+
+
+def _sphere_isosurface(r_cells, n, c):
+    """Triangles of phi = |x - c| - R sampled at the nodes of an n^3 grid."""
+    dx = 1.0 / n
+    R = r_cells * dx
+
+    def phi(q):
+        return math.sqrt(sum(((q[a] + 0.5) * dx - c[a]) ** 2 for a in range(3))) - R
+
+    lo = [max(0, int((c[a] - R) / dx) - 2) for a in range(3)]
+    hi = [min(n - 1, int((c[a] + R) / dx) + 2) for a in range(3)]
+    cubes = set()
+    for i in range(lo[0], hi[0]):
+        for j in range(lo[1], hi[1]):
+            for k in range(lo[2], hi[2]):
+                v = [phi((i + a, j + b, k + e)) for a in (0, 1) for b in (0, 1) for e in (0, 1)]
+                if min(v) < 0.0 <= max(v):
+                    cubes.add((i, j, k))
+    tris, keys = S.isosurface(phi, cubes, (n,) * 3, dx)
+    area = sum(0.5 * np.linalg.norm(S._cross(S._sub(p1, p0), S._sub(p2, p0))) for p0, p1, p2 in tris)
+    return tris, keys, area, R, dx
+
+
+def test_tetrahedral_isosurface_of_a_sphere_area_and_sample_coverage():
+    """The statistics that a marching-cubes surface of the same level set also
+    meets, checked against the exact sphere instead (section "Surface Particle
+    Sampling"): the triangulated area converges to 4 pi R^2 at second order in
+    dx / R, and the per-triangle Poisson samples lie on the sphere, cover it
+    uniformly (equal counts per octant, cos(polar angle) uniform, Archimedes) and
+    carry |dA| summing to the area."""
+    c = (0.513, 0.479, 0.507)   # off the node lattice
+    err = {}
+    for r_cells in (6.0, 12.0):
+        tris, keys, area, R, dx = _sphere_isosurface(r_cells, 32, c)
+        err[r_cells] = area / (4.0 * math.pi * R * R) - 1.0
+    assert abs(err[6.0]) < 0.01 and abs(err[12.0]) < 0.003
+    assert 3.0 < err[6.0] / err[12.0] < 5.5            # second order: halving dx / R quarters the error
+    density = 2.0 / (dx * dx)
+    s, dA = S.sample_triangles(tris, keys, seed=31, density=density)
+    N = s.shape[0]
+    assert abs(N / (density * area) - 1.0) < 4.0 / math.sqrt(density * area)
+    rel = s - np.asarray(c)
+    dist = np.linalg.norm(rel, axis=1)
+    assert np.all(np.abs(dist - R) < 0.05 * dx)
+    octant = (rel[:, 0] > 0) + 2 * (rel[:, 1] > 0) + 4 * (rel[:, 2] > 0)
+    counts = np.bincount(octant, minlength=8)
+    assert np.all(np.abs(counts - N / 8.0) < 5.0 * math.sqrt(N / 8.0))
+    hist = np.histogram(rel[:, 2] / dist, bins=10, range=(-1.0, 1.0))[0]
+    chi2 = float(np.sum((hist - N / 10.0) ** 2 / (N / 10.0)))
+    assert chi2 < 33.7                                   # 9 degrees of freedom, p = 1e-4
+    mag = np.linalg.norm(dA, axis=1)
+    assert abs(mag.sum() / area - 1.0) < 4.0 / math.sqrt(N)
+    # outward and normal to the sphere up to the facets' tilt
+    assert np.all(np.sum(dA * rel, axis=1) > 0.0)
+    assert np.mean(np.sum(dA * rel, axis=1) / (mag * dist)) > 0.99
