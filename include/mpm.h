@@ -189,7 +189,9 @@ mpm_status mpm_set_surface(mpm_ctx* ctx, int32_t scene, int64_t n, const double*
                            const double* Tbar);
 /* Reads samples back in set order: positions, area normals (carried through the
  * step), kind, surface coefficient gamma_r, the parent particle p(r) (index in
- * mpm_set_particles order) and the balance position b_r. NULL pointers skipped. */
+ * mpm_set_particles order) and the balance position b_r. NULL pointers skipped.
+ * Samples set by mpm_set_surface or made by mpm_generate_surface have parent -1
+ * (and an unset b_r) until the next mpm_resample. */
 mpm_status mpm_get_surface(mpm_ctx* ctx, int32_t scene, int64_t n, double* s, double* dA,
                            uint8_t* kind, double* gamma, int32_t* parent, double* bpos);
 

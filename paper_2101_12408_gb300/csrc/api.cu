@@ -149,6 +149,7 @@ __global__ void k_stage_surf_in(int n, int base, int scene, const double* __rest
     d.Tbar[k] = Tbar ? Tbar[i] : 0.0;
     d.sid[k] = i;
     d.ssc[k] = scene;
+    d.parent[k] = -1;   // no parent until mpm_resample
 }
 
 // gather particle fields back into set order: field id f, comps
@@ -169,14 +170,14 @@ __global__ void k_stage_out_u8(int np, int scene, int n, const int* __restrict__
     if (id >= 0 && id < n) out[id] = src[i];
 }
 
-__global__ void k_stage_parent(int ns, int scene, int n, const int* __restrict__ ssc, const int* __restrict__ sid,
+__global__ void k_stage_parent(int ns, int np, int scene, int n, const int* __restrict__ ssc, const int* __restrict__ sid,
                                const int* __restrict__ parent, const int* __restrict__ pid, int32_t* __restrict__ out) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ns || ssc[j] != scene) return;
     int id = sid[j];
     if (id < 0 || id >= n) return;
     int p = parent[j];
-    out[id] = p < 0 ? -1 : pid[p];
+    out[id] = (p < 0 || p >= np) ? -1 : pid[p];
 }
 
 __global__ void k_check_finite(int n, const double* __restrict__ a, int* err) {
@@ -579,7 +580,7 @@ mpm_status mpm_get_surface(mpm_ctx* c, int32_t scene, int64_t n, double* s, doub
         MPM_CUDA(cudaStreamSynchronize(st));
     }
     if (parent) {
-        MPM_LAUNCH k_stage_parent<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, scene, (int)n, d.ssc, d.sid, d.parent, d.pid,
+        MPM_LAUNCH k_stage_parent<<<nblk(c->ns, 256), 256, 0, st>>>((int)c->ns, (int)c->np, scene, (int)n, d.ssc, d.sid, d.parent, d.pid,
                                                          (int32_t*)d.dense_a);
         MPM_CUDA(cudaMemcpyAsync(parent, d.dense_a, sizeof(int32_t) * n, cudaMemcpyDefault, st));
         MPM_CUDA(cudaStreamSynchronize(st));

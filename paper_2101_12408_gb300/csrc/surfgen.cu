@@ -344,6 +344,7 @@ __global__ void k_tri_emit(long long ntri, const double* __restrict__ tv, const 
         d.Tbar[j] = S.T0;
         d.sid[j] = (int)(j - scene_first[scene]);
         d.ssc[j] = scene;
+        d.parent[j] = -1;   // no parent until mpm_resample
     }
 }
 
