@@ -338,7 +338,7 @@ def bench_ours(args, rank, world):
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": measured_traffic(), "peak_source": peak_kind,
-                     "kernel": "k_apply_cell + k_apply_general (Hessian-vector operator)",
+                     "kernel": "k_apply_pair + k_apply_surf + k_apply_general (Hessian-vector operator)",
                      "bytes_per_launch": abytes, "launch_ms": apply_avg_ms, "launches": prof["apply_launches"]},
         "counts": dict(counts, grid_blocks=cnt["blocks"], work_blocks=cnt["work_blocks"]),
         "applies_per_s": prof["apply_launches"] / (elapsed_ms * 1e-3),

@@ -196,7 +196,15 @@ __global__ void k_pack_volume(int np, Ptrs3 x, const double* __restrict__ J, Ptr
         rec.z = pu.a[2][i];
         bool general = !liq || S.mu_l != 0.0;
         rec.w = general ? R(-1) : (R)(dt * dt * S.lambda_l * Jn * Jn * v0);
-        if (rec_at >= 0) opk[rec_at] = rec;
+        if (rec_at >= 0) {
+            // pair-interleaved row: cells 2l, 2l+1 as x_A x_B y_A y_B z_A z_B kappa_A kappa_B
+            const int lc = (int)(rec_at & 63);
+            R* row = reinterpret_cast<R*>(opk + (rec_at - lc)) + 8 * (lc >> 1) + (lc & 1);
+            row[0] = rec.x;
+            row[2] = rec.y;
+            row[4] = rec.z;
+            row[6] = rec.w;
+        }
     }
     if (!liq) {
         for (int q = 0; q < 9; ++q) Fn.a[q][i] = (R)Fd[q];
@@ -542,7 +550,7 @@ struct ApplyArgs {
     const R* sKa;             // surface: per-sample records (SREC values: the projected-Hessian map, position)
     RPtr45<R> pK;             // solid: symmetric 9x9 map dL -> M of the projected Hessian (per iterate)
     int use_pK;
-    int samples_in_cell;      // projected mode with current maps: k_apply_cell applies the samples
+    int samples_in_cell;      // projected mode with current maps: k_apply_pair applies the samples
     const int* slot_gen;      // general particles per slot
     const R4<R>* opk;         // rank-major records: position in the block (cells), kappa (< 0: general)
     const int *wrows, *wroff; // per work block: record rows and their offset
@@ -554,19 +562,21 @@ struct ApplyArgs {
 };
 
 // ======================================================================
-// Hessian-vector operator, thread per cell (the production kernel)
+// Per-cell polynomial form of the liquid operator
 //
-// One CTA per block of 4x4x4 cells, one thread per cell. For a liquid particle
-// without viscosity the operator is rank one, u_i += kappa_p tr(dL_p) gradN_i(x_p),
-// and with the in-cell coordinate t in [0,1)^3 of the particle (x = (c + t) dx)
-// every 1-D weight and derivative is a polynomial of degree <= 2:
+// For a liquid particle without viscosity the operator is rank one,
+// u_i += kappa_p tr(dL_p) gradN_i(x_p), and with the in-cell coordinate t in
+// [0,1)^3 of the particle (x = (c + t) dx) every 1-D weight and derivative is a
+// polynomial of degree <= 2:
 //   w = (1/2 - t + t^2/2,  1/2 + t - t^2,  t^2/2),   dw/dt = (-1 + t, 1 - 2t, t).
 // So tr(dL)(t) = sum_ijk C_ijk tx^i ty^j tz^k with 26 coefficients (no t^2 t^2 t^2
 // term) fixed per cell by the 27 stencil values of p, and the cell's scatter is a
 // fixed linear map of the 26 moments M_ijk = sum_p s_p tx^i ty^j tz^k. Each cell
 // reads its 81 inputs and writes its 81 outputs once, whatever its particle count;
-// per particle only 26 + 26 multiply-adds remain. Solids, viscous liquids and
-// surface samples take the general per-particle path in the same CTA.
+// per particle only 26 + 26 multiply-adds remain. The transforms below (wT, dT,
+// wN, dN) are the 1-D pieces of those two maps; k_apply_pair applies them to two
+// cells at once, k_eval_cell and k_curv_cell one cell per thread. Solids, viscous
+// liquids and (exact-mode) surface samples take the general per-particle path.
 // Shared layout x + 8 y + 52 z: the 32 cells of a warp hit 32 distinct banks.
 // ======================================================================
 
@@ -835,8 +845,10 @@ __device__ __forceinline__ void load_halo_rows(const int* __restrict__ nbr, int 
         ph[c][h0 + 3] = m2;
         ph[c][h0 + 4] = m3;
         ph[c][h0 + 5] = nhi >= 0 ? p[nhi * 192 + c * 64 + base] : R(0);
+        if (ua) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) ua[c][h0 + k] = R(0);
+            for (int k = 0; k < 6; ++k) ua[c][h0 + k] = R(0);
+        }
     }
 }
 
@@ -874,7 +886,6 @@ __device__ __forceinline__ void flush_halo_rows(const int* __restrict__ nbr, int
 // nodes, and offsets whose z differs by 2 never meet (a warp's cells span two z
 // levels), so each phase below is a plain read-add-write by every lane with no
 // two lanes on one node; __syncwarp orders the phases.
-constexpr int KR2 = 8;   // record rows staged per chunk
 
 // every lane of the warp calls it; lanes with act = false only take part in the
 // phase ordering (two lanes may never write one node in one phase)
@@ -999,252 +1010,546 @@ __device__ __forceinline__ void flush_halo_rows_u(const int* __restrict__ nbr, i
     }
 }
 
+// ======================================================================
+// Hessian-vector operator on cells in x-pairs (the production kernel for the
+// rank-one liquid particles and the surface samples).
+//
+// One warp per block of 4x4x4 cells. Lane l = m + 2 ly + 8 lz owns the two
+// cells 2l and 2l+1, side by side in x: A at (2m, ly, lz) and B at
+// (2m+1, ly, lz). Every step of the per-cell polynomial form above is
+// the same for A and B, so the lane carries each quantity as a pair (A in .x, B
+// in .y) and uses paired float arithmetic, one instruction for both cells. The
+// stencils of A and B cover the x-nodes 2m..2m+2 and 2m+1..2m+3 of a row: the
+// lane reads those four nodes as two aligned pairs, and adds A's and B's node
+// values into the same four nodes before it writes them. The liquid records of
+// a row are stored pair-interleaved (x_A x_B y_A y_B z_A z_B kappa_A kappa_B for
+// the cells 2l, 2l+1), so a record pair arrives as four value pairs.
+// ======================================================================
+
+// paired arithmetic: float2 uses the paired float instructions, double2 plain pairs
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+template <typename R> struct VPair;
+template <> struct VPair<float> {
+    using T = float2;
+    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct VPair<double> {
+    using T = double2;
+    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+
+// the scalar transforms (wT, dT, wN, dN) on pairs
+template <typename V>
+__device__ __forceinline__ void pwT(V v0, V v1, V v2, V& o0, V& o1, V& o2, V h) {
+    o0 = vmul(vadd(v0, v1), h);
+    o1 = vsub(v1, v0);
+    o2 = vsub(vmul(vadd(v0, v2), h), v1);
+}
+template <typename V>
+__device__ __forceinline__ void pdT(V v0, V v1, V v2, V& o0, V& o1, V m2) {
+    o0 = vsub(v1, v0);
+    o1 = vfma(v1, m2, vadd(v0, v2));
+}
+template <typename V>
+__device__ __forceinline__ void pwN(V m0, V m1, V m2, V& n0, V& n1, V& n2, V h) {
+    n0 = vsub(vmul(vadd(m0, m2), h), m1);
+    n1 = vfma(m0, h, vsub(m1, m2));
+    n2 = vmul(m2, h);
+}
+template <typename V>
+__device__ __forceinline__ void pdN(V m0, V m1, V& n0, V& n1, V& n2, V m2) {
+    n0 = vsub(m1, m0);
+    n1 = vfma(m1, m2, m0);
+    n2 = m1;
+}
+
+// the four x-nodes 2m..2m+3 of halo row (y, z) of component q, as the pairs
+// (x0, x1) and (x2, x3)
 template <typename R>
-__global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell(ApplyArgs<R> a) {
-    __shared__ R ph[3][PN];
-    __shared__ __align__(16) R ua[3][UN];
-    __shared__ R4<R> sp[KR2 * 64];
-    __shared__ __align__(8) uint64_t bar;
-    int w = blockIdx.x;
-    int slot = a.work[w];
-    long long gb = a.work_gb[w];
-    int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    if (a.check_done && a.scal[bc.w].cg_done) return;
-    const int rows = a.wrows[w];
-    const R4<R>* recs = a.opk + (long long)a.wroff[w] * 64;
-    const int nchunk = (rows + KR2 - 1) / KR2;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
-    for (int i = threadIdx.x; i < (int)(3 * UN * sizeof(R) / 16); i += blockDim.x)
-        reinterpret_cast<int4*>(&ua[0][0])[i] = make_int4(0, 0, 0, 0);
-    __syncthreads();
-    if (threadIdx.x == 0 && nchunk > 0) {
-        uint32_t cnt = (uint32_t)min(KR2, rows) * 64u;
-        mbar_expect_tx(&bar, cnt * (uint32_t)sizeof(R4<R>));
-        bulk_g2s(sp, recs, cnt * (uint32_t)sizeof(R4<R>), &bar);
-    }
+__device__ __forceinline__ void row_pairs(const R* phq, int x0, int y, int z, typename VPair<R>::T& p01,
+                                          typename VPair<R>::T& p23) {
+    using V = typename VPair<R>::T;
+    const V* r = reinterpret_cast<const V*>(phq + pidx(x0, y, z));
+    p01 = r[0];
+    p23 = r[1];
+}
+
+// C = the coefficients of tr(dL) (without the 1/dx factor) of the cells A and B
+// of the pair at (2m, ly, lz): each component's separable transform, the
+// derivative axis first (it leaves two coefficients of three).
+template <typename R>
+__device__ __forceinline__ void pair_coefficients(const R (*ph)[PN], int m, int ly, int lz,
+                                                  typename VPair<R>::T (&C)[3][3][3]) {
+    using V = typename VPair<R>::T;
+    using P = VPair<R>;
+    const V h = P::make(R(0.5), R(0.5)), m2 = P::make(R(-2), R(-2));
+    const int x0 = 2 * m;
+    // x component: D along x, then W along y and z
     {
-        // the direction's halo: one neighbour lookup per (y, z) row, three components
-        for (int yz = threadIdx.x; yz < HE * HE; yz += blockDim.x) {
-            const int hy = yz % HE, hz = yz / HE;
-            int nmid, nlo, nhi, base;
-            halo_row<R>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
-            const int h0 = pidx(0, hy, hz);
+        V X[2][3][3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
-                if (nmid >= 0) {
-                    const R* src = a.p + nmid * 192 + c * 64 + base;
-                    if constexpr (sizeof(R) == 4) {
-                        float4 v = *reinterpret_cast<const float4*>(src);
-                        m0 = v.x; m1 = v.y; m2 = v.z; m3 = v.w;
-                    } else {
-                        m0 = src[0]; m1 = src[1]; m2 = src[2]; m3 = src[3];
-                    }
-                }
-                ph[c][h0] = nlo >= 0 ? a.p[nlo * 192 + c * 64 + base + 3] : R(0);
-                ph[c][h0 + 1] = m0;
-                ph[c][h0 + 2] = m1;
-                ph[c][h0 + 3] = m2;
-                ph[c][h0 + 4] = m3;
-                ph[c][h0 + 5] = nhi >= 0 ? a.p[nhi * 192 + c * 64 + base] : R(0);
+                V p01, p23;
+                row_pairs<R>(ph[0], x0, ly + b, lz + c, p01, p23);
+                const V p12 = P::make(p01.y, p23.x);
+                pdT<V>(p01, p12, p23, X[0][b][c], X[1][b][c], m2);
+            }
+        V Y[2][3][3];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pwT<V>(X[i][0][c], X[i][1][c], X[i][2][c], Y[i][0][c], Y[i][1][c], Y[i][2][c], h);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) pwT<V>(Y[i][j][0], Y[i][j][1], Y[i][j][2], C[i][j][0], C[i][j][1], C[i][j][2], h);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) C[2][j][k] = P::make(R(0), R(0));
+    }
+    // y component: D along y on the node pairs, W along x, then W along z
+    {
+        V Y01[2][3], Y23[2][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            V a01[3], a23[3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) row_pairs<R>(ph[1], x0, ly + b, lz + c, a01[b], a23[b]);
+            pdT<V>(a01[0], a01[1], a01[2], Y01[0][c], Y01[1][c], m2);
+            pdT<V>(a23[0], a23[1], a23[2], Y23[0][c], Y23[1][c], m2);
+        }
+        V X[3][2][3];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                pwT<V>(Y01[j][c], P::make(Y01[j][c].y, Y23[j][c].x), Y23[j][c], X[0][j][c], X[1][j][c], X[2][j][c], h);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                V g0, g1, g2;
+                pwT<V>(X[i][j][0], X[i][j][1], X[i][j][2], g0, g1, g2, h);
+                C[i][j][0] = vadd(C[i][j][0], g0);
+                C[i][j][1] = vadd(C[i][j][1], g1);
+                C[i][j][2] = vadd(C[i][j][2], g2);
+            }
+    }
+    // z component: D along z on the node pairs, W along y, then W along x
+    {
+        V Z01[3][2], Z23[3][2];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            V a01[3], a23[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) row_pairs<R>(ph[2], x0, ly + b, lz + c, a01[c], a23[c]);
+            pdT<V>(a01[0], a01[1], a01[2], Z01[b][0], Z01[b][1], m2);
+            pdT<V>(a23[0], a23[1], a23[2], Z23[b][0], Z23[b][1], m2);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            V y01[3], y23[3];
+            pwT<V>(Z01[0][k], Z01[1][k], Z01[2][k], y01[0], y01[1], y01[2], h);
+            pwT<V>(Z23[0][k], Z23[1][k], Z23[2][k], y23[0], y23[1], y23[2], h);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                V g0, g1, g2;
+                pwT<V>(y01[j], P::make(y01[j].y, y23[j].x), y23[j], g0, g1, g2, h);
+                C[0][j][k] = vadd(C[0][j][k], g0);
+                C[1][j][k] = vadd(C[1][j][k], g1);
+                C[2][j][k] = vadd(C[2][j][k], g2);
             }
         }
     }
-    __syncthreads();
-    const R inv_dx = (R)S.inv_dx;
-    const R s2 = inv_dx * inv_dx;
-    const int cell = threadIdx.x;
-    const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
-    const int wid = threadIdx.x >> 5;
-    const int cbeg = a.cell_start[gb * 64 + cell], cend = a.cell_start[gb * 64 + cell + 1];
-    R C[3][3][3], M[3][3][3];
+}
+
+// one component's node values of the pair, from its moments: N[b][c] holds, for
+// the halo row (ly + b, zb + c), the values to add at x-nodes 2m..2m+1 (lo) and
+// 2m+2..2m+3 (hi), A's and B's contributions summed
+template <typename V, typename P>
+__device__ __forceinline__ void pair_rows(const V (&Nx)[3][3][3], V (&lo)[3][3], V (&hi)[3][3]) {
 #pragma unroll
-    for (int q = 0; q < 27; ++q) {
-        (&C[0][0][0])[q] = R(0);
-        (&M[0][0][0])[q] = R(0);
-    }
-    if (cend > cbeg) cell_coefficients<R>(ph, lx, ly, lz, C);
-    KSum<R> pap;   // p . (H - M) p of this block's particles and samples
-    bool any = false, timed_out = false;
-    uint32_t parity_left = 0;
-    const int ncell = cend - cbeg;
-    for (int k = 0; k < nchunk; ++k) {
-        const int r0 = k * KR2;
-        bool ok = mbar_wait_bounded(&bar, (uint32_t)(k & 1), 1LL << 26);
-        if (__syncthreads_or(!ok)) {
-            timed_out = true;
-            parity_left = (uint32_t)(k & 1);
-            break;
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const V n0 = Nx[0][b][c], n1 = Nx[1][b][c], n2 = Nx[2][b][c];
+            lo[b][c] = P::make(n0.x, n1.x + n0.y);
+            hi[b][c] = P::make(n2.x + n1.y, n2.y);
         }
-        const int rhi = min(ncell, r0 + KR2);
-        for (int r = r0; r < rhi; ++r) {
-            R4<R> rec = sp[(r - r0) * 64 + cell];
-            if (rec.w < R(0)) continue;   // general particle: k_apply_general
-            any = true;
-            const R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
-            const R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
-            const R tz = fmin(fmax(rec.z - R(lz), R(0)), R(1));
-            // tr(dL)(t) by Horner's rule, z then y then x (no t^2 t^2 t^2 term)
-            R E[3];
+}
+
+// read-add-write of one component's rows into the lane's accumulation levels.
+// Phases: for each y offset b, the z offsets {0, 2} then {1}, the lo pairs then
+// the hi pairs; within a phase no two lanes of the warp write one node.
+template <typename R>
+__device__ __forceinline__ void pair_rmw(R* uq, int x0, int ly, int zb, const typename VPair<R>::T (&lo)[3][3],
+                                         const typename VPair<R>::T (&hi)[3][3]) {
+    using V = typename VPair<R>::T;
 #pragma unroll
-            for (int ii = 0; ii < 3; ++ii) {
-                R D[3];
+    for (int b = 0; b < 3; ++b) {
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    D[j] = (ii == 2 && j == 2) ? C[2][2][0] + tz * C[2][2][1] : C[ii][j][0] + tz * (C[ii][j][1] + tz * C[ii][j][2]);
-                E[ii] = D[0] + ty * (D[1] + ty * D[2]);
-            }
-            const R tr = E[0] + tx * (E[1] + tx * E[2]);
-            const R s = rec.w * s2 * tr;
-            pap.add(s * tr);
-            const R tz2 = tz * tz;
-            R sx = s;
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii) {
-                R sxy = sx;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    M[ii][j][0] += sxy;
-                    M[ii][j][1] += sxy * tz;
-                    if (!(ii == 2 && j == 2)) M[ii][j][2] += sxy * tz2;
-                    sxy *= ty;
-                }
-                sx *= tx;
+        for (int half = 0; half < 2; ++half) {
+            __syncwarp();
+            {
+                V* p0 = reinterpret_cast<V*>(uq + pidx(x0 + 2 * half, ly + b, zb));
+                V* p2 = reinterpret_cast<V*>(uq + pidx(x0 + 2 * half, ly + b, zb + 2));
+                const V v0 = *p0, v2 = *p2;
+                *p0 = vadd(v0, half ? hi[b][0] : lo[b][0]);
+                *p2 = vadd(v2, half ? hi[b][2] : lo[b][2]);
             }
         }
-        __syncthreads();
-        if (k + 1 < nchunk && threadIdx.x == 0) {
-            uint32_t cnt2 = (uint32_t)min(KR2, rows - (r0 + KR2)) * 64u;
-            mbar_expect_tx(&bar, cnt2 * (uint32_t)sizeof(R4<R>));
-            bulk_g2s(sp, recs + (long long)(r0 + KR2) * 64, cnt2 * (uint32_t)sizeof(R4<R>), &bar);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            __syncwarp();
+            V* p1 = reinterpret_cast<V*>(uq + pidx(x0 + 2 * half, ly + b, zb + 1));
+            *p1 = vadd(*p1, half ? hi[b][1] : lo[b][1]);
         }
     }
-    if (timed_out) {
-        if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
-        mbar_wait_bounded(&bar, parity_left, 1LL << 20);
-        return;
+    __syncwarp();
+}
+
+// node values (without the 1/dx factor) of the pair's moments, component by
+// component, added to the lane's accumulation levels (every lane calls it)
+template <typename R>
+__device__ __forceinline__ void pair_scatter(const typename VPair<R>::T (&M)[3][3][3], R (*ua)[UN], int m, int ly,
+                                             int zb) {
+    using V = typename VPair<R>::T;
+    using P = VPair<R>;
+    const V h = P::make(R(0.5), R(0.5)), m2 = P::make(R(-2), R(-2));
+    const int x0 = 2 * m;
+    V N[3][3][3];
+    V lo[3][3], hi[3][3];
+    {   // x: W along z, W along y, D along x
+        V T1[2][3][3], T2[2][3][3];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) pwN<V>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2], h);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pwN<V>(T1[i][0][c], T1[i][1][c], T1[i][2][c], T2[i][0][c], T2[i][1][c], T2[i][2][c], h);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pdN<V>(T2[0][b][c], T2[1][b][c], N[0][b][c], N[1][b][c], N[2][b][c], m2);
     }
-    // The block's surface samples (projected mode with current maps): their
-    // records (map and position, SREC values each) are staged into the record
-    // buffer by one bulk copy per chunk, the first issued here so that it lands
-    // while the warps scatter their cells.
-    const int sbeg = a.scell_start[gb * 64], nsm = a.samples_in_cell ? a.scell_start[gb * 64 + 64] - sbeg : 0;
-    constexpr int SCAP = (KR2 * 64 * 4) / SREC;   // samples per staged chunk
-    R* sbuf = reinterpret_cast<R*>(sp);
-    uint32_t phase = (uint32_t)nchunk;          // bulk copies completed on `bar` so far
-    if (nsm > 0 && threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)(min(nsm, SCAP) * SREC * sizeof(R));
+    pair_rows<V, P>(N, lo, hi);
+    pair_rmw<R>(ua[0], x0, ly, zb, lo, hi);
+    {   // y: W along z, W along x, D along y
+        V T1[3][2][3], T2[3][2][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) pwN<V>(M[i][j][0], M[i][j][1], M[i][j][2], T1[i][j][0], T1[i][j][1], T1[i][j][2], h);
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pwN<V>(T1[0][j][c], T1[1][j][c], T1[2][j][c], T2[0][j][c], T2[1][j][c], T2[2][j][c], h);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pdN<V>(T2[a][0][c], T2[a][1][c], N[a][0][c], N[a][1][c], N[a][2][c], m2);
+    }
+    pair_rows<V, P>(N, lo, hi);
+    pair_rmw<R>(ua[1], x0, ly, zb, lo, hi);
+    {   // z: W along x, W along y, D along z
+        V T1[3][3][2], T2[3][3][2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) pwN<V>(M[0][j][k], M[1][j][k], M[2][j][k], T1[0][j][k], T1[1][j][k], T1[2][j][k], h);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) pwN<V>(T1[a][0][k], T1[a][1][k], T1[a][2][k], T2[a][0][k], T2[a][1][k], T2[a][2][k], h);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) pdN<V>(T2[a][b][0], T2[a][b][1], N[a][b][0], N[a][b][1], N[a][b][2], m2);
+    }
+    pair_rows<V, P>(N, lo, hi);
+    pair_rmw<R>(ua[2], x0, ly, zb, lo, hi);
+}
+
+constexpr int KRP = 4;   // record rows staged per chunk by the pair kernel
+
+template <typename R>
+__global__ void __launch_bounds__(32, sizeof(R) == 4 ? 16 : 8) k_apply_pair(ApplyArgs<R> a) {
+    using V = typename VPair<R>::T;
+    using P = VPair<R>;
+    __shared__ __align__(16) R ph[3][PN];
+    __shared__ __align__(16) R ua[3][UN];
+    __shared__ __align__(16) R sp[KRP * 256];
+    __shared__ __align__(8) uint64_t bar;
+    const int w = blockIdx.x;
+    const int slot = a.work[w];
+    const long long gb = a.work_gb[w];
+    const int4 bc = a.coord[slot];
+    const SceneDev& S = a.sc[bc.w];
+    if (a.check_done && a.scal[bc.w].cg_done) return;
+    const int lane = threadIdx.x;
+    // liquid rows of the block: none when every particle takes the general path
+    const int npart = a.cell_start[gb * 64 + 64] - a.cell_start[gb * 64];
+    const int rows = (npart > a.slot_gen[slot]) ? a.wrows[w] : 0;
+    const R* recs = reinterpret_cast<const R*>(a.opk) + (long long)a.wroff[w] * 256;
+    const int nchunk = (rows + KRP - 1) / KRP;
+    if (lane == 0) mbar_init(&bar, 1);
+    for (int i = lane; i < (int)(3 * UN * sizeof(R) / 16); i += 32)
+        reinterpret_cast<int4*>(&ua[0][0])[i] = make_int4(0, 0, 0, 0);
+    __syncwarp();
+    if (lane == 0 && nchunk > 0) {
+        const uint32_t bytes = (uint32_t)(min(KRP, rows) * 256 * sizeof(R));
         mbar_expect_tx(&bar, bytes);
-        bulk_g2s(sbuf, a.sKa + (long long)sbeg * SREC, bytes, &bar);
+        bulk_g2s(sp, recs, bytes, &bar);
     }
-    // every lane of a warp takes part in its scatter phases (empty cells add zeros)
-    if (__any_sync(0xffffffffu, any)) cell_scatter_warp<R>(M, ua, lx, ly, lz + 2 * wid);
+    // the direction's halo: one neighbour lookup per (y, z) row, three components
+    for (int yz = lane; yz < HE * HE; yz += 32) {
+        const int hy = yz % HE, hz = yz / HE;
+        int nmid, nlo, nhi, base;
+        halo_row<R>(a.nbr, slot, hy, hz, nmid, nlo, nhi, base);
+        const int h0 = pidx(0, hy, hz);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            R m0 = R(0), m1 = R(0), m2 = R(0), m3 = R(0);
+            if (nmid >= 0) {
+                const R* src = a.p + nmid * 192 + c * 64 + base;
+                if constexpr (sizeof(R) == 4) {
+                    float4 v = *reinterpret_cast<const float4*>(src);
+                    m0 = v.x; m1 = v.y; m2 = v.z; m3 = v.w;
+                } else {
+                    m0 = src[0]; m1 = src[1]; m2 = src[2]; m3 = src[3];
+                }
+            }
+            ph[c][h0] = nlo >= 0 ? a.p[nlo * 192 + c * 64 + base + 3] : R(0);
+            ph[c][h0 + 1] = m0;
+            ph[c][h0 + 2] = m1;
+            ph[c][h0 + 3] = m2;
+            ph[c][h0 + 4] = m3;
+            ph[c][h0 + 5] = nhi >= 0 ? a.p[nhi * 192 + c * 64 + base] : R(0);
+        }
+    }
+    __syncwarp();
+    const R inv_dx = (R)S.inv_dx;
+    const int m = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
+    const int zb = lz + 2 * (lz >> 1);   // the lane's accumulation levels (region lz >> 1)
+    KSum<R> pap;   // p . (H - M) p of this block's particles and samples
+    if (rows > 0) {
+        V C[3][3][3], M[3][3][3];
+        pair_coefficients<R>(ph, m, ly, lz, C);
+        {
+            const R s2 = inv_dx * inv_dx;
+            const V s2v = P::make(s2, s2);
+#pragma unroll
+            for (int q = 0; q < 27; ++q) {
+                (&C[0][0][0])[q] = vmul((&C[0][0][0])[q], s2v);
+                (&M[0][0][0])[q] = P::make(R(0), R(0));
+            }
+        }
+        const V offx = P::make(R(2 * m), R(2 * m + 1)), offy = P::make(R(ly), R(ly)), offz = P::make(R(lz), R(lz));
+        V ks = P::make(R(0), R(0)), kc = P::make(R(0), R(0));   // compensated pair sum of s tr
+        for (int k = 0; k < nchunk; ++k) {
+            const int r0 = k * KRP;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar, (uint32_t)(k & 1), 1LL << 26))) {
+                // give the copy in flight a last bounded wait before the CTA leaves
+                if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+                mbar_wait_bounded(&bar, (uint32_t)(k & 1), 1LL << 20);
+                return;
+            }
+            const int rhi = min(rows, r0 + KRP);
+            for (int r = r0; r < rhi; ++r) {
+                const V* pr = reinterpret_cast<const V*>(sp + (r - r0) * 256 + 8 * lane);
+                const V tx = vsub(pr[0], offx), ty = vsub(pr[1], offy), tz = vsub(pr[2], offz);
+                V kap = pr[3];
+                kap.x = kap.x > R(0) ? kap.x : R(0);   // empty slot 0, general particle < 0
+                kap.y = kap.y > R(0) ? kap.y : R(0);
+                // s2 tr(dL)(t) by Horner's rule, z then y then x (no t^2 t^2 t^2 term)
+                V E[3];
+#pragma unroll
+                for (int ii = 0; ii < 3; ++ii) {
+                    V D[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        D[j] = (ii == 2 && j == 2) ? vfma(tz, C[2][2][1], C[2][2][0])
+                                                   : vfma(tz, vfma(tz, C[ii][j][2], C[ii][j][1]), C[ii][j][0]);
+                    E[ii] = vfma(ty, vfma(ty, D[2], D[1]), D[0]);
+                }
+                const V tr = vfma(tx, vfma(tx, E[2], E[1]), E[0]);
+                const V s = vmul(kap, tr);
+                {   // Kahan step on the pair: ks - kc += s tr / s2 (tr carries s2)
+                    const V y = vsub(vmul(s, tr), kc);
+                    const V t = vadd(ks, y);
+                    kc = vsub(vsub(t, ks), y);
+                    ks = t;
+                }
+                const V tz2 = vmul(tz, tz);
+                V sx = s;
+#pragma unroll
+                for (int ii = 0; ii < 3; ++ii) {
+                    V sxy = sx;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        M[ii][j][0] = vadd(M[ii][j][0], sxy);
+                        M[ii][j][1] = vfma(sxy, tz, M[ii][j][1]);
+                        if (!(ii == 2 && j == 2)) M[ii][j][2] = vfma(sxy, tz2, M[ii][j][2]);
+                        if (j < 2) sxy = vmul(sxy, ty);
+                    }
+                    if (ii < 2) sx = vmul(sx, tx);
+                }
+            }
+            __syncwarp();
+            if (k + 1 < nchunk && lane == 0) {
+                const uint32_t bytes = (uint32_t)(min(KRP, rows - (r0 + KRP)) * 256 * sizeof(R));
+                mbar_expect_tx(&bar, bytes);
+                bulk_g2s(sp, recs + (long long)(r0 + KRP) * 256, bytes, &bar);
+            }
+        }
+        // s tr carries s2 twice: p . K p = sum kappa s2 tr^2 = (s tr) / s2
+        const R inv_s2 = R(1) / (inv_dx * inv_dx);
+        pap.add((ks.x - kc.x) * inv_s2);
+        pap.add((ks.y - kc.y) * inv_s2);
+        pair_scatter<R>(M, ua, m, ly, zb);
+    }
+
+    // The block's surface samples (projected mode with current maps), staged by
+    // one bulk copy per chunk of SCAP records, in the order of their sorted
+    // cells. A pass takes the next ten samples of the chunk, three lanes per
+    // sample: lane q gathers row q of dF^, forms row block q of G = K dF^ and
+    // the node values of row q of G gradN over the sample's stencil, taken
+    // relative to its sorted cell (t clamped to [0, 1]). Samples of one cell are
+    // neighbours in the pass; their node values are summed into the first of
+    // them (a segmented suffix sum over the lane groups), which alone writes, so
+    // the writers of a pass lie in distinct cells. Each adds into its cell's
+    // accumulation levels (region sz >> 1, where the cells span two z levels):
+    // per stencil offset the writers of a pass write distinct nodes.
+    const int sbeg = a.scell_start[gb * 64], nsm = a.samples_in_cell ? a.scell_start[gb * 64 + 64] - sbeg : 0;
     if (nsm > 0) {
-        // A warp takes the samples of its own 32 cells, in rank order: pass r holds
-        // the r-th sample of every cell that has one, so the (up to ten) samples of
-        // one iteration lie in distinct cells and, per stencil offset, write
-        // distinct nodes. Each sample's stencil is taken relative to its sorted
-        // cell (t clamped to [0, 1]: the weights agree with the rounded position's),
-        // which keeps its nodes inside the warp's accumulation levels. Three lanes
-        // per sample: lane q gathers row q of dF^, forms row block q of G = K dF^
-        // from D_q and its two off-diagonal blocks, and adds row q of G gradN.
-        __shared__ int stab[NT_CELL / 32][32];
-        const int lane = threadIdx.x & 31;
+        constexpr int SCAP = (KRP * 256) / SREC;   // samples per staged chunk
+        __shared__ int cell_of[SCAP];               // sorted cell of each staged record
+        R* sbuf = sp;
+        uint32_t phase = (uint32_t)nchunk;         // bulk copies completed on `bar` so far
+        __syncwarp();
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(min(nsm, SCAP) * SREC * sizeof(R));
+            mbar_expect_tx(&bar, bytes);
+            bulk_g2s(sbuf, a.sKa + (long long)sbeg * SREC, bytes, &bar);
+        }
         const int si = lane / 3, q = lane - 3 * si;
         const int qa = q == 0 ? 1 : 0, qb = q == 2 ? 1 : 2;                 // the other two row blocks
         const int offA = q == 2 ? 27 : 18, offB = q == 0 ? 27 : 36;        // their 3x3 blocks
         const bool trA = q != 0, trB = q == 2;                              // below the diagonal: transposed
-        const int scs = a.scell_start[gb * 64 + cell] - sbeg, sce = a.scell_start[gb * 64 + cell + 1] - sbeg;
+        const int c2 = 2 * lane;
+        const int scsA = a.scell_start[gb * 64 + c2] - sbeg, scsB = a.scell_start[gb * 64 + c2 + 1] - sbeg;
+        const int sceB = a.scell_start[gb * 64 + c2 + 2] - sbeg;
         for (int c0 = 0; c0 < nsm; c0 += SCAP) {
-            const int c1 = min(nsm, c0 + SCAP);
-            const bool ok = mbar_wait_bounded(&bar, phase & 1u, 1LL << 26);
-            if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
+            const int c1 = min(nsm, c0 + SCAP), nc = c1 - c0;
+            // the owners of the two cells list their records of this chunk
+            for (int j = max(scsA, c0); j < min(scsB, c1); ++j) cell_of[j - c0] = c2;
+            for (int j = max(scsB, c0); j < min(sceB, c1); ++j) cell_of[j - c0] = c2 + 1;
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&bar, phase & 1u, 1LL << 26))) {
+                if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
                 mbar_wait_bounded(&bar, phase & 1u, 1LL << 20);
                 return;
             }
             ++phase;
-            const int cs = max(scs, c0), cnt = max(0, min(sce, c1) - cs);
-            const int maxcnt = __reduce_max_sync(0xffffffffu, cnt);
-            for (int r = 0; r < maxcnt; ++r) {
-                const unsigned mask = __ballot_sync(0xffffffffu, cnt > r);
-                const int n = __popc(mask);
-                if (cnt > r) stab[wid][__popc(mask & ((1u << lane) - 1u))] = lane;
-                __syncwarp();
-                for (int base = 0; base < n; base += 10) {
-                    const int k = base + si;
-                    const bool act = lane < 30 && k < n;
-                    const int cl = act ? stab[wid][k] : 0;
-                    const int jr = __shfl_sync(0xffffffffu, cs, cl) + r - c0;   // record in the chunk
-                    const int sc = wid * 32 + cl;
-                    const int sx = sc & 3, sy = (sc >> 2) & 3, sz = sc >> 4;
-                    const R* rec = sbuf + (act ? jr : 0) * SREC;
-                    R wgt[3][3], dw[3][3];
-                    {
-                        const R tt[3] = {fmin(fmax(rec[45] - R(sx), R(0)), R(1)), fmin(fmax(rec[46] - R(sy), R(0)), R(1)),
-                                         fmin(fmax(rec[47] - R(sz), R(0)), R(1))};
+            __syncwarp();
+            for (int base = 0; base < nc; base += 10) {
+                const int k = base + si;
+                const int kend = min(nc, base + 10);
+                const bool act = lane < 30 && k < kend;
+                const int sc = act ? cell_of[k] : -1;   // the sample's cell
+                const int scc = sc < 0 ? 0 : sc;
+                const int sx = scc & 3, sy = (scc >> 2) & 3, sz = scc >> 4;
+                const R* rec = sbuf + (act ? k : 0) * SREC;
+                R wgt[3][3], dw[3][3];
+                {
+                    const R tt[3] = {fmin(fmax(rec[45] - R(sx), R(0)), R(1)), fmin(fmax(rec[46] - R(sy), R(0)), R(1)),
+                                     fmin(fmax(rec[47] - R(sz), R(0)), R(1))};
 #pragma unroll
-                        for (int ax = 0; ax < 3; ++ax) {
-                            bspline<R>(tt[ax] + R(0.5), wgt[ax], dw[ax]);
+                    for (int ax = 0; ax < 3; ++ax) {
+                        bspline<R>(tt[ax] + R(0.5), wgt[ax], dw[ax]);
 #pragma unroll
-                            for (int kk = 0; kk < 3; ++kk) dw[ax][kk] *= inv_dx;
-                        }
+                        for (int kk = 0; kk < 3; ++kk) dw[ax][kk] *= inv_dx;
                     }
-                    const int lc[3] = {sx, sy, sz};
-                    R g[3] = {R(0), R(0), R(0)};
-                    if (act) gather_grad_row<R>(ph[q], lc, wgt, dw, g);
-                    const int l0 = 3 * si < 30 ? 3 * si : 0;
-                    R gA[3], gB[3];
+                }
+                const int lc[3] = {sx, sy, sz};
+                R g[3] = {R(0), R(0), R(0)};
+                if (act) gather_grad_row<R>(ph[q], lc, wgt, dw, g);
+                const int l0 = 3 * si < 30 ? 3 * si : 0;
+                R gA[3], gB[3];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    gA[e] = __shfl_sync(0xffffffffu, g[e], l0 + qa);
+                    gB[e] = __shfl_sync(0xffffffffu, g[e], l0 + qb);
+                }
+                R N[3][3][3];
+                if (act) {
+                    const R* Dq = rec + 6 * q;
+                    const R DM[3][3] = {{Dq[0], Dq[1], Dq[2]}, {Dq[1], Dq[3], Dq[4]}, {Dq[2], Dq[4], Dq[5]}};
+                    R bA[9], bB[9];
+#pragma unroll
+                    for (int mm = 0; mm < 9; ++mm) {
+                        bA[mm] = rec[offA + mm];
+                        bB[mm] = rec[offB + mm];
+                    }
+                    R m3[3];
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        gA[e] = __shfl_sync(0xffffffffu, g[e], l0 + qa);
-                        gB[e] = __shfl_sync(0xffffffffu, g[e], l0 + qb);
+                        R acc = R(0);
+#pragma unroll
+                        for (int f = 0; f < 3; ++f) {
+                            const R ka = trA ? bA[3 * f + e] : bA[3 * e + f];
+                            const R kb = trB ? bB[3 * f + e] : bB[3 * e + f];
+                            acc += DM[e][f] * g[f] + ka * gA[f] + kb * gB[f];
+                        }
+                        m3[e] = acc;
                     }
-                    R N[3][3][3];
-                    if (act) {
-                        const R* Dq = rec + 6 * q;
-                        const R DM[3][3] = {{Dq[0], Dq[1], Dq[2]}, {Dq[1], Dq[3], Dq[4]}, {Dq[2], Dq[4], Dq[5]}};
-                        R bA[9], bB[9];
+                    pap.add(m3[0] * g[0] + m3[1] * g[1] + m3[2] * g[2]);
 #pragma unroll
-                        for (int m = 0; m < 9; ++m) {
-                            bA[m] = rec[offA + m];
-                            bB[m] = rec[offB + m];
+                    for (int aa = 0; aa < 3; ++aa) {
+                        const R A0 = m3[0] * dw[0][aa], A1 = m3[1] * wgt[0][aa], A2 = m3[2] * wgt[0][aa];
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) {
+                            const R B0 = A0 * wgt[1][bb] + A1 * dw[1][bb], B1 = A2 * wgt[1][bb];
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc) N[aa][bb][cc] = B0 * wgt[2][cc] + B1 * dw[2][cc];
                         }
-                        R m3[3];
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) {
-                            R acc = R(0);
-#pragma unroll
-                            for (int f = 0; f < 3; ++f) {
-                                const R ka = trA ? bA[3 * f + e] : bA[3 * e + f];
-                                const R kb = trB ? bB[3 * f + e] : bB[3 * e + f];
-                                acc += DM[e][f] * g[f] + ka * gA[f] + kb * gB[f];
-                            }
-                            m3[e] = acc;
-                        }
-                        pap.add(m3[0] * g[0] + m3[1] * g[1] + m3[2] * g[2]);
-#pragma unroll
-                        for (int aa = 0; aa < 3; ++aa) {
-                            const R A0 = m3[0] * dw[0][aa], A1 = m3[1] * wgt[0][aa], A2 = m3[2] * wgt[0][aa];
-#pragma unroll
-                            for (int bb = 0; bb < 3; ++bb) {
-                                const R B0 = A0 * wgt[1][bb] + A1 * dw[1][bb], B1 = A2 * wgt[1][bb];
-#pragma unroll
-                                for (int cc = 0; cc < 3; ++cc) N[aa][bb][cc] = B0 * wgt[2][cc] + B1 * dw[2][cc];
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int m = 0; m < 27; ++m) (&N[0][0][0])[m] = R(0);
                     }
-                    // component q's accumulation levels of this warp
-                    rmw_phases<R>(ua[q], N, sx, sy, sz + 2 * wid, act);
+                } else {
+#pragma unroll
+                    for (int mm = 0; mm < 27; ++mm) (&N[0][0][0])[mm] = R(0);
                 }
-                __syncwarp();   // stab is rewritten by the next pass
+                // segmented suffix sum over the groups of one cell (a run of at
+                // most ten in a pass: steps 1, 2, 4, 8 while some run is longer)
+                for (int d = 1; d < 16; d *= 2) {
+                    const bool more = act && k + d < kend && cell_of[k + d] == sc;
+                    if (!__any_sync(0xffffffffu, more)) break;
+                    const int src = lane + 3 * d < 32 ? lane + 3 * d : lane;
+#pragma unroll
+                    for (int mm = 0; mm < 27; ++mm) {
+                        const R t = __shfl_sync(0xffffffffu, (&N[0][0][0])[mm], src);
+                        if (more) (&N[0][0][0])[mm] += t;
+                    }
+                }
+                const bool head = act && (k == base || cell_of[k - 1] != sc);
+                // component q's accumulation levels of the sample's cell
+                rmw_phases<R>(ua[q], N, sx, sy, sz + 2 * (sz >> 1), head);
             }
-            __syncthreads();   // both warps are done with this chunk
-            if (c1 < nsm && threadIdx.x == 0) {
+            __syncwarp();   // the warp is done with this chunk and its cell list
+            if (c1 < nsm && lane == 0) {
                 const uint32_t bytes = (uint32_t)(min(nsm - c1, SCAP) * SREC * sizeof(R));
                 mbar_expect_tx(&bar, bytes);
                 bulk_g2s(sbuf, a.sKa + (long long)(sbeg + c1) * SREC, bytes, &bar);
@@ -1253,9 +1558,9 @@ __global__ void __launch_bounds__(NT_CELL, sizeof(R) == 4 ? 12 : 1) k_apply_cell
     }
     if (a.pap) {
         const double v = pap.warp_total();
-        if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&a.scal[bc.w].pAp, v);
+        if (lane == 0 && v != 0.0) atomicAdd(&a.scal[bc.w].pAp, v);
     }
-    __syncthreads();
+    __syncwarp();
     flush_halo_rows_u<R>(a.nbr, slot, ua, a.u);
 }
 
@@ -1424,7 +1729,7 @@ __device__ __forceinline__ void scatter_sep_u(R (*ua)[UN], const int* lc, const 
 // samples. One CTA per block of the compact list, one thread per cell, two warps:
 // a thread's general particles share its cell's 27 nodes, so their node values
 // add up in registers (the stencil is taken relative to the cell, t clamped to
-// [0, 1], as in k_apply_cell), and each warp writes them once per cell into its
+// [0, 1], as in k_apply_pair), and each warp writes them once per cell into its
 // own accumulation levels in conflict-free phases. EXACT_SOLID: solids take the
 // exact dP (exact mode with solid buffers), else their projected 9x9 map.
 template <typename R, bool EXACT_SOLID>
@@ -1648,7 +1953,7 @@ __global__ void __launch_bounds__(32) k_eval_surf(EvalArgs<RS> a) {
 
 // ======================================================================
 // float64 objective / gradient and line search of non-viscous liquid particles,
-// thread per cell, with the per-cell polynomial form of k_apply_cell:
+// thread per cell, with the per-cell polynomial form of the operator:
 // tr L(t) = (1/dx) sum C_ijk t^ijk from the iterate's stencil values, and the
 // gradient dt lambda (J - 1) J^n V0 gradN_i scattered through 26 moments.
 // ======================================================================
@@ -1783,7 +2088,8 @@ __global__ void __launch_bounds__(NT_CELL) k_curv_cell(ApplyArgs<R> a) {
     const int cell = threadIdx.x;
     const int lx = cell & 3, ly = (cell >> 2) & 3, lz = cell >> 4;
     const int n = a.cell_start[gb * 64 + cell + 1] - a.cell_start[gb * 64 + cell];
-    const R4<R>* recs = a.opk + (long long)a.wroff[w] * 64 + cell;
+    // the cell's values in the pair-interleaved rows (k_pack_volume)
+    const R* recs = reinterpret_cast<const R*>(a.opk + (long long)a.wroff[w] * 64) + 8 * (cell >> 1) + (cell & 1);
     R acc = R(0);
     if (n > 0) {
         R C[3][3][3];
@@ -1791,7 +2097,12 @@ __global__ void __launch_bounds__(NT_CELL) k_curv_cell(ApplyArgs<R> a) {
         for (int q = 0; q < 27; ++q) (&C[0][0][0])[q] = R(0);
         cell_coefficients<R>(ph, lx, ly, lz, C);
         for (int r = 0; r < n; ++r) {
-            R4<R> rec = recs[(long long)r * 64];
+            const R* rr = recs + (long long)r * 256;
+            R4<R> rec;
+            rec.x = rr[0];
+            rec.y = rr[2];
+            rec.z = rr[4];
+            rec.w = rr[6];
             if (rec.w < R(0)) continue;
             R tx = fmin(fmax(rec.x - R(lx), R(0)), R(1));
             R ty = fmin(fmax(rec.y - R(ly), R(0)), R(1));
@@ -2999,6 +3310,9 @@ cudaError_t pack_step_t(mpm_ctx* c) {
     if (c->np > 0 && c->NW > 0) {
         cudaError_t e = size_records<R>(c);
         if (e != cudaSuccess) return e;
+        // slots past a cell's last particle stay zero (kappa 0): the operator
+        // reads whole rows
+        cudaMemsetAsync(d.opk, 0, (size_t)c->hcounts[4] * 64 * sizeof(R4<R>), st);
     }
     if (c->np > 0) {
         RPtr3<R> pu;
@@ -3153,7 +3467,7 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
         auto enqueue_chunk = [&]() -> cudaError_t {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
-                if (c->NW > 0) MPM_LAUNCH k_apply_cell<R><<<c->NW, NT_CELL, 0, st>>>(ap);
+                if (c->NW > 0) MPM_LAUNCH k_apply_pair<R><<<c->NW, 32, 0, st>>>(ap);
                 const int ng = ap.samples_in_cell ? c->n_gen_g : c->n_gen;
                 if (ng > 0) {
                     if (ap.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<R, false><<<ng, NT_CELL, 0, st>>>(ap);
@@ -3402,7 +3716,7 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
     if (c->NW == 0) return cudaSuccess;
     if (c->rsize == 4) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
-        MPM_LAUNCH k_apply_cell<float><<<c->NW, NT_CELL, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_pair<float><<<c->NW, 32, 0, c->st>>>(a);
         const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
         if (ng > 0) {
             if (a.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<float, false><<<ng, NT_CELL, 0, c->st>>>(a);
@@ -3410,7 +3724,7 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
         }
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
-        MPM_LAUNCH k_apply_cell<double><<<c->NW, NT_CELL, 0, c->st>>>(a);
+        MPM_LAUNCH k_apply_pair<double><<<c->NW, 32, 0, c->st>>>(a);
         const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
         if (ng > 0) {
             if (a.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<double, false><<<ng, NT_CELL, 0, c->st>>>(a);
