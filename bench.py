@@ -535,6 +535,7 @@ def main():
         "surface_generation": res.get("surface_generation"),
         "cg_launch": {"ctas_per_sm": prof["cg_ctas_per_sm"], "iters_per_check": prof["cg_chunk"],
                       "cuda_graphs": bool(prof["cg_graphs"]), "graph_error": prof["cg_graph_error"]},
+        "operator_tile": {"record_rows_per_chunk": prof["op_rows_per_chunk"]},
         "newton_iters": [[s["newton_iters"] for s in st] for st in res["stats"]] if len(scl) > 1
         else [st[0]["newton_iters"] for st in res["stats"]],
         "cg_iters": [st[0]["cg_iters"] for st in res["stats"]] if len(scl) == 1

@@ -298,6 +298,11 @@ typedef struct {
     int32_t cg_chunk;
     int32_t cg_graphs;            /* 1: CG chunks run as CUDA graphs */
     int32_t cg_graph_error;       /* cudaError_t of a refused capture, else 0 */
+    /* Hessian operator tile: record rows staged per bulk copy (2, 4 or 8), timed
+     * once per context on its first momentum solve; 0 before that solve. The
+     * environment variable MPM_OP_ROWS=2|4|8, read by mpm_create, fixes it. */
+    int32_t op_rows_per_chunk;
+    int32_t reserved_;
 } mpm_profile;
 
 /* enable != 0 resets the counters and starts accumulating; 0 stops. */

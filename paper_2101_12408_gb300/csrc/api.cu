@@ -2,6 +2,7 @@
 // the four phases of the time step.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -329,6 +330,12 @@ mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t pr
     }
     c->block_cap = bcap;
     c->has_solids = solids;
+    // MPM_OP_ROWS=2|4|8 fixes the operator's record rows per bulk copy instead of
+    // letting the first momentum solve time them (tests use it to cover each tile)
+    if (const char* ev = std::getenv("MPM_OP_ROWS")) {
+        const int r = std::atoi(ev);
+        if (r == 2 || r == 4 || r == 8) c->op_rows = r;
+    }
     Dev& d = c->d;
     long long P = c->Pcap, Sn = c->Scap, NBc = c->total_blocks, NN = bcap * 64;
     long long PS = solids ? P : 1;   // solid-only buffers
@@ -866,6 +873,8 @@ mpm_status mpm_get_profile(mpm_ctx* c, mpm_profile* out) {
     out->cg_chunk = c->cg_chunk;
     out->cg_graphs = c->use_graphs ? 1 : 0;
     out->cg_graph_error = c->graph_error;
+    out->op_rows_per_chunk = c->op_rows;
+    out->reserved_ = 0;
     return MPM_OK;
 }
 

@@ -119,6 +119,7 @@ struct mpm_ctx {
     int cg_ctas_per_sm = 0;         // 0: as many as fit
     int cg_chunk = 8;               // CG iterations per host check
     int tune_next = 0, tune_best = -1;
+    int op_rows = 0;                // operator record rows per bulk copy (0: not tuned yet, 4 used)
     double tune_best_ms = 0.0;
     cudaEvent_t tune_ev[2] = {};
     // surface generation: triangle records (grown on demand), per-scene counts

@@ -1285,9 +1285,9 @@ __device__ __forceinline__ void pair_scatter(const typename VPair<R>::T (&M)[3][
     pair_rmw<R>(ua[2], x0, ly, zb, lo, hi);
 }
 
-constexpr int KRP = 4;   // record rows staged per chunk by the pair kernel
-
-template <typename R>
+// KRP: record rows staged per bulk copy (2, 4 or 8, chosen by the autotuner in
+// cg_solve_t); the sample records share the staging buffer
+template <typename R, int KRP>
 __global__ void __launch_bounds__(32, sizeof(R) == 4 ? 16 : 8) k_apply_pair(ApplyArgs<R> a) {
     using V = typename VPair<R>::T;
     using P = VPair<R>;
@@ -1564,6 +1564,14 @@ __global__ void __launch_bounds__(32, sizeof(R) == 4 ? 16 : 8) k_apply_pair(Appl
     flush_halo_rows_u<R>(a.nbr, slot, ua, a.u);
 }
 
+
+// the liquid and sample operator with the context's record-row chunk
+template <typename R>
+void launch_apply_pair(mpm_ctx* c, const ApplyArgs<R>& a, cudaStream_t st, int rows_per_chunk) {
+    if (rows_per_chunk == 2) MPM_LAUNCH k_apply_pair<R, 2><<<c->NW, 32, 0, st>>>(a);
+    else if (rows_per_chunk == 8) MPM_LAUNCH k_apply_pair<R, 8><<<c->NW, 32, 0, st>>>(a);
+    else MPM_LAUNCH k_apply_pair<R, 4><<<c->NW, 32, 0, st>>>(a);
+}
 
 // Per-iterate projected Hessian of each solid particle (the reading of the
 // paper's "definiteness fix" for solids): the 9x9 Hessian of psi(F) from the
@@ -3463,11 +3471,38 @@ cudaError_t cg_solve_t(mpm_ctx* c, int NC_is_heat, int set_bnorm_in_init) {
         auto ap = make_apply_args<R>(c, d.cp, d.cu, MPM_HESS_PROJECTED, 1);
         ap.pap = 1;   // the operator kernels sum p . (H - M) p for the iteration
         MPM_LAUNCH k_cg_init<R, 3><<<nblk(nb, CG_SLOTS), CG_NT, 0, st>>>(a, nb, set_bnorm_in_init, 1);
+        // Autotuner, operator tile: the first momentum solve of a context times
+        // the liquid and sample operator with 2, 4 and 8 record rows per bulk
+        // copy (three applications each on the first CG direction, into the
+        // product vector, which is cleared afterwards) and keeps the fastest.
+        if (c->op_rows == 0 && c->NW > 0) {
+            auto at = ap;
+            at.pap = 0;
+            at.check_done = 0;
+            const int cand[3] = {2, 4, 8};
+            float best = 0.f;
+            int pick = 4;
+            for (int k = 0; k < 3; ++k) {
+                launch_apply_pair<R>(c, at, st, cand[k]);   // warm-up
+                cudaEventRecord(c->tune_ev[0], st);
+                for (int rep = 0; rep < 3; ++rep) launch_apply_pair<R>(c, at, st, cand[k]);
+                cudaEventRecord(c->tune_ev[1], st);
+                float ms = 0.f;
+                if (cudaEventSynchronize(c->tune_ev[1]) == cudaSuccess &&
+                    cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]) == cudaSuccess && (k == 0 || ms < best)) {
+                    best = ms;
+                    pick = cand[k];
+                }
+            }
+            c->op_rows = pick;
+            e0 = cudaMemsetAsync(d.cu, 0, (size_t)c->rsize * (size_t)nb * 192, st);
+            if (e0 != cudaSuccess) return e0;
+        }
         // one chunk of CG iterations: operator apply, then the cooperative vector kernel
         auto enqueue_chunk = [&]() -> cudaError_t {
             for (int k = 0; k < chunk; ++k) {
                 prof_mark_apply(c, true);
-                if (c->NW > 0) MPM_LAUNCH k_apply_pair<R><<<c->NW, 32, 0, st>>>(ap);
+                if (c->NW > 0) launch_apply_pair<R>(c, ap, st, c->op_rows);
                 const int ng = ap.samples_in_cell ? c->n_gen_g : c->n_gen;
                 if (ng > 0) {
                     if (ap.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<R, false><<<ng, NT_CELL, 0, st>>>(ap);
@@ -3716,7 +3751,7 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
     if (c->NW == 0) return cudaSuccess;
     if (c->rsize == 4) {
         auto a = make_apply_args<float>(c, p, u, mode, 0);
-        MPM_LAUNCH k_apply_pair<float><<<c->NW, 32, 0, c->st>>>(a);
+        launch_apply_pair<float>(c, a, c->st, c->op_rows);
         const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
         if (ng > 0) {
             if (a.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<float, false><<<ng, NT_CELL, 0, c->st>>>(a);
@@ -3724,7 +3759,7 @@ cudaError_t launch_apply(mpm_ctx* c, const void* p, void* u, int mode) {
         }
     } else {
         auto a = make_apply_args<double>(c, p, u, mode, 0);
-        MPM_LAUNCH k_apply_pair<double><<<c->NW, 32, 0, c->st>>>(a);
+        launch_apply_pair<double>(c, a, c->st, c->op_rows);
         const int ng = a.samples_in_cell ? c->n_gen_g : c->n_gen;
         if (ng > 0) {
             if (a.use_pK || !c->has_solids) MPM_LAUNCH k_apply_general<double, false><<<ng, NT_CELL, 0, c->st>>>(a);

@@ -76,7 +76,8 @@ class Profile(ctypes.Structure):
                 ("heat_apply_launches", ctypes.c_int64), ("heat_apply_ms", ctypes.c_double),
                 ("phase_ms", ctypes.c_double * 5), ("newton_iters", ctypes.c_int64), ("cg_iters", ctypes.c_int64),
                 ("heat_iters", ctypes.c_int64), ("cg_ctas_per_sm", ctypes.c_int32), ("cg_chunk", ctypes.c_int32),
-                ("cg_graphs", ctypes.c_int32), ("cg_graph_error", ctypes.c_int32)]
+                ("cg_graphs", ctypes.c_int32), ("cg_graph_error", ctypes.c_int32),
+                ("op_rows_per_chunk", ctypes.c_int32), ("reserved_", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(kernel_launches=self.kernel_launches, apply_launches=self.apply_launches, apply_ms=self.apply_ms,
@@ -84,7 +85,7 @@ class Profile(ctypes.Structure):
                     phase_ms=dict(zip(("resample", "p2g", "heat", "newton", "g2p"), list(self.phase_ms))),
                     newton_iters=self.newton_iters, cg_iters=self.cg_iters, heat_iters=self.heat_iters,
                     cg_ctas_per_sm=self.cg_ctas_per_sm, cg_chunk=self.cg_chunk, cg_graphs=self.cg_graphs,
-                    cg_graph_error=self.cg_graph_error)
+                    cg_graph_error=self.cg_graph_error, op_rows_per_chunk=self.op_rows_per_chunk)
 
 
 _vp = ctypes.c_void_p

@@ -457,3 +457,36 @@ def test_batched_scenes_match_the_oracle_scene_by_scene(prec):
         p = ctx.get_particles(k)
         assert relerr(p["v"], sim.sc.v) < tol, (k, sc.name, stats[k])
         assert relerr(p["x"], sim.sc.x) < 1e-9
+
+
+@pytest.mark.parametrize("rows", [2, 4, 8])
+@pytest.mark.parametrize("name", ["crowded", "dense_samples"])
+def test_every_operator_tile_matches_oracle(name, rows, monkeypatch):
+    """Each record-row chunk the autotuner can pick (fixed through MPM_OP_ROWS)
+    gives the oracle's operator, on scenes whose records and samples take
+    several staged chunks."""
+    monkeypatch.setenv("MPM_OP_ROWS", str(rows))
+    sc = OP_SCENES[name]()
+    ctx, sim = _setup(sc, mpm.PREC_FP32_FP64RED)
+    st, v = _iterate(sim)
+    ctx.set_velocity(0, v)
+    act = st.active[:, None]
+    dv = np.random.default_rng(4).standard_normal(v.shape) * act
+
+    def proj(u):
+        return oracle.apply_projector(sim.P, u) * act
+
+    ref = proj(st.hessvec(v, proj(dv), HESS_PROJECTED))
+    out = ctx.apply_hessian(0, dv, mode=HESS_PROJECTED)
+    assert relerr(out, ref) < TOL[mpm.PREC_FP32_FP64RED]
+    stiff_ref = ref - proj(st.m[:, None] * proj(dv))
+    assert relerr(out - proj(st.m[:, None] * proj(dv)), stiff_ref) < 1e-4
+
+
+def test_autotuner_picks_an_operator_tile():
+    sc = scenes.config(0)
+    ctx = mpm.Context(sc, precision=mpm.PREC_FP32_FP64RED)
+    ctx.load_scene(0)
+    ctx.profile_enable(True)
+    ctx.step()
+    assert ctx.profile()["op_rows_per_chunk"] in (2, 4, 8)
