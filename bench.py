@@ -81,6 +81,10 @@ def make_workload(name, drops=40):
         return scenes.incline(n_drops=drops)
     if name == "film":
         return scenes.film()
+    if name == "film27":
+        # the film at the configuration's particle count: 27 particles per cell
+        # (a 3x3x3 sub-cell lattice) in the same 6-cell layer, 2.49M particles
+        return scenes.film(ppc_axis=3)
     if name == "droplet":
         return scenes.droplet()
     if name == "wax":
@@ -466,7 +470,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="incline", choices=["incline", "film", "droplet", "wax", "batch"])
+    ap.add_argument("--workload", default="incline", choices=["incline", "film", "film27", "droplet", "wax", "batch"])
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--fp64-steps", type=int, default=-1,

@@ -316,6 +316,12 @@ def _small_film():
     return scenes.film(nx=24, ny=24, nz=12, height_cells=4, seed=41)
 
 
+def _small_film27():
+    # the film at 27 particles per cell (its configuration's particle count):
+    # viscous, so every particle takes the general operator path
+    return scenes.film(nx=16, ny=16, nz=12, height_cells=4, seed=47, ppc_axis=3)
+
+
 def _small_wax():
     sc = scenes.wax(nx=24, ny=24, nz=20, cube_cells=10, seed=42, b_heat=5000.0)
     return sc
@@ -363,7 +369,7 @@ def _sticky_ball():
     return sc
 
 
-WORKLOADS = {"film": _small_film, "wax": _small_wax, "incline": _small_incline,
+WORKLOADS = {"film": _small_film, "film27": _small_film27, "wax": _small_wax, "incline": _small_incline,
              "incline_friction": _small_incline_friction, "massless": _massless_droplet,
              "bowl_friction": _bowl_friction, "sticky_ball": _sticky_ball}
 
