@@ -1296,16 +1296,23 @@ __global__ void __launch_bounds__(32, sizeof(R) == 4 ? 16 : 8) k_apply_pair(Appl
     __shared__ __align__(16) R sp[KRP * 256];
     __shared__ __align__(8) uint64_t bar;
     const int w = blockIdx.x;
+    const int lane = threadIdx.x;
+    // The block's indices and counts are independent loads, issued together; the
+    // scene's done flag is read here but tested only once the first record copy
+    // and the halo loads are under way, so the two chains of dependent loads
+    // overlap.
     const int slot = a.work[w];
     const long long gb = a.work_gb[w];
+    const int wrows = a.wrows[w], wroff = a.wroff[w];
     const int4 bc = a.coord[slot];
-    const SceneDev& S = a.sc[bc.w];
-    if (a.check_done && a.scal[bc.w].cg_done) return;
-    const int lane = threadIdx.x;
-    // liquid rows of the block: none when every particle takes the general path
     const int npart = a.cell_start[gb * 64 + 64] - a.cell_start[gb * 64];
-    const int rows = (npart > a.slot_gen[slot]) ? a.wrows[w] : 0;
-    const R* recs = reinterpret_cast<const R*>(a.opk) + (long long)a.wroff[w] * 256;
+    const int ngen = a.slot_gen[slot];
+    const int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
+    const int done = a.check_done ? a.scal[bc.w].cg_done : 0;
+    const SceneDev& S = a.sc[bc.w];
+    // liquid rows of the block: none when every particle takes the general path
+    const int rows = (npart > ngen) ? wrows : 0;
+    const R* recs = reinterpret_cast<const R*>(a.opk) + (long long)wroff * 256;
     const int nchunk = (rows + KRP - 1) / KRP;
     if (lane == 0) mbar_init(&bar, 1);
     for (int i = lane; i < (int)(3 * UN * sizeof(R) / 16); i += 32)
@@ -1343,6 +1350,10 @@ __global__ void __launch_bounds__(32, sizeof(R) == 4 ? 16 : 8) k_apply_pair(Appl
         }
     }
     __syncwarp();
+    if (done) {   // the scene's CG has converged: let the first copy land, then leave
+        if (nchunk > 0) mbar_wait_bounded(&bar, 0u, 1LL << 26);
+        return;
+    }
     const R inv_dx = (R)S.inv_dx;
     const int m = lane & 1, ly = (lane >> 1) & 3, lz = lane >> 3;
     const int zb = lz + 2 * (lz >> 1);   // the lane's accumulation levels (region lz >> 1)
@@ -1435,7 +1446,7 @@ __global__ void __launch_bounds__(32, sizeof(R) == 4 ? 16 : 8) k_apply_pair(Appl
     // the writers of a pass lie in distinct cells. Each adds into its cell's
     // accumulation levels (region sz >> 1, where the cells span two z levels):
     // per stencil offset the writers of a pass write distinct nodes.
-    const int sbeg = a.scell_start[gb * 64], nsm = a.samples_in_cell ? a.scell_start[gb * 64 + 64] - sbeg : 0;
+    const int nsm = a.samples_in_cell ? send - sbeg : 0;
     if (nsm > 0) {
         constexpr int SCAP = (KRP * 256) / SREC;   // samples per staged chunk
         __shared__ int cell_of[SCAP];               // sorted cell of each staged record
