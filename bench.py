@@ -258,7 +258,21 @@ def oracle_baseline(sc, steps, warmup=0):
                       f"window {sample_where(sc)} ({min(cn)}-{max(cn)} particles each, {steps} timed steps after "
                       f"{warmup}); particle rates summed and scaled to the {total_particles(sc)}-particle workload",
             "host_cpu_count": cores,
-            "one_core": {"value": v1, "cores": 1, "particles": c1[0], "sec_per_step": s1[0]}}
+            "one_core": {"value": v1, "cores": 1, "particles": c1[0], "sec_per_step": s1[0]},
+            "droplet_full": oracle_droplet_full()}
+
+
+def oracle_droplet_full():
+    """The oracle on the whole small droplet (32^3 grid, r = 8 cells, ~17k
+    particles), one step on one core: a complete workload rather than a window."""
+    import oracle
+    sc = scenes.config(0)
+    sim = oracle.OracleSim(sc)
+    t = time.perf_counter()
+    sim.step()
+    sec = time.perf_counter() - t
+    return {"particles": sc.n_particles, "surface_samples": sc.n_surface, "sec_per_step": sec,
+            "steps_per_s": 1.0 / sec, "cores": 1}
 
 
 def job_rate(units, elapsed_ms, device=None):
