@@ -58,10 +58,10 @@ UNIT = "steps/s"
 # full workload, with the SHA-256 of the operator's source files it was
 # measured on. When those files have changed since, the line reports no traffic.
 # Captured on the 20-droplet variant of the inclined-plane workload (three
-# launches, 188.1 MB each against 137.9 MB of algorithmic bytes) and scaled to
+# launches, 188.2 MB each against 137.9 MB of algorithmic bytes) and scaled to
 # the full 8.27M-particle launch by its algorithmic bytes.
-NCU_TRAFFIC = {"bytes_per_apply": 309507782,
-               "source_sha256": "5de6eea476b4f3708f28c8a4f67b186d5c8a67f97c7e47d8797e0c6a2c735c07"}
+NCU_TRAFFIC = {"bytes_per_apply": 309628932,
+               "source_sha256": "28459b22a4f3042dd6cfa7fa386efe5ac33f61748cb85c7e43f5770191309544"}
 OPERATOR_SOURCES = ("paper_2101_12408_gb300/csrc/newton.cu", "paper_2101_12408_gb300/csrc/common.cuh")
 
 

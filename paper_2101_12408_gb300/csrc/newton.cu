@@ -1191,38 +1191,45 @@ __device__ __forceinline__ void pair_rows(const V (&Nx)[3][3][3], V (&lo)[3][3],
         }
 }
 
-// read-add-write of one component's rows into the lane's accumulation levels.
-// Phases: for each y offset b, the z offsets {0, 2} then {1}, the lo pairs then
-// the hi pairs; within a phase no two lanes of the warp write one node.
+// read-add-write of the three components' rows into the lane's accumulation
+// levels. Phases: for each y offset b, the z offsets {0, 2} then {1}, the lo pairs
+// then the hi pairs; within a phase no two lanes of the warp write one node. The
+// components go to separate arrays, so one phase carries all three (six
+// independent read-add-writes per lane where z offsets 0 and 2 go together).
 template <typename R>
-__device__ __forceinline__ void pair_rmw(R* uq, int x0, int ly, int zb, const typename VPair<R>::T (&lo)[3][3],
-                                         const typename VPair<R>::T (&hi)[3][3]) {
+__device__ __forceinline__ void pair_rmw3(R (*ua)[UN], int x0, int ly, int zb,
+                                          const typename VPair<R>::T (&lo)[3][3][3],
+                                          const typename VPair<R>::T (&hi)[3][3][3]) {
     using V = typename VPair<R>::T;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             __syncwarp();
-            {
-                V* p0 = reinterpret_cast<V*>(uq + pidx(x0 + 2 * half, ly + b, zb));
-                V* p2 = reinterpret_cast<V*>(uq + pidx(x0 + 2 * half, ly + b, zb + 2));
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                V* p0 = reinterpret_cast<V*>(ua[q] + pidx(x0 + 2 * half, ly + b, zb));
+                V* p2 = reinterpret_cast<V*>(ua[q] + pidx(x0 + 2 * half, ly + b, zb + 2));
                 const V v0 = *p0, v2 = *p2;
-                *p0 = vadd(v0, half ? hi[b][0] : lo[b][0]);
-                *p2 = vadd(v2, half ? hi[b][2] : lo[b][2]);
+                *p0 = vadd(v0, half ? hi[q][b][0] : lo[q][b][0]);
+                *p2 = vadd(v2, half ? hi[q][b][2] : lo[q][b][2]);
             }
         }
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             __syncwarp();
-            V* p1 = reinterpret_cast<V*>(uq + pidx(x0 + 2 * half, ly + b, zb + 1));
-            *p1 = vadd(*p1, half ? hi[b][1] : lo[b][1]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                V* p1 = reinterpret_cast<V*>(ua[q] + pidx(x0 + 2 * half, ly + b, zb + 1));
+                *p1 = vadd(*p1, half ? hi[q][b][1] : lo[q][b][1]);
+            }
         }
     }
     __syncwarp();
 }
 
 // node values (without the 1/dx factor) of the pair's moments, component by
-// component, added to the lane's accumulation levels (every lane calls it)
+// component, then added to the lane's accumulation levels (every lane calls it)
 template <typename R>
 __device__ __forceinline__ void pair_scatter(const typename VPair<R>::T (&M)[3][3][3], R (*ua)[UN], int m, int ly,
                                              int zb) {
@@ -1231,7 +1238,7 @@ __device__ __forceinline__ void pair_scatter(const typename VPair<R>::T (&M)[3][
     const V h = P::make(R(0.5), R(0.5)), m2 = P::make(R(-2), R(-2));
     const int x0 = 2 * m;
     V N[3][3][3];
-    V lo[3][3], hi[3][3];
+    V lo[3][3][3], hi[3][3][3];   // per component
     {   // x: W along z, W along y, D along x
         V T1[2][3][3], T2[2][3][3];
 #pragma unroll
@@ -1247,8 +1254,7 @@ __device__ __forceinline__ void pair_scatter(const typename VPair<R>::T (&M)[3][
 #pragma unroll
             for (int c = 0; c < 3; ++c) pdN<V>(T2[0][b][c], T2[1][b][c], N[0][b][c], N[1][b][c], N[2][b][c], m2);
     }
-    pair_rows<V, P>(N, lo, hi);
-    pair_rmw<R>(ua[0], x0, ly, zb, lo, hi);
+    pair_rows<V, P>(N, lo[0], hi[0]);
     {   // y: W along z, W along x, D along y
         V T1[3][2][3], T2[3][2][3];
 #pragma unroll
@@ -1264,8 +1270,7 @@ __device__ __forceinline__ void pair_scatter(const typename VPair<R>::T (&M)[3][
 #pragma unroll
             for (int c = 0; c < 3; ++c) pdN<V>(T2[a][0][c], T2[a][1][c], N[a][0][c], N[a][1][c], N[a][2][c], m2);
     }
-    pair_rows<V, P>(N, lo, hi);
-    pair_rmw<R>(ua[1], x0, ly, zb, lo, hi);
+    pair_rows<V, P>(N, lo[1], hi[1]);
     {   // z: W along x, W along y, D along z
         V T1[3][3][2], T2[3][3][2];
 #pragma unroll
@@ -1281,8 +1286,8 @@ __device__ __forceinline__ void pair_scatter(const typename VPair<R>::T (&M)[3][
 #pragma unroll
             for (int b = 0; b < 3; ++b) pdN<V>(T2[a][b][0], T2[a][b][1], N[a][b][0], N[a][b][1], N[a][b][2], m2);
     }
-    pair_rows<V, P>(N, lo, hi);
-    pair_rmw<R>(ua[2], x0, ly, zb, lo, hi);
+    pair_rows<V, P>(N, lo[2], hi[2]);
+    pair_rmw3<R>(ua, x0, ly, zb, lo, hi);
 }
 
 // KRP: record rows staged per bulk copy (2, 4 or 8, chosen by the autotuner in
