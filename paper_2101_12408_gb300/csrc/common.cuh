@@ -19,7 +19,8 @@ constexpr int BS = 4;       // block edge in nodes / cells
 constexpr int BN = 64;      // nodes per block
 constexpr int HE = 6;       // halo edge (block + one node each side)
 constexpr int HN = 216;     // halo nodes
-constexpr int MAX_LS = 16;  // line-search trials evaluated in one pass
+constexpr int MAX_LS = 16;  // line-search trials (alpha = 2^-k, k < MAX_LS)
+constexpr int LS_FIRST = 2; // trials the line search's first pass evaluates (alpha = 1, 1/2)
 
 // Per-scene constants.
 struct SceneDev {

@@ -2706,6 +2706,8 @@ struct LSArgs {
     int skip_poly;             // non-viscous liquid particles take the closed form (k_curv_cell)
     int skip_samples;          // surface samples are left to k_ls_surf
     const int* slot_gen;
+    int k0, k1;                // trials k0..k1-1 (alpha = 2^-k) of this pass; a pass with k0 > 0 runs
+                               // only for scenes whose earlier trials all failed (ls_pick < 0)
 };
 
 // R: arithmetic type; RD: type of the Newton direction
@@ -2720,7 +2722,7 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
     int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
     SceneScal& scl = a.scal[bc.w];
-    if (scl.newton_done) return;
+    if (scl.newton_done || (a.k0 > 0 && scl.ls_pick >= 0)) return;
     const bool poly = a.skip_poly && S.mu_l == 0.0;
     const bool no_samples = a.skip_samples || a.scell_start[gb * 64] == a.scell_start[gb * 64 + 64];
     if (poly && a.slot_gen[slot] == 0 && no_samples) return;
@@ -2733,6 +2735,8 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
     }
     __syncthreads();
     const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
+    const int k1 = a.k1 < nls ? a.k1 : nls;
+    const double alpha0 = ldexp(1.0, -a.k0);
     const R dt = (R)S.dt;
     double de[MAX_LS];
 #pragma unroll
@@ -2780,8 +2784,8 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
                 }
             (void)el;
             double cvis = 0.5 * S.dt * S.mu_l * Vn;
-            double alpha = 1.0;
-            for (int k = 0; k < nls; ++k) {
+            double alpha = alpha0;
+            for (int k = a.k0; k < k1; ++k) {
                 R dJ = (R)alpha * dt * trD * (R)Jn;
                 double dE = 0.5 * lam * v0 * (double)dJ * (double)(R(2) * jm1 + dJ);
                 dE += cvis * (2.0 * alpha * (double)ed + alpha * alpha * (double)dd);
@@ -2801,8 +2805,8 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
             solid_lame(S, Tn, mu_h, lam_h);
             const R mu = (R)mu_h, lam = (R)lam_h;
             R psi0 = fcr_psi<R>(Fc, mu, lam);
-            R alpha = 1;
-            for (int k = 0; k < nls; ++k) {
+            R alpha = (R)alpha0;
+            for (int k = a.k0; k < k1; ++k) {
                 R Fa[9];
 #pragma unroll
                 for (int q = 0; q < 9; ++q) A1[q] = dt * (L[q] + alpha * D[q]) + ((q % 4 == 0) ? R(1) : R(0));
@@ -2848,8 +2852,8 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
         }
         R n0 = sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
         double k = a.gamma[j];
-        R alpha = 1;
-        for (int kk = 0; kk < nls; ++kk) {
+        R alpha = (R)alpha0;
+        for (int kk = a.k0; kk < k1; ++kk) {
             R dc[3], cn[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
@@ -2862,7 +2866,7 @@ __global__ void __launch_bounds__(NT) k_linesearch(LSArgs<RD> a) {
             alpha *= R(0.5);
         }
     }
-    for (int k = 0; k < nls; ++k) block_atomic_sum<NT>(de[k], &scl.dphi[k], red);
+    for (int k = a.k0; k < k1; ++k) block_atomic_sum<NT>(de[k], &scl.dphi[k], red);
 }
 
 template <typename RD>
@@ -2875,7 +2879,7 @@ __global__ void __launch_bounds__(32) k_ls_surf(LSArgs<RD> a) {
     const int4 bc = a.coord[slot];
     const SceneDev& S = a.sc[bc.w];
     SceneScal& scl = a.scal[bc.w];
-    if (scl.newton_done) return;
+    if (scl.newton_done || (a.k0 > 0 && scl.ls_pick >= 0)) return;
     const int sbeg = a.scell_start[gb * 64], send = a.scell_start[gb * 64 + 64];
     if (send == sbeg) return;
     load_halo_rows<double>(a.nbr, slot, a.gv, pv, pd);   // pd zeroed, then filled below
@@ -2891,6 +2895,7 @@ __global__ void __launch_bounds__(32) k_ls_surf(LSArgs<RD> a) {
     }
     __syncthreads();
     const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
+    const int k1 = a.k1 < nls ? a.k1 : nls;
     const double dt = S.dt;
     double de[MAX_LS];
 #pragma unroll
@@ -2924,10 +2929,10 @@ __global__ void __launch_bounds__(32) k_ls_surf(LSArgs<RD> a) {
         // |c0 + alpha c1 + alpha^2 c2| - |c0| without cancellation
         const double n0 = sqrt(c0[0] * c0[0] + c0[1] * c0[1] + c0[2] * c0[2]);
         const double k = a.gamma[j];
-        double alpha = 1.0;
+        double alpha = ldexp(1.0, -a.k0);
 #pragma unroll
         for (int kk = 0; kk < MAX_LS; ++kk) {
-            if (kk < nls) {
+            if (kk >= a.k0 && kk < k1) {
                 double dc[3], cn[3];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
@@ -2938,14 +2943,14 @@ __global__ void __launch_bounds__(32) k_ls_surf(LSArgs<RD> a) {
                 const double num = 2.0 * (c0[0] * dc[0] + c0[1] * dc[1] + c0[2] * dc[2]) + dc[0] * dc[0] +
                                    dc[1] * dc[1] + dc[2] * dc[2];
                 de[kk] += k * num / (n1 + n0);
+                alpha *= 0.5;
             }
-            alpha *= 0.5;
         }
     }
 #pragma unroll
     for (int k = 0; k < MAX_LS; ++k) {
         const double v = warp_sum(de[k]);
-        if (k < nls && threadIdx.x == 0 && v != 0.0) atomicAdd(&scl.dphi[k], v);
+        if (k >= a.k0 && k < k1 && threadIdx.x == 0 && v != 0.0) atomicAdd(&scl.dphi[k], v);
     }
 }
 
@@ -2954,12 +2959,13 @@ __global__ void __launch_bounds__(32) k_ls_surf(LSArgs<RD> a) {
 template <typename R>
 __global__ void k_ls_nodes(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, SceneScal* __restrict__ scal,
                            const double* __restrict__ gm, const double* __restrict__ gvn, const double* __restrict__ gv,
-                           const double* __restrict__ grad, const double* __restrict__ grad_l, const R* __restrict__ d) {
+                           const double* __restrict__ grad, const double* __restrict__ grad_l, const R* __restrict__ d,
+                           int k0, int k1in) {
     int slot = blockIdx.x, l = threadIdx.x;
     int4 bc = coord[slot];
     const SceneDev& S = sc[bc.w];
     SceneScal& c = scal[bc.w];
-    if (c.newton_done) return;
+    if (c.newton_done || (k0 > 0 && c.ls_pick >= 0)) return;
     int t = slot * 64 + l;
     double m = gm[t];
     double dv = 0.0, dd = 0.0, gd = 0.0, sl = 0.0, ld = 0.0;
@@ -2975,31 +2981,44 @@ __global__ void k_ls_nodes(const int4* __restrict__ coord, const SceneDev* __res
         }
     }
     const int nls = S.max_ls < MAX_LS ? S.max_ls : MAX_LS;
-    double alpha = 1.0;
-    for (int k = 0; k < nls; ++k) {
+    const int k1 = k1in < nls ? k1in : nls;
+    double alpha = ldexp(1.0, -k0);
+    for (int k = k0; k < k1; ++k) {
         double e = 0.5 * m * (2.0 * alpha * dv + alpha * alpha * dd) - S.dt * alpha * m * gd + alpha * ld;
         e = warp_sum(e);
         if ((l & 31) == 0 && e != 0.0) atomicAdd(&c.dphi[k], e);
         alpha *= 0.5;
     }
-    sl = warp_sum(sl);
-    if ((l & 31) == 0 && sl != 0.0) atomicAdd(&c.slope, sl);
+    if (k0 == 0) {   // the slope, once per line search
+        sl = warp_sum(sl);
+        if ((l & 31) == 0 && sl != 0.0) atomicAdd(&c.slope, sl);
+    }
 }
 
-__global__ void k_ls_pick(SceneScal* scal, const SceneDev* sc, int nsc) {
+// Armijo test of trials k0..k1-1 (alpha = 2^-k), the first passing one wins. The
+// line search runs in two passes: trials 0 and 1 (alpha = 1, 1/2, which nearly
+// every Newton iteration accepts), then, only for scenes where both failed
+// (ls_pick < 0 after the first pick), the remaining trials; the result is the
+// same as testing all trials in order in one pass.
+__global__ void k_ls_pick(SceneScal* scal, const SceneDev* sc, int nsc, int k0, int k1in) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nsc) return;
     SceneScal& c = scal[s];
-    if (c.newton_done) return;
+    if (c.newton_done || (k0 > 0 && c.ls_pick >= 0)) return;
     const int nls = sc[s].max_ls < MAX_LS ? sc[s].max_ls : MAX_LS;
-    double alpha = 1.0;
+    const int k1 = k1in < nls ? k1in : nls;
+    double alpha = ldexp(1.0, -k0);
     int pick = nls;
-    for (int k = 0; k < nls; ++k) {
+    for (int k = k0; k < k1; ++k) {
         if (c.dphi[k] + 0.5 * alpha * alpha * c.dkd <= 1e-4 * alpha * c.slope) {
             pick = k;
             break;
         }
         alpha *= 0.5;
+    }
+    if (pick == nls && k1 < nls) {   // undecided: the next pass tests the rest
+        c.ls_pick = -1;
+        return;
     }
     c.ls_pick = pick;
     c.cg_total += c.cg_it;
@@ -3729,13 +3748,28 @@ cudaError_t newton_t(mpm_ctx* c) {
             a.skip_poly = 1;
             a.skip_samples = 1;
             a.slot_gen = d.slot_gen;
+            a.k0 = 0;
+            a.k1 = LS_FIRST;
             MPM_LAUNCH k_linesearch<double, R><<<c->NW, NT, 0, st>>>(a);
             if (c->ns > 0) MPM_LAUNCH k_ls_surf<R><<<c->NW, 32, 0, st>>>(a);
             auto cv = make_apply_args<R>(c, d.cx, nullptr, MPM_HESS_PROJECTED, 0);
             MPM_LAUNCH k_curv_cell<R><<<c->NW, NT_CELL, 0, st>>>(cv);
+            MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, d.ggrad_l,
+                                                        (const R*)d.cx, 0, LS_FIRST);
+            MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns, 0, LS_FIRST);
+            // the remaining trials, for scenes whose first two failed
+            a.k0 = LS_FIRST;
+            a.k1 = MAX_LS;
+            MPM_LAUNCH k_linesearch<double, R><<<c->NW, NT, 0, st>>>(a);
+            if (c->ns > 0) MPM_LAUNCH k_ls_surf<R><<<c->NW, 32, 0, st>>>(a);
+            MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, d.ggrad_l,
+                                                        (const R*)d.cx, LS_FIRST, MAX_LS);
+            MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns, LS_FIRST, MAX_LS);
+        } else {
+            MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, d.ggrad_l,
+                                                        (const R*)d.cx, 0, MAX_LS);
+            MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns, 0, MAX_LS);
         }
-        MPM_LAUNCH k_ls_nodes<R><<<nb, 64, 0, st>>>(d.slot_coord, d.sc, d.scal, d.gm, d.gvn, d.gv, d.ggrad, d.ggrad_l, (const R*)d.cx);
-        MPM_LAUNCH k_ls_pick<<<gs, 128, 0, st>>>(d.scal, d.sc, ns);
         MPM_LAUNCH k_newton_update<R><<<nb, 64, 0, st>>>(d.slot_coord, d.scal, (const R*)d.cx, d.gv);
     }
     // final explicit force evaluation: the loop ends right after evaluating the
