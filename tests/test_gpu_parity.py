@@ -409,7 +409,12 @@ def test_workload_step_matches_oracle(name, prec):
     ctx = mpm.Context(sc, precision=prec)
     ctx.load_scene(0)
     sim = oracle.OracleSim(sc)
-    tol = 1e-8 if prec == mpm.PREC_FP64 else 1e-5
+    # float64: both sides stop at 1e-10 relative residual, so they differ by up to
+    # the operator's conditioning times that stop. The small wax is the stiffest
+    # scene (its solid keeps the bulk modulus at every temperature, reading R15):
+    # two solves that sum in different orders differ there by up to 2.6e-8
+    # (measured in two of five runs), so it gets 1e-7
+    tol = (1e-7 if name == "wax" else 1e-8) if prec == mpm.PREC_FP64 else 1e-5
     for step in range(2):
         ctx.resample()
         ctx.p2g()
