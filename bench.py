@@ -61,16 +61,24 @@ UNIT = "steps/s"
 # launches, 188.2 MB each against 137.9 MB of algorithmic bytes) and scaled to
 # the full 8.27M-particle launch by its algorithmic bytes.
 NCU_TRAFFIC = {"bytes_per_apply": 309628932,
-               "source_sha256": "28459b22a4f3042dd6cfa7fa386efe5ac33f61748cb85c7e43f5770191309544"}
+               "source_sha256": "7890972c97652ef596a52a3114b444117caaff1e765b4b86414c6e6662cf9f9a"}
 OPERATOR_SOURCES = ("paper_2101_12408_gb300/csrc/newton.cu", "paper_2101_12408_gb300/csrc/common.cuh")
+# the parts of newton.cu the operator's launch runs: the record packing and the
+# operator section (argument struct, transforms, kernels, launch helper)
+OPERATOR_REGIONS = (("__global__ void k_pack_volume(", "__global__ void k_pack_surface("),
+                    ("// Hessian-vector operator (the hot kernel)", "// Per-iterate projected Hessian of each solid particle"))
 
 
 def operator_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in OPERATOR_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(ROOT, OPERATOR_SOURCES[0])) as fh:
+        text = fh.read()
+    for a, b in OPERATOR_REGIONS:
+        i = text.index(a)
+        h.update(text[i:text.index(b, i)].encode())
+    with open(os.path.join(ROOT, OPERATOR_SOURCES[1]), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()
 
 
