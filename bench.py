@@ -82,7 +82,11 @@ def operator_source_hash():
     return h.hexdigest()
 
 
-def measured_traffic():
+def measured_traffic(workload, drops):
+    """The captured traffic, for the workload it was scaled to (the 40-droplet
+    inclined plane) and the operator source it was captured on; else None."""
+    if workload != "incline" or drops != 40:
+        return None
     if NCU_TRAFFIC["bytes_per_apply"] is None or NCU_TRAFFIC["source_sha256"] != operator_source_hash():
         return None
     return NCU_TRAFFIC["bytes_per_apply"]
@@ -367,7 +371,7 @@ def bench_ours(args, rank, world):
         "stats": stats,
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": measured_traffic(), "peak_source": peak_kind,
+                     "traffic": measured_traffic(args.workload, args.drops), "peak_source": peak_kind,
                      "kernel": "k_apply_pair + k_apply_surf + k_apply_general (Hessian-vector operator)",
                      "bytes_per_launch": abytes, "launch_ms": apply_avg_ms, "launches": prof["apply_launches"]},
         "counts": dict(counts, grid_blocks=cnt["blocks"], work_blocks=cnt["work_blocks"]),
