@@ -502,7 +502,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="incline", choices=["incline", "film", "film27", "droplet", "wax", "batch"])
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=-1,
                     help="timed steps of the all-float64 form (-1: as many as --steps, after as many warm-up steps; "
                          "0: skip)")
