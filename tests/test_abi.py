@@ -75,6 +75,26 @@ def test_struct_layout_matches_the_header_compiled(tmp_path):
                    mpm.GridDesc.sphere.offset, mpm.GridDesc.sphere_mode.offset]
 
 
+def test_profile_layout_matches_the_header_compiled(tmp_path):
+    """The profile record the binding reads (the autotuner's choices at its end)."""
+    import shutil
+    import subprocess
+    from paper_2101_12408_gb300 import mpm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "profile.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "mpm.h"\n'
+        'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(mpm_profile), offsetof(mpm_profile, cg_ctas_per_sm),'
+        ' offsetof(mpm_profile, cg_graph_error), offsetof(mpm_profile, op_rows_per_chunk)); return 0; }\n')
+    exe = tmp_path / "profile"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(mpm.Profile), mpm.Profile.cg_ctas_per_sm.offset, mpm.Profile.cg_graph_error.offset,
+                   mpm.Profile.op_rows_per_chunk.offset]
+
+
 def test_invalid_arguments_rejected_without_gpu(lib):
     from paper_2101_12408_gb300 import mpm
     out = ctypes.c_void_p()
