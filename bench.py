@@ -28,7 +28,11 @@ Reported (one JSON line on rank 0):
                windows around the lower surfaces of its droplets, or around the
                centroid of a scene without droplets; same dx, parameters and
                plane), one window per host core in separate processes, scaled
-               per particle to the full workload; the one-thread figure beside it
+               per particle to the full workload; the one-thread figure beside it,
+               and one step of the whole 32^3 droplet on one thread (a complete
+               workload, no scaling)
+  operator_tile  the record rows per bulk copy the autotuner picked for the
+               Hessian operator
   --impl reference: the oracle alone, timed the same way on the host cores.
 Multi-GPU (torchrun): replicas only -- every rank advances its own copy of the
 workload; value is the sum over ranks (weak scaling, no collective on the path).
