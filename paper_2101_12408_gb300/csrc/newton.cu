@@ -3418,7 +3418,9 @@ cudaError_t cg_iter_capacity(int& grid, int per_sm_cap = 0) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         // the momentum CG runs the iteration that starts from a summed p . A p
-        const void* fn = NC == 3 ? (const void*)k_cg_iter2<R> : (const void*)k_cg_iter<R, NC>;
+        const void* fn;
+        if constexpr (NC == 3) fn = (const void*)k_cg_iter2<R>;
+        else fn = (const void*)k_cg_iter<R, NC>;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, CG_NT, 0);
         if (e != cudaSuccess) return e;
         if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -3454,7 +3456,7 @@ cudaError_t launch_cg_iter(mpm_ctx* c, CGArgs<R, NC>& a, int heat) {
     cfg.numAttrs = 1;
     c->launches++;
     if constexpr (NC == 3) return cudaLaunchKernelExC(&cfg, (const void*)k_cg_iter2<R>, args2);
-    return cudaLaunchKernelExC(&cfg, (const void*)k_cg_iter<R, NC>, args);
+    else return cudaLaunchKernelExC(&cfg, (const void*)k_cg_iter<R, NC>, args);
 }
 
 template <typename R>
