@@ -97,10 +97,10 @@ class OracleSim:
         self.massless = bool(self.prm.massless_surface)
 
     # (0) surface samples generated on the particles' union-of-spheres surface
-    def generate_surface(self, seed, per_cell_area=2.0):
+    def generate_surface(self, seed, per_cell_area=2.0, method="tetra"):
         sc = self.sc
         plane = (sc.plane_n, sc.plane_d) if sc.plane_mode else None
-        s, dA, kind, _ = generate(sc.x, sc.n, sc.dx, seed, per_cell_area, plane)
+        s, dA, kind, _ = generate(sc.x, sc.n, sc.dx, seed, per_cell_area, plane, method)
         sc.s, sc.dA, sc.kind = s, dA, kind
         sc.b = np.zeros(s.shape[0])
         sc.Tbar = np.full(s.shape[0], self.prm.T0)

@@ -21,9 +21,15 @@ Readings (the paper leaves these open):
   ordering of the axes), which triangulates every cube consistently with its
   neighbours and has no ambiguous cases; inside is phi < 0. Edge points by
   linear interpolation. Triangles face outward (towards phi >= 0).
+* Or by marching cubes, the paper's method (Chernyaev's): each cube's crossing
+  edges are joined into closed loops face by face, ambiguous faces resolved by
+  the asymptotic decider, and each loop is cut into a fan of triangles from its
+  first point (cube_loops). Interior ambiguities (tunnels through the cube) are
+  not formed: loops are built from face segments only.
 * Enumeration order (it fixes the random counters): cubes by the block-major key
   of their lowest corner (4x4x4 blocks, as the grid), then tetrahedron, then
-  triangle.
+  triangle; for marching cubes, loop then fan triangle, triangle t of cube q
+  taking counter slot 12 q + t.
 * Random numbers: the SplitMix64 generator (Steele, Lea, Flood 2014) seeded with
   `seed`; the value for counter k is its (k+1)-th output, and triangle t of
   tetrahedron e of cube key q draws counters ((6 q + e) 2 + t) 64 + j,
@@ -156,6 +162,133 @@ def tet_triangles(qv, pv, dx):
     return res
 
 
+# ---- marching cubes (the paper's isocontour method) ----
+#
+# Corner c = x + 2 y + 4 z of a cube. Edge 4 a + j + 2 k runs along axis a between
+# the two corners whose other two axes (in increasing order) have bits (j, k).
+# Face (w, s) is the face at coordinate s along axis w; its corners are listed
+# counter-clockwise as seen from outside the cube (the right-hand rule about its
+# outward normal), with in-face axes u = w + 1, v = w + 2 (mod 3), e_u x e_v = e_w.
+
+
+def _corner_bits(c):
+    return (c & 1, (c >> 1) & 1, (c >> 2) & 1)
+
+
+def _edge_corners(e):
+    a, jk = divmod(e, 4)
+    b, c = [ax for ax in range(3) if ax != a]
+    bits = [0, 0, 0]
+    bits[b] = jk & 1
+    bits[c] = jk >> 1
+    c0 = bits[0] + 2 * bits[1] + 4 * bits[2]
+    return c0, c0 + (1 << a)
+
+
+def _edge_index(ca, cb):
+    lo, hi = min(ca, cb), max(ca, cb)
+    for e in range(12):
+        if _edge_corners(e) == (lo, hi):
+            return e
+    raise ValueError("corners are not adjacent")
+
+
+def _face_corners(w, s):
+    u, v = (w + 1) % 3, (w + 2) % 3
+    uv = ((0, 0), (1, 0), (1, 1), (0, 1)) if s == 1 else ((0, 0), (0, 1), (1, 1), (1, 0))
+    out = []
+    for iu, iv in uv:
+        bits = [0, 0, 0]
+        bits[w], bits[u], bits[v] = s, iu, iv
+        out.append(bits[0] + 2 * bits[1] + 4 * bits[2])
+    return out
+
+
+FACES = [_face_corners(w, s) for w in range(3) for s in (0, 1)]
+
+
+def cube_loops(cphi):
+    """Closed loops of crossing edges of one cube (corner values cphi[8], inside
+    phi < 0), each ordered so that the surface it bounds faces outward.
+
+    On every face, walking its corners counter-clockwise from outside, a crossing
+    edge is entering (outside corner to inside corner) or leaving. Each face
+    segment runs from an entering crossing to a leaving one. A face with four
+    crossings (diagonal corners inside) is ambiguous; it is resolved by the
+    asymptotic decider (the sign of the bilinear interpolant at its saddle point,
+    Chernyaev's face test): the inside corners a, c join across the face when
+    phi_a phi_c > phi_b phi_d, and then each entering crossing pairs with the
+    leaving crossing before it, else with the one after it. Both cubes sharing a
+    face take the same decision from the same four values. Each crossing edge is
+    entering on exactly one of its two faces, so following the segments visits
+    disjoint closed loops; a loop starts at its smallest edge index."""
+    inside = [p < 0.0 for p in cphi]
+    nxt = {}
+    for fc in FACES:
+        cr = []   # (edge, entering?) in counter-clockwise order
+        for k in range(4):
+            a, b = fc[k], fc[(k + 1) % 4]
+            if inside[a] != inside[b]:
+                cr.append((_edge_index(a, b), inside[b]))
+        if len(cr) == 2:
+            ent = [e for e, en in cr if en][0]
+            lea = [e for e, en in cr if not en][0]
+            nxt[ent] = lea
+        elif len(cr) == 4:
+            ins = [c for c in fc if inside[c]]
+            out = [c for c in fc if not inside[c]]
+            joined = cphi[ins[0]] * cphi[ins[1]] > cphi[out[0]] * cphi[out[1]]
+            for k in range(4):
+                e, en = cr[k]
+                if en:
+                    nxt[e] = cr[(k - 1) % 4][0] if joined else cr[(k + 1) % 4][0]
+    loops, seen = [], set()
+    for e0 in sorted(nxt):
+        if e0 in seen:
+            continue
+        loop, e = [], e0
+        while e not in seen:
+            seen.add(e)
+            loop.append(e)
+            e = nxt[e]
+        assert e == e0, "face segments do not close"
+        loops.append(loop)
+    return loops
+
+
+def cube_triangles(q, cphi, dx):
+    """Marching-cubes triangles of the cube with lowest corner q: every loop of
+    cube_loops as a fan from its first point. Edge points by linear interpolation
+    from the inside corner to the outside one (the tetrahedral path's formula, so
+    a shared edge gives the same point in every cube)."""
+    tris = []
+    for loop in cube_loops(cphi):
+        pts = []
+        for e in loop:
+            ca, cb = _edge_corners(e)
+            i, o = (ca, cb) if cphi[ca] < 0.0 else (cb, ca)
+            qi = tuple(q[a] + _corner_bits(i)[a] for a in range(3))
+            qo = tuple(q[a] + _corner_bits(o)[a] for a in range(3))
+            pts.append(_edge_point(qi, qo, cphi[i], cphi[o], dx))
+        for k in range(1, len(pts) - 1):
+            tris.append((pts[0], pts[k], pts[k + 1]))
+    return tris
+
+
+def isosurface_cubes(phi_of, cubes, n, dx):
+    """Marching-cubes triangles and their counter keys over the cubes (lowest
+    corners) in block-major order: triangle t of the cube with key q has key
+    12 q + t (the same twelve counter slots per cube as the tetrahedral path)."""
+    tris, keys = [], []
+    for q in sorted(cubes, key=lambda q: block_key(q, n)):
+        key = block_key(q, n)
+        cphi = [phi_of((q[0] + (c & 1), q[1] + ((c >> 1) & 1), q[2] + (c >> 2))) for c in range(8)]
+        for t, tri in enumerate(cube_triangles(q, cphi, dx)):
+            tris.append(tri)
+            keys.append(12 * key + t)
+    return tris, keys
+
+
 def isosurface(phi_of, cubes, n, dx):
     """Triangles (list of (p0, p1, p2), keys) over the cubes (lowest corners), in the
     block-major order; phi_of(node) gives phi."""
@@ -204,9 +337,12 @@ def sample_triangles(tris, keys, seed, density):
     return np.array(s, np.float64).reshape(-1, 3), np.array(dA, np.float64).reshape(-1, 3)
 
 
-def generate(x, n, dx, seed, per_cell_area=2.0, plane=None):
+def generate(x, n, dx, seed, per_cell_area=2.0, plane=None, method="tetra"):
     """Surface samples of the particles x (origin 0): positions, dA, kind
-    (0 liquid-gas, 1 solid-liquid), and the triangles they came from."""
+    (0 liquid-gas, 1 solid-liquid), and the triangles they came from. method:
+    "tetra" (marching tetrahedra) or "cubes" (marching cubes)."""
+    if method not in ("tetra", "cubes"):
+        raise ValueError(f"unknown isosurface method {method!r}")
     x = np.asarray(x, np.float64)
     phi, clamp = level_set(x, n, dx)
 
@@ -220,7 +356,7 @@ def generate(x, n, dx, seed, per_cell_area=2.0, plane=None):
                 m = (q[0] - c[0], q[1] - c[1], q[2] - c[2])
                 if min(m) >= 0 and m[0] < n[0] - 1 and m[1] < n[1] - 1 and m[2] < n[2] - 1:
                     cubes.add(m)
-    tris, keys = isosurface(phi_of, cubes, n, dx)
+    tris, keys = (isosurface_cubes if method == "cubes" else isosurface)(phi_of, cubes, n, dx)
     s, dA = sample_triangles(tris, keys, seed, per_cell_area / (dx * dx))
     kind = np.zeros(s.shape[0], np.uint8)
     if plane is not None and s.shape[0]:
