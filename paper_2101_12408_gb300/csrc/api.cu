@@ -596,9 +596,16 @@ mpm_status mpm_get_surface(mpm_ctx* c, int32_t scene, int64_t n, double* s, doub
 }
 
 mpm_status mpm_generate_surface(mpm_ctx* c, uint64_t seed, double per_cell_area, int64_t* counts) {
+    return mpm_generate_surface_method(c, seed, per_cell_area, MPM_ISO_TETRAHEDRA, counts);
+}
+
+mpm_status mpm_generate_surface_method(mpm_ctx* c, uint64_t seed, double per_cell_area, int32_t method,
+                                       int64_t* counts) {
     if (!c) return MPM_ERR_INVALID_ARG;
     if (!(per_cell_area > 0.0) || !std::isfinite(per_cell_area))
         return fail(c, MPM_ERR_INVALID_ARG, "mpm_generate_surface: per_cell_area must be positive");
+    if (method != MPM_ISO_TETRAHEDRA && method != MPM_ISO_CUBES)
+        return fail(c, MPM_ERR_INVALID_ARG, "mpm_generate_surface_method: unknown isosurface method");
     if (c->hscene_cnt.size() != (size_t)c->nsc) {
         c->hscene_cnt.assign(c->nsc, 0ull);
         c->hscene_first.assign(c->nsc, 0ll);
@@ -606,7 +613,7 @@ mpm_status mpm_generate_surface(mpm_ctx* c, uint64_t seed, double per_cell_area,
     std::vector<long long> cnt(c->nsc, 0);
     int cap_err = 0;
     PhaseTimer timer(c, 0);
-    MPM_CUDA(launch_generate_surface(c, (unsigned long long)seed, per_cell_area, cnt.data(), &cap_err));
+    MPM_CUDA(launch_generate_surface(c, (unsigned long long)seed, per_cell_area, method, cnt.data(), &cap_err));
     MPM_CUDA(cudaStreamSynchronize(c->st));
     mpm_status s = check_device_error(c);
     if (s != MPM_OK) return s;

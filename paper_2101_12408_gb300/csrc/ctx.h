@@ -172,10 +172,11 @@ cudaError_t launch_mass_term(mpm_ctx* c, const void* p, void* u);
 
 // ---- surfgen.cu ----
 // Replaces every scene's surface samples with ones generated on the particles'
-// union-of-spheres surface; counts[s] receives scene s's count. A count above a
-// scene's max_surface sets *capacity_error and leaves the samples unchanged.
-cudaError_t launch_generate_surface(mpm_ctx* c, unsigned long long seed, double per_cell_area, long long* counts,
-                                    int* capacity_error);
+// union-of-spheres surface, triangulated by `method` (mpm_isosurface);
+// counts[s] receives scene s's count. A count above a scene's max_surface sets
+// *capacity_error and leaves the samples unchanged.
+cudaError_t launch_generate_surface(mpm_ctx* c, unsigned long long seed, double per_cell_area, int method,
+                                    long long* counts, int* capacity_error);
 
 // ---- heat.cu ----
 cudaError_t run_heat(mpm_ctx* c);

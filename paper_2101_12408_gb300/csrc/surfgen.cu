@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "ctx.h"
+#include "mcubes.cuh"
 
 namespace mpm {
 
@@ -262,6 +263,48 @@ __global__ void k_cube_emit(long long ncube, const int* __restrict__ list, CubeC
     }
 }
 
+// marching cubes (mcubes.cuh): triangles per cube, then the triangle records,
+// triangle t of the cube with key q taking counter slot 12 q + t
+__global__ void k_mc_count(long long ncube, const int* __restrict__ list, CubeCtx cc, int* __restrict__ cnt) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncube) return;
+    const SceneDev* S;
+    int scene, q[3];
+    double cphi[8];
+    long long key;
+    int n = 0;
+    if (cube_setup(cc, list, t, S, scene, q, cphi, key)) {
+        mc::Loops L;
+        mc::cube_loops(cphi, L);
+        n = L.ntri;
+    }
+    cnt[t] = n;
+}
+
+__global__ void k_mc_emit(long long ncube, const int* __restrict__ list, CubeCtx cc, const int* __restrict__ off,
+                          double* __restrict__ tv, long long* __restrict__ tkey, int* __restrict__ tscene) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ncube) return;
+    const SceneDev* S;
+    int scene, q[3];
+    double cphi[8];
+    long long key;
+    if (!cube_setup(cc, list, t, S, scene, q, cphi, key)) return;
+    const long long o = off[t];
+    const int room = off[t + 1] - off[t];   // the count pass walked the same loops
+    mc::cube_triangles(cphi, q, S->dx, S->origin, [&](int k, const double* p0, const double* p1, const double* p2) {
+        if (k >= room) return;
+        const long long r = o + k;
+        for (int a = 0; a < 3; ++a) {
+            tv[r * 9 + a] = p0[a];
+            tv[r * 9 + 3 + a] = p1[a];
+            tv[r * 9 + 6 + a] = p2[a];
+        }
+        tkey[r] = 12 * key + k;
+        tscene[r] = scene;
+    });
+}
+
 struct TriGeom {
     double n[3], nn;
 };
@@ -352,8 +395,8 @@ inline unsigned nblk(long long n, int nt) { return (unsigned)((n + nt - 1) / nt)
 
 }  // namespace
 
-cudaError_t launch_generate_surface(mpm_ctx* c, unsigned long long seed, double per_cell_area, long long* counts,
-                                    int* capacity_error) {
+cudaError_t launch_generate_surface(mpm_ctx* c, unsigned long long seed, double per_cell_area, int method,
+                                    long long* counts, int* capacity_error) {
     Dev& d = c->d;
     cudaStream_t st = c->st;
     *capacity_error = 0;
@@ -386,7 +429,11 @@ cudaError_t launch_generate_surface(mpm_ctx* c, unsigned long long seed, double 
         // triangles per cube, then the triangle records
         int* tcnt = d.cell_count;     // sort scratch until the next resample
         int* toff = d.scell_count;
-        MPM_LAUNCH k_cube_count<<<nblk(ncube, 128), 128, 0, st>>>(ncube, d.bwork, cc, tcnt);
+        if (method == MPM_ISO_CUBES) {
+            MPM_LAUNCH k_mc_count<<<nblk(ncube, 128), 128, 0, st>>>(ncube, d.bwork, cc, tcnt);
+        } else {
+            MPM_LAUNCH k_cube_count<<<nblk(ncube, 128), 128, 0, st>>>(ncube, d.bwork, cc, tcnt);
+        }
         launch_exclusive_scan(c, tcnt, toff, ncube, d.scan_tmp, st);
         cudaMemcpyAsync(c->hcounts + 5, toff + ncube, sizeof(int), cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
@@ -411,7 +458,11 @@ cudaError_t launch_generate_surface(mpm_ctx* c, unsigned long long seed, double 
             int* tscene = (int*)(tkey + ntri);
             int* kcnt = tscene + ntri;
             int* koff = kcnt + ntri + 1;
-            MPM_LAUNCH k_cube_emit<<<nblk(ncube, 128), 128, 0, st>>>(ncube, d.bwork, cc, toff, tv, tkey, tscene);
+            if (method == MPM_ISO_CUBES) {
+                MPM_LAUNCH k_mc_emit<<<nblk(ncube, 128), 128, 0, st>>>(ncube, d.bwork, cc, toff, tv, tkey, tscene);
+            } else {
+                MPM_LAUNCH k_cube_emit<<<nblk(ncube, 128), 128, 0, st>>>(ncube, d.bwork, cc, toff, tv, tkey, tscene);
+            }
             cudaMemsetAsync(d.scene_cnt, 0, sizeof(unsigned long long) * c->nsc, st);
             MPM_LAUNCH k_tri_count<<<nblk(ntri, 128), 128, 0, st>>>(ntri, tv, tkey, tscene, d.sc, seed, per_cell_area,
                                                                     kcnt, d.scene_cnt);

@@ -25,6 +25,8 @@ MPM_OK, MPM_ERR_INVALID_ARG, MPM_ERR_CAPACITY, MPM_ERR_CUDA, MPM_ERR_NOT_CONVERG
     MPM_ERR_NUMERIC, MPM_ERR_DOMAIN = range(8)
 PREC_FP64, PREC_FP32_FP64RED = 0, 1
 HESS_EXACT, HESS_PROJECTED = 0, 1
+ISO_TETRAHEDRA, ISO_CUBES = 0, 1
+ISO_METHODS = {"tetra": ISO_TETRAHEDRA, "cubes": ISO_CUBES}
 FIELD_MASS, FIELD_MOMENTUM, FIELD_VN, FIELD_THERMAL_MASS, FIELD_TN, FIELD_VHAT, FIELD_THAT, FIELD_ITERATE = range(8)
 FIELD_COMPS = {FIELD_MASS: 1, FIELD_MOMENTUM: 3, FIELD_VN: 3, FIELD_THERMAL_MASS: 1, FIELD_TN: 1, FIELD_VHAT: 3,
                FIELD_THAT: 1, FIELD_ITERATE: 3}
@@ -33,7 +35,7 @@ EXPORTED = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_set_particles", 
             "mpm_set_surface", "mpm_get_surface", "mpm_resample", "mpm_p2g", "mpm_get_grid", "mpm_set_velocity",
             "mpm_energy_gradient", "mpm_apply_hessian", "mpm_heat_apply", "mpm_newton_step", "mpm_g2p", "mpm_step",
             "mpm_sync", "mpm_counts", "mpm_profile_enable", "mpm_get_profile", "mpm_nearest_parent_noalloc",
-            "mpm_generate_surface", "mpm_profile_apply"]
+            "mpm_generate_surface", "mpm_generate_surface_method", "mpm_profile_apply"]
 
 
 class GridDesc(ctypes.Structure):
@@ -99,6 +101,7 @@ _lib.mpm_set_surface.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64] + [_vp] * 
 _lib.mpm_get_surface.argtypes = [_vp, ctypes.c_int32, ctypes.c_int64] + [_vp] * 6
 _lib.mpm_resample.argtypes = [_vp]
 _lib.mpm_generate_surface.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _vp]
+_lib.mpm_generate_surface_method.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_int32, _vp]
 _lib.mpm_p2g.argtypes = [_vp]
 _lib.mpm_get_grid.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp]
 _lib.mpm_set_velocity.argtypes = [_vp, ctypes.c_int32, _vp]
@@ -293,11 +296,19 @@ class Context:
         return out
 
     # ---- phases ----
-    def generate_surface(self, seed, per_cell_area=2.0):
+    def generate_surface(self, seed, per_cell_area=2.0, method="tetra"):
         """Replaces every scene's surface samples with ones generated on the
-        particles' union-of-spheres surface; returns the per-scene counts."""
+        particles' union-of-spheres surface, triangulated by marching tetrahedra
+        (method "tetra") or marching cubes ("cubes"); returns the per-scene counts."""
+        if method not in ISO_METHODS:
+            raise ValueError(f"unknown isosurface method {method!r}")
         cnt = np.zeros(len(self.scenes), np.int64)
-        self._check(_lib.mpm_generate_surface(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF, float(per_cell_area), _ptr(cnt)))
+        seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        if method == "tetra":
+            self._check(_lib.mpm_generate_surface(self.h, seed, float(per_cell_area), _ptr(cnt)))
+        else:
+            self._check(_lib.mpm_generate_surface_method(self.h, seed, float(per_cell_area), ISO_METHODS[method],
+                                                         _ptr(cnt)))
         for k in range(len(self.scenes)):
             self.ns[k] = int(cnt[k])
         return cnt

@@ -102,6 +102,9 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.mpm_create(None, 0, 1, None, ctypes.byref(out)) == mpm.MPM_ERR_INVALID_ARG
     assert lib.mpm_resample(None) == mpm.MPM_ERR_INVALID_ARG
     assert lib.mpm_destroy(None) == mpm.MPM_ERR_INVALID_ARG
+    for method in (mpm.ISO_TETRAHEDRA, mpm.ISO_CUBES, 7):
+        assert lib.mpm_generate_surface_method(None, ctypes.c_uint64(1), ctypes.c_double(2.0), ctypes.c_int32(method),
+                                               None) == mpm.MPM_ERR_INVALID_ARG
 
 
 def test_invalid_friction_and_massless_flag_rejected_without_gpu(lib):

@@ -94,3 +94,27 @@ def test_momentum_conserved_with_generated_surface():
     p = ctx.get_particles(0)
     np.testing.assert_allclose(np.sum(sc.m[:, None] * p["v"], 0), m0, rtol=0, atol=1e-10 * np.abs(m0).max())
     ctx.close()
+
+
+@pytest.mark.parametrize("make", [_droplet, _incline])
+def test_marching_cubes_samples_match_oracle(make):
+    """The same through marching cubes (the paper's isocontour method): the
+    device's loops, decider and fans against the oracle's, sample for sample."""
+    sc = make()
+    ctx = mpm.Context(sc, surface_capacity_factor=3.0)
+    ctx.load_scene(0)
+    plane = (sc.plane_n, sc.plane_d) if sc.plane_mode else None
+    for seed in (77, 78):
+        cnt = ctx.generate_surface(seed, 2.0, method="cubes")
+        s, dA, kind, _ = osurf.generate(sc.x, sc.n, sc.dx, seed, 2.0, plane, method="cubes")
+        assert int(cnt[0]) == s.shape[0] > 0
+        got = ctx.get_surface(0)
+        assert np.max(np.abs(got["s"] - s)) <= 1e-14
+        assert relerr(got["dA"], dA) <= 1e-13
+        np.testing.assert_array_equal(got["kind"], kind)
+    # the tetrahedral surface again from the same context: the two methods share its buffers
+    cnt = ctx.generate_surface(77, 2.0)
+    s, _, _, _ = osurf.generate(sc.x, sc.n, sc.dx, 77, 2.0, plane)
+    assert int(cnt[0]) == s.shape[0]
+    assert np.max(np.abs(ctx.get_surface(0)["s"] - s)) <= 1e-14
+    ctx.close()
