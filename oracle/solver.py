@@ -59,6 +59,18 @@ def pcg(apply, b, precond, rtol, maxit, neg_curv_exit=True):
     return x, it
 
 
+def armijo(phi, phi0, slope, max_ls, c=1e-4):
+    """Backtracking line search: the first of alpha = 1, 1/2, 1/4, ... (max_ls
+    trials) with phi(alpha) <= phi0 + c alpha slope (sufficient decrease along a
+    descent direction, slope < 0), or None when no trial passes."""
+    alpha = 1.0
+    for _ in range(max_ls):
+        if phi(alpha) <= phi0 + c * alpha * slope:
+            return alpha
+        alpha *= 0.5
+    return None
+
+
 def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False, friction=None):
     """Returns the end-of-step grid velocity and a stats dict.
 
@@ -90,15 +102,9 @@ def newton_solve(state, P, prm, hess_mode=HESS_PROJECTED, explicit=False, fricti
             stats["cg"].append(its)
             phi0 = state.energy(v)
             slope = float(np.sum(r * d))
-            alpha = 1.0
-            accepted = False
-            for _ in range(prm.max_ls):
-                if state.energy(v + alpha * d) <= phi0 + 1e-4 * alpha * slope:
-                    accepted = True
-                    break
-                alpha *= 0.5
+            alpha = armijo(lambda a: state.energy(v + a * d), phi0, slope, prm.max_ls)
             stats["newton"] = k + 1
-            if not accepted:
+            if alpha is None:
                 # no trial decreases Phi (round-off floor, or a CG direction that
                 # lost its meaning): keep the iterate and stop
                 stats["alpha"].append(0.0)

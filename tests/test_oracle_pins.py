@@ -336,6 +336,25 @@ def test_newton_zero_forces_is_free_fall():
     sim.resample(); sim.p2g(); sim.grid_update()
     act = sim.grid["m"] > 0
     np.testing.assert_allclose(sim.vhat[act], sim.vn[act] + sc.params.dt * np.array([0.0, -9.8, 1.0]), atol=1e-14)
+    # the initial guess P(v^n + dt g) already solves it: no Newton iteration
+    assert sim.stats["newton"] == 0
+
+
+def test_armijo_takes_the_first_sufficient_decrease():
+    """Backtracking over alpha = 1, 1/2, ...: the first trial whose decrease is at
+    least c alpha |slope| (c = 1e-4); an increase, however small, is never taken."""
+    from oracle.solver import armijo
+    # phi(alpha) = (alpha - 0.3)^2 - 0.09 has slope -0.6 at 0: alpha = 1 rises, 1/2 falls enough
+    assert armijo(lambda a: (a - 0.3) ** 2 - 0.09, 0.0, -0.6, 12) == 0.5
+    # a quadratic with its minimum at 1 takes the full step
+    assert armijo(lambda a: (a - 1.0) ** 2 - 1.0, 0.0, -2.0, 12) == 1.0
+    # a tiny rise along the direction: no trial passes
+    assert armijo(lambda a: 1e-5 * a, 0.0, -1.0, 12) is None
+    # a decrease smaller than c alpha |slope| is not sufficient
+    assert armijo(lambda a: -0.5e-4 * a, 0.0, -1.0, 3) is None
+    # the number of trials bounds the search: 1, 1/2, 1/4 only
+    assert armijo(lambda a: 0.0 if a < 0.2 else 1.0, 0.0, -1e-9, 3) is None
+    assert armijo(lambda a: -1.0 if a < 0.2 else 1.0, 0.0, -1.0, 4) == 0.125
 
 
 def test_newton_pure_liquid_is_one_step():
@@ -493,6 +512,42 @@ def test_heat_operator_symmetric_spd_and_balance():
     rhs = (-np.sum(sc.params.h * hs.area * Ts) + np.sum((sc.params.h * sc.Tbar + sc.b) * hs.area)
            + np.sum(sc.params.H * hs.Vn))
     np.testing.assert_allclose(lhs, rhs, rtol=1e-9)
+
+
+def test_heat_conduction_term_is_minus_k_laplacian_on_a_regular_lattice():
+    """Away from the particles' boundary the conduction rows are a weak form of
+    -div(K grad T) (section "Temperature Update"): sum_p K V_p gradN_i(x_p) .
+    grad T(x_p) = -int N_i K lap T = -K lap T V_i for a quadratic T, whose
+    quadratic B-spline interpolant has the exact gradient. On a regular lattice of
+    particles (two per cell and axis) the particle quadrature of it is exact, so
+    the rows equal -K lap T V_i with V_i = sum_p N_i(x_p) V_p; for T = cos(k x)
+    they approach K k^2 T_i V_i at second order in k dx."""
+    from oracle.spline import scatter
+    n, dx, K = (24, 12, 12), 1.0 / 24, 0.2
+    rng = np.random.default_rng(3)
+    x = scenes.lattice_in(lambda p: np.ones(p.shape[:-1], bool), np.array([2, 2, 2]), np.array([22, 10, 10]),
+                          dx, rng, 2, jitter=0.0)
+    V = np.full(x.shape[0], dx ** 3 / 8)
+    G = int(np.prod(n))
+    st = oracle.Stencil(x, dx, n)
+    mT = scatter(G, st.node, st.N)
+    no = np.zeros((0, 3))
+    hs = oracle.HeatSystem(n, dx, 1e-3, 1.0, K, 0.0, 0.0, mT, np.zeros(G), x, V, no, no, np.zeros(0), np.zeros(0))
+    Vi = scatter(G, st.node, st.N * V[:, None])
+    xi = oracle.node_positions(n, dx)
+    g = np.stack(np.unravel_index(np.arange(G), n, order="F"), -1)
+    inner = np.all((g >= [4, 4, 4]) & (g <= [19, 7, 7]), 1)
+    for T, lap in ((xi[:, 0] ** 2, 2.0), (xi[:, 1] ** 2 + xi[:, 2] ** 2, 4.0), (xi[:, 0] * xi[:, 2], 0.0)):
+        L = hs.apply(T) - hs.diag * np.where(hs.unknown, T, 0.0)
+        np.testing.assert_allclose(L[inner], -K * lap * Vi[inner], atol=1e-6 * K * 2.0 * Vi[inner].max())
+    errs = []
+    for period in (8, 16):
+        k = 2.0 * np.pi / (period * dx)
+        T = np.cos(k * xi[:, 0])
+        L = hs.apply(T) - hs.diag * np.where(hs.unknown, T, 0.0)
+        big = inner & (np.abs(T) > 0.5)
+        errs.append(np.max(np.abs(L[big] / (K * k * k * T[big] * Vi[big]) - 1.0)))
+    assert errs[1] < 0.05 and 3.0 < errs[0] / errs[1] < 5.0
 
 
 def test_heat_uniform_ambient_is_fixed_point():
@@ -1104,3 +1159,94 @@ def test_solid_at_the_melting_point_stores_the_liquids_energy():
     sol2.F = np.broadcast_to(np.array([[1.0, 0.1, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]]), sol.F.shape).copy()
     _, s2 = _state(sol2)
     assert s2.energy(v0) > 0
+
+
+# ----------------------------------------------------------------------------
+# Pins added where a planted mistake in the oracle went unnoticed by the others
+# ----------------------------------------------------------------------------
+
+def test_gamma_reads_a_uniform_temperature_exactly_at_every_sample():
+    """The renormalised interpolation of reading R9 returns a uniform grid
+    temperature unchanged at every sample, also where only part of the sample's
+    stencil carries thermal mass (samples on and just outside the surface)."""
+    sc = scenes.droplet(n=12, r_cells=3.0, seed=24, thermal=True)
+    sc.T[:] = 1.7
+    sc.gradT[:] = 0.0
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal((60, 3))
+    r = (3.0 + rng.uniform(-0.5, 1.2, (60, 1))) * sc.dx
+    sc.s = np.full(3, 0.5) + d / np.linalg.norm(d, axis=1, keepdims=True) * r
+    sc.dA = np.tile([0.0, 0.0, sc.dx ** 2], (60, 1))
+    sc.kind, sc.b, sc.Tbar = np.zeros(60, np.uint8), np.zeros(60), np.zeros(60)
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    st = oracle.Stencil(sc.s, sc.dx, sc.n)
+    has = sim.grid["mT"][st.node] > 0
+    partial = has.any(1) & ~has.all(1)
+    assert partial.sum() >= 20
+    np.testing.assert_allclose(sim.Tr[has.any(1)], 1.7, rtol=1e-13)
+
+
+@pytest.mark.parametrize("T,frac", [(298.0, 1.0), (299.25, 0.75), (300.5, 0.5), (303.0, 0.0), (320.0, 0.0)])
+def test_solid_shear_modulus_follows_youngs_modulus_of_temperature(T, frac):
+    """Section "Thermomechanical Material Dependence": the wax's Young's modulus
+    falls linearly from E0 at T0 to zero at the melting point, and the shear
+    modulus of isotropic elasticity is E / (2 (1 + nu)). Measured from the
+    fixed-corotated energy of a small simple shear (J = 1, so only the shear
+    modulus acts): psi = mu gamma^2 / 2 + O(gamma^4)."""
+    from oracle.step import solid_lame
+    prm = scenes.wax(nx=16, ny=16, nz=16, cube_cells=4).params
+    assert (prm.T0, prm.T_melt, prm.E0, prm.nu) == (298.0, 303.0, 1e4, 0.3)
+    mu, lam = solid_lame(np.array([T]), prm)
+    g = 1e-4
+    F = np.eye(3)[None].copy()
+    F[0, 0, 1] = g
+    psi = cst.fcr_energy(F, mu, lam)[0]
+    assert 2.0 * psi / g ** 2 == pytest.approx(frac * 1e4 / (2.0 * 1.3), rel=1e-7, abs=1e-9)
+
+
+def test_generated_kinds_are_the_resample_classification():
+    """Samples made on the particles' surface carry the interface kind that
+    resampling assigns (reading R13: solid-liquid within dx of the plane), so
+    both sides of the pipeline classify a generated sample alike."""
+    sc = scenes.incline(n=48, n_drops=2, r_range=(3.0, 5.0), seed=43, gap_cells=(0.0, 0.5))
+    sim = oracle.OracleSim(sc)
+    sim.generate_surface(5)
+    k0 = sim.sc.kind.copy()
+    d = sim.sc.s @ np.asarray(sc.plane_n) - sc.plane_d
+    assert np.sum((d > 0.5 * sc.dx) & (d < sc.dx)) > 10     # samples in the outer half of the band
+    sim.resample()
+    np.testing.assert_array_equal(k0, sim.sc.kind)
+    assert 0 < int(k0.sum()) < k0.size
+
+
+def test_viscous_term_weighs_the_current_volume():
+    """Eq. disc_force's viscous term integrates over the current volume V^n = J^n V^0:
+    for an affine grid velocity v = B x its energy is dt mu / 2 |sym B|^2 sum J^n V^0."""
+    sc = _moving_droplet(mu_l=0.3, lambda_l=0.0, gamma=0.0)
+    sc.J = RNG.uniform(0.4, 0.6, sc.J.shape)
+    sim, st = _state(sc)
+    B = RNG.standard_normal((3, 3))
+    v = _affine_grid_velocity(sc, B)
+    kin = 0.5 * np.sum(st.m[st.active] * np.sum((v - st.vn)[st.active] ** 2, -1))
+    S = 0.5 * (B + B.T)
+    expect = sc.params.dt * 0.3 / 2.0 * np.sum(S * S) * np.sum(sc.J * sc.V0)
+    np.testing.assert_allclose(st.energy(v) - kin, expect, rtol=1e-11)
+
+
+def test_closest_parent_ties_go_to_the_smaller_index():
+    """Reading R12: equal squared distances go to the smaller particle index
+    (exact ties by construction: offsets of powers of two)."""
+    from oracle.resample import nearest_parent
+    c = np.array([0.5, 0.5, 0.5])
+    h = 2.0 ** -6
+    offs = np.array([[h, 0, 0], [-h, 0, 0], [0, h, 0], [0, 0, -h]])
+    for perm in ([0, 1, 2, 3], [3, 2, 1, 0], [2, 0, 3, 1]):
+        x = np.vstack([c + 3 * h, c + offs[perm]])
+        p, best = nearest_parent(x, c[None])
+        assert p[0] == 1 and best[0] == h * h
+    # a particle a few ulps closer wins over the smaller index
+    x = np.vstack([c + [h, 0, 0], c + [h - 2.0 ** -48, 0, 0]])
+    assert x[1, 0] - c[0] < x[0, 0] - c[0]
+    assert nearest_parent(x, c[None])[0][0] == 1
