@@ -455,6 +455,60 @@ def test_uniform_heat_source_raises_temperature_by_dt_H_over_rho_cp():
     np.testing.assert_allclose(T[hs.unknown], 0.3 + rise, rtol=1e-12)
 
 
+@pytest.mark.parametrize("phase,scale", [(scenes.PHASE_LIQUID, 0.8), (scenes.PHASE_SOLID, 1.1)])
+def test_heat_source_acts_on_the_current_volume(phase, scale):
+    """The source is a power per unit current volume, V^n_p = J V^0_p (liquid J,
+    solid det F): a uniformly compressed liquid (J = 0.8) or stretched solid
+    (F = 1.1 I) warms by dt H J / (rho c_p) at every node with thermal mass."""
+    sc = scenes.droplet(n=12, r_cells=3.0, seed=24, thermal=True, rho=2.0)
+    sc.T[:] = 0.3
+    sc.gradT[:] = 0.0
+    sc.params.K = 0.0
+    sc.params.h = 0.0
+    sc.b[:] = 0.0
+    sc.params.H = 5.0
+    sc.params.cp = 0.8
+    sc.phase[:] = phase
+    if phase == scenes.PHASE_LIQUID:
+        sc.J[:] = scale
+        J = scale
+    else:
+        sc.F[:] = scale * np.eye(3)
+        J = scale ** 3
+    sim = oracle.OracleSim(sc)
+    sim.resample()
+    sim.p2g()
+    hs = sim.heat_system()
+    T, _ = oracle.heat_solve(hs, 1e-14, 5000)
+    np.testing.assert_allclose(T[hs.unknown], 0.3 + sc.params.dt * sc.params.H * J / (2.0 * sc.params.cp),
+                               rtol=1e-12)
+
+
+def test_sticky_plane_holds_what_lies_in_its_solid():
+    """A sticky plane (reading R14) fixes every node on its solid side: particles
+    deep in it stay where they are under gravity, while the nodes on the open
+    side keep all three components."""
+    from oracle.boundary import projector
+    n, dx = (16, 16, 16), 1.0 / 16
+    nrm = np.array([0.5, 0.8660254037844386, 0.0])
+    d = float(nrm @ np.array([0.5, 0.7, 0.5]))
+    walls = (scenes.WALL_NONE,) * 6
+    P = projector(n, dx, walls, tuple(nrm), d, scenes.WALL_STICKY)
+    below = oracle.node_positions(n, dx) @ nrm - d < 0
+    assert 0 < below.sum() < below.size
+    np.testing.assert_array_equal(P[below], 0.0)
+    np.testing.assert_array_equal(P[~below], np.broadcast_to(np.eye(3), P[~below].shape))
+    sc = scenes.droplet(n=16, r_cells=1.5, seed=26, gravity=(0.0, -9.8, 0.0), lambda_l=10.0, gamma=0.0,
+                        center=(0.5, 0.35, 0.5))
+    sc.plane_n, sc.plane_d, sc.plane_mode = tuple(nrm), d, scenes.WALL_STICKY
+    x0 = sc.x.copy()
+    assert np.all(x0 @ nrm - d < -3 * dx)
+    sim = oracle.OracleSim(sc)
+    sim.step()
+    np.testing.assert_array_equal(sim.sc.x, x0)
+    np.testing.assert_array_equal(sim.sc.v, 0.0)
+
+
 def test_affine_grid_motion_moves_particles_and_carries_samples_exactly():
     """Under an affine grid velocity a + B x the end of a step is a closed form:
     particles move to x + dt (a + B x), liquids scale J by 1 + dt tr B and solids
