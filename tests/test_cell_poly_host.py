@@ -1,0 +1,96 @@
+"""The per-cell polynomial form of the liquid operator (csrc/newton.cu:
+cell_coefficients with the 1-D transforms wT and dT, used by the float64
+liquid evaluation and the line-search curvature, and in paired form by the
+Hessian operator), built for the host from its source text, against the FP64
+oracle's per-particle definition tr L(x_p) = sum_i v_i . gradN_i(x_p) with
+quadratic B-splines (section "Transfer: P2G" weights, Eq. fe's J). The 26
+coefficients of a cell, evaluated at the particle's in-cell coordinate t, must
+give the same trace for any node velocities and any t in the cell."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.test_polar_host import _host_text, _template_function
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2101_12408_gb300", "csrc")
+
+SHIM = r"""
+namespace mpm {
+constexpr int PY = 8, PZ = 52, PN = 312;
+inline int pidx(int x, int y, int z) { return x + PY * y + PZ * z; }
+%s
+}
+// trace of dL (without 1/dx) at in-cell coordinates t for the cell (lx, ly, lz) of the halo
+extern "C" double h_cell_trace(const double* halo, int lx, int ly, int lz, double tx, double ty, double tz) {
+    double ph[3][mpm::PN];
+    for (int c = 0; c < 3; ++c) for (int k = 0; k < mpm::PN; ++k) ph[c][k] = halo[c * mpm::PN + k];
+    double C[3][3][3] = {};
+    mpm::cell_coefficients<double>(ph, lx, ly, lz, C);
+    const double px[3] = {1.0, tx, tx * tx}, py[3] = {1.0, ty, ty * ty}, pz[3] = {1.0, tz, tz * tz};
+    double tr = 0.0;
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) for (int k = 0; k < 3; ++k)
+        tr += C[i][j][k] * px[i] * py[j] * pz[k];
+    return tr;
+}
+extern "C" double h_c222(const double* halo, int lx, int ly, int lz) {
+    double ph[3][mpm::PN];
+    for (int c = 0; c < 3; ++c) for (int k = 0; k < mpm::PN; ++k) ph[c][k] = halo[c * mpm::PN + k];
+    double C[3][3][3] = {};
+    mpm::cell_coefficients<double>(ph, lx, ly, lz, C);
+    return C[2][2][2];
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    newton = open(os.path.join(CSRC, "newton.cu")).read()
+    funcs = [_template_function(newton, n) for n in ("wT", "dT", "cell_coefficients")]
+    d = tmp_path_factory.mktemp("cellpoly")
+    cpp = d / "cell_poly_host.cpp"
+    cpp.write_text(SHIM % _host_text("\n\n".join(funcs)))
+    so = str(d / "libcellpoly.so")
+    res = subprocess.run(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", str(cpp), "-o", so],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    L = ctypes.CDLL(so)
+    L.h_cell_trace.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 3 + [ctypes.c_double] * 3
+    L.h_cell_trace.restype = ctypes.c_double
+    L.h_c222.argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 3
+    L.h_c222.restype = ctypes.c_double
+    return L
+
+
+def test_cell_polynomial_equals_the_per_particle_trace(lib):
+    rng = np.random.default_rng(21)
+    # one 4^3 block and its halo (halo index = node index 0..5), inside a 7^3 grid so
+    # that a particle on the block's upper faces still has its stencil on the grid
+    # (the extra node layer carries zero weight and gradient there)
+    n = (7, 7, 7)
+    dx = 1.0 / 7
+    for trial in range(60):
+        v = np.zeros((7, 7, 7, 3))
+        v[:6, :6, :6] = rng.standard_normal((6, 6, 6, 3))
+        halo = np.zeros((3, 312))
+        for z in range(6):
+            for y in range(6):
+                for x in range(6):
+                    halo[:, x + 8 * y + 52 * z] = v[x, y, z]
+        v = v.transpose(2, 1, 0, 3).reshape(-1, 3)           # flat, x fastest
+        halo = np.ascontiguousarray(halo)
+        lc = rng.integers(0, 4, 3)          # cell (lx, ly, lz) of the block = grid cell lc + 1
+        t = rng.uniform(0.0, 1.0, 3)
+        if trial < 8:                        # cell faces and corners
+            t = rng.integers(0, 2, 3).astype(float)
+        xp = (lc + 1 + t) * dx
+        st = oracle.Stencil(xp[None], dx, n)
+        ref = float(np.einsum("qa,qa->", v[st.node[0]], st.dN[0]))
+        got = lib.h_cell_trace(halo.ctypes.data, int(lc[0]), int(lc[1]), int(lc[2]), *t) / dx
+        assert got == pytest.approx(ref, rel=1e-12, abs=1e-12 * np.abs(v).max() / dx)
+        # the x^2 y^2 z^2 coefficient vanishes: each term of the trace is at most linear along its own axis
+        assert lib.h_c222(halo.ctypes.data, int(lc[0]), int(lc[1]), int(lc[2])) == 0.0
