@@ -94,3 +94,70 @@ def test_cell_polynomial_equals_the_per_particle_trace(lib):
         assert got == pytest.approx(ref, rel=1e-12, abs=1e-12 * np.abs(v).max() / dx)
         # the x^2 y^2 z^2 coefficient vanishes: each term of the trace is at most linear along its own axis
         assert lib.h_c222(halo.ctypes.data, int(lc[0]), int(lc[1]), int(lc[2])) == 0.0
+
+
+SCATTER_SHIM = r"""
+namespace mpm {
+constexpr int UN = 1;   // the capture below replaces the halo writes
+static double g_cap[3][27];
+template <typename R>
+void rmw_phases(R* uq, const R (&N)[3][3][3], int, int, int, bool = true) {
+    const int q = (int)uq[0];   // the stub halo row carries its component index
+    for (int a = 0; a < 3; ++a) for (int b = 0; b < 3; ++b) for (int c = 0; c < 3; ++c)
+        g_cap[q][a + 3 * b + 9 * c] = N[a][b][c];
+}
+%s
+}
+// node values (without 1/dx) that the moment tensor of one particle of weight s
+// at in-cell coordinates t scatters to its 27 nodes, per component
+extern "C" void h_cell_scatter(double s, double tx, double ty, double tz, double* out) {
+    double M[3][3][3] = {};
+    const double px[3] = {1.0, tx, tx * tx}, py[3] = {1.0, ty, ty * ty}, pz[3] = {1.0, tz, tz * tz};
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) for (int k = 0; k < 3; ++k)
+        if (!(i == 2 && j == 2 && k == 2)) M[i][j][k] = s * px[i] * py[j] * pz[k];
+    double ua[3][1] = {{0.0}, {1.0}, {2.0}};
+    mpm::cell_scatter_warp<double>(M, ua, 0, 0, 0);
+    for (int q = 0; q < 3; ++q) for (int k = 0; k < 27; ++k) out[27 * q + k] = mpm::g_cap[q][k];
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def scatter_lib(tmp_path_factory):
+    newton = open(os.path.join(CSRC, "newton.cu")).read()
+    funcs = [_template_function(newton, n) for n in ("wN", "dN", "cell_scatter_warp")]
+    d = tmp_path_factory.mktemp("cellscatter")
+    cpp = d / "cell_scatter_host.cpp"
+    cpp.write_text(SCATTER_SHIM % _host_text("\n\n".join(funcs)))
+    so = str(d / "libcellscatter.so")
+    res = subprocess.run(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", str(cpp), "-o", so],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    L = ctypes.CDLL(so)
+    L.h_cell_scatter.argtypes = [ctypes.c_double] * 4 + [ctypes.c_void_p]
+    return L
+
+
+def test_cell_moments_scatter_to_the_weight_gradients(scatter_lib):
+    """The transposed map (cell_scatter_warp with wN and dN): the moments
+    sum_p s_p t_p^ijk of a cell scatter to node values sum_p s_p dx gradN_i(x_p),
+    the per-particle scatter of the liquid's gradient and Hessian product."""
+    rng = np.random.default_rng(22)
+    dx = 1.0 / 7
+    n = (7, 7, 7)
+    for trial in range(40):
+        t = rng.uniform(0.0, 1.0, 3) if trial >= 8 else rng.integers(0, 2, 3).astype(float)
+        s = rng.uniform(0.5, 2.0)
+        out = np.zeros(81)
+        scatter_lib.h_cell_scatter(s, *t, out.ctypes.data)
+        xp = (np.array([2.0, 2.0, 2.0]) + t) * dx        # cell (2, 2, 2): nodes 1..3 per axis
+        st = oracle.Stencil(xp[None], dx, n)
+        g = np.stack(np.unravel_index(st.node[0], n, order="F"), -1) - 1   # offsets 0..2 (t = 1: one cell up)
+        ref = np.zeros((3, 27))
+        for q in range(27):
+            a, b, c = g[q]
+            if max(a, b, c) <= 2:
+                ref[:, a + 3 * b + 9 * c] += s * dx * st.dN[0, q]
+            else:                                         # only on a face, where the weight and its gradient vanish
+                assert np.all(np.abs(st.dN[0, q]) < 1e-12)
+        np.testing.assert_allclose(out.reshape(3, 27), ref, atol=1e-12 * s, rtol=0)
