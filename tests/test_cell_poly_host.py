@@ -161,3 +161,102 @@ def test_cell_moments_scatter_to_the_weight_gradients(scatter_lib):
             else:                                         # only on a face, where the weight and its gradient vanish
                 assert np.all(np.abs(st.dN[0, q]) < 1e-12)
         np.testing.assert_allclose(out.reshape(3, 27), ref, atol=1e-12 * s, rtol=0)
+
+
+PAIR_SHIM = r"""
+#include <cmath>
+struct float2 { float x, y; };
+struct double2 { double x, y; };
+inline float2 make_float2(float a, float b) { return {a, b}; }
+inline double2 make_double2(double a, double b) { return {a, b}; }
+// the paired instructions, one rounding per element (fma for the fused form)
+inline float2 vadd(float2 a, float2 b) { return {a.x + b.x, a.y + b.y}; }
+inline float2 vmul(float2 a, float2 b) { return {a.x * b.x, a.y * b.y}; }
+inline float2 vfma(float2 a, float2 b, float2 c) { return {std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y)}; }
+inline float2 vsub(float2 a, float2 b) { return {a.x - b.x, a.y - b.y}; }
+inline double2 vadd(double2 a, double2 b) { return {a.x + b.x, a.y + b.y}; }
+inline double2 vmul(double2 a, double2 b) { return {a.x * b.x, a.y * b.y}; }
+inline double2 vfma(double2 a, double2 b, double2 c) { return {std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y)}; }
+inline double2 vsub(double2 a, double2 b) { return {a.x - b.x, a.y - b.y}; }
+namespace mpm {
+constexpr int PY = 8, PZ = 52, PN = 312;
+inline int pidx(int x, int y, int z) { return x + PY * y + PZ * z; }
+%s
+}
+template <typename R>
+static void pair(const double* halo, int m, int ly, int lz, double* out) {
+    alignas(16) R ph[3][mpm::PN];
+    for (int c = 0; c < 3; ++c) for (int k = 0; k < mpm::PN; ++k) ph[c][k] = (R)halo[c * mpm::PN + k];
+    typename mpm::VPair<R>::T C[3][3][3];
+    mpm::pair_coefficients<R>(ph, m, ly, lz, C);
+    for (int i = 0; i < 27; ++i) { out[i] = (&C[0][0][0])[i].x; out[27 + i] = (&C[0][0][0])[i].y; }
+}
+extern "C" void h_pair(const double* halo, int m, int ly, int lz, double* out) { pair<double>(halo, m, ly, lz, out); }
+extern "C" void h_pairf(const double* halo, int m, int ly, int lz, double* out) { pair<float>(halo, m, ly, lz, out); }
+extern "C" void h_cell(const double* halo, int lx, int ly, int lz, double* out) {
+    double ph[3][mpm::PN];
+    for (int c = 0; c < 3; ++c) for (int k = 0; k < mpm::PN; ++k) ph[c][k] = halo[c * mpm::PN + k];
+    double C[3][3][3] = {};
+    mpm::cell_coefficients<double>(ph, lx, ly, lz, C);
+    for (int i = 0; i < 27; ++i) out[i] = (&C[0][0][0])[i];
+}
+"""
+
+
+def _vpair_text(src):
+    i = src.index("template <typename R> struct VPair;")
+    j = src.index("// the scalar transforms (wT, dT, wN, dN) on pairs", i)
+    return src[i:j]
+
+
+@pytest.fixture(scope="module")
+def pair_lib(tmp_path_factory):
+    newton = open(os.path.join(CSRC, "newton.cu")).read()
+    text = _vpair_text(newton) + "\n\n".join(
+        _template_function(newton, n) for n in ("wT", "dT", "cell_coefficients"))
+    # the paired transforms (templates on the pair type) and the pair helpers,
+    # whose signatures span lines
+    for name in ("pwT", "pdT", "row_pairs", "pair_coefficients"):
+        k = newton.index("__device__ __forceinline__ void " + name + "(")
+        k = newton.rindex("template <", 0, k)
+        i = newton.index("{", newton.index(")", newton.index(name + "(", k)))
+        depth = 0
+        for j in range(i, len(newton)):
+            depth += newton[j] == "{"
+            depth -= newton[j] == "}"
+            if depth == 0:
+                break
+        text += "\n\n" + newton[k:j + 1]
+    d = tmp_path_factory.mktemp("pairpoly")
+    cpp = d / "pair_poly_host.cpp"
+    cpp.write_text(PAIR_SHIM % _host_text(text))
+    so = str(d / "libpairpoly.so")
+    res = subprocess.run(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", str(cpp), "-o", so],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    L = ctypes.CDLL(so)
+    for f in ("h_pair", "h_pairf", "h_cell"):
+        getattr(L, f).argtypes = [ctypes.c_void_p] + [ctypes.c_int] * 3 + [ctypes.c_void_p]
+    return L
+
+
+def test_paired_coefficients_equal_the_two_cells(pair_lib):
+    """The operator's paired form (pair_coefficients: the cells 2m and 2m+1 of a
+    row as one float pair, the middle node pair formed from two aligned pairs)
+    gives each cell's own 26 coefficients, in float64 to rounding and in float32
+    to float32 rounding."""
+    rng = np.random.default_rng(23)
+    for trial in range(30):
+        halo = np.ascontiguousarray(rng.standard_normal((3, 312)))
+        for m in (0, 1):
+            ly, lz = int(rng.integers(0, 4)), int(rng.integers(0, 4))
+            got = np.zeros(54)
+            pair_lib.h_pair(halo.ctypes.data, m, ly, lz, got.ctypes.data)
+            gotf = np.zeros(54)
+            pair_lib.h_pairf(halo.ctypes.data, m, ly, lz, gotf.ctypes.data)
+            for half, lx in ((0, 2 * m), (1, 2 * m + 1)):
+                ref = np.zeros(27)
+                pair_lib.h_cell(halo.ctypes.data, lx, ly, lz, ref.ctypes.data)
+                scale = np.abs(halo).max()
+                np.testing.assert_allclose(got[27 * half:27 * half + 27], ref, atol=1e-13 * scale, rtol=0)
+                np.testing.assert_allclose(gotf[27 * half:27 * half + 27], ref, atol=2e-6 * scale, rtol=0)
