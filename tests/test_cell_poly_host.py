@@ -260,3 +260,89 @@ def test_paired_coefficients_equal_the_two_cells(pair_lib):
                 scale = np.abs(halo).max()
                 np.testing.assert_allclose(got[27 * half:27 * half + 27], ref, atol=1e-13 * scale, rtol=0)
                 np.testing.assert_allclose(gotf[27 * half:27 * half + 27], ref, atol=2e-6 * scale, rtol=0)
+
+
+PAIR_SCATTER_SHIM = r"""
+#include <cmath>
+struct float2 { float x, y; };
+struct double2 { double x, y; };
+inline float2 make_float2(float a, float b) { return {a, b}; }
+inline double2 make_double2(double a, double b) { return {a, b}; }
+inline double2 vadd(double2 a, double2 b) { return {a.x + b.x, a.y + b.y}; }
+inline double2 vmul(double2 a, double2 b) { return {a.x * b.x, a.y * b.y}; }
+inline double2 vfma(double2 a, double2 b, double2 c) { return {std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y)}; }
+inline double2 vsub(double2 a, double2 b) { return {a.x - b.x, a.y - b.y}; }
+inline void __syncwarp() {}
+namespace mpm {
+constexpr int PY = 8, PZ = 52, PN = 312, UN = PZ * 8;
+inline int pidx(int x, int y, int z) { return x + PY * y + PZ * z; }
+%s
+}
+// one pair's node values: cells A = (2m, ly, z) and B = (2m+1, ly, z), one particle
+// each (weights sA, sB at in-cell coordinates tA, tB), accumulated into a zeroed halo
+extern "C" void h_pair_scatter(double sA, const double* tA, double sB, const double* tB, int m, int ly, int zb,
+                               double* ua_out) {
+    alignas(16) static double ua[3][mpm::UN];
+    for (int q = 0; q < 3; ++q) for (int k = 0; k < mpm::UN; ++k) ua[q][k] = 0.0;
+    double2 M[3][3][3];
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) for (int k = 0; k < 3; ++k) {
+        const bool skip = i == 2 && j == 2 && k == 2;
+        const double a = skip ? 0.0 : sA * std::pow(tA[0], i) * std::pow(tA[1], j) * std::pow(tA[2], k);
+        const double b = skip ? 0.0 : sB * std::pow(tB[0], i) * std::pow(tB[1], j) * std::pow(tB[2], k);
+        M[i][j][k] = {a, b};
+    }
+    mpm::pair_scatter<double>(M, ua, m, ly, zb);
+    for (int q = 0; q < 3; ++q) for (int k = 0; k < mpm::UN; ++k) ua_out[q * mpm::UN + k] = ua[q][k];
+}
+"""
+
+
+def _extract(src, name):
+    k = src.index("__device__ __forceinline__ void " + name + "(")
+    k = src.rindex("template <", 0, k)
+    i = src.index("{", src.index(")", src.index(name + "(", k)))
+    depth = 0
+    for j in range(i, len(src)):
+        depth += src[j] == "{"
+        depth -= src[j] == "}"
+        if depth == 0:
+            return src[k:j + 1]
+
+
+def test_paired_scatter_sends_both_cells_weight_gradients(tmp_path):
+    """The operator's paired output path (pair_scatter: paired transposed
+    transforms, the two cells' shared x-nodes summed by pair_rows, then the
+    read-add-write phases of pair_rmw3) puts sum_p s_p dx gradN_i(x_p) of both
+    cells of the pair on their nodes, and nothing elsewhere."""
+    newton = open(os.path.join(CSRC, "newton.cu")).read()
+    text = _vpair_text(newton)
+    for name in ("pwN", "pdN", "pair_rows", "pair_rmw3", "pair_scatter"):
+        text += "\n\n" + _extract(newton, name)
+    cpp = tmp_path / "pair_scatter_host.cpp"
+    cpp.write_text(PAIR_SCATTER_SHIM % _host_text(text))
+    so = str(tmp_path / "libpairscatter.so")
+    res = subprocess.run(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", str(cpp), "-o", so],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    L = ctypes.CDLL(so)
+    L.h_pair_scatter.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p] + \
+        [ctypes.c_int] * 3 + [ctypes.c_void_p]
+    rng = np.random.default_rng(24)
+    dx = 1.0 / 7
+    n = (7, 7, 7)
+    UN = 52 * 8
+    for trial in range(30):
+        m, ly, zb = int(rng.integers(0, 2)), int(rng.integers(0, 4)), int(rng.integers(0, 4))
+        tA, tB = np.ascontiguousarray(rng.uniform(0, 1, 3)), np.ascontiguousarray(rng.uniform(0, 1, 3))
+        sA, sB = rng.uniform(0.5, 2.0), rng.uniform(0.5, 2.0)
+        out = np.zeros(3 * UN)
+        L.h_pair_scatter(sA, tA.ctypes.data, sB, tB.ctypes.data, m, ly, zb, out.ctypes.data)
+        out = out.reshape(3, UN)
+        ref = np.zeros((3, UN))
+        for s, t, x0 in ((sA, tA, 2 * m), (sB, tB, 2 * m + 1)):
+            st = oracle.Stencil(((np.array([2.0, 2.0, 2.0]) + t) * dx)[None], dx, n)
+            g = np.stack(np.unravel_index(st.node[0], n, order="F"), -1) - 1
+            for q in range(27):
+                a, b, c = g[q]
+                ref[:, (x0 + a) + 8 * (ly + b) + 52 * (zb + c)] += s * dx * st.dN[0, q]
+        np.testing.assert_allclose(out, ref, atol=1e-12, rtol=0)
