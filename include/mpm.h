@@ -155,9 +155,13 @@ typedef struct {
 } mpm_stats;
 
 /* Creates a context for `n_scenes` independent scenes advanced together.
- * Allocates every device buffer once (particle state, grid, solver vectors,
- * scratch); no later call allocates. `stream` is a cudaStream_t (NULL: the
- * legacy default stream). precision: mpm_precision. */
+ * Allocates every fixed-size device buffer once (particle state, grid, solver
+ * vectors, scratch). Two buffers whose size depends on where the particles are
+ * grow later, and are kept once grown: the operator's packed particle records,
+ * in mpm_p2g when a block's fullest cell needs more rows than the buffer holds,
+ * and the triangle buffer of mpm_generate_surface(_method), when a surface has
+ * more triangles than it holds. Every other call allocates nothing. `stream` is
+ * a cudaStream_t (NULL: the legacy default stream). precision: mpm_precision. */
 mpm_status mpm_create(const mpm_scene_desc* scenes, int32_t n_scenes, int32_t precision,
                       void* stream, mpm_ctx** out);
 mpm_status mpm_destroy(mpm_ctx* ctx);
