@@ -1,9 +1,10 @@
-"""Planted-mistake check of the oracle's pins.
+"""Planted-mistake check of the oracle's pins and of the host builds of device code.
 
 Plants one plausible mistake at a time in a copy of the oracle (a wrong sign, a
 dropped term or factor, a transposed operand, a wrong threshold or tie rule) and
 runs the oracle's pins against the copy; a pin suite that lets a mistake through
-has a gap. The working tree is never modified: the repository's oracle, tests
+has a gap. Mistakes planted in the CUDA source (`dev_*`) are run against the
+tests that build that source for the host and compare it with the oracle. The working tree is never modified: the repository's oracle, tests
 and scene generators are copied to a temporary directory once, and each mistake
 is applied to the copy and undone there.
 
@@ -20,6 +21,9 @@ import sys
 import tempfile
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+# mistakes in the device source are checked by the host builds of that source
+HOST = ["tests/test_mc_host.py", "tests/test_polar_host.py", "tests/test_surface_map_host.py",
+        "tests/test_solid_map_host.py", "tests/test_cell_poly_host.py"]
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_surface.py", "tests/test_oracle_marching_cubes.py",
         "tests/test_scenes.py",
         "tests/test_golden.py::test_levelset_radius_is_the_papers_and_isolated_particles_cross_the_grid"]
@@ -90,13 +94,34 @@ MISTAKES = [
     ('sticky_plane_slip', 'oracle/boundary.py', '        if plane_mode == 2:\n            sticky |= on_plane', '        if plane_mode == 3:\n            sticky |= on_plane'),
     ('sphere_outside_flip', 'oracle/boundary.py', '    R, outside = float(sphere[3]), bool(sphere[4])', '    R, outside = float(sphere[3]), not bool(sphere[4])'),
     ('heat_Vn_source', 'oracle/step.py', 'Vn = np.where(sc.phase == 0, sc.J, np.linalg.det(sc.F)) * sc.V0', 'Vn = sc.V0'),
+    ('dev_mc_decider', 'paper_2101_12408_gb300/csrc/mcubes.cuh', 'const bool joined = rmul(cphi[fc[i0]], cphi[fc[i0 + 2]]) > rmul(', 'const bool joined = rmul(cphi[fc[i0]], cphi[fc[i0 + 2]]) < rmul('),
+    ('dev_mc_pairing', 'paper_2101_12408_gb300/csrc/mcubes.cuh', '(joined ? ce[(k + 3) & 3] : ce[(k + 1) & 3])', '(joined ? ce[(k + 1) & 3] : ce[(k + 3) & 3])'),
+    ('dev_mc_face_order', 'paper_2101_12408_gb300/csrc/mcubes.cuh', 'const int iu = s ? (k == 1 || k == 2) : (k >= 2);', 'const int iu = (k == 1 || k == 2);'),
+    ('dev_polar_cross', 'paper_2101_12408_gb300/csrc/polar.cuh', 'u[2][0] = u[0][1] * u[1][2] - u[0][2] * u[1][1];', 'u[2][0] = u[0][2] * u[1][1] - u[0][1] * u[1][2];'),
+    ('dev_polar_sort', 'paper_2101_12408_gb300/csrc/polar.cuh', 'if (lam[0] < lam[1]) swap_cols(V, lam, 0, 1);', ''),
+    ('dev_polar_kinv', 'paper_2101_12408_gb300/csrc/polar.cuh', 'R e[3] = {sig[1] + sig[2], sig[0] + sig[2], sig[0] + sig[1]};', 'R e[3] = {sig[0] + sig[2], sig[1] + sig[2], sig[0] + sig[1]};'),
+    ('dev_fcr_dR_sign', 'paper_2101_12408_gb300/csrc/polar.cuh', 'dP[k] = R(2) * mu * (dF[k] - dR[k])', 'dP[k] = R(2) * mu * (dF[k] + dR[k])'),
+    ('dev_surf_conformal', 'paper_2101_12408_gb300/csrc/newton.cu', 'R q = R(0.5) * k * an * (x12 - x21);', 'R q = R(0.5) * k * an * (x21 - x12);'),
+    ('dev_surf_dn', 'paper_2101_12408_gb300/csrc/newton.cu', '        R dn[3] = {(dc[0] - nd * nv[0]) * ic', '        R dn[3] = {(dc[0]) * ic'),
+    ('dev_frame_hand', 'paper_2101_12408_gb300/csrc/newton.cu', 't2[0] = u[1] * t1[2] - u[2] * t1[1];', 't2[0] = -(u[1] * t1[2] - u[2] * t1[1]);'),
+    ('dev_solid_twist', 'paper_2101_12408_gb300/csrc/newton.cu', 'lv = R(2) * mu - R(4) * mu / den + lam * (J - R(1)) * s[z];', 'lv = R(2) * mu + R(4) * mu / den + lam * (J - R(1)) * s[z];'),
+    ('dev_solid_pair', 'paper_2101_12408_gb300/csrc/newton.cu', 'lv = R(2) * mu - lam * (J - R(1)) * s[z];', 'lv = R(2) * mu + lam * (J - R(1)) * s[z];'),
+    ('dev_solid_clamp', 'paper_2101_12408_gb300/csrc/newton.cu', 'if (!(lv > R(0))) continue;', ''),
+    ('dev_solid_W', 'paper_2101_12408_gb300/csrc/newton.cu', 'matmul3_bt<R>(Qm, Fo, W);', 'matmul3<R>(Qm, Fo, W);'),
+    ('dev_wT', 'paper_2101_12408_gb300/csrc/newton.cu', 'o2 = R(0.5) * (v0 + v2) - v1;', 'o2 = R(0.5) * (v0 + v2) + v1;'),
+    ('dev_dT', 'paper_2101_12408_gb300/csrc/newton.cu', 'o1 = v0 - R(2) * v1 + v2;', 'o1 = v0 - R(2) * v1 - v2;'),
+    ('dev_wN', 'paper_2101_12408_gb300/csrc/newton.cu', 'n0 = R(0.5) * (m0 + m2) - m1;', 'n0 = R(0.5) * (m0 + m2) + m1;'),
+    ('dev_dN', 'paper_2101_12408_gb300/csrc/newton.cu', 'n1 = m0 - R(2) * m1;', 'n1 = m0 + R(2) * m1;'),
+    ('dev_pair_middle', 'paper_2101_12408_gb300/csrc/newton.cu', 'const V p12 = P::make(p01.y, p23.x);', 'const V p12 = P::make(p01.x, p23.y);'),
+    ('dev_pdN', 'paper_2101_12408_gb300/csrc/newton.cu', 'n1 = vfma(m1, m2, m0);', 'n1 = vfma(m0, m2, m1);'),
+    ('dev_pair_rows', 'paper_2101_12408_gb300/csrc/newton.cu', 'lo[b][c] = P::make(n0.x, n1.x + n0.y);', 'lo[b][c] = P::make(n0.x, n1.x);'),
 ]
 
 
 def _copy_tree(dst):
     for d in ("oracle", "tests", "paper_2101_12408_gb300", "include"):
         shutil.copytree(os.path.join(ROOT, d), os.path.join(dst, d),
-                        ignore=shutil.ignore_patterns("_build", "*.so", "*.o", "__pycache__", "csrc"))
+                        ignore=shutil.ignore_patterns("_build", "*.so", "*.o", "__pycache__"))
     # the pins import the binding package's scene generators only; its library is not needed
     with open(os.path.join(dst, "tests", "conftest.py"), "w") as fh:
         fh.write("import os, sys\n"
@@ -122,8 +147,9 @@ def main(names):
             with open(path, "w") as fh:
                 fh.write(src.replace(text, repl, 1))
             try:
+                tests = HOST if "/csrc/" in rel else PINS
                 r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                                    "-m", "not gpu"] + PINS, capture_output=True, text=True, cwd=tmp, timeout=900)
+                                    "-m", "not gpu"] + tests, capture_output=True, text=True, cwd=tmp, timeout=900)
                 out = r.stdout.strip().splitlines()
                 print(f"{name:24s} {'CAUGHT' if r.returncode else 'SURVIVED'}  {out[-1] if out else ''}", flush=True)
             finally:

@@ -51,7 +51,7 @@ def lib(tmp_path_factory):
     common = open(os.path.join(CSRC, "common.cuh")).read()
     polar = open(os.path.join(CSRC, "polar.cuh")).read()
     newton = open(os.path.join(CSRC, "newton.cu")).read()
-    helpers = [_template_function(common, n) for n in ("matmul3_bt",)]
+    helpers = [_template_function(common, n) for n in ("matmul3", "matmul3_bt")]
     helpers += [_template_function(polar, n) for n in ("jacobi_rot", "swap_cols", "svd3")]
     d = tmp_path_factory.mktemp("solidmap")
     cpp = d / "solid_map_host.cpp"
