@@ -627,7 +627,6 @@ mpm_status mpm_resample(mpm_ctx* c) {
     if (!c) return MPM_ERR_INVALID_ARG;
     PhaseTimer timer(c, 0);
     cudaStream_t st = c->st;
-    Dev& d = c->d;
     MPM_CUDA(launch_sort_particles(c));
     MPM_CUDA(launch_sort_surface(c));
     MPM_CUDA(cudaStreamSynchronize(st));

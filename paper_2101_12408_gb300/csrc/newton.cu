@@ -494,7 +494,6 @@ __device__ __forceinline__ void project3r(R* v, uint8_t code, const SceneDev& S,
 __global__ void k_node_grad(const int4* __restrict__ coord, const SceneDev* __restrict__ sc, SceneScal* __restrict__ scal,
                             const double* __restrict__ gm, const double* __restrict__ gvn, const double* __restrict__ gv,
                             const uint8_t* __restrict__ pcode, double* __restrict__ grad, int skip_done) {
-    __shared__ double red[2];
     int slot = blockIdx.x, l = threadIdx.x;
     int4 bc = coord[slot];
     const SceneDev& S = sc[bc.w];
@@ -521,7 +520,6 @@ __global__ void k_node_grad(const int4* __restrict__ coord, const SceneDev* __re
         atomicAdd(&scal[bc.w].rr, rr);
         atomicAdd(&scal[bc.w].phi_kin, ek);
     }
-    (void)red;
 }
 
 // ======================================================================

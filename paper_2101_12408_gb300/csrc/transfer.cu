@@ -11,18 +11,10 @@ namespace mpm {
 
 namespace {
 
-constexpr int NT = 128;
-
 __device__ __forceinline__ int node_slot_index(const SceneDev& S, const int* __restrict__ bslot, int gx, int gy, int gz) {
     long long gb = S.block_base + (gx >> 2) + (long long)S.nb[0] * ((gy >> 2) + (long long)S.nb[1] * (gz >> 2));
     int slot = bslot[gb];
     return slot < 0 ? -1 : slot * 64 + ((gx & 3) + 4 * (gy & 3) + 16 * (gz & 3));
-}
-
-__device__ __forceinline__ void load_pos(const double* const* x, int i, double p[3]) {
-    p[0] = x[0][i];
-    p[1] = x[1][i];
-    p[2] = x[2][i];
 }
 
 struct P3 { const double* a[3]; };
