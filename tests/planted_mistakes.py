@@ -94,6 +94,18 @@ MISTAKES = [
     ('sticky_plane_slip', 'oracle/boundary.py', '        if plane_mode == 2:\n            sticky |= on_plane', '        if plane_mode == 3:\n            sticky |= on_plane'),
     ('sphere_outside_flip', 'oracle/boundary.py', '    R, outside = float(sphere[3]), bool(sphere[4])', '    R, outside = float(sphere[3]), not bool(sphere[4])'),
     ('heat_Vn_source', 'oracle/step.py', 'Vn = np.where(sc.phase == 0, sc.J, np.linalg.det(sc.F)) * sc.V0', 'Vn = sc.V0'),
+    ('tet_orientation', 'oracle/surface.py', 'if (nrm[0] * g[0] + nrm[1] * g[1]) + nrm[2] * g[2] < 0.0:', 'if (nrm[0] * g[0] + nrm[1] * g[1]) + nrm[2] * g[2] > 0.0:'),
+    ('mc_decider', 'oracle/surface.py', 'joined = cphi[ins[0]] * cphi[ins[1]] > cphi[out[0]] * cphi[out[1]]', 'joined = cphi[ins[0]] * cphi[ins[1]] < cphi[out[0]] * cphi[out[1]]'),
+    ('mc_face_order', 'oracle/surface.py', 'uv = ((0, 0), (1, 0), (1, 1), (0, 1)) if s == 1 else ((0, 0), (0, 1), (1, 1), (1, 0))', 'uv = ((0, 0), (1, 0), (1, 1), (0, 1))'),
+    ('poisson_mean', 'oracle/surface.py', 'lam = density * area', 'lam = 0.5 * density * area'),
+    ('poisson_recursion', 'oracle/surface.py', 'p = p * lam / k', 'p = p * lam / (k + 1)'),
+    ('levelset_clamp', 'oracle/surface.py', 'phi = np.minimum(dd, CLAMP_FACTOR * dx) - r0', 'phi = np.minimum(dd, 1.0 * dx) - r0'),
+    ('melt_threshold', 'oracle/step.py', 'melt = (sc.phase == 1) & (sc.T > prm.T_melt)', 'melt = (sc.phase == 1) & (sc.T > prm.T_melt + 1.0)'),
+    ('freeze_never', 'oracle/step.py', 'freeze = (sc.phase == 0) & (sc.T < prm.T_melt)', 'freeze = (sc.phase == 0) & (sc.T < prm.T0 - 1e9)'),
+    ('gamma_clamp', 'oracle/step.py', 'g = np.clip(g0 + g1 * (T - prm.T0), gmin, gmax)', 'g = g0 + g1 * (T - prm.T0)'),
+    ('grid_T_unnormalised', 'oracle/step.py', 'self.Tn = np.where(mT > 0, out["mTT"] / np.where(mT > 0, mT, 1.0), 0.0)', 'self.Tn = np.where(mT > 0, out["mTT"], 0.0)'),
+    ('friction_stop', 'oracle/boundary.py', 's = np.where(tl > lim, 1.0 - lim / np.where(tl > 0, tl, 1.0), 0.0)', 's = np.where(tl > lim, 1.0 - lim / np.where(tl > 0, tl, 1.0), 1.0)'),
+    ('friction_plane_normal', 'oracle/step.py', 'normals[on_p] = nn / np.linalg.norm(nn)', 'normals[on_p] = -nn / np.linalg.norm(nn)'),
     ('dev_mc_decider', 'paper_2101_12408_gb300/csrc/mcubes.cuh', 'const bool joined = rmul(cphi[fc[i0]], cphi[fc[i0 + 2]]) > rmul(', 'const bool joined = rmul(cphi[fc[i0]], cphi[fc[i0 + 2]]) < rmul('),
     ('dev_mc_pairing', 'paper_2101_12408_gb300/csrc/mcubes.cuh', '(joined ? ce[(k + 3) & 3] : ce[(k + 1) & 3])', '(joined ? ce[(k + 1) & 3] : ce[(k + 3) & 3])'),
     ('dev_mc_face_order', 'paper_2101_12408_gb300/csrc/mcubes.cuh', 'const int iu = s ? (k == 1 || k == 2) : (k >= 2);', 'const int iu = (k == 1 || k == 2);'),

@@ -1304,3 +1304,44 @@ def test_closest_parent_ties_go_to_the_smaller_index():
     x = np.vstack([c + [h, 0, 0], c + [h - 2.0 ** -48, 0, 0]])
     assert x[1, 0] - c[0] < x[0, 0] - c[0]
     assert nearest_parent(x, c[None])[0][0] == 1
+
+
+@pytest.mark.parametrize("start,T,end", [(scenes.PHASE_SOLID, 303.4, scenes.PHASE_LIQUID),
+                                         (scenes.PHASE_LIQUID, 302.6, scenes.PHASE_SOLID),
+                                         (scenes.PHASE_SOLID, 302.6, scenes.PHASE_SOLID),
+                                         (scenes.PHASE_LIQUID, 303.4, scenes.PHASE_LIQUID)])
+def test_phase_change_at_the_melting_point(start, T, end):
+    """Section "Thermomechanical Material Dependence and Phase Change": a particle
+    whose temperature after the step lies above the melting point is liquid, one
+    below it solid, and a particle that changes phase starts from its rest state
+    (J = 1, F = I). A uniform temperature with no heat flow stays uniform through
+    the transfers, so every particle ends at T."""
+    sc = scenes.wax(nx=16, ny=16, nz=16, cube_cells=4)
+    sc.phase[:] = start
+    sc.T[:] = T
+    sc.gradT[:] = 0.0
+    sc.params.K = 0.0
+    sc.params.h = 0.0
+    sc.params.H = 0.0
+    sc.b[:] = 0.0
+    sc.params.gamma_p = (0.0, 0.0, 0.0, 0.0)
+    sc.params.gravity = (0.0, 0.0, 0.0)
+    sc.J[:] = 0.97
+    sc.F[:] = 1.01 * np.eye(3)
+    sim = oracle.OracleSim(sc)
+    sim.step()
+    np.testing.assert_allclose(sim.sc.T, T, rtol=1e-12)
+    np.testing.assert_array_equal(sim.sc.phase, end)
+    if end != start:
+        np.testing.assert_array_equal(sim.sc.J, 1.0)
+        np.testing.assert_array_equal(sim.sc.F, np.broadcast_to(np.eye(3), sim.sc.F.shape))
+
+
+def test_gamma_law_stays_in_its_range():
+    """The wax's gamma(T) = 0.1 - 0.01 (T - T0) is clamped to [0, 0.1] (reading R9):
+    below T0 it keeps 0.1, past T0 + 10 it is zero, never negative."""
+    from oracle.step import gamma_of
+    prm = scenes.wax(nx=16, ny=16, nz=16, cube_cells=4).params
+    T = np.array([prm.T0 - 5.0, prm.T0, prm.T0 + 5.0, prm.T0 + 10.0, prm.T0 + 50.0])
+    g = gamma_of(T, np.zeros(5, np.uint8), prm)
+    np.testing.assert_allclose(g, [0.1, 0.1, 0.05, 0.0, 0.0], atol=1e-15)
