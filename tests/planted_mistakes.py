@@ -106,6 +106,13 @@ MISTAKES = [
     ('grid_T_unnormalised', 'oracle/step.py', 'self.Tn = np.where(mT > 0, out["mTT"] / np.where(mT > 0, mT, 1.0), 0.0)', 'self.Tn = np.where(mT > 0, out["mTT"], 0.0)'),
     ('friction_stop', 'oracle/boundary.py', 's = np.where(tl > lim, 1.0 - lim / np.where(tl > 0, tl, 1.0), 0.0)', 's = np.where(tl > lim, 1.0 - lim / np.where(tl > 0, tl, 1.0), 1.0)'),
     ('friction_plane_normal', 'oracle/step.py', 'normals[on_p] = nn / np.linalg.norm(nn)', 'normals[on_p] = -nn / np.linalg.norm(nn)'),
+    ('sphere_kind_band', 'oracle/step.py', 'near |= sphere_phi_normal(sc.s, sc.sphere)[0] < sc.dx', 'near |= sphere_phi_normal(sc.s, sc.sphere)[0] < 0.5 * sc.dx'),
+    ('friction_sphere_normal', 'oracle/step.py', 'normals[on_s] = sphere_phi_normal(node_positions(sc.n, sc.dx)[on_s], sc.sphere)[1]', 'normals[on_s] = -sphere_phi_normal(node_positions(sc.n, sc.dx)[on_s], sc.sphere)[1]'),
+    ('friction_drops_normal', 'oracle/boundary.py', 'out[sel] = s[:, None] * t + vn[sel, None] * nsel', 'out[sel] = s[:, None] * t'),
+    ('fixed_nodes_free', 'oracle/boundary.py', '    P[full] = 0.0\n', '\n'),
+    ('osada_b1', 'oracle/surface.py', 'b1 = a * (1.0 - r2)', 'b1 = (1.0 - r2)'),
+    ('kmax', 'oracle/surface.py', 'KMAX = 31', 'KMAX = 3'),
+    ('cube_range', 'oracle/surface.py', 'if min(m) >= 0 and m[0] < n[0] - 1 and m[1] < n[1] - 1 and m[2] < n[2] - 1:', 'if min(m) >= 1 and m[0] < n[0] - 1 and m[1] < n[1] - 1 and m[2] < n[2] - 1:'),
     ('dev_mc_decider', 'paper_2101_12408_gb300/csrc/mcubes.cuh', 'const bool joined = rmul(cphi[fc[i0]], cphi[fc[i0 + 2]]) > rmul(', 'const bool joined = rmul(cphi[fc[i0]], cphi[fc[i0 + 2]]) < rmul('),
     ('dev_mc_pairing', 'paper_2101_12408_gb300/csrc/mcubes.cuh', '(joined ? ce[(k + 3) & 3] : ce[(k + 1) & 3])', '(joined ? ce[(k + 1) & 3] : ce[(k + 3) & 3])'),
     ('dev_mc_face_order', 'paper_2101_12408_gb300/csrc/mcubes.cuh', 'const int iu = s ? (k == 1 || k == 2) : (k >= 2);', 'const int iu = (k == 1 || k == 2);'),

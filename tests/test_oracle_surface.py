@@ -165,3 +165,17 @@ def test_tetrahedral_isosurface_of_a_sphere_area_and_sample_coverage():
     # outward and normal to the sphere up to the facets' tilt
     assert np.all(np.sum(dA * rel, axis=1) > 0.0)
     assert np.mean(np.sum(dA * rel, axis=1) / (mag * dist)) > 0.99
+
+
+@pytest.mark.parametrize("method", ["tetra", "cubes"])
+def test_surface_reaches_the_first_node_layer(method):
+    """Cubes whose lowest corner lies on the grid's first node layer belong to
+    the lattice too: a particle in cell 1 has its sphere cut by the cubes between
+    node layers 0 and 1, and the surface there is triangulated (it ends at the
+    grid's edge, where the nodes end)."""
+    n, dx = (10, 10, 10), 1.0 / 10
+    xp = np.array([[1.3 * dx, 4.55 * dx, 5.4 * dx]])
+    s, dA, kind, tris = S.generate(xp, n, dx, 3, 40.0, None, method)
+    pts = np.array([p for t in tris for p in t])
+    assert pts[:, 0].min() < 1.0 * dx          # between node layers 0 (0.5 dx) and 1 (1.5 dx)
+    assert np.any(s[:, 0] < 1.0 * dx)
