@@ -134,6 +134,7 @@ MISTAKES = [
     ('dev_pair_middle', 'paper_2101_12408_gb300/csrc/newton.cu', 'const V p12 = P::make(p01.y, p23.x);', 'const V p12 = P::make(p01.x, p23.y);'),
     ('dev_pdN', 'paper_2101_12408_gb300/csrc/newton.cu', 'n1 = vfma(m1, m2, m0);', 'n1 = vfma(m0, m2, m1);'),
     ('dev_pair_rows', 'paper_2101_12408_gb300/csrc/newton.cu', 'lo[b][c] = P::make(n0.x, n1.x + n0.y);', 'lo[b][c] = P::make(n0.x, n1.x);'),
+    ('dev_sample_exact_curv', 'paper_2101_12408_gb300/csrc/newton.cu', 'surf_G<R>(k * dt * dt, nv, dFh, av, G2);', 'surf_G<R>(k * dt * dt, nv, Fh, av, G2);'),
 ]
 
 

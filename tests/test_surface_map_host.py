@@ -8,7 +8,6 @@ cofactor curvature). The kernel stores only the upper triangle of the 9x9 map,
 so the map must be symmetric; it must also be positive semi-definite."""
 import ctypes
 import os
-import re
 import subprocess
 import types
 
@@ -141,3 +140,77 @@ def test_float_surface_map_within_float_rounding(lib):
         scale = np.abs(Ko).max()
         assert np.allclose(Kf, Ko, atol=2e-6 * scale, rtol=0)
         assert np.allclose(Kf, Kf.T, atol=2e-6 * scale, rtol=0)
+
+
+SAMPLE_G_SHIM = r"""
+#include <cmath>
+using std::fabs; using std::sqrt;
+enum { MPM_HESS_EXACT = 0, MPM_HESS_PROJECTED = 1 };
+namespace mpm {
+template <typename R> struct Cols { const R* a[9]; };
+template <typename R> struct ApplyArgs {   // the fields sample_G reads
+    Cols<R> sF, sa, sn;
+    const R* sg;
+    const R* sic;
+    int mode;
+};
+%s
+}
+// G (3x3) of one sample for a given dF^, in the exact or projected mode
+extern "C" void h_sample_G(const double* Fh, const double* a, const double* n, double k, double ic, int mode,
+                           const double* dFh, double dt, double* G) {
+    mpm::ApplyArgs<double> args;
+    for (int q = 0; q < 9; ++q) args.sF.a[q] = Fh + q;
+    for (int q = 0; q < 3; ++q) { args.sa.a[q] = a + q; args.sn.a[q] = n + q; }
+    args.sg = &k;
+    args.sic = &ic;
+    args.mode = mode;
+    mpm::sample_G<double>(args, 0, dFh, dt, G);
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def sample_lib(tmp_path_factory):
+    common = open(os.path.join(CSRC, "common.cuh")).read()
+    newton = open(os.path.join(CSRC, "newton.cu")).read()
+    helpers = [_template_function(common, n) for n in ("dcofactor", "matmul3")]
+    helpers += [_template_function(newton, n) for n in ("cross_mat", "surf_G", "tangent_frame", "add_conformal",
+                                                        "sample_G")]
+    d = tmp_path_factory.mktemp("sampleG")
+    cpp = d / "sample_G_host.cpp"
+    cpp.write_text(SAMPLE_G_SHIM % _host_text("\n\n".join(helpers)))
+    so = str(d / "libsampleG.so")
+    res = subprocess.run(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", str(cpp), "-o", so],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    L = ctypes.CDLL(so)
+    L.h_sample_G.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_double] * 2 + [ctypes.c_int, ctypes.c_void_p,
+                                                                             ctypes.c_double, ctypes.c_void_p]
+    return L
+
+
+def test_sample_term_in_both_modes_matches_the_oracle(sample_lib):
+    """sample_G (the general kernel's surface term, exact and projected) against
+    the oracle's exact term dn_a C_agd + n_a dC_agd and its projected term."""
+    from oracle.constitutive import EPS
+    rng = np.random.default_rng(13)
+    gamma, dt = 0.8, 1e-3
+    for Fh, a in _cases(rng):
+        c = cof(Fh[None])[0] @ a
+        cn = np.linalg.norm(c)
+        n = c / cn
+        st = types.SimpleNamespace(dA=a[None])
+        C = NewtonState._surface_C(st, Fh[None])[0]
+        X = rng.standard_normal((3, 3))
+        dc = np.einsum("agd,gd->a", C, X)
+        dn = (dc - n * np.dot(n, dc)) / cn
+        exact = np.einsum("a,agd->gd", dn, C) + np.einsum("a,agk,bdl,b,kl->gd", n, EPS, EPS, a, X)
+        proj = np.einsum("a,agd->gd", dn, C) + NewtonState._conformal_part(st, n[None], X[None])[0]
+        for mode, ref in ((0, exact), (1, proj)):
+            G = np.zeros(9)
+            args = [np.ascontiguousarray(v, np.float64) for v in (Fh, a, n, X)]
+            sample_lib.h_sample_G(args[0].ctypes.data, args[1].ctypes.data, args[2].ctypes.data, gamma, 1.0 / cn,
+                                  mode, args[3].ctypes.data, dt, G.ctypes.data)
+            want = gamma * dt * dt * ref
+            np.testing.assert_allclose(G.reshape(3, 3), want, atol=1e-12 * np.abs(want).max(), rtol=0)
