@@ -200,3 +200,53 @@ def test_stress_differential_against_central_differences(lib):
             e = lambda G: lib.h_psi(_p(np.ascontiguousarray(G)), mu, lam)  # noqa: E731
             assert (e(F + h * D) - e(F - h * D)) / (2 * h) == pytest.approx(np.sum(_P(F, mu, lam) * D), rel=1e-6,
                                                                             abs=1e-6)
+
+
+COF_SHIM = r"""
+namespace mpm {
+%s
+}
+extern "C" void h_cof(const double* F, double* C) { mpm::cofactor<double>(F, C); }
+extern "C" void h_dcof(const double* F, const double* D, double* C) { mpm::dcofactor<double>(F, D, C); }
+"""
+
+
+def test_cofactor_is_quadratic_as_the_line_search_uses_it(tmp_path):
+    """The line search forms cof(F + alpha D) a as c0 + alpha c1 + alpha^2 c2 with
+    c0 = cof(F) a, c1 = dcof(F)[D] a and c2 = cof(D) a (the cofactor is a quadratic
+    form in F), so its surface energy differences need no re-evaluation of cof per
+    trial. The device's cofactor and its derivative (csrc/common.cuh), built for
+    the host: cof(F) = det(F) F^-T, and the expansion holds for any alpha."""
+    common = open(os.path.join(CSRC, "common.cuh")).read()
+    cpp = tmp_path / "cof_host.cpp"
+    cpp.write_text(COF_SHIM % _host_text("\n\n".join(_template_function(common, n) for n in ("cofactor", "dcofactor"))))
+    so = str(tmp_path / "libcof.so")
+    res = subprocess.run(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", str(cpp), "-o", so],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    L = ctypes.CDLL(so)
+    L.h_cof.argtypes = [ctypes.c_void_p] * 2
+    L.h_dcof.argtypes = [ctypes.c_void_p] * 3
+    rng = np.random.default_rng(5)
+
+    def cof(F):
+        F = np.ascontiguousarray(F, np.float64)
+        C = np.zeros(9)
+        L.h_cof(_p(F), _p(C))
+        return C.reshape(3, 3)
+
+    def dcof(F, D):
+        F, D = np.ascontiguousarray(F, np.float64), np.ascontiguousarray(D, np.float64)
+        C = np.zeros(9)
+        L.h_dcof(_p(F), _p(D), _p(C))
+        return C.reshape(3, 3)
+
+    for _ in range(100):
+        F = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+        D = rng.standard_normal((3, 3))
+        a = rng.standard_normal(3)
+        np.testing.assert_allclose(cof(F), np.linalg.det(F) * np.linalg.inv(F).T, atol=1e-12)
+        for alpha in (1.0, 0.5, 0.125, 2.0 ** -11):
+            lhs = cof(F + alpha * D) @ a
+            rhs = cof(F) @ a + alpha * (dcof(F, D) @ a) + alpha * alpha * (cof(D) @ a)
+            np.testing.assert_allclose(lhs, rhs, atol=1e-12 * (1 + np.abs(lhs).max()))
