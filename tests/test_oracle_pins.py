@@ -645,6 +645,20 @@ def test_implicit_step_conserves_linear_momentum():
     np.testing.assert_allclose(np.sum(s.m[:, None] * s.v, 0), m0, atol=1e-10 * np.abs(m0).max())
 
 
+@pytest.mark.parametrize("method", ["tetra", "cubes"])
+def test_step_with_a_generated_surface_conserves_momentum(method):
+    """Section "Conservation": with samples generated on the particles' surface
+    (either triangulation), split, P2G, the implicit solve with its final force
+    evaluation, and the merge keep the particles' linear momentum."""
+    sc = scenes.droplet(n=16, r_cells=4.0, seed=33, v0=(0.2, 0.1, -0.3), spin=1.5, lambda_l=50.0)
+    m0 = np.sum(sc.m[:, None] * sc.v, 0)
+    sim = oracle.OracleSim(sc)
+    assert sim.generate_surface(9, 2.0, method) > 100
+    sim.step()
+    s = sim.sc
+    np.testing.assert_allclose(np.sum(s.m[:, None] * s.v, 0), m0, atol=1e-10 * np.abs(m0).max())
+
+
 def _analytic_fcr_hessian(F, mu, lam):
     """The 9x9 Hessian of the fixed-corotated energy from the analytic eigensystem of
     isotropic energies: with the signed SVD F = U diag(s) V^T, each pair (x, y)
