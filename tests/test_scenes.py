@@ -60,3 +60,28 @@ def test_benchmark_inputs_have_the_documented_sizes():
     f = scenes.config(1)
     assert (f.n_particles, f.n_surface) == (738048, 31752)
     assert f.params.rho == 1000.0 and f.params.lambda_l == 1e6
+
+
+def test_batch_workload_follows_its_recipe():
+    """The batched workload: 64 independent scenes with grid edges in [32, 96] and
+    particle counts in [5k, 300k] (both drawn log-uniform, so the smallest and the
+    largest tenth of each range are both represented), droplets and films and
+    constant and temperature-dependent gamma mixed, 5 439 405 particles in all."""
+    b = scenes.batch()
+    assert len(b) == 64
+    ns = np.array([s.n[0] for s in b])
+    cnt = np.array([s.n_particles for s in b])
+    assert ns.min() >= 32 and ns.max() <= 96
+    assert cnt.min() >= 5e3 * 0.9 and cnt.max() <= 3e5 * 1.1
+    assert int(cnt.sum()) == 5439405
+    # log-uniform: about half of the scenes below the geometric mean of each range
+    assert 20 <= np.sum(ns < np.sqrt(32 * 96)) <= 44
+    assert 20 <= np.sum(cnt < np.sqrt(5e3 * 3e5)) <= 44
+    drops = np.array(["droplet" in s.name for s in b])
+    thermal = np.array([s.params.thermal for s in b])
+    assert 20 <= drops.sum() <= 44 and 20 <= thermal.sum() <= 44
+    for s in b:
+        assert s.params.rho == 1000.0 and s.params.lambda_l == 1e6
+        lo = np.floor(s.x / s.dx).min(0)
+        hi = np.floor(s.x / s.dx).max(0)
+        assert np.all(lo >= 1) and np.all(hi <= np.asarray(s.n) - 2)   # every stencil on the grid
