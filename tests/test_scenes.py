@@ -85,3 +85,26 @@ def test_batch_workload_follows_its_recipe():
         lo = np.floor(s.x / s.dx).min(0)
         hi = np.floor(s.x / s.dx).max(0)
         assert np.all(lo >= 1) and np.all(hi <= np.asarray(s.n) - 2)   # every stencil on the grid
+
+
+def test_inclined_plane_workload_follows_its_recipe():
+    """The 8M-particle workload: 40 droplets with radii uniform in [9.3, 24.8]
+    cells on a 256^3 grid, disjoint and above a 30-degree slip plane through
+    (0.5, 0.2, 0.5) with gaps of 0.5 to 120 cells, gravity -9.8 along y, water in
+    SI units, samples on each droplet's sphere with the solid-liquid kind within
+    dx of the plane."""
+    sc = scenes.incline()
+    assert (sc.n_particles, sc.n_surface) == (8272476, 317603)
+    c, r = sc.meta["centers"], sc.meta["radii"] / sc.dx
+    assert len(r) == 40 and r.min() >= 9.3 and r.max() <= 24.8
+    gaps = np.linalg.norm(c[:, None] - c[None], axis=-1) - (r[:, None] + r[None]) * sc.dx
+    assert np.all(gaps[~np.eye(40, dtype=bool)] > 0.0)
+    nrm = np.asarray(sc.plane_n)
+    assert np.allclose(nrm, [-0.5, np.sqrt(3) / 2, 0.0]) and np.isclose(sc.plane_d, nrm @ [0.5, 0.2, 0.5])
+    assert np.all(sc.x @ nrm - sc.plane_d > 0.0)
+    assert sc.params.gravity == (0.0, -9.8, 0.0) and sc.params.rho == 1000.0 and sc.params.lambda_l == 1e6
+    # each droplet starts between 0.5 and 120 cells above the plane
+    gap = (c @ nrm - sc.plane_d) / sc.dx - r
+    assert gap.min() >= 0.5 and gap.max() <= 120.0
+    d = sc.s @ nrm - sc.plane_d
+    np.testing.assert_array_equal(sc.kind, (d < sc.dx).astype(np.uint8))
