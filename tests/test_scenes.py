@@ -108,3 +108,27 @@ def test_inclined_plane_workload_follows_its_recipe():
     assert gap.min() >= 0.5 and gap.max() <= 120.0
     d = sc.s @ nrm - sc.plane_d
     np.testing.assert_array_equal(sc.kind, (d < sc.dx).astype(np.uint8))
+
+
+def test_wax_workload_follows_its_recipe():
+    """The melting-wax workload: a 96^3-cell solid cube at 8 particles per cell
+    (7 077 888) resting on the sticky floor of a 256x256x128 grid at T0, samples on
+    its five free faces with outward area vectors (none on the face on the floor),
+    the -x face heated at b = 50, Robin convection h = 0.5 towards T0 everywhere,
+    E(T) from 1e4 at 298 to 0 at the melting point 303, phase change on."""
+    sc = scenes.wax()
+    assert sc.n == (256, 256, 128) and sc.n_particles == 96 ** 3 * 8
+    lo, hi = sc.x.min(0) / sc.dx, sc.x.max(0) / sc.dx
+    assert np.all(hi - lo < 96) and np.all(hi - lo > 95.5) and lo[2] < 2.5
+    assert np.all(sc.phase == scenes.PHASE_SOLID) and np.all(sc.T == 298.0)
+    p = sc.params
+    assert (p.E0, p.T0, p.T_melt, p.h) == (1e4, 298.0, 303.0, 0.5) and p.phase_change and p.thermal
+    nrm = sc.dA / np.linalg.norm(sc.dA, axis=1, keepdims=True)
+    faces = {tuple(v) for v in np.round(nrm, 12)}
+    assert faces == {(-1.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)}
+    minus_x = np.isclose(nrm[:, 0], -1.0)
+    np.testing.assert_array_equal(sc.b, np.where(minus_x, 50.0, 0.0))
+    assert np.all(sc.Tbar == 298.0)
+    # outward: every sample lies on the side of the cube its area vector points to
+    centre = 0.5 * (sc.x.min(0) + sc.x.max(0))
+    assert np.all(np.sum((sc.s - centre) * nrm, 1) > 0.0)
