@@ -132,3 +132,24 @@ def test_wax_workload_follows_its_recipe():
     # outward: every sample lies on the side of the cube its area vector points to
     centre = 0.5 * (sc.x.min(0) + sc.x.max(0))
     assert np.all(np.sum((sc.s - centre) * nrm, 1) > 0.0)
+
+
+def test_film_workload_follows_its_recipe():
+    """The Marangoni film: a 6-cell liquid layer over the sticky floor of a
+    128x128x32 grid with slip side walls and an open top, samples on the top face
+    only (reaching the side walls' node layers, reading R26), a Gaussian hot spot
+    of sigma = 10 cells and Delta T = 1 at the centre, gamma(T) = 1 - 0.5 (T - T0)
+    clamped at 0, Robin convection h = 5 towards T0, rho c_p = 1, K = 0.1, dt = 5e-4."""
+    sc = scenes.config(1)
+    assert sc.n == (128, 128, 32)
+    assert sc.walls == (scenes.WALL_SLIP,) * 4 + (scenes.WALL_STICKY, scenes.WALL_NONE)
+    lo, hi = sc.x.min(0) / sc.dx, sc.x.max(0) / sc.dx
+    assert np.all(lo > 2.0) and lo[2] < 2.25 and hi[2] < 8.0 and hi[2] > 7.75 and np.all(hi[:2] < 126.0)
+    assert np.all(sc.s[:, 2] == 8.0 * sc.dx) and np.all(sc.dA[:, :2] == 0.0) and np.all(sc.dA[:, 2] > 0.0)
+    assert sc.s[:, 0].min() < 2.0 * sc.dx and sc.s[:, 0].max() > 126.0 * sc.dx
+    p = sc.params
+    r2 = np.sum((sc.x[:, :2] / sc.dx - 64.0) ** 2, 1)
+    np.testing.assert_allclose(sc.T, p.T0 + np.exp(-r2 / (2.0 * 10.0 ** 2)), atol=0.02)
+    assert sc.T.max() > p.T0 + 0.99
+    assert p.gamma_law == scenes.GAMMA_LINEAR and p.gamma_p[:3] == (1.0, -0.5, 0.0) and p.gamma_p[3] >= 1e30
+    assert (p.h, p.K, p.dt) == (5.0, 0.1, 5e-4) and np.isclose(p.rho * p.cp, 1.0) and np.all(sc.Tbar == p.T0)
