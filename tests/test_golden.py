@@ -75,3 +75,20 @@ def test_gpu_step_matches_stored_oracle_values(prec):
     ctx.g2p()
     part = ctx.get_particles(0)
     assert np.max(np.abs(part["v"][ref["particles"]] - np.array(ref["v"]))) < max(tol, 1e-7) * ref["v_absmax"]
+
+
+def test_wax_workload_uses_the_papers_candle_constants():
+    """The melting-wax workload takes the candle examples' printed constants:
+    ambient and melting temperatures, K, c_p, no internal source, the Robin h and
+    the heating rate b on the heated face, and a surface coefficient at T0 among
+    the compared ones."""
+    from paper_2101_12408_gb300 import scenes
+    v = {k: e["value"] for k, e in _paper().items()}
+    sc = scenes.wax(nx=16, ny=16, nz=16, cube_cells=4)
+    p = sc.params
+    assert p.T0 == v["candle_ambient_temperature"] and p.T_melt == v["candle_melting_point"]
+    assert p.K == v["candle_thermal_diffusivity"] and p.cp == v["candle_specific_heat"]
+    assert p.H == v["candle_internal_heat_source"] and p.h == v["candle_robin_h"]
+    assert set(np.unique(sc.b)) == {0.0, v["candle_robin_b"]}
+    assert p.gamma_p[0] in v["candle_surface_coefficients"]
+    assert np.all(sc.Tbar == v["candle_ambient_temperature"])
