@@ -92,3 +92,25 @@ def test_wax_workload_uses_the_papers_candle_constants():
     assert set(np.unique(sc.b)) == {0.0, v["candle_robin_b"]}
     assert p.gamma_p[0] in v["candle_surface_coefficients"]
     assert np.all(sc.Tbar == v["candle_ambient_temperature"])
+
+
+def test_papers_contact_angle_ratios_and_the_oracles_energy_minimum():
+    """The paper's settling-droplet figure pairs k_SL / k_LG ratios with contact
+    angles through Young's relation theta = arccos(-k_SL / k_LG). For the
+    hydrophobic 135-degree case the oracle's surface energy of resting caps (the
+    samples, interface kinds and coefficients of reading R13) is smallest within
+    a degree of it at 10 and 20 cells of radius."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_pins import _cap_energy
+    e = _paper()["contact_angle_ratios"]
+    for ratio, angle in zip(e["value"], e["angles_deg"]):
+        assert math.degrees(math.acos(-ratio)) == pytest.approx(angle, abs=1e-9)
+    k_sl = e["value"][2]
+    volume = 2.0 / 3.0 * math.pi * (10 / 64) ** 3
+    for n in (64, 128):
+        ths = 135.0 + np.arange(-10.0, 10.5, 5.0)
+        es = np.array([_cap_energy(t, volume, k_sl, n) for t in ths])
+        assert np.argmin(es) == 2
+        q = np.polyfit(ths, es, 2)
+        assert abs(-q[1] / (2 * q[0]) - 135.0) < 1.0
